@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Throughput of the exact kNN query path (buffer k-d tree, LazySearch) on GB300.
+
+One step = one ``bkd_query`` over the whole query set of the workload: every
+round of FindLeafBatch, buffer insertion and ProcessAllBuffers, the binary64
+re-check and fallback, with the tree resident in HBM.  Default workload: n =
+2^26 reference points and m = 2^24 queries in R^10 drawn from a 32-component
+isotropic Gaussian mixture (stand-in for photometric colour features), k =
+10, tree height 16 (65,536 leaves of 1,024 points).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank builds the same tree and answers its own query set
+(queries are independent: no data-path collective); rank 0 prints one JSON
+line with the whole-job queries/s.  ``--impl reference`` times the binary64
+CPU oracle (classical k-d tree, OpenMP on all host cores) on bounded query
+samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = ("kNN queries/s (k=10, d=10) FP32 vs BF16-screened; p50/p99 "
+          "latency; % roofline")
+LEAF_SRC = os.path.join(ROOT, "paper_1512_02831_gb300", "csrc", "k_leaf.cuh")
+TRAFFIC_NOTE = os.path.join(ROOT, "profiles",
+                            "leaf_kernel_mixture64M_traffic.txt")
+
+WORKLOADS = {"mixture64M": workloads.MIXTURE_64M,
+             "uniform64K": workloads.UNIFORM_64K}
+
+
+def args_():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS),
+                    default="mixture64M")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu),
+                 f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                 "-lms", "200"], stdout=open(self.path, "w"),
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [],
+                    "note": "nvidia-smi unavailable"}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                smax.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def leaf_traffic_per_launch():
+    """DRAM bytes per leaf-kernel launch from the committed ncu summary, if
+    it was taken on the current leaf kernel source."""
+    try:
+        text = open(TRAFFIC_NOTE).read()
+    except OSError:
+        return None
+    sha = hashlib.sha256(open(LEAF_SRC, "rb").read()).hexdigest()[:16]
+    m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.e+]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != sha:
+        return None
+    return float(m_b.group(1))
+
+
+def cpu_baseline(P, Q, w, seconds: float, seed: int = 7):
+    """The binary64 oracle's k-d tree (Sec. 2.3), as it stands, timed on a
+    bounded sample of the workload's queries on all host cores."""
+    import oracle
+    t0 = time.perf_counter()
+    tree = oracle.build_tree(P, w.height)
+    build_s = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    probe = Q[rng.choice(Q.shape[0], 256, replace=False)]
+    t0 = time.perf_counter()
+    tree.knn(probe, w.k)
+    per_q = (time.perf_counter() - t0) / 256
+    s = int(min(Q.shape[0], max(256, seconds / max(per_q, 1e-9))))
+    rows = np.sort(rng.choice(Q.shape[0], s, replace=False))
+    t0 = time.perf_counter()
+    res = tree.knn(Q[rows], w.k)
+    dt = time.perf_counter() - t0
+    info = {"value": s / dt, "unit": "queries/s",
+            "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": (f"{s} of {Q.shape[0]} queries (seeded), binary64 "
+                       f"classical k-d tree of height {w.height}, OpenMP "
+                       f"over queries; tree build {build_s:.1f} s not "
+                       f"counted; query phase {dt:.1f} s")}
+    return info, rows, res
+
+
+# ------------------------------------------------------------------- arms
+def run_reference(a, w):
+    """Reference arm: the oracle on bounded samples of the same workload."""
+    import oracle
+    P = w.points()
+    Q = w.queries()
+    tree = oracle.build_tree(P, w.height)
+    rng = np.random.default_rng(11)
+    probe = Q[rng.choice(Q.shape[0], 256, replace=False)]
+    t0 = time.perf_counter()
+    tree.knn(probe, w.k)
+    per_q = (time.perf_counter() - t0) / 256
+    budget = 150.0 / max(1, a.steps + a.warmup)    # seconds per step
+    s = int(min(Q.shape[0], max(256, budget / max(per_q, 1e-9))))
+    times = []
+    for step in range(a.warmup + a.steps):
+        rows = rng.choice(Q.shape[0], s, replace=False)
+        t0 = time.perf_counter()
+        tree.knn(Q[rows], w.k)
+        if step >= a.warmup:
+            times.append(time.perf_counter() - t0)
+    total = float(np.sum(times))
+    value = s * a.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value,
+        "unit": "queries/s", "n_gpus": a.gpus, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": 1000 * total / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": dict(w.describe(), sample_queries_per_step=s),
+        "cpu_baseline": {"value": value, "unit": "queries/s",
+                         "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": f"{s} seeded queries per step of "
+                                   f"{Q.shape[0]}, binary64 k-d tree"},
+        "e2e": {"value": value, "unit": "queries/s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a, w, rank, world, local_rank):
+    import torch
+    import paper_1512_02831_gb300 as bkd
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    P = w.points()
+    Q = w.queries(stream=rank)
+    m, k, d = Q.shape[0], w.k, w.d
+    t0 = time.perf_counter()
+    tree = bkd.bkd_build(P, w.height)
+    build_s = time.perf_counter() - t0
+    Qd = torch.from_numpy(Q).to(dev)
+    out_i = torch.empty((m, k), dtype=torch.int64, device=dev)
+    out_d = torch.empty((m, k), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    stats_keys = ("rounds", "leaf_visits", "pairs", "resorted", "fallback",
+                  "leaf_kernel_ms", "kernel_launches", "leaf_launches")
+    for _ in range(a.warmup):
+        bkd.bkd_query(tree, Qd, k, out_i, out_d)
+    barrier()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    vis = [v for v in vis.split(",") if v.strip()]
+    smi_index = (vis[local_rank] if local_rank < len(vis)
+                 and vis[local_rank].strip().isdigit() else local_rank)
+    clocks = Clocks(smi_index)
+    clocks.start()
+    acc = {s: 0.0 for s in stats_keys}
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(a.steps):
+        bkd.bkd_query(tree, Qd, k, out_i, out_d)
+        for s in stats_keys:
+            acc[s] += bkd.bkd_get_stat(tree, s)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = max_over_ranks(ms)
+    value = world * m * a.steps / (ms_max / 1000.0)
+
+    # end to end through the same call, host buffers (pinned), copies inside
+    Qh = torch.from_numpy(Q).pin_memory()
+    oi_h = torch.empty((m, k), dtype=torch.int64).pin_memory()
+    od_h = torch.empty((m, k), dtype=torch.float32).pin_memory()
+    bkd.bkd_query(tree, Qh, k, oi_h, od_h)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(a.e2e_steps):
+        bkd.bkd_query(tree, Qh, k, oi_h, od_h)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * m * a.e2e_steps / e2e_s, "unit": "queries/s",
+           "h2d_bytes_per_step": int(Q.nbytes),
+           "d2h_bytes_per_step": int(oi_h.numel() * 8 + od_h.numel() * 4),
+           "buffers": "pinned host, bkd_query copies in and out"}
+    same = bool(torch.equal(oi_h, out_i.cpu()))
+
+    # roofline of the dominant kernel (leaf brute force)
+    peaks = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070)
+    peak_ops = 128 * sm_count * sm_max * 1e6 / 1e12      # Top/s
+    ops = 2 * d * acc["pairs"]
+    leaf_s = acc["leaf_kernel_ms"] / 1000.0
+    achieved = ops / leaf_s / 1e12 if leaf_s > 0 else 0.0
+    traffic = leaf_traffic_per_launch()
+    roofline = {
+        "bound": "alu", "kernel": "leaf_kernel (ProcessAllBuffers)",
+        "achieved": achieved, "peak": peak_ops, "unit": "Top/s",
+        "frac": achieved / peak_ops,
+        "traffic": traffic,
+        "basis": (f"FP32 pipe operations: 2*d = {2 * d} per scored (query, "
+                  f"point) pair (d subtractions + d multiply-adds); peak = "
+                  f"128 FP32 lanes x {sm_count} SMs x {sm_max:.0f} MHz "
+                  f"(max SM clock of measured peaks); time = CUDA events "
+                  f"around every leaf-kernel launch on its stream"),
+        "leaf_share_of_step": leaf_s / (ms / 1000.0),
+        "flop_view": {"flops_per_pair": 3 * d,
+                      "achieved_tflops": 1.5 * achieved,
+                      "peak_tflops_fma2": 2 * peak_ops},
+    }
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s",
+        "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": ("synthetic: seeded Gaussian mixture (32 isotropic "
+                 "components, centres U[0,1]^10, sigma logU[0.02,0.2], "
+                 "Dirichlet(1) weights); per-rank query sets"),
+        "config": dict(w.describe(), precision="fp32 exact path",
+                       parallelism=f"replicas x{world}, queries sharded",
+                       l2=("inputs larger than L2 (leaf structure 2.7 GB, "
+                           "queries 0.67 GB) - no flush needed"),
+                       tree_build_s=round(build_s, 2)),
+        "e2e": e2e,
+        "gpu_launches": int(acc["kernel_launches"]),
+        "roofline": roofline,
+        "clocks": clk,
+        "path": {"rounds_per_step": acc["rounds"] / a.steps,
+                 "leaf_visits_per_query": acc["leaf_visits"] / (m * a.steps),
+                 "pairs_per_step": acc["pairs"] / a.steps,
+                 "leaf_kernel_ms_per_step": acc["leaf_kernel_ms"] / a.steps,
+                 "leaf_launches_per_step": acc["leaf_launches"] / a.steps,
+                 "resorted_per_step": acc["resorted"] / a.steps,
+                 "fallback_per_step": acc["fallback"] / a.steps,
+                 "e2e_matches_device_run": same},
+    }
+    bkd.bkd_free(tree)
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        info, rows, ref = cpu_baseline(P, Q, w, a.cpu_seconds)
+        line["cpu_baseline"] = info
+        got = out_i.cpu().numpy()[rows]
+        exempt = ref.gap_exempt(1e-6)
+        line["parity_sample"] = {
+            "queries": int(len(rows)),
+            "index_rows_equal": int((got == ref.idx).all(1).sum()),
+            "gap_exempt": int(exempt.sum()),
+            "non_exempt_mismatch": int((~exempt & ~(got == ref.idx).all(1))
+                                       .sum())}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    a = args_()
+    w = WORKLOADS[a.workload]
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if a.impl == "reference":
+        if rank == 0:
+            run_reference(a, w)
+        return
+    run_ours(a, w, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

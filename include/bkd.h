@@ -1,0 +1,171 @@
+/*
+ * bkd.h -- C ABI of the GB300 buffer k-d tree (exact k-nearest neighbours).
+ *
+ * Method: Gieseke, Oancea, Mahabal, Igel, Heskes, "Bigger Buffer k-d Trees on
+ * Multi-Many-Core Systems".  Problem statement (Sec. 2.2): given reference
+ * points P = {x_1..x_n} and queries Q = {q_1..q_m} in R^d, return for every
+ * query its k >= 1 nearest reference points in Euclidean distance.  The
+ * search structure is the buffer k-d tree (Sec. 2.4): a pointer-less top tree
+ * of median splits plus a leaf structure holding the rearranged points; the
+ * query runs LazySearch (Algorithm 1): repeated FindLeafBatch /
+ * buffer insertion / ProcessAllBuffers rounds.  When the leaf structure does
+ * not fit in device memory it stays in pinned host memory and is streamed in
+ * leaf chunks with double-buffered copies (Sec. 3).
+ *
+ * Conventions shared by every call:
+ *   - Points and queries are float32, row-major: point i occupies
+ *     P[i*d .. i*d + d).  Pointers may be host or device memory (detected with
+ *     cudaPointerGetAttributes); the caller owns them.
+ *   - Results: out_idx (int64) holds 0-based row indices of P; out_dist
+ *     (float32) holds SQUARED Euclidean distances.  Both are m x k,
+ *     row-major, host or device memory owned by the caller.  Row j lists the
+ *     neighbours of query j in ascending order of (exact distance, index): a
+ *     tie goes to the smaller index.  The returned float32 distances are
+ *     non-decreasing along a row.
+ *   - Exactness: indices equal those of a binary64 computation of the same
+ *     definition, except where a query's k-th and (k+1)-th neighbours are at
+ *     distances too close to separate in binary64 (then any valid k-nearest
+ *     set is returned).  Distances agree with binary64 to within
+ *     (d + 3) * 2^-24 relative.
+ *   - Inputs must be finite with magnitude below 2^60; anything else is
+ *     rejected with BKD_EINVAL.
+ *   - Every call returns BKD_OK (0) or a negative status; bkd_last_error()
+ *     then describes the failure.  On failure the outputs are unspecified and
+ *     the tree stays usable unless the status is BKD_ECUDA.
+ *   - A tree handle is not thread-safe: one thread (or external locking) per
+ *     handle.  Different handles may be used from different threads.
+ *   - Work runs on the tree's stream (BKD_OPT_STREAM; by default a stream the
+ *     library creates).  Calls return after their results are complete in
+ *     the caller's output buffers.
+ */
+#ifndef BKD_H
+#define BKD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define BKD_OK 0
+#define BKD_EINVAL (-1)       /* bad argument (null, range, non-finite input) */
+#define BKD_ENOMEM (-2)       /* device or pinned host allocation failed      */
+#define BKD_ECUDA (-3)        /* CUDA runtime error; the handle should be freed */
+#define BKD_ETIMEOUT (-4)     /* a bounded device-side wait ran out           */
+#define BKD_EUNSUPPORTED (-5) /* valid request outside this build's limits    */
+
+/* ------------------------------------------------------------------ limits */
+#define BKD_MAX_DIM 32        /* d <= BKD_MAX_DIM                              */
+#define BKD_MAX_K 31          /* k <= BKD_MAX_K                                */
+#define BKD_MAX_HEIGHT 24     /* height <= BKD_MAX_HEIGHT                      */
+
+/* ----------------------------------------------------------------- options
+ * Set with bkd_set_option (after build) or passed as (key, value) pairs to
+ * bkd_build_with (at build).  Unknown keys are rejected with BKD_EINVAL. */
+enum bkd_option {
+  /* cudaStream_t (as an integer) on which all work of the handle runs;
+   * 0 selects the library's own stream.  Any time. */
+  BKD_OPT_STREAM = 1,
+  /* Bytes of device memory the leaf structure may occupy.  If the leaf
+   * structure is larger, the tree is built in chunked ("bigger") mode: it
+   * stays in pinned host memory and is streamed (Sec. 3.2).  Build only;
+   * default: 60% of the device memory free at build time. */
+  BKD_OPT_DEVICE_MEM_CAP = 2,
+  /* Number N of leaf chunks in chunked mode (Sec. 3.2, "1 < N << n").  0
+   * (default) picks the smallest N whose two chunk buffers fit the cap.  A
+   * value >= 1 at build forces chunked mode with that N.  Build only. */
+  BKD_OPT_CHUNKS = 3,
+  /* Maximum number of queries in flight in one LazySearch (the bounded query
+   * memory of Sec. 3.2, "Multi-Many-Core Querying"); larger query sets are
+   * processed in consecutive slices.  0 (default) = all m at once. */
+  BKD_OPT_MAX_ACTIVE = 4
+};
+
+/* ------------------------------------------------------------------- stats
+ * Counters of the most recent bkd_query on the handle (bkd_get_stat). */
+enum bkd_stat {
+  BKD_STAT_ROUNDS = 1,         /* LazySearch iterations (Algorithm 1 loop)   */
+  BKD_STAT_LEAF_VISITS = 2,    /* (query, leaf) pairs processed              */
+  BKD_STAT_PAIRS = 3,          /* (query, reference point) distances scored  */
+  BKD_STAT_RESORTED = 4,       /* queries re-ordered by binary64 distances   */
+  BKD_STAT_FALLBACK = 5,       /* queries re-searched in binary64            */
+  BKD_STAT_LEAF_KERNEL_MS = 6, /* summed device time of the leaf kernel      */
+  BKD_STAT_CHUNK_BYTES = 7,    /* host-to-device leaf-chunk bytes (chunked)  */
+  BKD_STAT_COPY_MS = 8,        /* summed device time of the chunk copies     */
+  BKD_STAT_LEAF_LAUNCHES = 9,  /* launches of the leaf kernel                */
+  BKD_STAT_KERNEL_LAUNCHES = 10 /* all kernel launches of the query          */
+};
+
+typedef struct bkd_tree bkd_tree; /* opaque; owned by the library */
+
+/* bkd_build -- construction phase (Sec. 2.3 median splits; Sec. 3.1 "build
+ * the top tree on the host and store it on the device").
+ *   P       n x d float32 reference points, host or device.  Read only during
+ *           the call; the library keeps its own rearranged copy.
+ *   n       number of points, 1 <= n; 2^height <= n.
+ *   d       dimension, 1 <= d <= BKD_MAX_DIM.
+ *   height  h: the top tree has 2^h - 1 split values and 2^h leaves, leaf
+ *           sizes differ by at most one.  0 <= h <= BKD_MAX_HEIGHT.
+ *   out     receives the new handle (NULL on failure).
+ * Node v at level i splits its points at the median of dimension i mod d:
+ * the floor(size/2) points smallest by (x_{i mod d}, index) go left; the
+ * split value is the smallest coordinate of the right half.
+ * Errors: BKD_EINVAL, BKD_ENOMEM, BKD_ECUDA, BKD_EUNSUPPORTED. */
+int bkd_build(const float* P, int64_t n, int d, int height, bkd_tree** out);
+
+/* bkd_build_with -- bkd_build with build-time options: `options` holds
+ * `n_options` (key, value) pairs, keys from enum bkd_option. */
+int bkd_build_with(const float* P, int64_t n, int d, int height,
+                   const int64_t* options, int n_options, bkd_tree** out);
+
+/* bkd_query -- query phase: LazySearch (Algorithm 1) with FindLeafBatch,
+ * buffer insertion and ProcessAllBuffers on the device; in chunked mode
+ * ProcessAllBuffers streams the leaf chunks (Sec. 3.2, Brute / Copy / Wait).
+ *   t         handle from bkd_build.
+ *   Q         m x d float32 queries (same d as the tree), host or device.
+ *   m         number of queries, m >= 0 (m == 0 returns at once).
+ *   k         neighbours per query, 1 <= k <= min(n, BKD_MAX_K).
+ *   out_idx   m x k int64, host or device (caller-owned).
+ *   out_dist  m x k float32 squared distances, host or device.
+ * Errors: BKD_EINVAL, BKD_ENOMEM, BKD_ECUDA, BKD_ETIMEOUT,
+ * BKD_EUNSUPPORTED. */
+int bkd_query(bkd_tree* t, const float* Q, int64_t m, int k, int64_t* out_idx,
+              float* out_dist);
+
+/* bkd_set_option -- sets a run-time option (enum bkd_option) on a handle.
+ * Build-only keys are rejected with BKD_EINVAL. */
+int bkd_set_option(bkd_tree* t, int key, int64_t value);
+
+/* bkd_get_stat -- reads a counter of the last query (enum bkd_stat). */
+int bkd_get_stat(const bkd_tree* t, int key, double* value);
+
+/* bkd_tree_shape -- n, d, height, chunked mode (0/1) and chunk count N of a
+ * handle.  Any output pointer may be NULL. */
+int bkd_tree_shape(const bkd_tree* t, int64_t* n, int* d, int* height,
+                   int* chunked, int* chunks);
+
+/* bkd_export_tree -- copies the tree to caller-owned HOST arrays (for
+ * inspection and tests):
+ *   split    2^h - 1 float32 split values in heap order (node v has children
+ *            2v+1 and 2v+2); may be NULL
+ *   leaf_lo  2^h + 1 int64: leaf l holds leaf-structure positions
+ *            [leaf_lo[l], leaf_lo[l+1]); may be NULL
+ *   perm     n int64: original index of leaf-structure position p; may be
+ *            NULL */
+int bkd_export_tree(const bkd_tree* t, float* split, int64_t* leaf_lo,
+                    int64_t* perm);
+
+/* bkd_free -- releases the handle and all its device / pinned memory.
+ * NULL is ignored. */
+void bkd_free(bkd_tree* t);
+
+/* bkd_last_error -- message of the last failed call on this thread ("" if
+ * none).  The string stays valid until the thread's next bkd_* call. */
+const char* bkd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BKD_H */

@@ -1,0 +1,222 @@
+"""GB300 buffer k-d tree: exact k-nearest-neighbour search on one GPU.
+
+Thin Python binding of the C ABI declared in ``include/bkd.h``.  It only
+marshals arguments: every step of the search (FindLeafBatch, buffer
+insertion, ProcessAllBuffers, the chunk streamer, the binary64 re-check) runs
+in the CUDA library ``_build/libbkd.so``.  There is no CPU path: if the
+library cannot be built or loaded, every call raises.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); float32
+row-major points / queries, int64 / float32 outputs.
+
+    tree = bkd_build(P, height=8)
+    idx, dist = bkd_query(tree, Q, k=10)
+    bkd_free(tree)
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import _build_lib
+
+BKD_OK = 0
+BKD_EINVAL = -1
+BKD_ENOMEM = -2
+BKD_ECUDA = -3
+BKD_ETIMEOUT = -4
+BKD_EUNSUPPORTED = -5
+BKD_MAX_DIM = 32
+BKD_MAX_K = 31
+BKD_MAX_HEIGHT = 24
+
+OPTIONS = {"stream": 1, "device_mem_cap": 2, "chunks": 3, "max_active": 4}
+STATS = {"rounds": 1, "leaf_visits": 2, "pairs": 3, "resorted": 4,
+         "fallback": 5, "leaf_kernel_ms": 6, "chunk_bytes": 7, "copy_ms": 8,
+         "leaf_launches": 9, "kernel_launches": 10}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class BkdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"bkd error {code}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build_lib.LIB
+
+
+def load():
+    """Builds (if needed) and loads libbkd.so; raises if that fails."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(_build_lib.build())
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        lib.bkd_build.argtypes = [vp, i64, i32, i32, ctypes.POINTER(vp)]
+        lib.bkd_build_with.argtypes = [vp, i64, i32, i32, vp, i32,
+                                       ctypes.POINTER(vp)]
+        lib.bkd_query.argtypes = [vp, vp, i64, i32, vp, vp]
+        lib.bkd_set_option.argtypes = [vp, i32, i64]
+        lib.bkd_get_stat.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
+        lib.bkd_tree_shape.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.bkd_export_tree.argtypes = [vp, vp, vp, vp]
+        lib.bkd_free.argtypes = [vp]
+        lib.bkd_free.restype = None
+        lib.bkd_last_error.restype = ctypes.c_char_p
+        for f in ("bkd_build", "bkd_build_with", "bkd_query", "bkd_set_option",
+                  "bkd_get_stat", "bkd_tree_shape", "bkd_export_tree"):
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != BKD_OK:
+        raise BkdError(rc, load().bkd_last_error().decode())
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.split(".")[0] == "torch"
+
+
+def _ptr(x, dtype: str, rows_cols=None):
+    """(pointer, shape) of a contiguous numpy array / torch tensor."""
+    if _is_torch(x):
+        import torch
+        want = {"f32": torch.float32, "i64": torch.int64}[dtype]
+        if x.dtype != want or not x.is_contiguous():
+            raise TypeError(f"expected a contiguous {want} tensor")
+        return x.data_ptr(), tuple(x.shape)
+    want = {"f32": np.float32, "i64": np.int64}[dtype]
+    if not isinstance(x, np.ndarray) or x.dtype != want \
+            or not x.flags.c_contiguous:
+        raise TypeError(f"expected a C-contiguous {np.dtype(want)} array")
+    return x.ctypes.data, x.shape
+
+
+class Tree:
+    """Owning wrapper of a ``bkd_tree*`` handle."""
+
+    def __init__(self, handle: int, keepalive=None):
+        self.handle = ctypes.c_void_p(handle)
+        self._keepalive = keepalive
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def close(self):
+        if self.handle and self.handle.value:
+            load().bkd_free(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    @property
+    def shape(self):
+        return bkd_tree_shape(self)
+
+    def query(self, Q, k: int, out_idx=None, out_dist=None):
+        return bkd_query(self, Q, k, out_idx, out_dist)
+
+    def stat(self, name: str) -> float:
+        return bkd_get_stat(self, name)
+
+
+def bkd_build(P, height: int, **options) -> Tree:
+    """``bkd_build`` / ``bkd_build_with``: P is (n, d) float32."""
+    lib = load()
+    p, shape = _ptr(P, "f32")
+    if len(shape) != 2:
+        raise ValueError("P must be (n, d)")
+    n, d = shape
+    out = ctypes.c_void_p()
+    if options:
+        flat = []
+        for key, val in options.items():
+            if key not in OPTIONS:
+                raise ValueError(f"unknown option {key}")
+            flat += [OPTIONS[key], int(val)]
+        arr = (ctypes.c_int64 * len(flat))(*flat)
+        _check(lib.bkd_build_with(p, n, d, height, arr, len(options),
+                                  ctypes.byref(out)))
+    else:
+        _check(lib.bkd_build(p, n, d, height, ctypes.byref(out)))
+    return Tree(out.value)
+
+
+def bkd_query(tree: Tree, Q, k: int, out_idx=None, out_dist=None):
+    """``bkd_query``: returns (idx int64 (m, k), dist float32 (m, k)), on the
+    same device as Q unless output buffers are given."""
+    lib = load()
+    q, shape = _ptr(Q, "f32")
+    if len(shape) != 2:
+        raise ValueError("Q must be (m, d)")
+    m = shape[0]
+    if out_idx is None or out_dist is None:
+        if _is_torch(Q):
+            import torch
+            out_idx = torch.empty((m, k), dtype=torch.int64, device=Q.device)
+            out_dist = torch.empty((m, k), dtype=torch.float32,
+                                   device=Q.device)
+        else:
+            out_idx = np.empty((m, k), np.int64)
+            out_dist = np.empty((m, k), np.float32)
+    oi, si = _ptr(out_idx, "i64")
+    od, sd = _ptr(out_dist, "f32")
+    if tuple(si) != (m, k) or tuple(sd) != (m, k):
+        raise ValueError("outputs must be (m, k)")
+    if _is_torch(Q) and Q.is_cuda:
+        import torch
+        _check(lib.bkd_set_option(tree.handle, OPTIONS["stream"],
+                                  torch.cuda.current_stream(Q.device)
+                                  .cuda_stream))
+    _check(lib.bkd_query(tree.handle, q, m, k, oi, od))
+    return out_idx, out_dist
+
+
+def bkd_set_option(tree: Tree, name: str, value: int):
+    _check(load().bkd_set_option(tree.handle, OPTIONS[name], int(value)))
+
+
+def bkd_get_stat(tree: Tree, name: str) -> float:
+    v = ctypes.c_double()
+    _check(load().bkd_get_stat(tree.handle, STATS[name], ctypes.byref(v)))
+    return v.value
+
+
+def bkd_tree_shape(tree: Tree) -> dict:
+    n, d, h = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+    ch, nc = ctypes.c_int(), ctypes.c_int()
+    _check(load().bkd_tree_shape(tree.handle, ctypes.byref(n), ctypes.byref(d),
+                                 ctypes.byref(h), ctypes.byref(ch),
+                                 ctypes.byref(nc)))
+    return {"n": n.value, "d": d.value, "height": h.value,
+            "chunked": bool(ch.value), "chunks": nc.value}
+
+
+def bkd_export_tree(tree: Tree):
+    """(split (2^h-1,) float32, leaf_lo (2^h+1,) int64, perm (n,) int64)."""
+    s = bkd_tree_shape(tree)
+    L = 1 << s["height"]
+    split = np.empty(max(L - 1, 1), np.float32)
+    leaf_lo = np.empty(L + 1, np.int64)
+    perm = np.empty(s["n"], np.int64)
+    _check(load().bkd_export_tree(tree.handle, split.ctypes.data,
+                                  leaf_lo.ctypes.data, perm.ctypes.data))
+    return split[:L - 1], leaf_lo, perm
+
+
+def bkd_free(tree: Tree):
+    tree.close()
+
+
+def bkd_last_error() -> str:
+    return load().bkd_last_error().decode()

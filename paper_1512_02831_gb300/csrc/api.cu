@@ -1,0 +1,709 @@
+// api.cu -- C ABI, device memory, and the LazySearch driver (Algorithm 1).
+//
+// Query phase, per call (Sec. 2.4, Algorithm 1; Sec. 3.2):
+//   init      queries copied and padded, candidate lists +inf, every query
+//             in the active list (the `input` queue)
+//   round     FindLeafBatch over all active queries -> next leaf or -1;
+//             buffer insertion = counting sort of the active queries by
+//             leaf id (queries with -1 retire); ProcessAllBuffers over every
+//             non-empty buffer; the processed queries form the next round's
+//             active list (the `reinsert` queue).  All active queries are
+//             fetched every round (M = all, buffers unbounded), so each round
+//             triggers ProcessAllBuffers.
+//   finish    re-check against the binary64 error bound, binary64 fallback
+//             search where needed, results to the caller.
+// Chunked ("bigger") mode keeps the leaf structure in pinned host memory and
+// runs ProcessAllBuffers chunk by chunk: Brute on the compute stream over
+// chunk j while the copy stream moves chunk j+1 into the other device chunk
+// buffer, with events in place of the paper's blocking Wait (Sec. 3.2,
+// "Brute / Copy / Wait" on two command queues).  Chunks are whole leaves; the
+// order alternates direction every round so the chunk processed last stays
+// resident for the next round (the paper's prefetch of the first chunk).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "bkd.h"
+#include "bkd_internal.h"
+
+using namespace bkd;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CU(call)                                                            \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess)                                                  \
+      return fail(e_ == cudaErrorMemoryAllocation ? BKD_ENOMEM : BKD_ECUDA, \
+                  "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                  __FILE__, __LINE__);                                      \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev)
+      cudaSetDevice(prev);
+  }
+};
+
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaError_t ensure(size_t count) {
+    if (count <= n && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+    if (e == cudaSuccess) n = count;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+}  // namespace
+
+struct bkd_tree {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t own_stream = nullptr, stream = nullptr, copy_stream = nullptr;
+  HostTree host;
+  DevTree dev{};
+  int64_t n_leaves = 0;
+  // resident storage
+  float* d_pts = nullptr;
+  int64_t* d_orig = nullptr;
+  float* d_split = nullptr;
+  int32_t* d_leaf_cnt = nullptr;
+  // chunked storage
+  bool chunked = false;
+  int n_chunks = 0;
+  float* h_pts = nullptr;        // pinned, mapped
+  int64_t* h_orig = nullptr;     // pinned, mapped
+  std::vector<int32_t> chunk_leaf;
+  int32_t* d_chunk_leaf = nullptr;
+  float* d_chunk_buf[2] = {nullptr, nullptr};
+  int buf_chunk[2] = {-1, -1};
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+  // query workspace
+  DevBuf<float> qdev, qpad, lst_d;
+  DevBuf<uint32_t> lst_i, act_a, act_b, fb_list;
+  DevBuf<int32_t> state, leaf_of, cnt, off, cursor, toff, chunk_item;
+  DevBuf<Item> items;
+  DevBuf<int64_t> out_idx;
+  DevBuf<float> out_dist;
+  Counters* d_ctr = nullptr;
+  Counters* h_ctr = nullptr;     // pinned
+  int32_t* h_chunk_item = nullptr;
+  int max_active = 0;
+  // timing
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> leaf_ev, copy_ev;
+  // stats of the last query
+  double st_rounds = 0, st_visits = 0, st_pairs = 0, st_resorted = 0,
+         st_fallback = 0, st_leaf_ms = 0, st_chunk_bytes = 0, st_copy_ms = 0,
+         st_leaf_launches = 0, st_launches = 0;
+
+  cudaEvent_t next_event() {
+    if (ev_used == ev_pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      ev_pool.push_back(e);
+    }
+    return ev_pool[ev_used++];
+  }
+};
+
+namespace {
+
+void release(bkd_tree* t) {
+  if (!t) return;
+  cudaSetDevice(t->device);
+  if (t->stream) cudaStreamSynchronize(t->stream);
+  if (t->copy_stream) cudaStreamSynchronize(t->copy_stream);
+  cudaFree(t->d_pts);
+  cudaFree(t->d_orig);
+  cudaFree(t->d_split);
+  cudaFree(t->d_leaf_cnt);
+  cudaFree(t->d_chunk_leaf);
+  cudaFree(t->d_chunk_buf[0]);
+  cudaFree(t->d_chunk_buf[1]);
+  if (t->h_pts) cudaFreeHost(t->h_pts);
+  if (t->h_orig) cudaFreeHost(t->h_orig);
+  t->qdev.release();
+  t->qpad.release();
+  t->lst_d.release();
+  t->lst_i.release();
+  t->act_a.release();
+  t->act_b.release();
+  t->fb_list.release();
+  t->state.release();
+  t->leaf_of.release();
+  t->cnt.release();
+  t->off.release();
+  t->cursor.release();
+  t->toff.release();
+  t->chunk_item.release();
+  t->items.release();
+  t->out_idx.release();
+  t->out_dist.release();
+  cudaFree(t->d_ctr);
+  if (t->h_ctr) cudaFreeHost(t->h_ctr);
+  if (t->h_chunk_item) cudaFreeHost(t->h_chunk_item);
+  for (auto e : t->ev_pool) cudaEventDestroy(e);
+  for (int b = 0; b < 2; ++b) {
+    if (t->ev_copied[b]) cudaEventDestroy(t->ev_copied[b]);
+    if (t->ev_free[b]) cudaEventDestroy(t->ev_free[b]);
+  }
+  if (t->own_stream) cudaStreamDestroy(t->own_stream);
+  if (t->copy_stream) cudaStreamDestroy(t->copy_stream);
+  delete[] t->host.split;
+  delete[] t->host.leaf_lo;
+  delete[] t->host.perm;
+  delete t;
+}
+
+// Parallel finiteness / magnitude check of host data.
+bool host_values_ok(const float* P, int64_t count) {
+  unsigned w = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  if (count < (1 << 20)) w = 1;
+  std::vector<char> ok(w, 1);
+  std::vector<std::thread> th;
+  for (unsigned i = 0; i < w; ++i)
+    th.emplace_back([&, i] {
+      const int64_t lo = count * i / w, hi = count * (i + 1) / w;
+      for (int64_t j = lo; j < hi; ++j)
+        if (!(std::fabs(P[j]) < 1.152921504606846976e18f)) {
+          ok[i] = 0;
+          break;
+        }
+    });
+  for (auto& x : th) x.join();
+  for (char c : ok)
+    if (!c) return false;
+  return true;
+}
+
+int build_impl(const float* P, int64_t n, int d, int height,
+               const int64_t* options, int n_options, bkd_tree** out) {
+  if (!out) return fail(BKD_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!P) return fail(BKD_EINVAL, "P is NULL");
+  if (n < 1) return fail(BKD_EINVAL, "n must be >= 1 (got %lld)", (long long)n);
+  if (d < 1 || d > BKD_MAX_DIM)
+    return fail(BKD_EINVAL, "d must be in [1, %d] (got %d)", BKD_MAX_DIM, d);
+  if (height < 0 || height > BKD_MAX_HEIGHT)
+    return fail(BKD_EINVAL, "height must be in [0, %d] (got %d)",
+                BKD_MAX_HEIGHT, height);
+  if (((int64_t)1 << height) > n)
+    return fail(BKD_EINVAL, "2^height = %lld leaves exceed n = %lld",
+                (long long)((int64_t)1 << height), (long long)n);
+  if (n_options < 0 || (n_options > 0 && !options))
+    return fail(BKD_EINVAL, "bad options array");
+  int64_t cap = -1, chunks = 0;
+  for (int i = 0; i < n_options; ++i) {
+    const int64_t key = options[2 * i], val = options[2 * i + 1];
+    if (key == BKD_OPT_DEVICE_MEM_CAP) {
+      if (val < 0) return fail(BKD_EINVAL, "device memory cap must be >= 0");
+      cap = val;
+    } else if (key == BKD_OPT_CHUNKS) {
+      if (val < 0 || val > (1 << 20))
+        return fail(BKD_EINVAL, "chunk count out of range");
+      chunks = val;
+    } else if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE) {
+      // applied after construction below
+    } else {
+      return fail(BKD_EINVAL, "unknown build option %lld", (long long)key);
+    }
+  }
+
+  bkd_tree* t = new (std::nothrow) bkd_tree();
+  if (!t) return fail(BKD_ENOMEM, "host allocation failed");
+  auto bail = [&](int code) {
+    release(t);
+    return code;
+  };
+  if (cudaGetDevice(&t->device) != cudaSuccess)
+    return bail(fail(BKD_ECUDA, "no CUDA device"));
+  cudaDeviceGetAttribute(&t->sm_count, cudaDevAttrMultiProcessorCount,
+                         t->device);
+  if (cudaStreamCreateWithFlags(&t->own_stream, cudaStreamNonBlocking) !=
+          cudaSuccess ||
+      cudaStreamCreateWithFlags(&t->copy_stream, cudaStreamNonBlocking) !=
+          cudaSuccess)
+    return bail(fail(BKD_ECUDA, "stream creation failed"));
+  t->stream = t->own_stream;
+
+  // points on the host
+  std::vector<float> hostP;
+  const float* Ph = P;
+  if (is_device_ptr(P)) {
+    try {
+      hostP.resize((size_t)(n * d));
+    } catch (...) {
+      return bail(fail(BKD_ENOMEM, "host copy of P failed"));
+    }
+    if (cudaMemcpy(hostP.data(), P, sizeof(float) * n * d,
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+      return bail(fail(BKD_ECUDA, "copy of P to the host failed"));
+    Ph = hostP.data();
+  }
+  if (!host_values_ok(Ph, n * d))
+    return bail(fail(BKD_EINVAL, "P holds a non-finite or |x| >= 2^60 value"));
+
+  if (const char* msg = build_host_tree(Ph, n, d, height, &t->host))
+    return bail(fail(BKD_ENOMEM, "%s", msg));
+  HostTree& H = t->host;
+  const int64_t L = (int64_t)1 << height;
+  t->n_leaves = L;
+  const int64_t slots = L * H.lcap;
+  if (slots >= (int64_t)0xffffffff)
+    return bail(fail(BKD_EUNSUPPORTED,
+                     "leaf structure of %lld slots exceeds 2^32 - 1",
+                     (long long)slots));
+  const size_t pts_bytes = (size_t)slots * H.Dp * sizeof(float);
+  const size_t orig_bytes = (size_t)slots * sizeof(int64_t);
+
+  // choose resident or chunked mode
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  if (cap < 0) cap = (int64_t)(0.6 * (double)free_b);
+  bool chunked = chunks >= 1 || (int64_t)pts_bytes > cap;
+  if (chunked && chunks == 0) {
+    for (chunks = 2; chunks < L; ++chunks) {
+      const int64_t leaves = (L + chunks - 1) / chunks;
+      if (2 * leaves * H.lcap * H.Dp * 4 <= cap) break;
+    }
+    chunks = std::min<int64_t>(chunks, L);
+  }
+  if (chunked) chunks = std::min<int64_t>(chunks, L);
+  t->chunked = chunked;
+  t->n_chunks = chunked ? (int)chunks : 0;
+
+  // split values and leaf sizes
+  std::vector<int32_t> leaf_cnt(L);
+  for (int64_t l = 0; l < L; ++l)
+    leaf_cnt[l] = (int32_t)(H.leaf_lo[l + 1] - H.leaf_lo[l]);
+  const int64_t nsplit = std::max<int64_t>(L - 1, 1);
+  if (cudaMalloc(&t->d_split, nsplit * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&t->d_leaf_cnt, L * sizeof(int32_t)) != cudaSuccess)
+    return bail(fail(BKD_ENOMEM, "device allocation failed (tree)"));
+  if (cudaMemcpy(t->d_split, H.split, nsplit * sizeof(float),
+                 cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(t->d_leaf_cnt, leaf_cnt.data(), L * sizeof(int32_t),
+                 cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(fail(BKD_ECUDA, "upload of the top tree failed"));
+
+  if (!chunked) {
+    std::vector<float> qbuf;
+    std::vector<int64_t> obuf;
+    try {
+      qbuf.resize(pts_bytes / sizeof(float));
+      obuf.resize(slots);
+    } catch (...) {
+      return bail(fail(BKD_ENOMEM, "host staging of the leaf structure"));
+    }
+    fill_quads(Ph, H, 0, L, qbuf.data(), obuf.data());
+    if (cudaMalloc(&t->d_pts, pts_bytes) != cudaSuccess ||
+        cudaMalloc(&t->d_orig, orig_bytes) != cudaSuccess)
+      return bail(fail(BKD_ENOMEM, "device allocation of %zu bytes failed",
+                       pts_bytes + orig_bytes));
+    if (cudaMemcpy(t->d_pts, qbuf.data(), pts_bytes, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(t->d_orig, obuf.data(), orig_bytes,
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(fail(BKD_ECUDA, "upload of the leaf structure failed"));
+  } else {
+    if (cudaHostAlloc(&t->h_pts, pts_bytes,
+                      cudaHostAllocMapped | cudaHostAllocPortable) !=
+            cudaSuccess ||
+        cudaHostAlloc(&t->h_orig, orig_bytes,
+                      cudaHostAllocMapped | cudaHostAllocPortable) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return bail(fail(BKD_ENOMEM, "pinned host allocation of %zu bytes failed",
+                       pts_bytes + orig_bytes));
+    }
+    fill_quads(Ph, H, 0, L, t->h_pts, t->h_orig);
+    t->chunk_leaf.resize(t->n_chunks + 1);
+    for (int c = 0; c <= t->n_chunks; ++c)  // C_c = ceil(c L / N), leaves
+      t->chunk_leaf[c] = (int32_t)((c * L + t->n_chunks - 1) / t->n_chunks);
+    int64_t max_leaves = 0;
+    for (int c = 0; c < t->n_chunks; ++c)
+      max_leaves = std::max<int64_t>(max_leaves,
+                                     t->chunk_leaf[c + 1] - t->chunk_leaf[c]);
+    const size_t buf_bytes = (size_t)max_leaves * H.lcap * H.Dp * sizeof(float);
+    if (cudaMalloc(&t->d_chunk_buf[0], buf_bytes) != cudaSuccess ||
+        cudaMalloc(&t->d_chunk_buf[1], buf_bytes) != cudaSuccess ||
+        cudaMalloc(&t->d_chunk_leaf, (t->n_chunks + 1) * sizeof(int32_t)) !=
+            cudaSuccess)
+      return bail(fail(BKD_ENOMEM, "device chunk buffers (%zu bytes each)",
+                       buf_bytes));
+    if (cudaMemcpy(t->d_chunk_leaf, t->chunk_leaf.data(),
+                   (t->n_chunks + 1) * sizeof(int32_t),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(fail(BKD_ECUDA, "upload of chunk bounds failed"));
+    for (int b = 0; b < 2; ++b)
+      if (cudaEventCreateWithFlags(&t->ev_copied[b], cudaEventDisableTiming) !=
+              cudaSuccess ||
+          cudaEventCreateWithFlags(&t->ev_free[b], cudaEventDisableTiming) !=
+              cudaSuccess)
+        return bail(fail(BKD_ECUDA, "event creation failed"));
+  }
+  if (cudaMalloc(&t->d_ctr, sizeof(Counters)) != cudaSuccess ||
+      cudaHostAlloc(&t->h_ctr, sizeof(Counters), cudaHostAllocDefault) !=
+          cudaSuccess ||
+      cudaHostAlloc(&t->h_chunk_item, (t->n_chunks + 2) * sizeof(int32_t),
+                    cudaHostAllocDefault) != cudaSuccess)
+    return bail(fail(BKD_ENOMEM, "counter allocation failed"));
+
+  DevTree& D = t->dev;
+  D.split = t->d_split;
+  D.pts = chunked ? t->h_pts : t->d_pts;
+  D.orig = chunked ? t->h_orig : t->d_orig;
+  D.leaf_cnt = t->d_leaf_cnt;
+  D.n = n;
+  D.d = d;
+  D.Dp = H.Dp;
+  D.h = height;
+  D.lcap = H.lcap;
+  for (int i = 0; i < n_options; ++i) {
+    const int64_t key = options[2 * i], val = options[2 * i + 1];
+    if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE) {
+      int rc = bkd_set_option(t, (int)key, val);
+      if (rc != BKD_OK) return bail(rc);
+    }
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess)
+    return bail(fail(BKD_ECUDA, "build failed: %s",
+                     cudaGetErrorString(cudaGetLastError())));
+  *out = t;
+  return BKD_OK;
+}
+
+// One LazySearch over queries already in t->qdev[0..m) (row-major m x d).
+// Results go to device buffers out_idx / out_dist.
+int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
+  const int K = k + 1;
+  const int cap = list_capacity(K);
+  const DevTree& D = t->dev;
+  const int Dp = D.Dp;
+  cudaStream_t s = t->stream;
+  const int64_t L = t->n_leaves;
+  const int64_t max_items = m / kTileQ + L + 1;
+  CU(t->qpad.ensure(m * Dp));
+  CU(t->lst_d.ensure(m * K));
+  CU(t->lst_i.ensure(m * K));
+  CU(t->state.ensure(m));
+  CU(t->act_a.ensure(m));
+  CU(t->act_b.ensure(m));
+  CU(t->leaf_of.ensure(m));
+  CU(t->fb_list.ensure(m));
+  CU(t->cnt.ensure(L));
+  CU(t->cursor.ensure(L));
+  CU(t->off.ensure(L + 1));
+  CU(t->toff.ensure(L + 1));
+  CU(t->items.ensure(max_items));
+  if (t->chunked) CU(t->chunk_item.ensure(t->n_chunks + 1));
+
+  CU(cudaMemsetAsync(t->d_ctr, 0, sizeof(Counters), s));
+  CU(launch_init(t->qdev.p, m, D.d, Dp, t->qpad.p, t->lst_d.p, t->lst_i.p, K,
+                 t->state.p, t->act_a.p, t->d_ctr, s));
+  t->st_launches += 1;
+  uint32_t* act = t->act_a.p;
+  uint32_t* nxt = t->act_b.p;
+  int n_act = (int)m;
+  const int grid_max = leaf_kernel_grid(Dp, cap, D.lcap, t->sm_count);
+  int round = 0;
+  while (n_act > 0) {
+    CU(launch_find_leaf(D, t->qpad.p, act, n_act, t->state.p, t->lst_d.p, K,
+                        t->leaf_of.p, s));
+    CU(launch_bucket(t->leaf_of.p, act, n_act, (int)L, t->d_leaf_cnt,
+                     t->cnt.p, t->off.p, t->cursor.p, t->toff.p, t->items.p,
+                     nxt, t->d_ctr, s));
+    t->st_launches += 4;
+    if (t->chunked) {
+      CU(launch_chunk_items(t->toff.p, t->d_chunk_leaf, t->n_chunks,
+                            t->chunk_item.p, s));
+      CU(cudaMemcpyAsync(t->h_chunk_item, t->chunk_item.p,
+                         (t->n_chunks + 1) * sizeof(int32_t),
+                         cudaMemcpyDeviceToHost, s));
+      t->st_launches += 1;
+    }
+    CU(cudaMemcpyAsync(t->h_ctr, t->d_ctr, sizeof(Counters),
+                       cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (t->h_ctr->err & kErrNonFinite)
+      return fail(BKD_EINVAL, "Q holds a non-finite or |x| >= 2^60 value");
+    const int n_next = t->h_ctr->n_next;
+    const int n_items = t->h_ctr->n_items;
+    if (n_next == 0) break;
+    t->st_rounds += 1;
+    t->st_visits += n_next;
+    t->st_pairs += (double)t->h_ctr->pairs;
+    if (!t->chunked) {
+      const int grid = std::min(grid_max, n_items);
+      cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
+      if (e0) cudaEventRecord(e0, s);
+      CU(launch_leaf(Dp, cap, t->items.p, 0, n_items, t->d_ctr, t->d_pts, 0,
+                     t->d_leaf_cnt, D.lcap, nxt, t->qpad.p, t->lst_d.p,
+                     t->lst_i.p, K, grid, s));
+      if (e1) cudaEventRecord(e1, s);
+      if (e0 && e1) t->leaf_ev.push_back({e0, e1});
+      t->st_leaf_launches += 1;
+      t->st_launches += 1;
+    } else {
+      // Brute / Copy / Wait over the chunks holding buffered queries
+      const int N = t->n_chunks;
+      const bool forward = (round % 2) == 0;
+      int prev_b = -1;
+      for (int i = 0; i < N; ++i) {
+        const int c = forward ? i : N - 1 - i;
+        const int ilo = t->h_chunk_item[c], ihi = t->h_chunk_item[c + 1];
+        if (ihi <= ilo) continue;
+        int b;
+        if (t->buf_chunk[0] == c)
+          b = 0;
+        else if (t->buf_chunk[1] == c)
+          b = 1;
+        else
+          b = prev_b < 0 ? (t->buf_chunk[0] == -1 ? 0 : 1) : 1 - prev_b;
+        const int64_t leaf_a = t->chunk_leaf[c], leaf_b = t->chunk_leaf[c + 1];
+        if (t->buf_chunk[b] != c) {
+          const size_t off_f = (size_t)leaf_a * D.lcap * Dp;
+          const size_t bytes =
+              (size_t)(leaf_b - leaf_a) * D.lcap * Dp * sizeof(float);
+          CU(cudaStreamWaitEvent(t->copy_stream, t->ev_free[b], 0));
+          cudaEvent_t c0 = t->next_event(), c1 = t->next_event();
+          if (c0) cudaEventRecord(c0, t->copy_stream);
+          CU(cudaMemcpyAsync(t->d_chunk_buf[b], t->h_pts + off_f, bytes,
+                             cudaMemcpyHostToDevice, t->copy_stream));
+          if (c1) cudaEventRecord(c1, t->copy_stream);
+          if (c0 && c1) t->copy_ev.push_back({c0, c1});
+          CU(cudaEventRecord(t->ev_copied[b], t->copy_stream));
+          t->buf_chunk[b] = c;
+          t->st_chunk_bytes += (double)bytes;
+        }
+        CU(cudaStreamWaitEvent(s, t->ev_copied[b], 0));
+        const int grid = std::min(grid_max, ihi - ilo);
+        cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
+        if (e0) cudaEventRecord(e0, s);
+        CU(launch_leaf(Dp, cap, t->items.p, ilo, ihi, t->d_ctr,
+                       t->d_chunk_buf[b], leaf_a, t->d_leaf_cnt, D.lcap, nxt,
+                       t->qpad.p, t->lst_d.p, t->lst_i.p, K, grid, s));
+        if (e1) cudaEventRecord(e1, s);
+        if (e0 && e1) t->leaf_ev.push_back({e0, e1});
+        CU(cudaEventRecord(t->ev_free[b], s));
+        t->st_leaf_launches += 1;
+        t->st_launches += 1;
+        prev_b = b;
+      }
+    }
+    std::swap(act, nxt);
+    n_act = n_next;
+    ++round;
+  }
+  CU(launch_recheck(D, m, k, K, t->qpad.p, t->lst_d.p, t->lst_i.p, out_idx,
+                    out_dist, t->fb_list.p, t->d_ctr, s));
+  CU(cudaMemcpyAsync(t->h_ctr, t->d_ctr, sizeof(Counters),
+                     cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  t->st_launches += 1;
+  const int n_fb = t->h_ctr->n_fallback;
+  t->st_fallback += n_fb;
+  t->st_resorted += t->h_ctr->n_resorted;
+  if (n_fb > 0) {
+    CU(launch_fallback(D, n_fb, t->fb_list.p, k, K, t->qpad.p, t->lst_d.p,
+                       out_idx, out_dist, s));
+    t->st_launches += 1;
+  }
+  return BKD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bkd_build(const float* P, int64_t n, int d, int height, bkd_tree** out) {
+  g_err.clear();
+  return build_impl(P, n, d, height, nullptr, 0, out);
+}
+
+int bkd_build_with(const float* P, int64_t n, int d, int height,
+                   const int64_t* options, int n_options, bkd_tree** out) {
+  g_err.clear();
+  return build_impl(P, n, d, height, options, n_options, out);
+}
+
+int bkd_query(bkd_tree* t, const float* Q, int64_t m, int k, int64_t* out_idx,
+              float* out_dist) {
+  g_err.clear();
+  if (!t) return fail(BKD_EINVAL, "tree is NULL");
+  if (m < 0) return fail(BKD_EINVAL, "m must be >= 0");
+  if (k < 1 || k > t->dev.n)
+    return fail(BKD_EINVAL, "k must be in [1, n] (got %d)", k);
+  if (k > BKD_MAX_K)
+    return fail(BKD_EUNSUPPORTED, "k = %d exceeds BKD_MAX_K = %d", k,
+                BKD_MAX_K);
+  if (m > 0 && (!Q || !out_idx || !out_dist))
+    return fail(BKD_EINVAL, "Q / out_idx / out_dist is NULL");
+  if (m >= (int64_t)1 << 31)
+    return fail(BKD_EUNSUPPORTED, "m >= 2^31; slice the query set");
+  DeviceGuard guard(t->device);
+  t->st_rounds = t->st_visits = t->st_pairs = t->st_resorted =
+      t->st_fallback = t->st_leaf_ms = t->st_chunk_bytes = t->st_copy_ms =
+          t->st_leaf_launches = t->st_launches = 0;
+  t->ev_used = 0;
+  t->leaf_ev.clear();
+  t->copy_ev.clear();
+  if (m == 0) return BKD_OK;
+  const int d = t->dev.d;
+  cudaStream_t s = t->stream;
+  const bool q_dev = is_device_ptr(Q);
+  const bool o_dev = is_device_ptr(out_idx) && is_device_ptr(out_dist);
+  const int64_t slice = t->max_active > 0 ? t->max_active : m;
+  CU(t->qdev.ensure(std::min(slice, m) * d));
+  if (!o_dev) {
+    CU(t->out_idx.ensure(m * k));
+    CU(t->out_dist.ensure(m * k));
+  }
+  for (int64_t q0 = 0; q0 < m; q0 += slice) {
+    const int64_t mm = std::min(slice, m - q0);
+    CU(cudaMemcpyAsync(t->qdev.p, Q + q0 * d, sizeof(float) * mm * d,
+                       q_dev ? cudaMemcpyDeviceToDevice
+                             : cudaMemcpyHostToDevice,
+                       s));
+    int64_t* oi = o_dev ? out_idx + q0 * k : t->out_idx.p + q0 * k;
+    float* od = o_dev ? out_dist + q0 * k : t->out_dist.p + q0 * k;
+    int rc = search(t, mm, k, oi, od);
+    if (rc != BKD_OK) return rc;
+  }
+  if (!o_dev) {
+    CU(cudaMemcpyAsync(out_idx, t->out_idx.p, sizeof(int64_t) * m * k,
+                       cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(out_dist, t->out_dist.p, sizeof(float) * m * k,
+                       cudaMemcpyDeviceToHost, s));
+  }
+  CU(cudaStreamSynchronize(s));
+  if (t->copy_stream) CU(cudaStreamSynchronize(t->copy_stream));
+  for (auto& pr : t->leaf_ev) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess)
+      t->st_leaf_ms += ms;
+  }
+  for (auto& pr : t->copy_ev) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess)
+      t->st_copy_ms += ms;
+  }
+  cudaGetLastError();
+  return BKD_OK;
+}
+
+int bkd_set_option(bkd_tree* t, int key, int64_t value) {
+  g_err.clear();
+  if (!t) return fail(BKD_EINVAL, "tree is NULL");
+  switch (key) {
+    case BKD_OPT_STREAM:
+      t->stream = value ? reinterpret_cast<cudaStream_t>(value) : t->own_stream;
+      return BKD_OK;
+    case BKD_OPT_MAX_ACTIVE:
+      if (value < 0 || value >= ((int64_t)1 << 31))
+        return fail(BKD_EINVAL, "max active out of range");
+      t->max_active = (int)value;
+      return BKD_OK;
+    case BKD_OPT_DEVICE_MEM_CAP:
+    case BKD_OPT_CHUNKS:
+      return fail(BKD_EINVAL, "option %d applies at build only", key);
+    default:
+      return fail(BKD_EINVAL, "unknown option %d", key);
+  }
+}
+
+int bkd_get_stat(const bkd_tree* t, int key, double* value) {
+  g_err.clear();
+  if (!t || !value) return fail(BKD_EINVAL, "NULL argument");
+  switch (key) {
+    case BKD_STAT_ROUNDS: *value = t->st_rounds; break;
+    case BKD_STAT_LEAF_VISITS: *value = t->st_visits; break;
+    case BKD_STAT_PAIRS: *value = t->st_pairs; break;
+    case BKD_STAT_RESORTED: *value = t->st_resorted; break;
+    case BKD_STAT_FALLBACK: *value = t->st_fallback; break;
+    case BKD_STAT_LEAF_KERNEL_MS: *value = t->st_leaf_ms; break;
+    case BKD_STAT_CHUNK_BYTES: *value = t->st_chunk_bytes; break;
+    case BKD_STAT_COPY_MS: *value = t->st_copy_ms; break;
+    case BKD_STAT_LEAF_LAUNCHES: *value = t->st_leaf_launches; break;
+    case BKD_STAT_KERNEL_LAUNCHES: *value = t->st_launches; break;
+    default: return fail(BKD_EINVAL, "unknown stat %d", key);
+  }
+  return BKD_OK;
+}
+
+int bkd_tree_shape(const bkd_tree* t, int64_t* n, int* d, int* height,
+                   int* chunked, int* chunks) {
+  g_err.clear();
+  if (!t) return fail(BKD_EINVAL, "tree is NULL");
+  if (n) *n = t->dev.n;
+  if (d) *d = t->dev.d;
+  if (height) *height = t->dev.h;
+  if (chunked) *chunked = t->chunked ? 1 : 0;
+  if (chunks) *chunks = t->n_chunks;
+  return BKD_OK;
+}
+
+int bkd_export_tree(const bkd_tree* t, float* split, int64_t* leaf_lo,
+                    int64_t* perm) {
+  g_err.clear();
+  if (!t) return fail(BKD_EINVAL, "tree is NULL");
+  const int64_t L = t->n_leaves;
+  if (split && L > 1) std::memcpy(split, t->host.split, sizeof(float) * (L - 1));
+  if (leaf_lo) std::memcpy(leaf_lo, t->host.leaf_lo, sizeof(int64_t) * (L + 1));
+  if (perm) std::memcpy(perm, t->host.perm, sizeof(int64_t) * t->dev.n);
+  return BKD_OK;
+}
+
+void bkd_free(bkd_tree* t) { release(t); }
+
+const char* bkd_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

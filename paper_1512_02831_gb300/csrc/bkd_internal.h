@@ -1,0 +1,136 @@
+// bkd_internal.h -- shared declarations of the buffer k-d tree library.
+//
+// Device data layout (HBM, or pinned host memory in chunked mode):
+//   top tree   float split[2^h - 1], heap order (node v: children 2v+1, 2v+2;
+//              level(v) = floor(log2(v+1)); split dimension = level mod d).
+//   leaf structure "quads": slot s of the leaf structure belongs to leaf
+//              s / Lcap (Lcap = largest leaf size rounded up to 4); groups of
+//              four consecutive slots form a quad of Dp float4 (Dp >= d is the
+//              compiled dimension), dimension-major inside the quad:
+//                  coord(s, i) = pts[(s/4)*4*Dp + 4*i + s%4].
+//              Slots past a leaf's size and dimensions past d hold +inf / 0,
+//              so a padded slot scores +inf and a padded dimension adds an
+//              exact zero.
+//   orig       int64 orig[slot]: row of P at that slot, -1 for padding.
+//   queries    float qpad[m * Dp], zero-padded rows.
+//   k-best     float lst_d[m * K], uint32 lst_i[m * K] (K = k + 1 entries,
+//              ascending, lst_d[q*K + K-1] is the pruning bound); slots.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace bkd {
+
+constexpr int kTileQ = 128;       // queries per leaf work item (= CTA size)
+constexpr int kStart = -1;        // traversal state: root not yet entered
+constexpr int kDone = -2;         // traversal state: root reached twice
+constexpr uint32_t kNoSlot = 0xffffffffu;
+
+// Compiled dimensions of the leaf kernel and compiled list capacities.
+constexpr int kDims[] = {2, 4, 6, 8, 10, 12, 16, 24, 32};
+constexpr int kCaps[] = {2, 4, 8, 12, 16, 32};
+
+int padded_dim(int d);       // smallest compiled dimension >= d (0: none)
+int list_capacity(int K);    // smallest compiled capacity >= K (0: none)
+
+// One unit of ProcessAllBuffers work: up to kTileQ buffered queries
+// (positions [start, start+count) of the bucketed active list) against
+// every point of one leaf.
+struct Item {
+  int32_t leaf;
+  int32_t start;
+  int32_t count;
+  int32_t pad;
+};
+
+// Device-side round counters, copied to the host once per round.
+struct Counters {
+  int32_t n_next;           // queries bucketed into some leaf this round
+  int32_t n_items;          // work items this round
+  unsigned long long pairs; // (query, point) pairs the round scores
+  int32_t n_fallback;       // queries sent to the binary64 search
+  int32_t n_resorted;       // queries re-ordered by binary64 distances
+  int32_t err;              // device-detected input errors (bit mask)
+  int32_t pad;
+};
+
+constexpr int kErrNonFinite = 1;
+
+// Everything the kernels need about the tree.
+struct DevTree {
+  const float* split;      // 2^h - 1 (device)
+  const float* pts;        // quads (device in resident mode, mapped host in
+                           // chunked mode; used by the binary64 checks)
+  const int64_t* orig;     // slot -> original index (device or mapped host)
+  const int32_t* leaf_cnt; // points per leaf (device)
+  int64_t n;
+  int d, Dp, h;
+  int64_t lcap;            // slots per leaf (multiple of 4)
+};
+
+// ------------------------------------------------------------- launchers
+cudaError_t launch_init(const float* Q, int64_t m, int d, int Dp, float* qpad,
+                        float* lst_d, uint32_t* lst_i, int K, int32_t* state,
+                        uint32_t* act, Counters* ctr, cudaStream_t s);
+
+cudaError_t launch_find_leaf(const DevTree& t, const float* qpad,
+                             const uint32_t* act, int n_act, int32_t* state,
+                             const float* lst_d, int K, int32_t* leaf_of,
+                             cudaStream_t s);
+
+cudaError_t launch_bucket(const int32_t* leaf_of, const uint32_t* act,
+                          int n_act, int n_leaves, const int32_t* leaf_cnt,
+                          int32_t* cnt, int32_t* off, int32_t* cursor,
+                          int32_t* toff, Item* items, uint32_t* next,
+                          Counters* ctr, cudaStream_t s);
+
+// chunk_item[c] = first item of chunk c (leaves [chunk_leaf[c],
+// chunk_leaf[c+1])), for c = 0..n_chunks.
+cudaError_t launch_chunk_items(const int32_t* toff, const int32_t* chunk_leaf,
+                               int n_chunks, int32_t* chunk_item,
+                               cudaStream_t s);
+
+// ProcessAllBuffers over items [item_lo, item_hi) (item_hi < 0: read the
+// count from ctr).  pts/leaf0: the quads of leaf `leaf0` start at pts.
+cudaError_t launch_leaf(int Dp, int cap, const Item* items, int item_lo,
+                        int item_hi, const Counters* ctr, const float* pts,
+                        int64_t leaf0, const int32_t* leaf_cnt, int64_t lcap,
+                        const uint32_t* act, const float* qpad, float* lst_d,
+                        uint32_t* lst_i, int K, int grid, cudaStream_t s);
+
+int leaf_kernel_grid(int Dp, int cap, int64_t lcap, int sm_count);
+
+cudaError_t launch_recheck(const DevTree& t, int64_t m, int k, int K,
+                           const float* qpad, const float* lst_d,
+                           const uint32_t* lst_i, int64_t* out_idx,
+                           float* out_dist, uint32_t* fb_list, Counters* ctr,
+                           cudaStream_t s);
+
+cudaError_t launch_fallback(const DevTree& t, int n_fb, const uint32_t* fb_list,
+                            int k, int K, const float* qpad, const float* lst_d,
+                            int64_t* out_idx, float* out_dist, cudaStream_t s);
+
+// Host tree construction (build.cpp).
+struct HostTree {
+  int64_t n = 0;
+  int d = 0, Dp = 0, h = 0;
+  int64_t lcap = 0;
+  float* split = nullptr;     // 2^h - 1 (at least one element)
+  int64_t* leaf_lo = nullptr; // 2^h + 1
+  int64_t* perm = nullptr;    // n
+};
+
+// Builds split / leaf_lo / perm of the median-split tree over host P.
+// Returns 0 or an error message (static string).
+const char* build_host_tree(const float* P, int64_t n, int d, int h,
+                            HostTree* out);
+
+// Writes the quads and orig arrays for leaves [leaf_lo_id, leaf_hi_id)
+// into host buffers (`pts` and `orig` point at leaf leaf_lo_id's first slot).
+void fill_quads(const float* P, const HostTree& t, int64_t leaf_lo_id,
+                int64_t leaf_hi_id, float* pts, int64_t* orig);
+
+}  // namespace bkd

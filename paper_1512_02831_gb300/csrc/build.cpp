@@ -1,0 +1,178 @@
+// build.cpp -- host construction of the buffer k-d tree (Sec. 2.3, Sec. 3.1).
+//
+// The node at level i splits its points at the median of dimension i mod d
+// (Sec. 2.3).  For a node over leaf-structure positions [lo, hi) the
+// floor((hi-lo)/2) points smallest by the key (x_s, original index) go to
+// [lo, mid), mid = lo + floor((hi-lo)/2); the split value is the smallest
+// x_s of the right half.  Splitting stops after h levels, giving 2^h leaves
+// whose sizes differ by at most one.  Sec. 3.1 builds the top tree on the
+// host with linear-time selection; std::nth_element (introselect) is used per
+// node, so one level costs O(n) and the whole build O(h n).
+//
+// Each level gathers the node-local keys (x_s, index) into a contiguous array
+// (one pass over the points in their current order), selects the median of
+// every node in parallel, and keeps the new order for the next level.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "bkd_internal.h"
+
+namespace bkd {
+namespace {
+
+struct Key {
+  float x;
+  int32_t pad;
+  int64_t idx;
+};
+
+inline bool key_less(const Key& a, const Key& b) {
+  return a.x < b.x || (a.x == b.x && a.idx < b.idx);
+}
+
+int worker_count() {
+  unsigned t = std::thread::hardware_concurrency();
+  if (t == 0) t = 4;
+  return (int)std::min(t, 64u);
+}
+
+// Runs f(lo, hi) over [0, n) split into contiguous ranges, one per worker.
+template <class F>
+void parallel_ranges(int64_t n, F f) {
+  const int w = worker_count();
+  if (n < (1 << 16) || w == 1) {
+    f((int64_t)0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int i = 0; i < w; ++i) {
+    int64_t lo = n * i / w, hi = n * (i + 1) / w;
+    th.emplace_back([=] { f(lo, hi); });
+  }
+  for (auto& t : th) t.join();
+}
+
+// Runs g(j) for j in [0, count), items handed out dynamically.
+template <class G>
+void parallel_items(int64_t count, G g) {
+  const int w = (int)std::min<int64_t>(worker_count(), count);
+  if (w <= 1) {
+    for (int64_t j = 0; j < count; ++j) g(j);
+    return;
+  }
+  std::atomic<int64_t> next{0};
+  std::vector<std::thread> th;
+  for (int i = 0; i < w; ++i)
+    th.emplace_back([&] {
+      for (int64_t j; (j = next.fetch_add(1)) < count;) g(j);
+    });
+  for (auto& t : th) t.join();
+}
+
+}  // namespace
+
+int padded_dim(int d) {
+  for (int D : kDims)
+    if (D >= d) return D;
+  return 0;
+}
+
+int list_capacity(int K) {
+  for (int c : kCaps)
+    if (c >= K) return c;
+  return 0;
+}
+
+const char* build_host_tree(const float* P, int64_t n, int d, int h,
+                            HostTree* out) {
+  const int64_t L = (int64_t)1 << h;
+  out->n = n;
+  out->d = d;
+  out->h = h;
+  out->Dp = padded_dim(d);
+  try {
+    out->split = new float[std::max<int64_t>(L - 1, 1)];
+    out->leaf_lo = new int64_t[L + 1];
+    out->perm = new int64_t[n];
+  } catch (...) {
+    return "host allocation failed (tree arrays)";
+  }
+  out->split[0] = 0.f;
+  std::vector<Key> keys;
+  std::vector<int64_t> bounds, nb;
+  try {
+    keys.resize(h > 0 ? n : 0);
+    bounds.reserve(L + 1);
+    nb.reserve(L + 1);
+  } catch (...) {
+    return "host allocation failed (build keys)";
+  }
+  int64_t* ord = out->perm;
+  parallel_ranges(n, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i) ord[i] = i;
+  });
+  bounds.assign({0, n});
+  for (int level = 0; level < h; ++level) {
+    const int s = level % d;
+    parallel_ranges(n, [&](int64_t lo, int64_t hi) {
+      for (int64_t i = lo; i < hi; ++i) {
+        keys[i].x = P[ord[i] * d + s];
+        keys[i].pad = 0;
+        keys[i].idx = ord[i];
+      }
+    });
+    const int64_t nodes = (int64_t)1 << level;
+    nb.assign(2 * nodes + 1, 0);
+    parallel_items(nodes, [&](int64_t j) {
+      const int64_t lo = bounds[j], hi = bounds[j + 1];
+      const int64_t mid = lo + (hi - lo) / 2;
+      std::nth_element(keys.begin() + lo, keys.begin() + mid,
+                       keys.begin() + hi, key_less);
+      out->split[(nodes - 1) + j] = keys[mid].x;
+      nb[2 * j] = lo;
+      nb[2 * j + 1] = mid;
+    });
+    nb[2 * nodes] = n;
+    parallel_ranges(n, [&](int64_t lo, int64_t hi) {
+      for (int64_t i = lo; i < hi; ++i) ord[i] = keys[i].idx;
+    });
+    bounds.swap(nb);
+  }
+  int64_t maxleaf = 0;
+  for (int64_t l = 0; l <= L; ++l) out->leaf_lo[l] = bounds[l];
+  for (int64_t l = 0; l < L; ++l)
+    maxleaf = std::max(maxleaf, bounds[l + 1] - bounds[l]);
+  out->lcap = (maxleaf + 3) / 4 * 4;
+  return nullptr;
+}
+
+void fill_quads(const float* P, const HostTree& t, int64_t leaf_a,
+                int64_t leaf_b, float* pts, int64_t* orig) {
+  const int d = t.d, Dp = t.Dp;
+  const int64_t lcap = t.lcap;
+  const float inf = INFINITY;
+  parallel_items(leaf_b - leaf_a, [&](int64_t j) {
+    const int64_t leaf = leaf_a + j;
+    const int64_t lo = t.leaf_lo[leaf], cnt = t.leaf_lo[leaf + 1] - lo;
+    for (int64_t u = 0; u < lcap; ++u) {
+      const int64_t slot = j * lcap + u;  // relative to leaf_a's first slot
+      float* quad = pts + (slot >> 2) * 4 * Dp;
+      const int lane = (int)(slot & 3);
+      if (u < cnt) {
+        const int64_t row = t.perm[lo + u];
+        const float* x = P + row * d;
+        for (int i = 0; i < Dp; ++i) quad[4 * i + lane] = i < d ? x[i] : 0.f;
+        orig[slot] = row;
+      } else {
+        for (int i = 0; i < Dp; ++i) quad[4 * i + lane] = inf;
+        orig[slot] = -1;
+      }
+    }
+  });
+}
+
+}  // namespace bkd

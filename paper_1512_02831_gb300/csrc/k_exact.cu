@@ -1,0 +1,231 @@
+// k_exact.cu -- turning the float32 candidate lists into exact answers.
+//
+// After LazySearch every query holds the k+1 smallest float32 distances
+// v_0 <= ... <= v_k over all n points (exact pruning, see k_traverse.cu).
+// The answer is defined by binary64 distances and the smaller-index tie rule
+// (Sec. 2.2 problem statement).  With u = 2^-24 the float32 value of a
+// distance D64 obeys |v - D64| <= gam * D64 + eta, gam = (d + 3) u (the
+// d+2 roundings of the float32 chain plus the binary64 rounding of D64, with
+// margin) and eta = 2^-120 (subnormal underflow).  Hence D64 lies in
+// [lo(v), hi(v)] with lo(v) = (v - eta) / (1 + gam), hi(v) = (v + eta) /
+// (1 - gam), and "a certainly below b" means hi(a) < lo(b).
+//
+//   * k-th certainly below (k+1)-th: the first k list entries are exactly
+//     the k nearest points (every other point scores >= v_k).
+//       - all adjacent entries certainly ordered: the float32 order is the
+//         exact order; output as is.
+//       - otherwise: recompute the k distances in binary64 (same operation
+//         order as the oracle) and sort by (D64, index).
+//   * otherwise (a near tie at the k / k+1 boundary): the query is searched
+//     again in binary64 by the fallback kernel below, a classical depth-first
+//     k-d tree search (Sec. 2.3) with the exact key, pruning far children iff
+//     plane^2 > min(current k-th D64, hi(v_{k-1})) -- hi(v_{k-1}) bounds the
+//     true k-th distance from above because k points score at most v_{k-1}.
+#include "bkd.h"
+#include "bkd_internal.h"
+
+namespace bkd {
+namespace {
+
+__device__ __forceinline__ double lo_bound(float v, double gam, double eta) {
+  return ((double)v - eta) / (1.0 + gam);
+}
+__device__ __forceinline__ double hi_bound(float v, double gam, double eta) {
+  return ((double)v + eta) / (1.0 - gam);
+}
+
+__device__ __forceinline__ float coord(const float* pts, int Dp, uint64_t slot,
+                                       int i) {
+  return pts[(slot >> 2) * 4 * (uint64_t)Dp + 4 * i + (slot & 3)];
+}
+
+// binary64 squared distance, terms added in dimension order from 0.0 with
+// one rounding per operation (the oracle's sequence).
+__device__ double dist64(const float* qp, const float* pts, int Dp, int d,
+                         uint64_t slot) {
+  double acc = 0.0;
+  for (int i = 0; i < d; ++i) {
+    const double t = __dsub_rn((double)qp[i], (double)coord(pts, Dp, slot, i));
+    acc = __dadd_rn(acc, __dmul_rn(t, t));
+  }
+  return acc;
+}
+
+__device__ __forceinline__ bool key_less(double da, int64_t ia, double db,
+                                         int64_t ib) {
+  return da < db || (da == db && ia < ib);
+}
+
+__global__ void recheck_kernel(DevTree t, int64_t m, int k, int K,
+                               const float* __restrict__ qpad,
+                               const float* __restrict__ lst_d,
+                               const uint32_t* __restrict__ lst_i,
+                               int64_t* __restrict__ out_idx,
+                               float* __restrict__ out_dist,
+                               uint32_t* __restrict__ fb_list, Counters* ctr,
+                               double gam, double eta) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= m) return;
+  const float* v = lst_d + q * K;
+  const uint32_t* sl = lst_i + q * K;
+  const float vk = v[k];
+  const bool member_ok =
+      isinf(vk) || hi_bound(v[k - 1], gam, eta) < lo_bound(vk, gam, eta);
+  if (!member_ok) {
+    const int j = atomicAdd(&ctr->n_fallback, 1);
+    fb_list[j] = (uint32_t)q;
+    return;
+  }
+  bool order_ok = true;
+  for (int j = 0; j + 1 < k; ++j)
+    order_ok &= hi_bound(v[j], gam, eta) < lo_bound(v[j + 1], gam, eta);
+  if (order_ok) {
+    for (int j = 0; j < k; ++j) {
+      out_idx[q * k + j] = t.orig[sl[j]];
+      out_dist[q * k + j] = v[j];
+    }
+    return;
+  }
+  atomicAdd(&ctr->n_resorted, 1);
+  double dd[BKD_MAX_K];
+  int64_t ii[BKD_MAX_K];
+  const float* qp = qpad + q * t.Dp;
+  for (int j = 0; j < k; ++j) {
+    const double dv = dist64(qp, t.pts, t.Dp, t.d, sl[j]);
+    const int64_t iv = t.orig[sl[j]];
+    int p = j;
+    while (p > 0 && key_less(dv, iv, dd[p - 1], ii[p - 1])) {
+      dd[p] = dd[p - 1];
+      ii[p] = ii[p - 1];
+      --p;
+    }
+    dd[p] = dv;
+    ii[p] = iv;
+  }
+  for (int j = 0; j < k; ++j) {
+    out_idx[q * k + j] = ii[j];
+    out_dist[q * k + j] = (float)dd[j];
+  }
+}
+
+constexpr int kFbWarps = 4;
+
+// One warp per query.  Lane j < k owns entry j of the sorted binary64 list.
+__global__ void __launch_bounds__(32 * kFbWarps)
+    fallback_kernel(DevTree t, int n_fb, const uint32_t* __restrict__ fb_list,
+                    int k, int K, const float* __restrict__ qpad,
+                    const float* __restrict__ lst_d,
+                    int64_t* __restrict__ out_idx,
+                    float* __restrict__ out_dist, double gam, double eta) {
+  const int lane = threadIdx.x & 31;
+  const int first_leaf = (1 << t.h) - 1;
+  for (int f = blockIdx.x * kFbWarps + (threadIdx.x >> 5); f < n_fb;
+       f += gridDim.x * kFbWarps) {
+    const int64_t q = fb_list[f];
+    const float* qp = qpad + q * t.Dp;
+    const double seed = hi_bound(lst_d[q * K + (k - 1)], gam, eta);
+    double myd = __longlong_as_double(0x7ff0000000000000ll);  // +inf
+    int64_t myi = INT64_MAX;
+    int cnt = 0;  // warp-uniform
+    int node = 0;
+    for (int level = 0; node < first_leaf; ++level)
+      node = 2 * node + (qp[level % t.d] < t.split[node] ? 1 : 2);
+    for (;;) {
+      // ---- scan the leaf
+      const int leaf = node - first_leaf;
+      const int np = t.leaf_cnt[leaf];
+      const uint64_t base = (uint64_t)leaf * (uint64_t)t.lcap;
+      for (int u0 = 0; u0 < np; u0 += 32) {
+        const int u = u0 + lane;
+        double dv = 0.0;
+        int64_t iv = 0;
+        bool cand = false;
+        if (u < np) {
+          dv = dist64(qp, t.pts, t.Dp, t.d, base + u);
+          iv = t.orig[base + u];
+          cand = dv <= seed;
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, cand);
+        while (mask) {
+          const int src = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const double cd = __shfl_sync(0xffffffffu, dv, src);
+          const int64_t ci = __shfl_sync(0xffffffffu, iv, src);
+          const double kd = __shfl_sync(0xffffffffu, myd, k - 1);
+          const int64_t ki = __shfl_sync(0xffffffffu, myi, k - 1);
+          if (cnt == k && !key_less(cd, ci, kd, ki)) continue;
+          const bool less = lane < cnt && key_less(myd, myi, cd, ci);
+          const int pos = __popc(__ballot_sync(0xffffffffu, less));
+          const double upd = __shfl_up_sync(0xffffffffu, myd, 1);
+          const int64_t upi = __shfl_up_sync(0xffffffffu, myi, 1);
+          if (lane > pos) {
+            myd = upd;
+            myi = upi;
+          } else if (lane == pos) {
+            myd = cd;
+            myi = ci;
+          }
+          cnt = min(cnt + 1, k);
+        }
+      }
+      // ---- climb to the next far child worth visiting
+      const double kd = __shfl_sync(0xffffffffu, myd, k - 1);
+      const double bound = cnt == k ? fmin(kd, seed) : seed;
+      for (;;) {
+        if (node == 0) {
+          node = kDone;
+          break;
+        }
+        const int parent = (node - 1) >> 1;
+        const int s = (31 - __clz(parent + 1)) % t.d;
+        const float sv = t.split[parent];
+        const bool near_left = qp[s] < sv;
+        if (((node & 1) != 0) == near_left) {
+          const double tt = __dsub_rn((double)qp[s], (double)sv);
+          if (__dmul_rn(tt, tt) <= bound) {
+            node = near_left ? 2 * parent + 2 : 2 * parent + 1;
+            break;
+          }
+        }
+        node = parent;
+      }
+      if (node == kDone) break;
+      for (int level = 31 - __clz(node + 1); node < first_leaf; ++level)
+        node = 2 * node + (qp[level % t.d] < t.split[node] ? 1 : 2);
+    }
+    if (lane < k) {
+      out_idx[q * k + lane] = myi;
+      out_dist[q * k + lane] = (float)myd;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_recheck(const DevTree& t, int64_t m, int k, int K,
+                           const float* qpad, const float* lst_d,
+                           const uint32_t* lst_i, int64_t* out_idx,
+                           float* out_dist, uint32_t* fb_list, Counters* ctr,
+                           cudaStream_t s) {
+  if (m == 0) return cudaSuccess;
+  const double gam = (t.d + 3) * 5.9604644775390625e-08;  // (d+3) 2^-24
+  const double eta = 7.52316384526264e-37;                // 2^-120
+  recheck_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(
+      t, m, k, K, qpad, lst_d, lst_i, out_idx, out_dist, fb_list, ctr, gam,
+      eta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fallback(const DevTree& t, int n_fb, const uint32_t* fb_list,
+                            int k, int K, const float* qpad, const float* lst_d,
+                            int64_t* out_idx, float* out_dist, cudaStream_t s) {
+  if (n_fb == 0) return cudaSuccess;
+  const double gam = (t.d + 3) * 5.9604644775390625e-08;
+  const double eta = 7.52316384526264e-37;
+  const int grid = (n_fb + kFbWarps - 1) / kFbWarps;
+  fallback_kernel<<<grid < 4096 ? grid : 4096, 32 * kFbWarps, 0, s>>>(
+      t, n_fb, fb_list, k, K, qpad, lst_d, out_idx, out_dist, gam, eta);
+  return cudaGetLastError();
+}
+
+}  // namespace bkd

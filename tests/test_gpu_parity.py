@@ -1,0 +1,233 @@
+"""Parity of the CUDA path against the binary64 oracle (needs a GPU).
+
+Sizes span several leaves, several query tiles of the leaf kernel and ragged
+tails (n not a multiple of 2^h or of 4, m not a multiple of the tile).  Edge
+cases: height 0 (one leaf = brute force), k = n, a single point, all points
+identical, exact ties on integer grids, duplicate rows, queries equal to
+reference points, far-away queries, every compiled dimension.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1512_02831_gb300 as bkd
+import workloads
+from parity import check
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_cases.json")
+
+
+def run(P, Q, k, h, **opts):
+    tree = bkd.bkd_build(P, h, **opts)
+    try:
+        idx, dist = bkd.bkd_query(tree, Q, k)
+        stats = {s: bkd.bkd_get_stat(tree, s) for s in bkd.STATS}
+    finally:
+        bkd.bkd_free(tree)
+    return idx, dist, stats
+
+
+def test_hand_cases_exact():
+    data = json.load(open(GOLDEN))
+    for case in data["cases"]:
+        P = np.array(case["P"], np.float32)
+        for qc in case["queries"]:
+            Q = np.array([qc["q"]], np.float32)
+            for h in range(0, int(math.log2(P.shape[0])) + 1):
+                idx, dist, _ = run(P, Q, qc["k"], h)
+                assert idx[0].tolist() == qc["idx"], (case["name"], qc, h)
+                assert dist[0].tolist() == [float(x) for x in qc["dist"]]
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 7, 10, 11, 16, 20, 27, 32])
+def test_every_dimension(d):
+    rng = np.random.default_rng(d)
+    n = 3000 + d
+    P = rng.standard_normal((n, d)).astype(np.float32)
+    Q = rng.standard_normal((517, d)).astype(np.float32)
+    k = 7
+    h = 5
+    idx, dist, _ = run(P, Q, k, h)
+    check(P, Q, k, idx, dist, oracle.brute_knn(P, Q, k))
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 7, 8, 11, 15, 16, 31])
+def test_every_list_capacity(k):
+    P = workloads.uniform(5000, 6, 7)
+    Q = workloads.uniform(700, 6, 8)
+    idx, dist, _ = run(P, Q, k, 6)
+    check(P, Q, k, idx, dist, oracle.brute_knn(P, Q, k))
+
+
+@pytest.mark.parametrize("n,h", [(1, 0), (2, 1), (5, 0), (17, 2), (31, 4),
+                                 (1000, 9), (4097, 3), (10007, 10)])
+def test_ragged_sizes_and_heights(n, h):
+    rng = np.random.default_rng(n)
+    P = rng.random((n, 3), dtype=np.float32)
+    Q = rng.random((300, 3), dtype=np.float32)
+    k = min(n, 5)
+    idx, dist, _ = run(P, Q, k, h)
+    check(P, Q, k, idx, dist, oracle.brute_knn(P, Q, k))
+
+
+def test_k_equals_n():
+    P = workloads.uniform(29, 4, 3)
+    Q = workloads.uniform(50, 4, 4)
+    idx, dist, _ = run(P, Q, 29 if 29 <= bkd.BKD_MAX_K else 31, 2)
+    check(P, Q, 29, idx, dist, oracle.brute_knn(P, Q, 29))
+
+
+def test_all_points_identical():
+    P = np.full((600, 5), 0.25, np.float32)
+    Q = np.concatenate([np.full((3, 5), 0.25, np.float32),
+                        workloads.uniform(40, 5, 1)])
+    idx, dist, stats = run(P, Q, 9, 4)
+    ref = oracle.brute_knn(P, Q, 9)
+    check(P, Q, 9, idx, dist, ref)
+    assert (idx == np.arange(9)).all()   # all tie: smallest indices win
+    assert stats["fallback"] == Q.shape[0]
+
+
+def test_integer_grid_ties():
+    rng = np.random.default_rng(12)
+    P = rng.integers(0, 5, (4000, 3)).astype(np.float32)
+    Q = (rng.integers(-2, 12, (1000, 3)) * 0.5).astype(np.float32)
+    for k in (1, 6, 20):
+        idx, dist, stats = run(P, Q, k, 6)
+        check(P, Q, k, idx, dist, oracle.brute_knn(P, Q, k))
+
+
+def test_duplicates_and_queries_on_points():
+    P = workloads.with_duplicates(workloads.uniform(8000, 10, 5), 0.05, 2)
+    Q = np.concatenate([P[::97], workloads.uniform(500, 10, 6)])
+    idx, dist, _ = run(P, Q, 10, 7)
+    check(P, Q, 10, idx, dist, oracle.brute_knn(P, Q, 10))
+
+
+def test_far_queries_and_tiny_scales():
+    rng = np.random.default_rng(21)
+    P = (rng.standard_normal((3000, 4)) * 1e-6).astype(np.float32)
+    Q = np.concatenate([
+        (rng.standard_normal((100, 4)) * 1e-6).astype(np.float32),
+        (rng.standard_normal((100, 4)) * 1e3).astype(np.float32)])
+    idx, dist, _ = run(P, Q, 5, 5)
+    check(P, Q, 5, idx, dist, oracle.brute_knn(P, Q, 5))
+
+
+def test_uniform_65536_full_queryset():
+    """n=65,536, m=16,384, d=10, uniform [0,1)^10 (seeds 0 / 1), k=10,
+    height 8 (256 leaves of 256 points): every query against brute force."""
+    w = workloads.UNIFORM_64K
+    P, Q = w.points(), w.queries()
+    idx, dist, stats = run(P, Q, w.k, w.height)
+    info = check(P, Q, w.k, idx, dist, oracle.brute_knn(P, Q, w.k))
+    assert stats["rounds"] >= 2 and stats["pairs"] > 0
+    print("uniform 64K:", info, stats)
+
+
+def test_mixture_scaled():
+    w = workloads.scaled(workloads.MIXTURE_64M, 1 << 20, 1 << 15, 10)
+    P, Q = w.points(), w.queries()
+    idx, dist, stats = run(P, Q, w.k, w.height)
+    rows = np.arange(0, Q.shape[0], 4)
+    ref = oracle.brute_knn(P, Q[rows], w.k)
+    print("mixture 2^20:", check(P, Q, w.k, idx, dist, ref, rows), stats)
+
+
+def test_tree_matches_oracle_tree():
+    """The library's median-split tree equals the oracle's (same rule,
+    independent code): split values, leaf bounds and leaf membership."""
+    P = workloads.mixture(20000, workloads.mixture_params(7, 8, .05, .2, 0), 3)
+    for h in (0, 3, 8):
+        tree = bkd.bkd_build(P, h)
+        split, leaf_lo, perm = bkd.bkd_export_tree(tree)
+        bkd.bkd_free(tree)
+        ot = oracle.build_tree(P, h)
+        assert np.array_equal(leaf_lo, ot.leaf_lo)
+        assert np.array_equal(split, ot.split[:len(split)])
+        sizes = np.diff(leaf_lo)
+        mine = np.empty(P.shape[0], np.int64)
+        mine[perm] = np.repeat(np.arange(1 << h), sizes)
+        assert np.array_equal(mine, ot.leaf_of_point())
+
+
+@pytest.mark.parametrize("chunks", [1, 2, 3, 10])
+def test_chunked_mode_is_bit_identical(chunks):
+    """Streaming the leaf structure in N leaf chunks (Sec. 3.2) changes only
+    the schedule: results equal the resident run bit for bit."""
+    w = workloads.scaled(workloads.MIXTURE_64M, 1 << 17, 1 << 13, 9)
+    P, Q = w.points(), w.queries()
+    idx0, dist0, _ = run(P, Q, w.k, w.height)
+    idx1, dist1, st = run(P, Q, w.k, w.height, chunks=chunks)
+    assert np.array_equal(idx0, idx1) and np.array_equal(dist0, dist1)
+    if chunks > 2:
+        assert st["chunk_bytes"] > 0
+    check(P, Q, w.k, idx1, dist1, oracle.brute_knn(P, Q[:512], w.k),
+          rows=np.arange(512))
+
+
+def test_chunked_by_memory_cap():
+    P = workloads.uniform(50000, 10, 1)
+    Q = workloads.uniform(3000, 10, 2)
+    tree = bkd.bkd_build(P, 7, device_mem_cap=400_000)
+    shape = bkd.bkd_tree_shape(tree)
+    idx, dist = bkd.bkd_query(tree, Q, 10)
+    bkd.bkd_free(tree)
+    assert shape["chunked"] and shape["chunks"] >= 2
+    check(P, Q, 10, idx, dist, oracle.brute_knn(P, Q, 10))
+
+
+def test_query_slicing_is_bit_identical():
+    P = workloads.uniform(30000, 8, 3)
+    Q = workloads.uniform(5000, 8, 4)
+    idx0, dist0, _ = run(P, Q, 10, 7)
+    idx1, dist1, _ = run(P, Q, 10, 7, max_active=777)
+    assert np.array_equal(idx0, idx1) and np.array_equal(dist0, dist1)
+
+
+def test_device_pointers_and_streams():
+    torch = pytest.importorskip("torch")
+    P = workloads.uniform(20000, 10, 1)
+    Q = workloads.uniform(3000, 10, 2)
+    Pd = torch.from_numpy(P).cuda()
+    Qd = torch.from_numpy(Q).cuda()
+    tree = bkd.bkd_build(Pd, 6)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        idx, dist = bkd.bkd_query(tree, Qd, 10)
+    s.synchronize()
+    assert idx.is_cuda and dist.is_cuda
+    idx_h, dist_h = bkd.bkd_query(tree, Q, 10)
+    bkd.bkd_free(tree)
+    assert np.array_equal(idx.cpu().numpy(), idx_h)
+    check(P, Q, 10, idx_h, dist_h, oracle.brute_knn(P, Q, 10))
+
+
+def test_rejects_non_finite_queries_and_stays_usable():
+    P = workloads.uniform(2000, 3, 1)
+    tree = bkd.bkd_build(P, 3)
+    Q = workloads.uniform(10, 3, 2)
+    Q[4, 1] = np.nan
+    with pytest.raises(bkd.BkdError) as e:
+        bkd.bkd_query(tree, Q, 3)
+    assert e.value.code == bkd.BKD_EINVAL
+    Q[4, 1] = 0.5
+    idx, dist = bkd.bkd_query(tree, Q, 3)
+    bkd.bkd_free(tree)
+    check(P, Q, 3, idx, dist, oracle.brute_knn(P, Q, 3))
+
+
+def test_empty_query_set_and_bad_k():
+    P = workloads.uniform(100, 2, 1)
+    tree = bkd.bkd_build(P, 2)
+    idx, dist = bkd.bkd_query(tree, np.zeros((0, 2), np.float32), 4)
+    assert idx.shape == (0, 4)
+    with pytest.raises(bkd.BkdError):
+        bkd.bkd_query(tree, np.zeros((3, 2), np.float32), 101)
+    bkd.bkd_free(tree)

@@ -125,11 +125,13 @@ class Workload:
             P = with_duplicates(P, self.duplicates, 3)
         return P
 
-    def queries(self, m: int | None = None) -> np.ndarray:
+    def queries(self, m: int | None = None, stream: int = 0) -> np.ndarray:
+        """Query set; ``stream`` > 0 draws an independent set of the same
+        distribution (one per process when the queries are sharded)."""
         m = self.m if m is None else m
         if self.kind == "uniform":
-            return uniform(m, self.d, 1)
-        return mixture(m, self._params(), 2)
+            return uniform(m, self.d, 1 + 1000 * stream)
+        return mixture(m, self._params(), 2 + 1000 * stream)
 
     def _params(self) -> MixtureParams:
         return mixture_params(self.d, self.components, self.sigma_lo,
