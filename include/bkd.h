@@ -59,6 +59,9 @@ extern "C" {
 #define BKD_MAX_DIM 32        /* d <= BKD_MAX_DIM                              */
 #define BKD_MAX_K 31          /* k <= BKD_MAX_K                                */
 #define BKD_MAX_HEIGHT 24     /* height <= BKD_MAX_HEIGHT                      */
+#define BKD_STATIC_MAX_QUERIES 4096      /* m limit of bkd_query_static      */
+#define BKD_STATIC_MAX_HEIGHT 16         /* tree height limit of it          */
+#define BKD_STATIC_SCRATCH_BYTES 4194304 /* its static device scratch area   */
 
 /* ----------------------------------------------------------------- options
  * Set with bkd_set_option (after build) or passed as (key, value) pairs to
@@ -132,6 +135,32 @@ int bkd_build_with(const float* P, int64_t n, int d, int height,
  * BKD_EUNSUPPORTED. */
 int bkd_query(bkd_tree* t, const float* Q, int64_t m, int k, int64_t* out_idx,
               float* out_dist);
+
+/* bkd_query_static -- bkd_query that performs no memory allocation.
+ * The paper has no counterpart; this entry point exists for callers that
+ * cannot call cudaMalloc / cudaFree while answering queries: a process whose
+ * device memory is owned entirely by its own pool allocator, or a
+ * latency-critical loop that cannot let cudaFree synchronise the device.
+ * It runs the same kernels as bkd_query, with its workspace in a fixed
+ * BKD_STATIC_SCRATCH_BYTES area of static device memory inside the library
+ * (held by every GPU that loads the library until the process exits).
+ *   t         handle from bkd_build; must be resident (not chunked) and of
+ *             height <= BKD_STATIC_MAX_HEIGHT.
+ *   Q         m x d float32 queries in DEVICE memory.
+ *   m         0 <= m <= BKD_STATIC_MAX_QUERIES; larger m is rejected with
+ *             BKD_EINVAL (split the call or use bkd_query).
+ *   k         1 <= k <= min(n, BKD_MAX_K).
+ *   out_idx, out_dist  m x k, DEVICE memory, same meaning as bkd_query.
+ * Results equal bkd_query's.  Host pointers are rejected (BKD_EINVAL); a
+ * chunked tree gives BKD_EUNSUPPORTED.
+ * The first call on a device looks up the scratch area's device address
+ * (cudaGetSymbolAddress, with the tree's device current); make that first
+ * call before any stream capture.  All calls on a device share the one
+ * scratch area and each call overwrites it: calls whose GPU work overlaps --
+ * from several threads, or on several streams -- race and corrupt each
+ * other's results; serialise them. */
+int bkd_query_static(bkd_tree* t, const float* Q, int64_t m, int k,
+                     int64_t* out_idx, float* out_dist);
 
 /* bkd_set_option -- sets a run-time option (enum bkd_option) on a handle.
  * Build-only keys are rejected with BKD_EINVAL. */

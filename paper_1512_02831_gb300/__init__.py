@@ -31,6 +31,8 @@ BKD_EUNSUPPORTED = -5
 BKD_MAX_DIM = 32
 BKD_MAX_K = 31
 BKD_MAX_HEIGHT = 24
+BKD_STATIC_MAX_QUERIES = 4096
+BKD_STATIC_MAX_HEIGHT = 16
 
 OPTIONS = {"stream": 1, "device_mem_cap": 2, "chunks": 3, "max_active": 4}
 STATS = {"rounds": 1, "leaf_visits": 2, "pairs": 3, "resorted": 4,
@@ -63,6 +65,7 @@ def load():
         lib.bkd_build_with.argtypes = [vp, i64, i32, i32, vp, i32,
                                        ctypes.POINTER(vp)]
         lib.bkd_query.argtypes = [vp, vp, i64, i32, vp, vp]
+        lib.bkd_query_static.argtypes = [vp, vp, i64, i32, vp, vp]
         lib.bkd_set_option.argtypes = [vp, i32, i64]
         lib.bkd_get_stat.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         lib.bkd_tree_shape.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -70,7 +73,8 @@ def load():
         lib.bkd_free.argtypes = [vp]
         lib.bkd_free.restype = None
         lib.bkd_last_error.restype = ctypes.c_char_p
-        for f in ("bkd_build", "bkd_build_with", "bkd_query", "bkd_set_option",
+        for f in ("bkd_build", "bkd_build_with", "bkd_query",
+                  "bkd_query_static", "bkd_set_option",
                   "bkd_get_stat", "bkd_tree_shape", "bkd_export_tree"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
@@ -179,6 +183,21 @@ def bkd_query(tree: Tree, Q, k: int, out_idx=None, out_dist=None):
                                   torch.cuda.current_stream(Q.device)
                                   .cuda_stream))
     _check(lib.bkd_query(tree.handle, q, m, k, oi, od))
+    return out_idx, out_dist
+
+
+def bkd_query_static(tree: Tree, Q, k: int, out_idx, out_dist):
+    """``bkd_query_static``: the allocation-free query.  Q, out_idx and
+    out_dist must be caller-allocated CUDA tensors ((m, d) float32, (m, k)
+    int64, (m, k) float32); m <= BKD_STATIC_MAX_QUERIES."""
+    lib = load()
+    q, shape = _ptr(Q, "f32")
+    oi, si = _ptr(out_idx, "i64")
+    od, sd = _ptr(out_dist, "f32")
+    m = shape[0]
+    if tuple(si) != (m, k) or tuple(sd) != (m, k):
+        raise ValueError("outputs must be (m, k)")
+    _check(lib.bkd_query_static(tree.handle, q, m, k, oi, od))
     return out_idx, out_dist
 
 

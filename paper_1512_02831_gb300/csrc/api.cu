@@ -562,6 +562,33 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
 
 }  // namespace
 
+namespace bkd {
+
+TreeView view_of(const bkd_tree* t) {
+  TreeView v;
+  v.device = t->device;
+  v.sm_count = t->sm_count;
+  v.stream = t->stream;
+  v.dev = t->dev;
+  v.n_leaves = t->n_leaves;
+  v.chunked = t->chunked;
+  v.d_pts = t->d_pts;
+  v.h_ctr = t->h_ctr;
+  return v;
+}
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+}  // namespace bkd
+
 extern "C" {
 
 int bkd_build(const float* P, int64_t n, int d, int height, bkd_tree** out) {

@@ -22,6 +22,8 @@
 #include <cstddef>
 #include <cstdint>
 
+struct bkd_tree;
+
 namespace bkd {
 
 constexpr int kTileQ = 128;       // queries per leaf work item (= CTA size)
@@ -112,6 +114,22 @@ cudaError_t launch_recheck(const DevTree& t, int64_t m, int k, int K,
 cudaError_t launch_fallback(const DevTree& t, int n_fb, const uint32_t* fb_list,
                             int k, int K, const float* qpad, const float* lst_d,
                             int64_t* out_idx, float* out_dist, cudaStream_t s);
+
+// Read-only view of a tree handle for entry points outside api.cu.
+struct TreeView {
+  int device;
+  int sm_count;
+  cudaStream_t stream;
+  DevTree dev;
+  int64_t n_leaves;
+  bool chunked;
+  const float* d_pts;        // resident leaf structure (nullptr if chunked)
+  Counters* h_ctr;           // pinned host counter block of the handle
+};
+TreeView view_of(const struct ::bkd_tree* t);
+
+// Records the calling thread's bkd_last_error() message; returns `code`.
+int set_error(int code, const char* fmt, ...);
 
 // Host tree construction (build.cpp).
 struct HostTree {
