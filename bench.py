@@ -42,7 +42,11 @@ TRAFFIC_NOTE = os.path.join(ROOT, "profiles",
                             "leaf_kernel_mixture64M_traffic.txt")
 
 WORKLOADS = {"mixture64M": workloads.MIXTURE_64M,
-             "uniform64K": workloads.UNIFORM_64K}
+             "uniform64K": workloads.UNIFORM_64K,
+             # same distribution, 1/4 of the points, 1/16 of the queries
+             # (leaf structure 0.67 GB > L2): the case ncu captures
+             "mixture16M": workloads.scaled(workloads.MIXTURE_64M, 1 << 24,
+                                            1 << 20, 14)}
 
 
 def args_():
@@ -240,7 +244,8 @@ def run_ours(a, w, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
 
     stats_keys = ("rounds", "leaf_visits", "pairs", "resorted", "fallback",
-                  "leaf_kernel_ms", "kernel_launches", "leaf_launches")
+                  "leaf_kernel_ms", "kernel_launches", "leaf_launches",
+                  "tail_queries", "tail_visits", "tail_pairs", "tail_ms")
     for _ in range(a.warmup):
         bkd.bkd_query(tree, Qd, k, out_i, out_d)
     barrier()
@@ -326,7 +331,12 @@ def run_ours(a, w, rank, world, local_rank):
         "roofline": roofline,
         "clocks": clk,
         "path": {"rounds_per_step": acc["rounds"] / a.steps,
-                 "leaf_visits_per_query": acc["leaf_visits"] / (m * a.steps),
+                 "leaf_visits_per_query": (acc["leaf_visits"]
+                                           + acc["tail_visits"])
+                 / (m * a.steps),
+                 "tail_queries_per_step": acc["tail_queries"] / a.steps,
+                 "tail_visits_per_step": acc["tail_visits"] / a.steps,
+                 "tail_ms_per_step": acc["tail_ms"] / a.steps,
                  "pairs_per_step": acc["pairs"] / a.steps,
                  "leaf_kernel_ms_per_step": acc["leaf_kernel_ms"] / a.steps,
                  "leaf_launches_per_step": acc["leaf_launches"] / a.steps,

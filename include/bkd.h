@@ -82,22 +82,31 @@ enum bkd_option {
   /* Maximum number of queries in flight in one LazySearch (the bounded query
    * memory of Sec. 3.2, "Multi-Many-Core Querying"); larger query sets are
    * processed in consecutive slices.  0 (default) = all m at once. */
-  BKD_OPT_MAX_ACTIVE = 4
+  BKD_OPT_MAX_ACTIVE = 4,
+  /* When at most this many queries remain active, they finish in one launch
+   * (one warp per query walks its remaining leaves) instead of one
+   * LazySearch round per leaf.  -1 (default) = automatic (8192); 0 = never.
+   * Results do not depend on it.  Any time. */
+  BKD_OPT_TAIL_QUERIES = 5
 };
 
 /* ------------------------------------------------------------------- stats
  * Counters of the most recent bkd_query on the handle (bkd_get_stat). */
 enum bkd_stat {
   BKD_STAT_ROUNDS = 1,         /* LazySearch iterations (Algorithm 1 loop)   */
-  BKD_STAT_LEAF_VISITS = 2,    /* (query, leaf) pairs processed              */
-  BKD_STAT_PAIRS = 3,          /* (query, reference point) distances scored  */
+  BKD_STAT_LEAF_VISITS = 2,    /* (query, leaf) pairs of the LazySearch rounds */
+  BKD_STAT_PAIRS = 3,          /* distances scored by the leaf kernel        */
   BKD_STAT_RESORTED = 4,       /* queries re-ordered by binary64 distances   */
   BKD_STAT_FALLBACK = 5,       /* queries re-searched in binary64            */
   BKD_STAT_LEAF_KERNEL_MS = 6, /* summed device time of the leaf kernel      */
   BKD_STAT_CHUNK_BYTES = 7,    /* host-to-device leaf-chunk bytes (chunked)  */
   BKD_STAT_COPY_MS = 8,        /* summed device time of the chunk copies     */
   BKD_STAT_LEAF_LAUNCHES = 9,  /* launches of the leaf kernel                */
-  BKD_STAT_KERNEL_LAUNCHES = 10 /* all kernel launches of the query          */
+  BKD_STAT_KERNEL_LAUNCHES = 10, /* all kernel launches of the query         */
+  BKD_STAT_TAIL_QUERIES = 11,  /* queries finished by the tail kernel        */
+  BKD_STAT_TAIL_VISITS = 12,   /* (query, leaf) visits of the tail kernel    */
+  BKD_STAT_TAIL_PAIRS = 13,    /* distances scored by the tail kernel        */
+  BKD_STAT_TAIL_MS = 14        /* device time of the tail kernel             */
 };
 
 typedef struct bkd_tree bkd_tree; /* opaque; owned by the library */

@@ -114,6 +114,7 @@ struct bkd_tree {
   int64_t* d_orig = nullptr;
   float* d_split = nullptr;
   int32_t* d_leaf_cnt = nullptr;
+  float* d_box = nullptr;
   // chunked storage
   bool chunked = false;
   int n_chunks = 0;
@@ -135,14 +136,16 @@ struct bkd_tree {
   Counters* h_ctr = nullptr;     // pinned
   int32_t* h_chunk_item = nullptr;
   int max_active = 0;
+  int tail_queries = -1;
   // timing
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> leaf_ev, copy_ev;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> leaf_ev, copy_ev, tail_ev;
   // stats of the last query
   double st_rounds = 0, st_visits = 0, st_pairs = 0, st_resorted = 0,
          st_fallback = 0, st_leaf_ms = 0, st_chunk_bytes = 0, st_copy_ms = 0,
-         st_leaf_launches = 0, st_launches = 0;
+         st_leaf_launches = 0, st_launches = 0, st_tail_queries = 0,
+         st_tail_visits = 0, st_tail_pairs = 0, st_tail_ms = 0;
 
   cudaEvent_t next_event() {
     if (ev_used == ev_pool.size()) {
@@ -165,6 +168,7 @@ void release(bkd_tree* t) {
   cudaFree(t->d_orig);
   cudaFree(t->d_split);
   cudaFree(t->d_leaf_cnt);
+  cudaFree(t->d_box);
   cudaFree(t->d_chunk_leaf);
   cudaFree(t->d_chunk_buf[0]);
   cudaFree(t->d_chunk_buf[1]);
@@ -250,7 +254,8 @@ int build_impl(const float* P, int64_t n, int d, int height,
       if (val < 0 || val > (1 << 20))
         return fail(BKD_EINVAL, "chunk count out of range");
       chunks = val;
-    } else if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE) {
+    } else if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE ||
+               key == BKD_OPT_TAIL_QUERIES) {
       // applied after construction below
     } else {
       return fail(BKD_EINVAL, "unknown build option %lld", (long long)key);
@@ -328,6 +333,21 @@ int build_impl(const float* P, int64_t n, int d, int height,
   if (cudaMalloc(&t->d_split, nsplit * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&t->d_leaf_cnt, L * sizeof(int32_t)) != cudaSuccess)
     return bail(fail(BKD_ENOMEM, "device allocation failed (tree)"));
+  {
+    const int64_t nodes = 2 * L - 1;
+    std::vector<float> box;
+    try {
+      box.resize((size_t)nodes * 2 * d);
+    } catch (...) {
+      return bail(fail(BKD_ENOMEM, "host allocation failed (boxes)"));
+    }
+    fill_boxes(Ph, H, box.data());
+    if (cudaMalloc(&t->d_box, box.size() * sizeof(float)) != cudaSuccess)
+      return bail(fail(BKD_ENOMEM, "device allocation failed (boxes)"));
+    if (cudaMemcpy(t->d_box, box.data(), box.size() * sizeof(float),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(fail(BKD_ECUDA, "upload of the node boxes failed"));
+  }
   if (cudaMemcpy(t->d_split, H.split, nsplit * sizeof(float),
                  cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(t->d_leaf_cnt, leaf_cnt.data(), L * sizeof(int32_t),
@@ -402,6 +422,7 @@ int build_impl(const float* P, int64_t n, int d, int height,
   D.pts = chunked ? t->h_pts : t->d_pts;
   D.orig = chunked ? t->h_orig : t->d_orig;
   D.leaf_cnt = t->d_leaf_cnt;
+  D.box = t->d_box;
   D.n = n;
   D.d = d;
   D.Dp = H.Dp;
@@ -409,7 +430,8 @@ int build_impl(const float* P, int64_t n, int d, int height,
   D.lcap = H.lcap;
   for (int i = 0; i < n_options; ++i) {
     const int64_t key = options[2 * i], val = options[2 * i + 1];
-    if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE) {
+    if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE ||
+        key == BKD_OPT_TAIL_QUERIES) {
       int rc = bkd_set_option(t, (int)key, val);
       if (rc != BKD_OK) return bail(rc);
     }
@@ -450,12 +472,33 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   CU(launch_init(t->qdev.p, m, D.d, Dp, t->qpad.p, t->lst_d.p, t->lst_i.p, K,
                  t->state.p, t->act_a.p, t->d_ctr, s));
   t->st_launches += 1;
+  // reject non-finite queries before any traversal (the tail kernel may take
+  // every query without a single round)
+  CU(cudaMemcpyAsync(t->h_ctr, t->d_ctr, sizeof(Counters),
+                     cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (t->h_ctr->err & kErrNonFinite)
+    return fail(BKD_EINVAL, "Q holds a non-finite or |x| >= 2^60 value");
   uint32_t* act = t->act_a.p;
   uint32_t* nxt = t->act_b.p;
   int n_act = (int)m;
   const int grid_max = leaf_kernel_grid(Dp, cap, D.lcap, t->sm_count);
   int round = 0;
+  const int tail = t->tail_queries >= 0 ? t->tail_queries : 8192;
   while (n_act > 0) {
+    if (n_act <= tail) {
+      // finish the remaining queries in one launch, one warp per query
+      cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
+      if (e0) cudaEventRecord(e0, s);
+      CU(launch_tail(D, t->chunked ? t->h_pts : t->d_pts, act, n_act,
+                     t->state.p, t->qpad.p, t->lst_d.p, t->lst_i.p, K,
+                     t->d_ctr, t->sm_count, s));
+      if (e1) cudaEventRecord(e1, s);
+      if (e0 && e1) t->tail_ev.push_back({e0, e1});
+      t->st_tail_queries += n_act;
+      t->st_launches += 1;
+      break;
+    }
     CU(launch_find_leaf(D, t->qpad.p, act, n_act, t->state.p, t->lst_d.p, K,
                         t->leaf_of.p, s));
     CU(launch_bucket(t->leaf_of.p, act, n_act, (int)L, t->d_leaf_cnt,
@@ -549,8 +592,13 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
                      cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   t->st_launches += 1;
+  if (t->h_ctr->err & kErrBadList)
+    return fail(BKD_ECUDA, "internal error: a finished candidate list holds "
+                           "an empty entry");
   const int n_fb = t->h_ctr->n_fallback;
   t->st_fallback += n_fb;
+  t->st_tail_visits += (double)t->h_ctr->tail_visits;
+  t->st_tail_pairs += (double)t->h_ctr->tail_pairs;
   t->st_resorted += t->h_ctr->n_resorted;
   if (n_fb > 0) {
     CU(launch_fallback(D, n_fb, t->fb_list.p, k, K, t->qpad.p, t->lst_d.p,
@@ -619,10 +667,12 @@ int bkd_query(bkd_tree* t, const float* Q, int64_t m, int k, int64_t* out_idx,
   DeviceGuard guard(t->device);
   t->st_rounds = t->st_visits = t->st_pairs = t->st_resorted =
       t->st_fallback = t->st_leaf_ms = t->st_chunk_bytes = t->st_copy_ms =
-          t->st_leaf_launches = t->st_launches = 0;
+          t->st_leaf_launches = t->st_launches = t->st_tail_queries =
+              t->st_tail_visits = t->st_tail_pairs = t->st_tail_ms = 0;
   t->ev_used = 0;
   t->leaf_ev.clear();
   t->copy_ev.clear();
+  t->tail_ev.clear();
   if (m == 0) return BKD_OK;
   const int d = t->dev.d;
   cudaStream_t s = t->stream;
@@ -663,6 +713,11 @@ int bkd_query(bkd_tree* t, const float* Q, int64_t m, int k, int64_t* out_idx,
     if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess)
       t->st_copy_ms += ms;
   }
+  for (auto& pr : t->tail_ev) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess)
+      t->st_tail_ms += ms;
+  }
   cudaGetLastError();
   return BKD_OK;
 }
@@ -678,6 +733,11 @@ int bkd_set_option(bkd_tree* t, int key, int64_t value) {
       if (value < 0 || value >= ((int64_t)1 << 31))
         return fail(BKD_EINVAL, "max active out of range");
       t->max_active = (int)value;
+      return BKD_OK;
+    case BKD_OPT_TAIL_QUERIES:
+      if (value < -1 || value >= ((int64_t)1 << 31))
+        return fail(BKD_EINVAL, "tail query count out of range");
+      t->tail_queries = (int)value;
       return BKD_OK;
     case BKD_OPT_DEVICE_MEM_CAP:
     case BKD_OPT_CHUNKS:
@@ -701,6 +761,10 @@ int bkd_get_stat(const bkd_tree* t, int key, double* value) {
     case BKD_STAT_COPY_MS: *value = t->st_copy_ms; break;
     case BKD_STAT_LEAF_LAUNCHES: *value = t->st_leaf_launches; break;
     case BKD_STAT_KERNEL_LAUNCHES: *value = t->st_launches; break;
+    case BKD_STAT_TAIL_QUERIES: *value = t->st_tail_queries; break;
+    case BKD_STAT_TAIL_VISITS: *value = t->st_tail_visits; break;
+    case BKD_STAT_TAIL_PAIRS: *value = t->st_tail_pairs; break;
+    case BKD_STAT_TAIL_MS: *value = t->st_tail_ms; break;
     default: return fail(BKD_EINVAL, "unknown stat %d", key);
   }
   return BKD_OK;

@@ -15,6 +15,8 @@
 //   queries    float qpad[m * Dp], zero-padded rows.
 //   k-best     float lst_d[m * K], uint32 lst_i[m * K] (K = k + 1 entries,
 //              ascending, lst_d[q*K + K-1] is the pruning bound); slots.
+//   boxes      float box[(2^(h+1) - 1) * 2d]: tight bounding box of the
+//              points under each heap node (min row, then max row).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -57,9 +59,12 @@ struct Counters {
   int32_t n_resorted;       // queries re-ordered by binary64 distances
   int32_t err;              // device-detected input errors (bit mask)
   int32_t pad;
+  unsigned long long tail_pairs;   // (query, point) pairs of the tail kernel
+  unsigned long long tail_visits;  // (query, leaf) visits of the tail kernel
 };
 
-constexpr int kErrNonFinite = 1;
+constexpr int kErrNonFinite = 1;   // a query holds a non-finite / huge value
+constexpr int kErrBadList = 2;     // a finished list holds an empty entry
 
 // Everything the kernels need about the tree.
 struct DevTree {
@@ -68,6 +73,7 @@ struct DevTree {
                            // chunked mode; used by the binary64 checks)
   const int64_t* orig;     // slot -> original index (device or mapped host)
   const int32_t* leaf_cnt; // points per leaf (device)
+  const float* box;        // per-node bounding boxes, 2d floats each (device)
   int64_t n;
   int d, Dp, h;
   int64_t lcap;            // slots per leaf (multiple of 4)
@@ -104,6 +110,13 @@ cudaError_t launch_leaf(int Dp, int cap, const Item* items, int item_lo,
                         uint32_t* lst_i, int K, int grid, cudaStream_t s);
 
 int leaf_kernel_grid(int Dp, int cap, int64_t lcap, int sm_count);
+
+// Runs the traversal of each of the n_act queries in `act` to its end (one
+// warp per query); `pts` is the leaf structure (device or mapped host).
+cudaError_t launch_tail(const DevTree& t, const float* pts,
+                        const uint32_t* act, int n_act, int32_t* state,
+                        const float* qpad, float* lst_d, uint32_t* lst_i,
+                        int K, Counters* ctr, int sm_count, cudaStream_t s);
 
 cudaError_t launch_recheck(const DevTree& t, int64_t m, int k, int K,
                            const float* qpad, const float* lst_d,
@@ -145,6 +158,11 @@ struct HostTree {
 // Returns 0 or an error message (static string).
 const char* build_host_tree(const float* P, int64_t n, int d, int h,
                             HostTree* out);
+
+// Bounding box of the points under every heap node (2^(h+1) - 1 nodes):
+// box[v*2d .. v*2d+d) = per-dimension minimum, box[v*2d+d .. v*2d+2d) =
+// maximum.
+void fill_boxes(const float* P, const HostTree& t, float* box);
 
 // Writes the quads and orig arrays for leaves [leaf_lo_id, leaf_hi_id)
 // into host buffers (`pts` and `orig` point at leaf leaf_lo_id's first slot).

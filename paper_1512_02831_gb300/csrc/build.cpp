@@ -175,4 +175,34 @@ void fill_quads(const float* P, const HostTree& t, int64_t leaf_a,
   });
 }
 
+void fill_boxes(const float* P, const HostTree& t, float* box) {
+  const int d = t.d;
+  const int64_t L = (int64_t)1 << t.h;
+  const int64_t first_leaf = L - 1;
+  parallel_items(L, [&](int64_t leaf) {
+    float* lo = box + (first_leaf + leaf) * 2 * d;
+    float* hi = lo + d;
+    for (int i = 0; i < d; ++i) {
+      lo[i] = INFINITY;
+      hi[i] = -INFINITY;
+    }
+    for (int64_t p = t.leaf_lo[leaf]; p < t.leaf_lo[leaf + 1]; ++p) {
+      const float* x = P + t.perm[p] * d;
+      for (int i = 0; i < d; ++i) {
+        lo[i] = std::min(lo[i], x[i]);
+        hi[i] = std::max(hi[i], x[i]);
+      }
+    }
+  });
+  for (int64_t v = first_leaf - 1; v >= 0; --v) {
+    float* b = box + v * 2 * d;
+    const float* l = box + (2 * v + 1) * 2 * d;
+    const float* r = box + (2 * v + 2) * 2 * d;
+    for (int i = 0; i < d; ++i) {
+      b[i] = std::min(l[i], r[i]);
+      b[d + i] = std::max(l[d + i], r[d + i]);
+    }
+  }
+}
+
 }  // namespace bkd

@@ -18,11 +18,13 @@
 //         order as the oracle) and sort by (D64, index).
 //   * otherwise (a near tie at the k / k+1 boundary): the query is searched
 //     again in binary64 by the fallback kernel below, a classical depth-first
-//     k-d tree search (Sec. 2.3) with the exact key, pruning far children iff
-//     plane^2 > min(current k-th D64, hi(v_{k-1})) -- hi(v_{k-1}) bounds the
-//     true k-th distance from above because k points score at most v_{k-1}.
+//     k-d tree search (Sec. 2.3) with the exact key, skipping subtrees whose
+//     binary64 bounding-box distance exceeds min(current k-th D64,
+//     hi(v_{k-1})) -- hi(v_{k-1}) bounds the true k-th distance from above
+//     because k points score at most v_{k-1}.
 #include "bkd.h"
 #include "bkd_internal.h"
+#include "traverse.cuh"
 
 namespace bkd {
 namespace {
@@ -68,6 +70,19 @@ __global__ void recheck_kernel(DevTree t, int64_t m, int k, int K,
   if (q >= m) return;
   const float* v = lst_d + q * K;
   const uint32_t* sl = lst_i + q * K;
+  // Every finished list holds k real entries (k <= n and finite inputs make
+  // every point score finitely); anything else is reported, never followed.
+  const uint64_t nslots = (uint64_t)t.lcap << t.h;
+  for (int j = 0; j < k; ++j) {
+    if ((uint64_t)sl[j] >= nslots) {
+      atomicOr(&ctr->err, kErrBadList);
+      for (int i = 0; i < k; ++i) {
+        out_idx[q * k + i] = -1;
+        out_dist[q * k + i] = __int_as_float(0x7fc00000);
+      }
+      return;
+    }
+  }
   const float vk = v[k];
   const bool member_ok =
       isinf(vk) || hi_bound(v[k - 1], gam, eta) < lo_bound(vk, gam, eta);
@@ -127,10 +142,11 @@ __global__ void __launch_bounds__(32 * kFbWarps)
     double myd = __longlong_as_double(0x7ff0000000000000ll);  // +inf
     int64_t myi = INT64_MAX;
     int cnt = 0;  // warp-uniform
-    int node = 0;
-    for (int level = 0; node < first_leaf; ++level)
-      node = 2 * node + (qp[level % t.d] < t.split[node] ? 1 : 2);
+    int node = kStart;
     for (;;) {
+      const double kd = __shfl_sync(0xffffffffu, myd, k - 1);
+      node = next_leaf<F64Bound>(t, qp, node, cnt == k ? fmin(kd, seed) : seed);
+      if (node == kDone) break;
       // ---- scan the leaf
       const int leaf = node - first_leaf;
       const int np = t.leaf_cnt[leaf];
@@ -151,9 +167,9 @@ __global__ void __launch_bounds__(32 * kFbWarps)
           mask &= mask - 1;
           const double cd = __shfl_sync(0xffffffffu, dv, src);
           const int64_t ci = __shfl_sync(0xffffffffu, iv, src);
-          const double kd = __shfl_sync(0xffffffffu, myd, k - 1);
+          const double kd2 = __shfl_sync(0xffffffffu, myd, k - 1);
           const int64_t ki = __shfl_sync(0xffffffffu, myi, k - 1);
-          if (cnt == k && !key_less(cd, ci, kd, ki)) continue;
+          if (cnt == k && !key_less(cd, ci, kd2, ki)) continue;
           const bool less = lane < cnt && key_less(myd, myi, cd, ci);
           const int pos = __popc(__ballot_sync(0xffffffffu, less));
           const double upd = __shfl_up_sync(0xffffffffu, myd, 1);
@@ -168,30 +184,6 @@ __global__ void __launch_bounds__(32 * kFbWarps)
           cnt = min(cnt + 1, k);
         }
       }
-      // ---- climb to the next far child worth visiting
-      const double kd = __shfl_sync(0xffffffffu, myd, k - 1);
-      const double bound = cnt == k ? fmin(kd, seed) : seed;
-      for (;;) {
-        if (node == 0) {
-          node = kDone;
-          break;
-        }
-        const int parent = (node - 1) >> 1;
-        const int s = (31 - __clz(parent + 1)) % t.d;
-        const float sv = t.split[parent];
-        const bool near_left = qp[s] < sv;
-        if (((node & 1) != 0) == near_left) {
-          const double tt = __dsub_rn((double)qp[s], (double)sv);
-          if (__dmul_rn(tt, tt) <= bound) {
-            node = near_left ? 2 * parent + 2 : 2 * parent + 1;
-            break;
-          }
-        }
-        node = parent;
-      }
-      if (node == kDone) break;
-      for (int level = 31 - __clz(node + 1); node < first_leaf; ++level)
-        node = 2 * node + (qp[level % t.d] < t.split[node] ? 1 : 2);
     }
     if (lane < k) {
       out_idx[q * k + lane] = myi;

@@ -65,6 +65,30 @@ __device__ __forceinline__ void list_insert(float (&Ld)[KT], uint32_t (&Li)[KT],
   }
 }
 
+// Float32 distances of one query (coordinates duplicated into packed pairs
+// qq[i] = (q_i, q_i)) to the four points of a quad b[0..D).
+template <int D>
+__device__ __forceinline__ void quad_dist(const float4* __restrict__ b,
+                                          const uint64_t (&qq)[D], float& e0,
+                                          float& e1, float& e2, float& e3) {
+  uint64_t a01, a23;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const float4 v = b[i];
+    const uint64_t d01 = sub2(qq[i], pk2(v.x, v.y));
+    const uint64_t d23 = sub2(qq[i], pk2(v.z, v.w));
+    if (i == 0) {
+      a01 = mul2(d01, d01);
+      a23 = mul2(d23, d23);
+    } else {
+      a01 = fma2(d01, d01, a01);
+      a23 = fma2(d23, d23, a23);
+    }
+  }
+  upk2(a01, e0, e1);
+  upk2(a23, e2, e3);
+}
+
 template <int D, int KT>
 __global__ void __launch_bounds__(kTileQ)
     leaf_kernel(const Item* __restrict__ items, int item_lo, int item_hi,
@@ -118,24 +142,8 @@ __global__ void __launch_bounds__(kTileQ)
         float bound = Ld[KT - 1];
 #pragma unroll 2
         for (int g = 0; g < sq; ++g) {
-          const float4* b = sm + g * D;
-          uint64_t a01, a23;
-#pragma unroll
-          for (int i = 0; i < D; ++i) {
-            const float4 v = b[i];
-            const uint64_t d01 = sub2(qq[i], pk2(v.x, v.y));
-            const uint64_t d23 = sub2(qq[i], pk2(v.z, v.w));
-            if (i == 0) {
-              a01 = mul2(d01, d01);
-              a23 = mul2(d23, d23);
-            } else {
-              a01 = fma2(d01, d01, a01);
-              a23 = fma2(d23, d23, a23);
-            }
-          }
           float e0, e1, e2, e3;
-          upk2(a01, e0, e1);
-          upk2(a23, e2, e3);
+          quad_dist<D>(sm + g * D, qq, e0, e1, e2, e3);
           if (fminf(fminf(e0, e1), fminf(e2, e3)) < bound) {
             const uint32_t id = slot0 + (uint32_t)(s0 + g) * 4u;
             if (e0 < bound) {

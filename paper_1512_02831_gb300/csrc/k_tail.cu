@@ -1,0 +1,127 @@
+// k_tail.cu -- finishing the last active queries without further rounds.
+//
+// LazySearch advances every active query by one leaf per round (Algorithm 1),
+// so the number of rounds equals the largest number of leaves any single
+// query visits, while the number of active queries -- and with it the work
+// per round -- decays.  Once few queries remain, each further round is mostly
+// fixed cost (traversal, bucketing, a launch over a few buffers of one query
+// each).  This kernel takes the remaining queries and runs each one's
+// traversal to the end: one warp per query, the same traversal step as
+// FindLeafBatch (traverse.cuh), the leaf's quads split across the lanes, and
+// the same float32 distance chain as the leaf kernel.  The candidate list is
+// spread over the warp (lane j holds entry j) and a candidate is inserted iff
+// its distance is strictly below the last entry, so the list ends with the
+// same multiset of k+1 smallest float32 distances as the round-by-round path.
+#include "bkd.h"
+#include "k_leaf.cuh"
+#include "traverse.cuh"
+
+namespace bkd {
+namespace {
+
+constexpr int kTailWarps = 4;
+
+template <int D>
+__global__ void __launch_bounds__(kTailWarps * 32)
+    tail_kernel(DevTree t, const float4* __restrict__ pts,
+                const uint32_t* __restrict__ act, int n_act,
+                int32_t* __restrict__ state, const float* __restrict__ qpad,
+                float* __restrict__ lst_d, uint32_t* __restrict__ lst_i, int K,
+                Counters* ctr) {
+  const int lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
+  const int first_leaf = (1 << t.h) - 1;
+  const int64_t qpl = t.lcap >> 2;
+  unsigned long long pairs = 0, visits = 0;
+  for (int w = blockIdx.x * kTailWarps + (threadIdx.x >> 5); w < n_act;
+       w += gridDim.x * kTailWarps) {
+    const uint32_t q = act[w];
+    const float* qp = qpad + (size_t)q * D;
+    uint64_t qq[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const float x = qp[i];
+      qq[i] = pk2(x, x);
+    }
+    float myd = __int_as_float(0x7f800000);
+    uint32_t myi = kNoSlot;
+    if (lane < K) {
+      myd = lst_d[(size_t)q * K + lane];
+      myi = lst_i[(size_t)q * K + lane];
+    }
+    float bound = __shfl_sync(full, myd, K - 1);
+    int node = state[q];
+    for (;;) {
+      node = next_leaf<F32Bound>(t, qp, node, bound);
+      if (node == kDone) break;
+      const int leaf = node - first_leaf;
+      const int np = t.leaf_cnt[leaf];
+      const int nq = (np + 3) >> 2;
+      const float4* lq = pts + (int64_t)leaf * qpl * D;
+      const uint32_t slot0 = (uint32_t)((int64_t)leaf * t.lcap);
+      ++visits;
+      pairs += (unsigned long long)np;
+      for (int g0 = 0; g0 < nq; g0 += 32) {
+        const int g = g0 + lane;
+        float e[4] = {__int_as_float(0x7f800000), __int_as_float(0x7f800000),
+                      __int_as_float(0x7f800000), __int_as_float(0x7f800000)};
+        if (g < nq) quad_dist<D>(lq + (int64_t)g * D, qq, e[0], e[1], e[2], e[3]);
+        unsigned mask = __ballot_sync(
+            full, fminf(fminf(e[0], e[1]), fminf(e[2], e[3])) < bound);
+        while (mask) {
+          const int src = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const uint32_t id = slot0 + (uint32_t)(g0 + src) * 4u;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float cd = __shfl_sync(full, e[j], src);
+            if (cd < bound) {  // warp-uniform
+              const int pos = __popc(__ballot_sync(full, lane < K && myd <= cd));
+              const float upd = __shfl_up_sync(full, myd, 1);
+              const uint32_t upi = __shfl_up_sync(full, myi, 1);
+              if (lane > pos) {
+                myd = upd;
+                myi = upi;
+              } else if (lane == pos) {
+                myd = cd;
+                myi = id + j;
+              }
+              bound = __shfl_sync(full, myd, K - 1);
+            }
+          }
+        }
+      }
+    }
+    if (lane < K) {
+      lst_d[(size_t)q * K + lane] = myd;
+      lst_i[(size_t)q * K + lane] = myi;
+    }
+    if (lane == 0) state[q] = kDone;
+  }
+  if (lane == 0 && visits) {
+    atomicAdd(&ctr->tail_pairs, pairs);
+    atomicAdd(&ctr->tail_visits, visits);
+  }
+}
+
+#define BKD_TAIL_CASE(DIM)                                                   \
+  case DIM:                                                                  \
+    tail_kernel<DIM><<<grid, kTailWarps * 32, 0, s>>>(                       \
+        t, reinterpret_cast<const float4*>(pts), act, n_act, state, qpad,    \
+        lst_d, lst_i, K, ctr);                                               \
+    return cudaGetLastError();
+
+}  // namespace
+
+cudaError_t launch_tail(const DevTree& t, const float* pts,
+                        const uint32_t* act, int n_act, int32_t* state,
+                        const float* qpad, float* lst_d, uint32_t* lst_i,
+                        int K, Counters* ctr, int sm_count, cudaStream_t s) {
+  if (n_act <= 0) return cudaSuccess;
+  const int grid = std::min((n_act + kTailWarps - 1) / kTailWarps,
+                            sm_count * 16);
+  switch (t.Dp) { BKD_LEAF_DIMS(BKD_TAIL_CASE) default: break; }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace bkd

@@ -4,29 +4,16 @@
 // to the next leaf it has to visit, or reports -1 once the traversal has
 // reached the root twice.  The traversal is the classical k-d tree search of
 // Sec. 2.3: walk down to the cell containing q; on the way back up, visit the
-// far child of a node iff the squared distance of q to that node's splitting
-// hyperplane could still beat the current candidate bound, otherwise prune.
+// far child of a node iff it could still hold a better candidate, otherwise
+// prune.
 //
-// The traversal is stackless.  A query's whole state is the heap index of the
-// leaf it visited last: in a complete binary tree the parent of v is
-// (v-1)/2, and whether v was the near child follows from q and the parent's
-// split, so climbing from the last leaf re-derives the backtracking stack.
-//
-// Pruning is exact, not heuristic.  The bound is the (k+1)-th entry of the
-// query's float32 candidate list and a candidate enters the list only if its
-// float32 distance is strictly below the bound.  The leaf kernel forms the
-// float32 distance as fl(fl(q_0-x_0)^2), then fma(fl(q_i-x_i), fl(q_i-x_i),
-// acc) for i = 1..d-1; each step is monotone in |q_i - x_i| and never drops
-// below its accumulator, so every point beyond the hyperplane scores at least
-// plane = fl(fl(q_s - split)^2).  A subtree with plane >= bound therefore
-// holds no point that could enter the list, now or later (the bound only
-// shrinks).
+// The traversal step itself (stackless, exact bounding-box pruning) is
+// next_leaf() in traverse.cuh, shared with the tail and fallback kernels.
 #include "bkd_internal.h"
+#include "traverse.cuh"
 
 namespace bkd {
 namespace {
-
-__device__ __forceinline__ int level_of(int v) { return 31 - __clz(v + 1); }
 
 __global__ void init_kernel(const float* __restrict__ Q, int64_t m, int d,
                             int Dp, float* __restrict__ qpad,
@@ -52,8 +39,7 @@ __global__ void init_kernel(const float* __restrict__ Q, int64_t m, int d,
   if (bad) atomicOr(&ctr->err, kErrNonFinite);
 }
 
-__global__ void find_leaf_kernel(const float* __restrict__ split, int h, int d,
-                                 int Dp, const float* __restrict__ qpad,
+__global__ void find_leaf_kernel(DevTree t, const float* __restrict__ qpad,
                                  const uint32_t* __restrict__ act, int n_act,
                                  int32_t* __restrict__ state,
                                  const float* __restrict__ lst_d, int K,
@@ -61,48 +47,13 @@ __global__ void find_leaf_kernel(const float* __restrict__ split, int h, int d,
   const int pos = blockIdx.x * blockDim.x + threadIdx.x;
   if (pos >= n_act) return;
   const uint32_t q = act[pos];
-  const float* qp = qpad + (size_t)q * Dp;
-  const int first_leaf = (1 << h) - 1;
-  int node = state[q];
-  if (node == kStart) {
-    node = 0;
-  } else {
-    const float bound = lst_d[(size_t)q * K + (K - 1)];
-    // climb from the last leaf; at most h steps
-    for (;;) {
-      if (node == 0) {
-        node = kDone;
-        break;
-      }
-      const int parent = (node - 1) >> 1;
-      const int s = level_of(parent) % d;
-      const float sv = __ldg(split + parent);
-      const float qs = qp[s];
-      const bool near_left = qs < sv;
-      const bool from_left = (node & 1) != 0;
-      if (from_left == near_left) {  // returning from the near child
-        const float t = __fsub_rn(qs, sv);
-        const float plane = __fmul_rn(t, t);
-        if (plane < bound) {  // far child may hold a better candidate
-          node = near_left ? 2 * parent + 2 : 2 * parent + 1;
-          break;
-        }
-      }
-      node = parent;
-    }
-  }
-  if (node == kDone) {
-    state[q] = kDone;
-    leaf_of[pos] = -1;
-    return;
-  }
-  // descend to the cell of q inside the subtree of `node`
-  for (int level = level_of(node); node < first_leaf; ++level) {
-    const int s = level % d;
-    node = 2 * node + (qp[s] < __ldg(split + node) ? 1 : 2);
-  }
-  state[q] = node;
-  leaf_of[pos] = node - first_leaf;
+  const float* qp = qpad + (size_t)q * t.Dp;
+  const int node = state[q];
+  const float bound = node == kStart ? __int_as_float(0x7f800000)
+                                     : lst_d[(size_t)q * K + (K - 1)];
+  const int next = next_leaf<F32Bound>(t, qp, node, bound);
+  state[q] = next;
+  leaf_of[pos] = next == kDone ? -1 : next - ((1 << t.h) - 1);
 }
 
 // ------------------------------------------------------------- bucketing
@@ -239,8 +190,8 @@ cudaError_t launch_find_leaf(const DevTree& t, const float* qpad,
                              const float* lst_d, int K, int32_t* leaf_of,
                              cudaStream_t s) {
   if (n_act == 0) return cudaSuccess;
-  find_leaf_kernel<<<blocks(n_act, 256), 256, 0, s>>>(
-      t.split, t.h, t.d, t.Dp, qpad, act, n_act, state, lst_d, K, leaf_of);
+  find_leaf_kernel<<<blocks(n_act, 256), 256, 0, s>>>(t, qpad, act, n_act,
+                                                      state, lst_d, K, leaf_of);
   return cudaGetLastError();
 }
 

@@ -160,6 +160,9 @@ int run_static(const TreeView& v, char* base, const float* Q, int64_t m, int k,
                        ctr, s));
   SQ_CU(cudaMemcpyAsync(h, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
   SQ_CU(cudaStreamSynchronize(s));
+  if (h->err & kErrBadList)
+    return set_error(BKD_ECUDA, "internal error: a finished candidate list "
+                                "holds an empty entry");
   if (h->n_fallback > 0)
     SQ_CU(launch_fallback(D, h->n_fallback, fb, k, K, qpad, lst_d, out_idx,
                           out_dist, s));

@@ -24,6 +24,10 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_cases.json")
 
 
 def run(P, Q, k, h, **opts):
+    """Build + query.  Unless a test says otherwise, every query goes
+    through the LazySearch rounds (tail kernel off), so the round path is what
+    the parity cases exercise; the tail kernel has tests of its own."""
+    opts.setdefault("tail_queries", 0)
     tree = bkd.bkd_build(P, h, **opts)
     try:
         idx, dist = bkd.bkd_query(tree, Q, k)
@@ -125,7 +129,7 @@ def test_uniform_65536_full_queryset():
     height 8 (256 leaves of 256 points): every query against brute force."""
     w = workloads.UNIFORM_64K
     P, Q = w.points(), w.queries()
-    idx, dist, stats = run(P, Q, w.k, w.height)
+    idx, dist, stats = run(P, Q, w.k, w.height, tail_queries=-1)
     info = check(P, Q, w.k, idx, dist, oracle.brute_knn(P, Q, w.k))
     assert stats["rounds"] >= 2 and stats["pairs"] > 0
     print("uniform 64K:", info, stats)
@@ -134,7 +138,7 @@ def test_uniform_65536_full_queryset():
 def test_mixture_scaled():
     w = workloads.scaled(workloads.MIXTURE_64M, 1 << 20, 1 << 15, 10)
     P, Q = w.points(), w.queries()
-    idx, dist, stats = run(P, Q, w.k, w.height)
+    idx, dist, stats = run(P, Q, w.k, w.height, tail_queries=-1)
     rows = np.arange(0, Q.shape[0], 4)
     ref = oracle.brute_knn(P, Q[rows], w.k)
     print("mixture 2^20:", check(P, Q, w.k, idx, dist, ref, rows), stats)
@@ -231,3 +235,35 @@ def test_empty_query_set_and_bad_k():
     with pytest.raises(bkd.BkdError):
         bkd.bkd_query(tree, np.zeros((3, 2), np.float32), 101)
     bkd.bkd_free(tree)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "mixture"])
+def test_tail_kernel_is_bit_identical(kind):
+    """Finishing the last queries in one launch (one warp per query) instead
+    of one LazySearch round per leaf changes only the schedule."""
+    if kind == "uniform":
+        P, Q = workloads.uniform(60000, 10, 1), workloads.uniform(6000, 10, 2)
+    else:
+        w = workloads.scaled(workloads.MIXTURE_64M, 1 << 17, 6000, 7)
+        P, Q = w.points(), w.queries()
+    res = {}
+    for tail in (0, 500, -1, 10 ** 6):
+        idx, dist, st = run(P, Q, 10, 7, tail_queries=tail)
+        res[tail] = (idx, dist, st)
+    base_i, base_d, base_st = res[0]
+    assert base_st["tail_queries"] == 0
+    assert res[10 ** 6][2]["tail_queries"] == Q.shape[0]
+    assert res[10 ** 6][2]["rounds"] == 0
+    for tail, (i, dd, st) in res.items():
+        assert np.array_equal(i, base_i) and np.array_equal(dd, base_d), tail
+    check(P, Q, 10, base_i, base_d, oracle.brute_knn(P, Q[:1000], 10),
+          rows=np.arange(1000))
+
+
+def test_tail_kernel_in_chunked_mode():
+    w = workloads.scaled(workloads.MIXTURE_64M, 1 << 16, 3000, 8)
+    P, Q = w.points(), w.queries()
+    i0, d0, _ = run(P, Q, 10, 8, tail_queries=0)
+    i1, d1, st = run(P, Q, 10, 8, chunks=3, tail_queries=1500)
+    assert st["tail_queries"] > 0
+    assert np.array_equal(i0, i1) and np.array_equal(d0, d1)
