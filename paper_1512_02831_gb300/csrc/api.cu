@@ -137,6 +137,7 @@ struct bkd_tree {
   int32_t* h_chunk_item = nullptr;
   int max_active = 0;
   int tail_queries = -1;
+  int leaf_variant = kLeafPipe;
   // timing
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
@@ -255,7 +256,7 @@ int build_impl(const float* P, int64_t n, int d, int height,
         return fail(BKD_EINVAL, "chunk count out of range");
       chunks = val;
     } else if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE ||
-               key == BKD_OPT_TAIL_QUERIES) {
+               key == BKD_OPT_TAIL_QUERIES || key == BKD_OPT_LEAF_VARIANT) {
       // applied after construction below
     } else {
       return fail(BKD_EINVAL, "unknown build option %lld", (long long)key);
@@ -431,7 +432,7 @@ int build_impl(const float* P, int64_t n, int d, int height,
   for (int i = 0; i < n_options; ++i) {
     const int64_t key = options[2 * i], val = options[2 * i + 1];
     if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE ||
-        key == BKD_OPT_TAIL_QUERIES) {
+        key == BKD_OPT_TAIL_QUERIES || key == BKD_OPT_LEAF_VARIANT) {
       int rc = bkd_set_option(t, (int)key, val);
       if (rc != BKD_OK) return bail(rc);
     }
@@ -452,7 +453,9 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   const int Dp = D.Dp;
   cudaStream_t s = t->stream;
   const int64_t L = t->n_leaves;
-  const int64_t max_items = m / kTileQ + L + 1;
+  const int64_t max_items = m / kPipeTile + L + 1;
+  const int variant = t->leaf_variant;
+  const int tile = leaf_tile(variant);
   CU(t->qpad.ensure(m * Dp));
   CU(t->lst_d.ensure(m * K));
   CU(t->lst_i.ensure(m * K));
@@ -462,7 +465,7 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   CU(t->leaf_of.ensure(m));
   CU(t->fb_list.ensure(m));
   CU(t->cnt.ensure(L));
-  CU(t->cursor.ensure(L));
+  CU(t->cursor.ensure(std::max<int64_t>(L, 4)));  // also holds the scan's tile sums
   CU(t->off.ensure(L + 1));
   CU(t->toff.ensure(L + 1));
   CU(t->items.ensure(max_items));
@@ -482,7 +485,8 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   uint32_t* act = t->act_a.p;
   uint32_t* nxt = t->act_b.p;
   int n_act = (int)m;
-  const int grid_max = leaf_kernel_grid(Dp, cap, D.lcap, t->sm_count);
+  const int grid_max =
+      leaf_kernel_grid(variant, Dp, cap, D.lcap, t->sm_count);
   int round = 0;
   const int tail = t->tail_queries >= 0 ? t->tail_queries : 8192;
   while (n_act > 0) {
@@ -501,7 +505,7 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
     }
     CU(launch_find_leaf(D, t->qpad.p, act, n_act, t->state.p, t->lst_d.p, K,
                         t->leaf_of.p, s));
-    CU(launch_bucket(t->leaf_of.p, act, n_act, (int)L, t->d_leaf_cnt,
+    CU(launch_bucket(t->leaf_of.p, act, n_act, (int)L, tile, t->d_leaf_cnt,
                      t->cnt.p, t->off.p, t->cursor.p, t->toff.p, t->items.p,
                      nxt, t->d_ctr, s));
     t->st_launches += 4;
@@ -518,6 +522,8 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
     CU(cudaStreamSynchronize(s));
     if (t->h_ctr->err & kErrNonFinite)
       return fail(BKD_EINVAL, "Q holds a non-finite or |x| >= 2^60 value");
+    if (t->h_ctr->err & kErrTimeout)
+      return fail(BKD_ETIMEOUT, "a leaf-segment copy did not complete");
     const int n_next = t->h_ctr->n_next;
     const int n_items = t->h_ctr->n_items;
     if (n_next == 0) break;
@@ -525,10 +531,11 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
     t->st_visits += n_next;
     t->st_pairs += (double)t->h_ctr->pairs;
     if (!t->chunked) {
-      const int grid = std::min(grid_max, n_items);
+      const int grid = std::min(grid_max, leaf_grid_units(variant, n_items));
       cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
       if (e0) cudaEventRecord(e0, s);
-      CU(launch_leaf(Dp, cap, t->items.p, 0, n_items, t->d_ctr, t->d_pts, 0,
+      CU(launch_leaf(variant, Dp, cap, t->items.p, 0, n_items, t->d_ctr,
+                     t->d_pts, 0,
                      t->d_leaf_cnt, D.lcap, nxt, t->qpad.p, t->lst_d.p,
                      t->lst_i.p, K, grid, s));
       if (e1) cudaEventRecord(e1, s);
@@ -568,10 +575,11 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
           t->st_chunk_bytes += (double)bytes;
         }
         CU(cudaStreamWaitEvent(s, t->ev_copied[b], 0));
-        const int grid = std::min(grid_max, ihi - ilo);
+        const int grid =
+            std::min(grid_max, leaf_grid_units(variant, ihi - ilo));
         cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
         if (e0) cudaEventRecord(e0, s);
-        CU(launch_leaf(Dp, cap, t->items.p, ilo, ihi, t->d_ctr,
+        CU(launch_leaf(variant, Dp, cap, t->items.p, ilo, ihi, t->d_ctr,
                        t->d_chunk_buf[b], leaf_a, t->d_leaf_cnt, D.lcap, nxt,
                        t->qpad.p, t->lst_d.p, t->lst_i.p, K, grid, s));
         if (e1) cudaEventRecord(e1, s);
@@ -592,6 +600,8 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
                      cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
   t->st_launches += 1;
+  if (t->h_ctr->err & kErrTimeout)
+    return fail(BKD_ETIMEOUT, "a leaf-segment copy did not complete");
   if (t->h_ctr->err & kErrBadList)
     return fail(BKD_ECUDA, "internal error: a finished candidate list holds "
                            "an empty entry");
@@ -733,6 +743,11 @@ int bkd_set_option(bkd_tree* t, int key, int64_t value) {
       if (value < 0 || value >= ((int64_t)1 << 31))
         return fail(BKD_EINVAL, "max active out of range");
       t->max_active = (int)value;
+      return BKD_OK;
+    case BKD_OPT_LEAF_VARIANT:
+      if (value != kLeafPipe && value != kLeafCta)
+        return fail(BKD_EINVAL, "leaf variant must be 0 or 1");
+      t->leaf_variant = (int)value;
       return BKD_OK;
     case BKD_OPT_TAIL_QUERIES:
       if (value < -1 || value >= ((int64_t)1 << 31))

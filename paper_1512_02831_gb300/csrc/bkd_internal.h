@@ -28,7 +28,18 @@ struct bkd_tree;
 
 namespace bkd {
 
-constexpr int kTileQ = 128;       // queries per leaf work item (= CTA size)
+constexpr int kTileQ = 128;       // queries per item of the CTA leaf kernel
+constexpr int kPipeTile = 64;     // queries per item of the pipelined kernel
+
+// ProcessAllBuffers variants (BKD_OPT_LEAF_VARIANT).
+constexpr int kLeafPipe = 0;      // one 64-thread CTA per item of <= 64
+                                  // queries, leaf streamed through two
+                                  // shared-memory segments by TMA bulk copies
+constexpr int kLeafCta = 1;       // one CTA per item of <= 128 queries, leaf
+                                  // staged in shared memory
+inline int leaf_tile(int variant) {
+  return variant == kLeafCta ? kTileQ : kPipeTile;
+}
 constexpr int kStart = -1;        // traversal state: root not yet entered
 constexpr int kDone = -2;         // traversal state: root reached twice
 constexpr uint32_t kNoSlot = 0xffffffffu;
@@ -40,7 +51,7 @@ constexpr int kCaps[] = {2, 4, 8, 12, 16, 32};
 int padded_dim(int d);       // smallest compiled dimension >= d (0: none)
 int list_capacity(int K);    // smallest compiled capacity >= K (0: none)
 
-// One unit of ProcessAllBuffers work: up to kTileQ buffered queries
+// One unit of ProcessAllBuffers work: up to leaf_tile() buffered queries
 // (positions [start, start+count) of the bucketed active list) against
 // every point of one leaf.
 struct Item {
@@ -65,6 +76,7 @@ struct Counters {
 
 constexpr int kErrNonFinite = 1;   // a query holds a non-finite / huge value
 constexpr int kErrBadList = 2;     // a finished list holds an empty entry
+constexpr int kErrTimeout = 4;     // a bounded device-side wait ran out
 
 // Everything the kernels need about the tree.
 struct DevTree {
@@ -89,8 +101,11 @@ cudaError_t launch_find_leaf(const DevTree& t, const float* qpad,
                              const float* lst_d, int K, int32_t* leaf_of,
                              cudaStream_t s);
 
+// cursor must hold max(n_leaves, 4) int32: between the two scan passes it
+// carries one 16-byte partial sum per 2,048 leaves.
 cudaError_t launch_bucket(const int32_t* leaf_of, const uint32_t* act,
-                          int n_act, int n_leaves, const int32_t* leaf_cnt,
+                          int n_act, int n_leaves, int tile,
+                          const int32_t* leaf_cnt,
                           int32_t* cnt, int32_t* off, int32_t* cursor,
                           int32_t* toff, Item* items, uint32_t* next,
                           Counters* ctr, cudaStream_t s);
@@ -103,13 +118,18 @@ cudaError_t launch_chunk_items(const int32_t* toff, const int32_t* chunk_leaf,
 
 // ProcessAllBuffers over items [item_lo, item_hi) (item_hi < 0: read the
 // count from ctr).  pts/leaf0: the quads of leaf `leaf0` start at pts.
-cudaError_t launch_leaf(int Dp, int cap, const Item* items, int item_lo,
-                        int item_hi, const Counters* ctr, const float* pts,
+cudaError_t launch_leaf(int variant, int Dp, int cap, const Item* items,
+                        int item_lo,
+                        int item_hi, Counters* ctr, const float* pts,
                         int64_t leaf0, const int32_t* leaf_cnt, int64_t lcap,
                         const uint32_t* act, const float* qpad, float* lst_d,
                         uint32_t* lst_i, int K, int grid, cudaStream_t s);
 
-int leaf_kernel_grid(int Dp, int cap, int64_t lcap, int sm_count);
+int leaf_kernel_grid(int variant, int Dp, int cap, int64_t lcap,
+                     int sm_count);
+
+// Items of a launch over `n_items` that one grid slot (CTA or warp) takes.
+int leaf_grid_units(int variant, int n_items);
 
 // Runs the traversal of each of the n_act queries in `act` to its end (one
 // warp per query); `pts` is the leaf structure (device or mapped host).

@@ -58,7 +58,7 @@ __global__ void find_leaf_kernel(DevTree t, const float* __restrict__ qpad,
 
 // ------------------------------------------------------------- bucketing
 // Buffer insertion of Algorithm 1 as a counting sort by leaf id: histogram,
-// exclusive scan (also of per-leaf work items of kTileQ queries), scatter.
+// exclusive scan (also of per-leaf work items of `tile` queries), scatter.
 // The order of queries inside a leaf's buffer is irrelevant to the results.
 
 __global__ void hist_kernel(const int32_t* __restrict__ leaf_of, int n,
@@ -69,30 +69,108 @@ __global__ void hist_kernel(const int32_t* __restrict__ leaf_of, int n,
   if (l >= 0) atomicAdd(cnt + l, 1);
 }
 
-constexpr int kScanThreads = 1024;
+// Two-pass scan over the leaves, 2,048 leaves (8 per thread) per block:
+// scan_parts_kernel sums each tile, scan_write_kernel adds the sums of the
+// tiles before it and writes the offsets, the work items and the totals.
+constexpr int kScanBlock = 256;
+constexpr int kScanPer = 8;
+constexpr int kScanTile = kScanBlock * kScanPer;
 
-// One block: exclusive scans of cnt (-> off) and of ceil(cnt / kTileQ)
-// (-> toff), the item list, and the round totals.
-__global__ void __launch_bounds__(kScanThreads)
-    scan_kernel(const int32_t* __restrict__ cnt, int L,
-                const int32_t* __restrict__ leaf_cnt,
-                int32_t* __restrict__ off, int32_t* __restrict__ toff,
-                Item* __restrict__ items, Counters* ctr) {
-  __shared__ int32_t s_q[kScanThreads / 32], s_t[kScanThreads / 32];
-  __shared__ unsigned long long s_p[kScanThreads / 32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int per = (L + kScanThreads - 1) / kScanThreads;
-  const int lo = min(L, tid * per), hi = min(L, lo + per);
-  int32_t sq = 0, st = 0;
-  unsigned long long sp = 0;
+struct ScanPart {
+  int32_t q, t;                // queries and work items of the tile
+  unsigned long long p;        // (query, point) pairs of the tile
+};
+
+__device__ __forceinline__ void tile_sums(const int32_t* __restrict__ cnt,
+                                          int L, int tile,
+                                          const int32_t* __restrict__ leaf_cnt,
+                                          int lo, int32_t& q, int32_t& t,
+                                          unsigned long long& p) {
+  q = 0;
+  t = 0;
+  p = 0;
+  const int hi = min(L, lo + kScanPer);
   for (int l = lo; l < hi; ++l) {
     const int c = cnt[l];
-    sq += c;
-    st += (c + kTileQ - 1) / kTileQ;
-    sp += (unsigned long long)c * (unsigned long long)leaf_cnt[l];
+    q += c;
+    t += (c + tile - 1) / tile;
+    p += (unsigned long long)c * (unsigned long long)leaf_cnt[l];
   }
-  // inclusive warp scans
-  int32_t iq = sq, it = st;
+}
+
+__global__ void __launch_bounds__(kScanBlock)
+    scan_parts_kernel(const int32_t* __restrict__ cnt, int L, int tile,
+                      const int32_t* __restrict__ leaf_cnt,
+                      ScanPart* __restrict__ parts) {
+  __shared__ int32_t sq[kScanBlock / 32], st[kScanBlock / 32];
+  __shared__ unsigned long long sp[kScanBlock / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t q, t;
+  unsigned long long p;
+  tile_sums(cnt, L, tile, leaf_cnt,
+            blockIdx.x * kScanTile + threadIdx.x * kScanPer, q, t, p);
+  for (int o = 16; o > 0; o >>= 1) {
+    q += __shfl_down_sync(0xffffffffu, q, o);
+    t += __shfl_down_sync(0xffffffffu, t, o);
+    p += __shfl_down_sync(0xffffffffu, p, o);
+  }
+  if (lane == 0) {
+    sq[warp] = q;
+    st[warp] = t;
+    sp[warp] = p;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ScanPart r{0, 0, 0};
+    for (int w = 0; w < kScanBlock / 32; ++w) {
+      r.q += sq[w];
+      r.t += st[w];
+      r.p += sp[w];
+    }
+    parts[blockIdx.x] = r;
+  }
+}
+
+__global__ void __launch_bounds__(kScanBlock)
+    scan_write_kernel(const int32_t* __restrict__ cnt, int L, int tile,
+                      const int32_t* __restrict__ leaf_cnt,
+                      const ScanPart* __restrict__ parts,
+                      int32_t* __restrict__ off, int32_t* __restrict__ toff,
+                      Item* __restrict__ items, Counters* ctr) {
+  __shared__ int32_t wq[kScanBlock / 32], wt[kScanBlock / 32];
+  __shared__ int32_t bq0, bt0;
+  __shared__ unsigned long long ptot;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool last = blockIdx.x == gridDim.x - 1;
+  // prefix of the tiles before this one (and, in the last block, the pairs
+  // of all tiles)
+  if (warp == 0) {
+    int32_t q = 0, t = 0;
+    unsigned long long p = 0;
+    const int np = last ? gridDim.x : blockIdx.x;
+    for (int j = lane; j < np; j += 32) {
+      if (j < (int)blockIdx.x) {
+        q += parts[j].q;
+        t += parts[j].t;
+      }
+      p += parts[j].p;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      q += __shfl_down_sync(0xffffffffu, q, o);
+      t += __shfl_down_sync(0xffffffffu, t, o);
+      p += __shfl_down_sync(0xffffffffu, p, o);
+    }
+    if (lane == 0) {
+      bq0 = q;
+      bt0 = t;
+      ptot = p;
+    }
+  }
+  const int lo = blockIdx.x * kScanTile + threadIdx.x * kScanPer;
+  int32_t q, t;
+  unsigned long long p;
+  tile_sums(cnt, L, tile, leaf_cnt, lo, q, t, p);
+  int32_t iq = q, it = t;  // inclusive warp scans
   for (int o = 1; o < 32; o <<= 1) {
     const int32_t a = __shfl_up_sync(0xffffffffu, iq, o);
     const int32_t b = __shfl_up_sync(0xffffffffu, it, o);
@@ -101,55 +179,41 @@ __global__ void __launch_bounds__(kScanThreads)
       it += b;
     }
   }
-  unsigned long long wp = sp;
-  for (int o = 16; o > 0; o >>= 1) wp += __shfl_down_sync(0xffffffffu, wp, o);
   if (lane == 31) {
-    s_q[warp] = iq;
-    s_t[warp] = it;
-  }
-  if (lane == 0) s_p[warp] = wp;
-  __syncthreads();
-  if (warp == 0) {
-    int32_t a = s_q[lane], b = s_t[lane];
-    unsigned long long p = s_p[lane];
-    for (int o = 1; o < 32; o <<= 1) {
-      const int32_t x = __shfl_up_sync(0xffffffffu, a, o);
-      const int32_t y = __shfl_up_sync(0xffffffffu, b, o);
-      if (lane >= o) {
-        a += x;
-        b += y;
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) p += __shfl_down_sync(0xffffffffu, p, o);
-    s_q[lane] = a;
-    s_t[lane] = b;
-    if (lane == 0) s_p[0] = p;
+    wq[warp] = iq;
+    wt[warp] = it;
   }
   __syncthreads();
-  int32_t bq = (warp > 0 ? s_q[warp - 1] : 0) + iq - sq;
-  int32_t bt = (warp > 0 ? s_t[warp - 1] : 0) + it - st;
+  int32_t xq = bq0, xt = bt0;  // exclusive prefix of this thread
+  for (int w = 0; w < warp; ++w) {
+    xq += wq[w];
+    xt += wt[w];
+  }
+  xq += iq - q;
+  xt += it - t;
+  const int hi = min(L, lo + kScanPer);
   for (int l = lo; l < hi; ++l) {
     const int c = cnt[l];
-    const int nt = (c + kTileQ - 1) / kTileQ;
-    off[l] = bq;
-    toff[l] = bt;
+    const int nt = (c + tile - 1) / tile;
+    off[l] = xq;
+    toff[l] = xt;
     for (int j = 0; j < nt; ++j) {
       Item w;
       w.leaf = l;
-      w.start = bq + j * kTileQ;
-      w.count = min(kTileQ, c - j * kTileQ);
+      w.start = xq + j * tile;
+      w.count = min(tile, c - j * tile);
       w.pad = 0;
-      items[bt + j] = w;
+      items[xt + j] = w;
     }
-    bq += c;
-    bt += nt;
+    xq += c;
+    xt += nt;
   }
-  if (tid == kScanThreads - 1) {
-    off[L] = s_q[31];
-    toff[L] = s_t[31];
-    ctr->n_next = s_q[31];
-    ctr->n_items = s_t[31];
-    ctr->pairs = s_p[0];
+  if (last && threadIdx.x == kScanBlock - 1) {
+    off[L] = xq;
+    toff[L] = xt;
+    ctr->n_next = xq;
+    ctr->n_items = xt;
+    ctr->pairs = ptot;
   }
 }
 
@@ -196,17 +260,25 @@ cudaError_t launch_find_leaf(const DevTree& t, const float* qpad,
 }
 
 cudaError_t launch_bucket(const int32_t* leaf_of, const uint32_t* act,
-                          int n_act, int n_leaves, const int32_t* leaf_cnt,
+                          int n_act, int n_leaves, int tile,
+                          const int32_t* leaf_cnt,
                           int32_t* cnt, int32_t* off, int32_t* cursor,
                           int32_t* toff, Item* items, uint32_t* next,
                           Counters* ctr, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * n_leaves, s);
   if (e != cudaSuccess) return e;
+  if (n_act > 0) hist_kernel<<<blocks(n_act, 256), 256, 0, s>>>(leaf_of, n_act, cnt);
+  // the cursor array (4 bytes per leaf) holds the 16-byte tile sums (one per
+  // 2,048 leaves) until the scan is done, then is cleared for the scatter
+  ScanPart* parts = reinterpret_cast<ScanPart*>(cursor);
+  const int nparts = blocks(n_leaves, kScanTile);
+  scan_parts_kernel<<<nparts, kScanBlock, 0, s>>>(cnt, n_leaves, tile,
+                                                  leaf_cnt, parts);
+  scan_write_kernel<<<nparts, kScanBlock, 0, s>>>(cnt, n_leaves, tile,
+                                                  leaf_cnt, parts, off, toff,
+                                                  items, ctr);
   e = cudaMemsetAsync(cursor, 0, sizeof(int32_t) * n_leaves, s);
   if (e != cudaSuccess) return e;
-  if (n_act > 0) hist_kernel<<<blocks(n_act, 256), 256, 0, s>>>(leaf_of, n_act, cnt);
-  scan_kernel<<<1, kScanThreads, 0, s>>>(cnt, n_leaves, leaf_cnt, off, toff,
-                                         items, ctr);
   if (n_act > 0)
     scatter_kernel<<<blocks(n_act, 256), 256, 0, s>>>(leaf_of, act, n_act, off,
                                                       cursor, next);

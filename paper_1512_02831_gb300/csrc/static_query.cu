@@ -50,7 +50,7 @@ constexpr int64_t kOffOff = kOffCursor + align_up(kL * 4);
 constexpr int64_t kOffToff = kOffOff + align_up((kL + 1) * 4);
 constexpr int64_t kOffItems = kOffToff + align_up((kL + 1) * 4);
 constexpr int64_t kOffCtr =
-    kOffItems + align_up((kQ / kTileQ + kL + 1) * (int64_t)sizeof(Item));
+    kOffItems + align_up((kQ / kPipeTile + kL + 1) * (int64_t)sizeof(Item));
 constexpr int64_t kScratchBytes = kOffCtr + align_up(sizeof(Counters));
 static_assert(kScratchBytes <= BKD_STATIC_SCRATCH_BYTES,
               "BKD_STATIC_SCRATCH_BYTES too small for the static layout");
@@ -136,11 +136,13 @@ int run_static(const TreeView& v, char* base, const float* Q, int64_t m, int k,
   SQ_CU(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
   SQ_CU(launch_init(Q, m, D.d, D.Dp, qpad, lst_d, lst_i, K, state, act, ctr,
                     s));
-  const int grid_max = leaf_kernel_grid(D.Dp, cap, D.lcap, v.sm_count);
+  const int grid_max =
+      leaf_kernel_grid(kLeafPipe, D.Dp, cap, D.lcap, v.sm_count);
   int n_act = (int)m;
   while (n_act > 0) {
     SQ_CU(launch_find_leaf(D, qpad, act, n_act, state, lst_d, K, leaf_of, s));
-    SQ_CU(launch_bucket(leaf_of, act, n_act, (int)v.n_leaves, D.leaf_cnt, cnt,
+    SQ_CU(launch_bucket(leaf_of, act, n_act, (int)v.n_leaves, kPipeTile,
+                        D.leaf_cnt, cnt,
                         off, cursor, toff, items, nxt, ctr, s));
     SQ_CU(cudaMemcpyAsync(h, ctr, sizeof(Counters), cudaMemcpyDeviceToHost,
                           s));
@@ -148,11 +150,14 @@ int run_static(const TreeView& v, char* base, const float* Q, int64_t m, int k,
     if (h->err & kErrNonFinite)
       return set_error(BKD_EINVAL,
                        "Q holds a non-finite or |x| >= 2^60 value");
+    if (h->err & kErrTimeout)
+      return set_error(BKD_ETIMEOUT, "a leaf-segment copy did not complete");
     const int n_next = h->n_next, n_items = h->n_items;
     if (n_next == 0) break;
-    SQ_CU(launch_leaf(D.Dp, cap, items, 0, n_items, ctr, v.d_pts, 0,
-                      D.leaf_cnt, D.lcap, nxt, qpad, lst_d, lst_i, K,
-                      std::min(grid_max, n_items), s));
+    SQ_CU(launch_leaf(kLeafPipe, D.Dp, cap, items, 0, n_items, ctr, v.d_pts,
+                      0, D.leaf_cnt, D.lcap, nxt, qpad, lst_d, lst_i, K,
+                      std::min(grid_max, leaf_grid_units(kLeafPipe, n_items)),
+                      s));
     std::swap(act, nxt);
     n_act = n_next;
   }
@@ -160,6 +165,8 @@ int run_static(const TreeView& v, char* base, const float* Q, int64_t m, int k,
                        ctr, s));
   SQ_CU(cudaMemcpyAsync(h, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
   SQ_CU(cudaStreamSynchronize(s));
+  if (h->err & kErrTimeout)
+    return set_error(BKD_ETIMEOUT, "a leaf-segment copy did not complete");
   if (h->err & kErrBadList)
     return set_error(BKD_ECUDA, "internal error: a finished candidate list "
                                 "holds an empty entry");
