@@ -61,9 +61,6 @@ def args_():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--leaf-variant", type=int, default=0, choices=[0, 1],
-                    help="ProcessAllBuffers kernel: 0 pipelined 64-query "
-                         "items, 1 staged 128-query items")
     return ap.parse_args()
 
 
@@ -241,7 +238,6 @@ def run_ours(a, w, rank, world, local_rank):
     t0 = time.perf_counter()
     tree = bkd.bkd_build(P, w.height)
     build_s = time.perf_counter() - t0
-    bkd.bkd_set_option(tree, "leaf_variant", a.leaf_variant)
     Qd = torch.from_numpy(Q).to(dev)
     out_i = torch.empty((m, k), dtype=torch.int64, device=dev)
     out_d = torch.empty((m, k), dtype=torch.float32, device=dev)
@@ -326,9 +322,6 @@ def run_ours(a, w, rank, world, local_rank):
                  "components, centres U[0,1]^10, sigma logU[0.02,0.2], "
                  "Dirichlet(1) weights); per-rank query sets"),
         "config": dict(w.describe(), precision="fp32 exact path",
-                       leaf_variant=("TMA-pipelined items of <= 64 queries"
-                                     if a.leaf_variant == 0 else
-                                     "staged items of <= 128 queries"),
                        parallelism=f"replicas x{world}, queries sharded",
                        l2=("inputs larger than L2 (leaf structure 2.7 GB, "
                            "queries 0.67 GB) - no flush needed"),

@@ -87,13 +87,7 @@ enum bkd_option {
    * (one warp per query walks its remaining leaves) instead of one
    * LazySearch round per leaf.  -1 (default) = automatic (8192); 0 = never.
    * Results do not depend on it.  Any time. */
-  BKD_OPT_TAIL_QUERIES = 5,
-  /* ProcessAllBuffers kernel: 0 (default) = one 64-thread CTA per buffer
-   * slice of <= 64 queries, the leaf streamed through shared memory by TMA
-   * bulk copies; 1 = one 128-thread CTA per slice of <= 128 queries, the
-   * whole leaf staged in shared memory by the threads.  Results do not depend
-   * on it.  Any time. */
-  BKD_OPT_LEAF_VARIANT = 6
+  BKD_OPT_TAIL_QUERIES = 5
 };
 
 /* ------------------------------------------------------------------- stats

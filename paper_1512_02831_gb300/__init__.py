@@ -35,7 +35,7 @@ BKD_STATIC_MAX_QUERIES = 4096
 BKD_STATIC_MAX_HEIGHT = 16
 
 OPTIONS = {"stream": 1, "device_mem_cap": 2, "chunks": 3, "max_active": 4,
-           "tail_queries": 5, "leaf_variant": 6}
+           "tail_queries": 5}
 STATS = {"rounds": 1, "leaf_visits": 2, "pairs": 3, "resorted": 4,
          "fallback": 5, "leaf_kernel_ms": 6, "chunk_bytes": 7, "copy_ms": 8,
          "leaf_launches": 9, "kernel_launches": 10, "tail_queries": 11,

@@ -137,7 +137,6 @@ struct bkd_tree {
   int32_t* h_chunk_item = nullptr;
   int max_active = 0;
   int tail_queries = -1;
-  int leaf_variant = kLeafPipe;
   // timing
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
@@ -256,7 +255,7 @@ int build_impl(const float* P, int64_t n, int d, int height,
         return fail(BKD_EINVAL, "chunk count out of range");
       chunks = val;
     } else if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE ||
-               key == BKD_OPT_TAIL_QUERIES || key == BKD_OPT_LEAF_VARIANT) {
+               key == BKD_OPT_TAIL_QUERIES) {
       // applied after construction below
     } else {
       return fail(BKD_EINVAL, "unknown build option %lld", (long long)key);
@@ -432,7 +431,7 @@ int build_impl(const float* P, int64_t n, int d, int height,
   for (int i = 0; i < n_options; ++i) {
     const int64_t key = options[2 * i], val = options[2 * i + 1];
     if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE ||
-        key == BKD_OPT_TAIL_QUERIES || key == BKD_OPT_LEAF_VARIANT) {
+        key == BKD_OPT_TAIL_QUERIES) {
       int rc = bkd_set_option(t, (int)key, val);
       if (rc != BKD_OK) return bail(rc);
     }
@@ -454,8 +453,6 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   cudaStream_t s = t->stream;
   const int64_t L = t->n_leaves;
   const int64_t max_items = m / kPipeTile + L + 1;
-  const int variant = t->leaf_variant;
-  const int tile = leaf_tile(variant);
   CU(t->qpad.ensure(m * Dp));
   CU(t->lst_d.ensure(m * K));
   CU(t->lst_i.ensure(m * K));
@@ -485,30 +482,20 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   uint32_t* act = t->act_a.p;
   uint32_t* nxt = t->act_b.p;
   int n_act = (int)m;
-  const int grid_max =
-      leaf_kernel_grid(variant, Dp, cap, D.lcap, t->sm_count);
-  int round = 0;
+  const int grid_max = leaf_kernel_grid(Dp, cap, t->sm_count);
   const int tail = t->tail_queries >= 0 ? t->tail_queries : 8192;
-  while (n_act > 0) {
-    if (n_act <= tail) {
-      // finish the remaining queries in one launch, one warp per query
-      cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
-      if (e0) cudaEventRecord(e0, s);
-      CU(launch_tail(D, t->chunked ? t->h_pts : t->d_pts, act, n_act,
-                     t->state.p, t->qpad.p, t->lst_d.p, t->lst_i.p, K,
-                     t->d_ctr, t->sm_count, s));
-      if (e1) cudaEventRecord(e1, s);
-      if (e0 && e1) t->tail_ev.push_back({e0, e1});
-      t->st_tail_queries += n_act;
-      t->st_launches += 1;
-      break;
-    }
+  // A round: FindLeafBatch over the active queries (it also counts every
+  // query into its next leaf), bucketing by leaf, ProcessAllBuffers.
+  int round = 0;
+  for (;;) {
+    CU(cudaMemsetAsync(t->cnt.p, 0, sizeof(int32_t) * L, s));
     CU(launch_find_leaf(D, t->qpad.p, act, n_act, t->state.p, t->lst_d.p, K,
-                        t->leaf_of.p, s));
-    CU(launch_bucket(t->leaf_of.p, act, n_act, (int)L, tile, t->d_leaf_cnt,
-                     t->cnt.p, t->off.p, t->cursor.p, t->toff.p, t->items.p,
-                     nxt, t->d_ctr, s));
-    t->st_launches += 4;
+                        t->leaf_of.p, t->cnt.p, s));
+    t->st_launches += 1;
+    CU(launch_bucket(t->leaf_of.p, act, n_act, (int)L, kPipeTile,
+                     t->d_leaf_cnt, t->cnt.p, t->off.p, t->cursor.p,
+                     t->toff.p, t->items.p, nxt, t->d_ctr, s));
+    t->st_launches += 3;
     if (t->chunked) {
       CU(launch_chunk_items(t->toff.p, t->d_chunk_leaf, t->n_chunks,
                             t->chunk_item.p, s));
@@ -520,24 +507,34 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
     CU(cudaMemcpyAsync(t->h_ctr, t->d_ctr, sizeof(Counters),
                        cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    if (t->h_ctr->err & kErrNonFinite)
-      return fail(BKD_EINVAL, "Q holds a non-finite or |x| >= 2^60 value");
     if (t->h_ctr->err & kErrTimeout)
       return fail(BKD_ETIMEOUT, "a leaf-segment copy did not complete");
     const int n_next = t->h_ctr->n_next;
     const int n_items = t->h_ctr->n_items;
     if (n_next == 0) break;
+    if (n_next <= tail) {
+      // finish the remaining queries in one launch, one warp per query,
+      // starting from each one's pending leaf
+      cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
+      if (e0) cudaEventRecord(e0, s);
+      CU(launch_tail(D, t->chunked ? t->h_pts : t->d_pts, nxt, n_next,
+                     t->state.p, t->qpad.p, t->lst_d.p, t->lst_i.p, K,
+                     t->d_ctr, t->sm_count, s));
+      if (e1) cudaEventRecord(e1, s);
+      if (e0 && e1) t->tail_ev.push_back({e0, e1});
+      t->st_tail_queries += n_next;
+      t->st_launches += 1;
+      break;
+    }
     t->st_rounds += 1;
     t->st_visits += n_next;
     t->st_pairs += (double)t->h_ctr->pairs;
     if (!t->chunked) {
-      const int grid = std::min(grid_max, leaf_grid_units(variant, n_items));
+      const int grid = std::min(grid_max, n_items);
       cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
       if (e0) cudaEventRecord(e0, s);
-      CU(launch_leaf(variant, Dp, cap, t->items.p, 0, n_items, t->d_ctr,
-                     t->d_pts, 0,
-                     t->d_leaf_cnt, D.lcap, nxt, t->qpad.p, t->lst_d.p,
-                     t->lst_i.p, K, grid, s));
+      CU(launch_leaf(D, cap, t->items.p, 0, n_items, t->d_ctr, t->d_pts, 0,
+                     nxt, t->qpad.p, t->lst_d.p, t->lst_i.p, K, grid, s));
       if (e1) cudaEventRecord(e1, s);
       if (e0 && e1) t->leaf_ev.push_back({e0, e1});
       t->st_leaf_launches += 1;
@@ -575,13 +572,12 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
           t->st_chunk_bytes += (double)bytes;
         }
         CU(cudaStreamWaitEvent(s, t->ev_copied[b], 0));
-        const int grid =
-            std::min(grid_max, leaf_grid_units(variant, ihi - ilo));
+        const int grid = std::min(grid_max, ihi - ilo);
         cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
         if (e0) cudaEventRecord(e0, s);
-        CU(launch_leaf(variant, Dp, cap, t->items.p, ilo, ihi, t->d_ctr,
-                       t->d_chunk_buf[b], leaf_a, t->d_leaf_cnt, D.lcap, nxt,
-                       t->qpad.p, t->lst_d.p, t->lst_i.p, K, grid, s));
+        CU(launch_leaf(D, cap, t->items.p, ilo, ihi, t->d_ctr,
+                       t->d_chunk_buf[b], leaf_a, nxt, t->qpad.p, t->lst_d.p,
+                       t->lst_i.p, K, grid, s));
         if (e1) cudaEventRecord(e1, s);
         if (e0 && e1) t->leaf_ev.push_back({e0, e1});
         CU(cudaEventRecord(t->ev_free[b], s));
@@ -743,11 +739,6 @@ int bkd_set_option(bkd_tree* t, int key, int64_t value) {
       if (value < 0 || value >= ((int64_t)1 << 31))
         return fail(BKD_EINVAL, "max active out of range");
       t->max_active = (int)value;
-      return BKD_OK;
-    case BKD_OPT_LEAF_VARIANT:
-      if (value != kLeafPipe && value != kLeafCta)
-        return fail(BKD_EINVAL, "leaf variant must be 0 or 1");
-      t->leaf_variant = (int)value;
       return BKD_OK;
     case BKD_OPT_TAIL_QUERIES:
       if (value < -1 || value >= ((int64_t)1 << 31))

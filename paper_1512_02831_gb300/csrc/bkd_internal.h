@@ -28,18 +28,7 @@ struct bkd_tree;
 
 namespace bkd {
 
-constexpr int kTileQ = 128;       // queries per item of the CTA leaf kernel
-constexpr int kPipeTile = 64;     // queries per item of the pipelined kernel
-
-// ProcessAllBuffers variants (BKD_OPT_LEAF_VARIANT).
-constexpr int kLeafPipe = 0;      // one 64-thread CTA per item of <= 64
-                                  // queries, leaf streamed through two
-                                  // shared-memory segments by TMA bulk copies
-constexpr int kLeafCta = 1;       // one CTA per item of <= 128 queries, leaf
-                                  // staged in shared memory
-inline int leaf_tile(int variant) {
-  return variant == kLeafCta ? kTileQ : kPipeTile;
-}
+constexpr int kPipeTile = 64;     // queries per ProcessAllBuffers work item
 constexpr int kStart = -1;        // traversal state: root not yet entered
 constexpr int kDone = -2;         // traversal state: root reached twice
 constexpr uint32_t kNoSlot = 0xffffffffu;
@@ -51,7 +40,7 @@ constexpr int kCaps[] = {2, 4, 8, 12, 16, 32};
 int padded_dim(int d);       // smallest compiled dimension >= d (0: none)
 int list_capacity(int K);    // smallest compiled capacity >= K (0: none)
 
-// One unit of ProcessAllBuffers work: up to leaf_tile() buffered queries
+// One unit of ProcessAllBuffers work: up to kPipeTile buffered queries
 // (positions [start, start+count) of the bucketed active list) against
 // every point of one leaf.
 struct Item {
@@ -96,19 +85,25 @@ cudaError_t launch_init(const float* Q, int64_t m, int d, int Dp, float* qpad,
                         float* lst_d, uint32_t* lst_i, int K, int32_t* state,
                         uint32_t* act, Counters* ctr, cudaStream_t s);
 
+// FindLeafBatch from the traversal states in `state` (kStart for the first
+// round): next leaf per position of `act` in leaf_of (-1: done), the new
+// pending leaf in state, and +1 in cnt[leaf] for every query that goes on.
 cudaError_t launch_find_leaf(const DevTree& t, const float* qpad,
                              const uint32_t* act, int n_act, int32_t* state,
                              const float* lst_d, int K, int32_t* leaf_of,
-                             cudaStream_t s);
+                             int32_t* cnt, cudaStream_t s);
 
-// cursor must hold max(n_leaves, 4) int32: between the two scan passes it
-// carries one 16-byte partial sum per 2,048 leaves.
+// Buffer insertion from per-leaf counts `cnt` (filled by FindLeafBatch):
+// offsets, work items of `tile` queries, round totals, and the active list
+// bucketed by leaf into `next`.  cursor must hold max(n_leaves, 4) int32:
+// between the two scan passes it carries one 16-byte partial sum per 2,048
+// leaves.
 cudaError_t launch_bucket(const int32_t* leaf_of, const uint32_t* act,
                           int n_act, int n_leaves, int tile,
-                          const int32_t* leaf_cnt,
-                          int32_t* cnt, int32_t* off, int32_t* cursor,
-                          int32_t* toff, Item* items, uint32_t* next,
-                          Counters* ctr, cudaStream_t s);
+                          const int32_t* leaf_cnt, const int32_t* cnt,
+                          int32_t* off, int32_t* cursor, int32_t* toff,
+                          Item* items, uint32_t* next, Counters* ctr,
+                          cudaStream_t s);
 
 // chunk_item[c] = first item of chunk c (leaves [chunk_leaf[c],
 // chunk_leaf[c+1])), for c = 0..n_chunks.
@@ -117,22 +112,18 @@ cudaError_t launch_chunk_items(const int32_t* toff, const int32_t* chunk_leaf,
                                cudaStream_t s);
 
 // ProcessAllBuffers over items [item_lo, item_hi) (item_hi < 0: read the
-// count from ctr).  pts/leaf0: the quads of leaf `leaf0` start at pts.
-cudaError_t launch_leaf(int variant, int Dp, int cap, const Item* items,
-                        int item_lo,
-                        int item_hi, Counters* ctr, const float* pts,
-                        int64_t leaf0, const int32_t* leaf_cnt, int64_t lcap,
-                        const uint32_t* act, const float* qpad, float* lst_d,
-                        uint32_t* lst_i, int K, int grid, cudaStream_t s);
+// count from ctr).  pts / leaf0: the quads of leaf `leaf0` start at pts.
+cudaError_t launch_leaf(const DevTree& t, int cap, const Item* items,
+                        int item_lo, int item_hi, Counters* ctr,
+                        const float* pts, int64_t leaf0, const uint32_t* act,
+                        const float* qpad, float* lst_d, uint32_t* lst_i,
+                        int K, int grid, cudaStream_t s);
 
-int leaf_kernel_grid(int variant, int Dp, int cap, int64_t lcap,
-                     int sm_count);
-
-// Items of a launch over `n_items` that one grid slot (CTA or warp) takes.
-int leaf_grid_units(int variant, int n_items);
+int leaf_kernel_grid(int Dp, int cap, int sm_count);
 
 // Runs the traversal of each of the n_act queries in `act` to its end (one
-// warp per query); `pts` is the leaf structure (device or mapped host).
+// warp per query); state[q] is the query's pending (not yet scanned) leaf.
+// `pts` is the leaf structure (device or mapped host).
 cudaError_t launch_tail(const DevTree& t, const float* pts,
                         const uint32_t* act, int n_act, int32_t* state,
                         const float* qpad, float* lst_d, uint32_t* lst_i,
@@ -183,6 +174,18 @@ const char* build_host_tree(const float* P, int64_t n, int d, int h,
 // box[v*2d .. v*2d+d) = per-dimension minimum, box[v*2d+d .. v*2d+2d) =
 // maximum.
 void fill_boxes(const float* P, const HostTree& t, float* box);
+
+// k-halves of 16 dimensions the BF16 screen uses (1 for d <= 16, else 2).
+inline int screen_halves(int d) { return d <= 16 ? 1 : 2; }
+
+// Data of the BF16 screen, per leaf: the centre c (midpoint of the leaf's
+// bounding box), every point's offset bf16(fl(x - c)) packed as bf16 pairs
+// (8 words per point and k-half, in m16n8k16 B-fragment order, see
+// build.cpp), its squared norm pn (binary64 sum rounded to float; +inf for
+// padding slots), and per leaf bmax (upper bound on the offset rounding
+// error norm) and pnmax (largest pn).
+void fill_screen(const float* P, const HostTree& t, uint32_t* words,
+                 float* pn, float* center, float* bmax, float* pnmax);
 
 // Writes the quads and orig arrays for leaves [leaf_lo_id, leaf_hi_id)
 // into host buffers (`pts` and `orig` point at leaf leaf_lo_id's first slot).

@@ -205,4 +205,82 @@ void fill_boxes(const float* P, const HostTree& t, float* box) {
   }
 }
 
+namespace {
+
+// float -> bfloat16, round to nearest even (inputs are finite).
+inline uint16_t bf16_rn(float f) {
+  uint32_t x;
+  std::memcpy(&x, &f, 4);
+  const uint32_t lsb = (x >> 16) & 1u;
+  return (uint16_t)((x + 0x7fffu + lsb) >> 16);
+}
+
+inline float bf16_to_float(uint16_t h) {
+  const uint32_t x = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &x, 4);
+  return f;
+}
+
+}  // namespace
+
+void fill_screen(const float* P, const HostTree& t, uint32_t* words,
+                 float* pn, float* center, float* bmax, float* pnmax) {
+  const int d = t.d;
+  const int kh = screen_halves(d);
+  const int64_t lcap = t.lcap;
+  const int64_t L = (int64_t)1 << t.h;
+  // BF16 rounding error (relative, round to nearest) with margin, and its
+  // effect on a norm: |w_hat - w| <= rho |w|, |w| <= |w_hat| / (1 - rho).
+  const double rho = std::ldexp(1.0, -9) * (1.0 + 1e-4);
+  const double tiny = std::ldexp(1.0, -126) * std::sqrt((double)d);
+  parallel_items(L, [&](int64_t leaf) {
+    const int64_t lo = t.leaf_lo[leaf], cnt = t.leaf_lo[leaf + 1] - lo;
+    float* c = center + leaf * d;
+    for (int i = 0; i < d; ++i) {
+      float mn = INFINITY, mx = -INFINITY;
+      for (int64_t u = 0; u < cnt; ++u) {
+        const float x = P[t.perm[lo + u] * d + i];
+        mn = std::min(mn, x);
+        mx = std::max(mx, x);
+      }
+      c[i] = 0.5f * mn + 0.5f * mx;
+    }
+    double wmax = 0.0;
+    float pmax = 0.f;
+    for (int64_t u = 0; u < lcap; ++u) {
+      uint16_t hv[32] = {0};
+      float pv = INFINITY;
+      if (u < cnt) {
+        const float* x = P + t.perm[lo + u] * d;
+        double ss = 0.0;
+        for (int i = 0; i < d; ++i) {
+          hv[i] = bf16_rn(x[i] - c[i]);
+          const double w = bf16_to_float(hv[i]);
+          ss += w * w;
+        }
+        pv = (float)ss;
+        wmax = std::max(wmax, std::sqrt(ss));
+        pmax = std::max(pmax, pv);
+      }
+      pn[leaf * lcap + u] = pv;
+      for (int h = 0; h < kh; ++h) {
+        // 8 words per point and k-half, word j = dims (2j, 2j+1) of the
+        // half, stored in the order w0 w4 w1 w5 w2 w6 w3 w7 so that lane
+        // (g, t) of an m16n8k16 B fragment reads words t, t+4 with one
+        // 8-byte load.
+        uint32_t* rec = words + ((leaf * kh + h) * lcap + u) * 8;
+        for (int j = 0; j < 8; ++j) {
+          const int k0 = 16 * h + 2 * j;
+          const uint32_t wj = (uint32_t)hv[k0] | ((uint32_t)hv[k0 + 1] << 16);
+          rec[j < 4 ? 2 * j : 2 * (j - 4) + 1] = wj;
+        }
+      }
+    }
+    bmax[leaf] = std::nextafter((float)(rho / (1.0 - rho) * wmax + tiny),
+                                INFINITY);
+    pnmax[leaf] = std::nextafter(pmax, INFINITY);
+  });
+}
+
 }  // namespace bkd

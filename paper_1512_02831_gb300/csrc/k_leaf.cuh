@@ -2,11 +2,11 @@
 // fused in (Algorithm 1; Sec. 3.2 "each thread compares a particular query
 // with all reference points stored in the associated leaf").
 //
-// One CTA takes one work item at a time: up to kTileQ buffered queries of one
-// leaf.  The leaf's quads are staged in shared memory (segments of at most
-// `seg_quads` quads); every thread owns one query, holds its coordinates and
-// its sorted candidate list in registers and streams over the staged points,
-// reading each quad with warp-broadcast float4 loads.
+// One 64-thread CTA takes one work item at a time: up to 64 buffered queries
+// of one leaf, one query per thread.  Each thread holds its query's
+// coordinates and sorted candidate list in registers and streams over the
+// leaf's quads, which arrive in shared memory through a two-buffer TMA
+// pipeline and are read with warp-broadcast float4 loads.
 //
 // Distance arithmetic (float32, round-to-nearest, no reassociation):
 //     e = fl(fl(q_0 - x_0)^2);  e = fma(fl(q_i - x_i), fl(q_i - x_i), e), i=1..D-1
@@ -87,95 +87,6 @@ __device__ __forceinline__ void quad_dist(const float4* __restrict__ b,
   }
   upk2(a01, e0, e1);
   upk2(a23, e2, e3);
-}
-
-template <int D, int KT>
-__global__ void __launch_bounds__(kTileQ)
-    leaf_kernel(const Item* __restrict__ items, int item_lo, int item_hi,
-                const Counters* __restrict__ ctr,
-                const float4* __restrict__ pts, int64_t leaf0,
-                const int32_t* __restrict__ leaf_cnt, int64_t lcap,
-                const uint32_t* __restrict__ act,
-                const float* __restrict__ qpad, float* __restrict__ lst_d,
-                uint32_t* __restrict__ lst_i, int K, int seg_quads) {
-  extern __shared__ float4 sm[];
-  const int hi = item_hi >= 0 ? item_hi : ctr->n_items;
-  const int tid = threadIdx.x;
-  const int64_t qpl = lcap >> 2;  // quads per leaf
-  const int sent = KT - K;        // sentinel entries in front of the list
-  for (int it = item_lo + blockIdx.x; it < hi; it += gridDim.x) {
-    const Item w = items[it];
-    const int nq = (leaf_cnt[w.leaf] + 3) >> 2;
-    const float4* src = pts + (int64_t)(w.leaf - leaf0) * qpl * D;
-    const bool on = tid < w.count;
-    uint32_t q = 0;
-    uint64_t qq[D];
-    float Ld[KT];
-    uint32_t Li[KT];
-    if (on) {
-      q = act[w.start + tid];
-      const float* qp = qpad + (size_t)q * D;
-#pragma unroll
-      for (int i = 0; i < D; ++i) {
-        const float x = qp[i];
-        qq[i] = pk2(x, x);
-      }
-#pragma unroll
-      for (int i = 0; i < KT; ++i) {
-        if (i < sent) {
-          Ld[i] = -1.f;
-          Li[i] = kNoSlot;
-        } else {
-          Ld[i] = lst_d[(size_t)q * K + (i - sent)];
-          Li[i] = lst_i[(size_t)q * K + (i - sent)];
-        }
-      }
-    }
-    const uint32_t slot0 = (uint32_t)((int64_t)w.leaf * lcap);
-    for (int s0 = 0; s0 < nq; s0 += seg_quads) {
-      const int sq = min(seg_quads, nq - s0);
-      __syncthreads();  // the previous segment / item is no longer read
-      const float4* seg = src + (int64_t)s0 * D;
-      for (int i = tid; i < sq * D; i += kTileQ) sm[i] = seg[i];
-      __syncthreads();
-      if (on) {
-        float bound = Ld[KT - 1];
-#pragma unroll 2
-        for (int g = 0; g < sq; ++g) {
-          float e0, e1, e2, e3;
-          quad_dist<D>(sm + g * D, qq, e0, e1, e2, e3);
-          if (fminf(fminf(e0, e1), fminf(e2, e3)) < bound) {
-            const uint32_t id = slot0 + (uint32_t)(s0 + g) * 4u;
-            if (e0 < bound) {
-              list_insert<KT>(Ld, Li, e0, id);
-              bound = Ld[KT - 1];
-            }
-            if (e1 < bound) {
-              list_insert<KT>(Ld, Li, e1, id + 1);
-              bound = Ld[KT - 1];
-            }
-            if (e2 < bound) {
-              list_insert<KT>(Ld, Li, e2, id + 2);
-              bound = Ld[KT - 1];
-            }
-            if (e3 < bound) {
-              list_insert<KT>(Ld, Li, e3, id + 3);
-              bound = Ld[KT - 1];
-            }
-          }
-        }
-      }
-    }
-    if (on) {
-#pragma unroll
-      for (int i = 0; i < KT; ++i) {
-        if (i >= sent) {
-          lst_d[(size_t)q * K + (i - sent)] = Ld[i];
-          lst_i[(size_t)q * K + (i - sent)] = Li[i];
-        }
-      }
-    }
-  }
 }
 
 // ---------------------------------------------------------------- TMA
@@ -264,8 +175,8 @@ __device__ __forceinline__ void issue_segment(
 }
 
 // ProcessAllBuffers, pipelined: one 64-thread CTA per item of <= 64 queries
-// of one leaf (one query per thread, as in the CTA kernel above), but the
-// leaf is streamed through two shared-memory segment buffers of 128 points
+// of one leaf (one query per thread); the leaf is streamed through two
+// shared-memory segment buffers of 128 points
 // that one thread fills with TMA bulk copies, one segment ahead of the
 // consumers and across item boundaries.  Small CTAs and small buffers keep
 // many items resident per SM, so a partly filled item idles few lanes and
@@ -399,16 +310,15 @@ __global__ void __launch_bounds__(kPipeThreads)
 }
 
 // Per-capacity launchers, defined once per capacity in k_leaf_c<KT>.cu.
-#define BKD_LEAF_ARGS                                                       \
-  int variant, int Dp, const Item *items, int item_lo, int item_hi, Counters *ctr, \
+#define BKD_LEAF_ARGS                                                        \
+  int Dp, const Item *items, int item_lo, int item_hi, Counters *ctr,       \
       const float *pts, int64_t leaf0, const int32_t *leaf_cnt,             \
       int64_t lcap, const uint32_t *act, const float *qpad, float *lst_d,   \
-      uint32_t *lst_i, int K, int grid, int seg_quads, size_t smem,         \
-      cudaStream_t s
+      uint32_t *lst_i, int K, int grid, cudaStream_t s
 
-#define BKD_LEAF_DECLARE(CAP)                           \
-  cudaError_t leaf_launch_c##CAP(BKD_LEAF_ARGS);        \
-  const void* leaf_kernel_c##CAP(int variant, int Dp);
+#define BKD_LEAF_DECLARE(CAP)                    \
+  cudaError_t leaf_launch_c##CAP(BKD_LEAF_ARGS); \
+  const void* leaf_kernel_c##CAP(int Dp);
 
 BKD_LEAF_DECLARE(2)
 BKD_LEAF_DECLARE(4)
@@ -419,23 +329,16 @@ BKD_LEAF_DECLARE(32)
 
 #define BKD_LEAF_DIMS(X) X(2) X(4) X(6) X(8) X(10) X(12) X(16) X(24) X(32)
 
-#define BKD_LEAF_CASE_LAUNCH(DIM)                                            \
-  case DIM:                                                                  \
-    if (variant == kLeafCta)                                                 \
-      leaf_kernel<DIM, KT><<<grid, kTileQ, smem, s>>>(                       \
-          items, item_lo, item_hi, ctr, reinterpret_cast<const float4*>(pts), \
-          leaf0, leaf_cnt, lcap, act, qpad, lst_d, lst_i, K, seg_quads);     \
-    else                                                                     \
-      leaf_pipe_kernel<DIM, KT><<<grid, kPipeThreads, 0, s>>>(               \
-          items, item_lo, item_hi, ctr, reinterpret_cast<const float4*>(pts), \
-          leaf0, leaf_cnt, lcap, act, qpad, lst_d, lst_i, K);                \
+#define BKD_LEAF_CASE_LAUNCH(DIM)                                             \
+  case DIM:                                                                   \
+    leaf_pipe_kernel<DIM, KT><<<grid, kPipeThreads, 0, s>>>(                  \
+        items, item_lo, item_hi, ctr, reinterpret_cast<const float4*>(pts),    \
+        leaf0, leaf_cnt, lcap, act, qpad, lst_d, lst_i, K);                   \
     return cudaGetLastError();
 
-#define BKD_LEAF_CASE_PTR(DIM)                                           \
-  case DIM:                                                              \
-    return variant == kLeafCta                                           \
-               ? reinterpret_cast<const void*>(&leaf_kernel<DIM, KT>)    \
-               : reinterpret_cast<const void*>(&leaf_pipe_kernel<DIM, KT>);
+#define BKD_LEAF_CASE_PTR(DIM) \
+  case DIM:                    \
+    return reinterpret_cast<const void*>(&leaf_pipe_kernel<DIM, KT>);
 
 #define BKD_LEAF_DEFINE(CAP)                                            \
   cudaError_t leaf_launch_c##CAP(BKD_LEAF_ARGS) {                       \
@@ -443,7 +346,7 @@ BKD_LEAF_DECLARE(32)
     switch (Dp) { BKD_LEAF_DIMS(BKD_LEAF_CASE_LAUNCH) default: break; } \
     return cudaErrorInvalidValue;                                       \
   }                                                                     \
-  const void* leaf_kernel_c##CAP(int variant, int Dp) {                 \
+  const void* leaf_kernel_c##CAP(int Dp) {                              \
     constexpr int KT = CAP;                                             \
     switch (Dp) { BKD_LEAF_DIMS(BKD_LEAF_CASE_PTR) default: break; }    \
     return nullptr;                                                     \

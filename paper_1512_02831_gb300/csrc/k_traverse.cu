@@ -43,7 +43,8 @@ __global__ void find_leaf_kernel(DevTree t, const float* __restrict__ qpad,
                                  const uint32_t* __restrict__ act, int n_act,
                                  int32_t* __restrict__ state,
                                  const float* __restrict__ lst_d, int K,
-                                 int32_t* __restrict__ leaf_of) {
+                                 int32_t* __restrict__ leaf_of,
+                                 int32_t* __restrict__ cnt) {
   const int pos = blockIdx.x * blockDim.x + threadIdx.x;
   if (pos >= n_act) return;
   const uint32_t q = act[pos];
@@ -53,21 +54,21 @@ __global__ void find_leaf_kernel(DevTree t, const float* __restrict__ qpad,
                                      : lst_d[(size_t)q * K + (K - 1)];
   const int next = next_leaf<F32Bound>(t, qp, node, bound);
   state[q] = next;
-  leaf_of[pos] = next == kDone ? -1 : next - ((1 << t.h) - 1);
+  if (next == kDone) {
+    leaf_of[pos] = -1;
+  } else {
+    const int leaf = next - ((1 << t.h) - 1);
+    leaf_of[pos] = leaf;
+    atomicAdd(cnt + leaf, 1);
+  }
 }
 
 // ------------------------------------------------------------- bucketing
-// Buffer insertion of Algorithm 1 as a counting sort by leaf id: histogram,
-// exclusive scan (also of per-leaf work items of `tile` queries), scatter.
+// Buffer insertion of Algorithm 1 as a counting sort by leaf id: the
+// histogram is counted where the next leaf is found (FindLeafBatch, or the
+// leaf kernel's fused step); here follow the exclusive scan (also of per-leaf
+// work items of `tile` queries) and the scatter.
 // The order of queries inside a leaf's buffer is irrelevant to the results.
-
-__global__ void hist_kernel(const int32_t* __restrict__ leaf_of, int n,
-                            int32_t* __restrict__ cnt) {
-  const int pos = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pos >= n) return;
-  const int l = leaf_of[pos];
-  if (l >= 0) atomicAdd(cnt + l, 1);
-}
 
 // Two-pass scan over the leaves, 2,048 leaves (8 per thread) per block:
 // scan_parts_kernel sums each tile, scan_write_kernel adds the sums of the
@@ -252,22 +253,19 @@ cudaError_t launch_init(const float* Q, int64_t m, int d, int Dp, float* qpad,
 cudaError_t launch_find_leaf(const DevTree& t, const float* qpad,
                              const uint32_t* act, int n_act, int32_t* state,
                              const float* lst_d, int K, int32_t* leaf_of,
-                             cudaStream_t s) {
+                             int32_t* cnt, cudaStream_t s) {
   if (n_act == 0) return cudaSuccess;
-  find_leaf_kernel<<<blocks(n_act, 256), 256, 0, s>>>(t, qpad, act, n_act,
-                                                      state, lst_d, K, leaf_of);
+  find_leaf_kernel<<<blocks(n_act, 256), 256, 0, s>>>(
+      t, qpad, act, n_act, state, lst_d, K, leaf_of, cnt);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bucket(const int32_t* leaf_of, const uint32_t* act,
                           int n_act, int n_leaves, int tile,
-                          const int32_t* leaf_cnt,
-                          int32_t* cnt, int32_t* off, int32_t* cursor,
-                          int32_t* toff, Item* items, uint32_t* next,
-                          Counters* ctr, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * n_leaves, s);
-  if (e != cudaSuccess) return e;
-  if (n_act > 0) hist_kernel<<<blocks(n_act, 256), 256, 0, s>>>(leaf_of, n_act, cnt);
+                          const int32_t* leaf_cnt, const int32_t* cnt,
+                          int32_t* off, int32_t* cursor, int32_t* toff,
+                          Item* items, uint32_t* next, Counters* ctr,
+                          cudaStream_t s) {
   // the cursor array (4 bytes per leaf) holds the 16-byte tile sums (one per
   // 2,048 leaves) until the scan is done, then is cleared for the scatter
   ScanPart* parts = reinterpret_cast<ScanPart*>(cursor);
@@ -277,7 +275,7 @@ cudaError_t launch_bucket(const int32_t* leaf_of, const uint32_t* act,
   scan_write_kernel<<<nparts, kScanBlock, 0, s>>>(cnt, n_leaves, tile,
                                                   leaf_cnt, parts, off, toff,
                                                   items, ctr);
-  e = cudaMemsetAsync(cursor, 0, sizeof(int32_t) * n_leaves, s);
+  cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(int32_t) * n_leaves, s);
   if (e != cudaSuccess) return e;
   if (n_act > 0)
     scatter_kernel<<<blocks(n_act, 256), 256, 0, s>>>(leaf_of, act, n_act, off,

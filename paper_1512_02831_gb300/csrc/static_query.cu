@@ -136,14 +136,15 @@ int run_static(const TreeView& v, char* base, const float* Q, int64_t m, int k,
   SQ_CU(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
   SQ_CU(launch_init(Q, m, D.d, D.Dp, qpad, lst_d, lst_i, K, state, act, ctr,
                     s));
-  const int grid_max =
-      leaf_kernel_grid(kLeafPipe, D.Dp, cap, D.lcap, v.sm_count);
+  const int grid_max = leaf_kernel_grid(D.Dp, cap, v.sm_count);
   int n_act = (int)m;
-  while (n_act > 0) {
-    SQ_CU(launch_find_leaf(D, qpad, act, n_act, state, lst_d, K, leaf_of, s));
+  for (;;) {
+    SQ_CU(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * v.n_leaves, s));
+    SQ_CU(launch_find_leaf(D, qpad, act, n_act, state, lst_d, K, leaf_of,
+                           cnt, s));
     SQ_CU(launch_bucket(leaf_of, act, n_act, (int)v.n_leaves, kPipeTile,
-                        D.leaf_cnt, cnt,
-                        off, cursor, toff, items, nxt, ctr, s));
+                        D.leaf_cnt, cnt, off, cursor, toff, items, nxt, ctr,
+                        s));
     SQ_CU(cudaMemcpyAsync(h, ctr, sizeof(Counters), cudaMemcpyDeviceToHost,
                           s));
     SQ_CU(cudaStreamSynchronize(s));
@@ -154,10 +155,8 @@ int run_static(const TreeView& v, char* base, const float* Q, int64_t m, int k,
       return set_error(BKD_ETIMEOUT, "a leaf-segment copy did not complete");
     const int n_next = h->n_next, n_items = h->n_items;
     if (n_next == 0) break;
-    SQ_CU(launch_leaf(kLeafPipe, D.Dp, cap, items, 0, n_items, ctr, v.d_pts,
-                      0, D.leaf_cnt, D.lcap, nxt, qpad, lst_d, lst_i, K,
-                      std::min(grid_max, leaf_grid_units(kLeafPipe, n_items)),
-                      s));
+    SQ_CU(launch_leaf(D, cap, items, 0, n_items, ctr, v.d_pts, 0, nxt, qpad,
+                      lst_d, lst_i, K, std::min(grid_max, n_items), s));
     std::swap(act, nxt);
     n_act = n_next;
   }

@@ -49,25 +49,23 @@ def test_hand_cases_exact():
                 assert dist[0].tolist() == [float(x) for x in qc["dist"]]
 
 
-@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 7, 10, 11, 16, 20, 27, 32])
-def test_every_dimension(d, variant):
+def test_every_dimension(d):
     rng = np.random.default_rng(d)
     n = 3000 + d
     P = rng.standard_normal((n, d)).astype(np.float32)
     Q = rng.standard_normal((517, d)).astype(np.float32)
     k = 7
     h = 5
-    idx, dist, _ = run(P, Q, k, h, leaf_variant=variant)
+    idx, dist, _ = run(P, Q, k, h)
     check(P, Q, k, idx, dist, oracle.brute_knn(P, Q, k))
 
 
-@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 7, 8, 11, 15, 16, 31])
-def test_every_list_capacity(k, variant):
+def test_every_list_capacity(k):
     P = workloads.uniform(5000, 6, 7)
     Q = workloads.uniform(700, 6, 8)
-    idx, dist, _ = run(P, Q, k, 6, leaf_variant=variant)
+    idx, dist, _ = run(P, Q, k, 6)
     check(P, Q, k, idx, dist, oracle.brute_knn(P, Q, k))
 
 
@@ -269,18 +267,3 @@ def test_tail_kernel_in_chunked_mode():
     i1, d1, st = run(P, Q, 10, 8, chunks=3, tail_queries=1500)
     assert st["tail_queries"] > 0
     assert np.array_equal(i0, i1) and np.array_equal(d0, d1)
-
-
-def test_leaf_variants_are_bit_identical():
-    """The warp-granular and the CTA ProcessAllBuffers kernels score the same
-    pairs with the same arithmetic: identical results, resident and chunked."""
-    w = workloads.scaled(workloads.MIXTURE_64M, 1 << 18, 1 << 14, 8)
-    P, Q = w.points(), w.queries()
-    i0, d0, s0 = run(P, Q, 10, 8, leaf_variant=1)
-    i1, d1, s1 = run(P, Q, 10, 8, leaf_variant=0)
-    i2, d2, _ = run(P, Q, 10, 8, leaf_variant=0, chunks=3)
-    assert s0["pairs"] == s1["pairs"]
-    assert np.array_equal(i0, i1) and np.array_equal(d0, d1)
-    assert np.array_equal(i0, i2) and np.array_equal(d0, d2)
-    check(P, Q, 10, i1, d1, oracle.brute_knn(P, Q[:800], 10),
-          rows=np.arange(800))
