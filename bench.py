@@ -236,7 +236,7 @@ def run_ours(a, w, rank, world, local_rank):
     Q = w.queries(stream=rank)
     m, k, d = Q.shape[0], w.k, w.d
     t0 = time.perf_counter()
-    tree = bkd.bkd_build(P, w.height)
+    tree = bkd.bkd_build(P, w.height, precision=1)
     build_s = time.perf_counter() - t0
     Qd = torch.from_numpy(Q).to(dev)
     out_i = torch.empty((m, k), dtype=torch.int64, device=dev)
@@ -245,31 +245,49 @@ def run_ours(a, w, rank, world, local_rank):
 
     stats_keys = ("rounds", "leaf_visits", "pairs", "resorted", "fallback",
                   "leaf_kernel_ms", "kernel_launches", "leaf_launches",
-                  "tail_queries", "tail_visits", "tail_pairs", "tail_ms")
-    for _ in range(a.warmup):
-        bkd.bkd_query(tree, Qd, k, out_i, out_d)
-    barrier()
+                  "tail_queries", "tail_visits", "tail_pairs", "tail_ms",
+                  "screen_kept", "screen_pairs", "screen_ms")
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     vis = [v for v in vis.split(",") if v.strip()]
     smi_index = (vis[local_rank] if local_rank < len(vis)
                  and vis[local_rank].strip().isdigit() else local_rank)
-    clocks = Clocks(smi_index)
-    clocks.start()
-    acc = {s: 0.0 for s in stats_keys}
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    barrier()
-    ev0.record(stream)
-    for _ in range(a.steps):
-        bkd.bkd_query(tree, Qd, k, out_i, out_d)
-        for s in stats_keys:
-            acc[s] += bkd.bkd_get_stat(tree, s)
-    ev1.record(stream)
-    barrier()
-    clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    ms_max = max_over_ranks(ms)
-    value = world * m * a.steps / (ms_max / 1000.0)
+
+    def timed(precision: int) -> dict:
+        """W warm-up + K timed bkd_query steps with leaf scoring
+        `precision` (0 float32, 1 BF16 screen + float32 rescoring)."""
+        bkd.bkd_set_option(tree, "precision", precision)
+        for _ in range(a.warmup):
+            bkd.bkd_query(tree, Qd, k, out_i, out_d)
+        barrier()
+        clocks = Clocks(smi_index)
+        clocks.start()
+        acc = {s: 0.0 for s in stats_keys}
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        ev0.record(stream)
+        for _ in range(a.steps):
+            bkd.bkd_query(tree, Qd, k, out_i, out_d)
+            for s in stats_keys:
+                acc[s] += bkd.bkd_get_stat(tree, s)
+        ev1.record(stream)
+        barrier()
+        clk = clocks.stop()
+        ms = ev0.elapsed_time(ev1)
+        ms_max = max_over_ranks(ms)
+        return {"acc": acc, "clk": clk, "ms": ms, "ms_max": ms_max,
+                "value": world * m * a.steps / (ms_max / 1000.0),
+                "idx": out_i.clone(), "dist": out_d.clone()}
+
+    runs = {0: timed(0), 1: timed(1)}
+    identical = bool(torch.equal(runs[0]["idx"], runs[1]["idx"])
+                     and torch.equal(runs[0]["dist"], runs[1]["dist"]))
+    head = 1 if runs[1]["value"] > runs[0]["value"] else 0
+    acc, clk, ms, ms_max = (runs[head][x] for x in ("acc", "clk", "ms",
+                                                     "ms_max"))
+    value = runs[head]["value"]
+    bkd.bkd_set_option(tree, "precision", head)
+    out_i.copy_(runs[head]["idx"])
 
     # end to end through the same call, host buffers (pinned), copies inside
     Qh = torch.from_numpy(Q).pin_memory()
@@ -288,40 +306,64 @@ def run_ours(a, w, rank, world, local_rank):
            "buffers": "pinned host, bkd_query copies in and out"}
     same = bool(torch.equal(oi_h, out_i.cpu()))
 
-    # roofline of the dominant kernel (leaf brute force)
+    # rooflines: the float32 leaf kernel (from the float32 run) and the BF16
+    # screen kernel (from the screened run)
     peaks = measured_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070)
     peak_ops = 128 * sm_count * sm_max * 1e6 / 1e12      # Top/s
-    ops = 2 * d * acc["pairs"]
-    leaf_s = acc["leaf_kernel_ms"] / 1000.0
-    achieved = ops / leaf_s / 1e12 if leaf_s > 0 else 0.0
-    traffic = leaf_traffic_per_launch()
-    roofline = {
-        "bound": "alu", "kernel": "leaf_kernel (ProcessAllBuffers)",
+    a0 = runs[0]["acc"]
+    leaf_s = a0["leaf_kernel_ms"] / 1000.0
+    achieved = 2 * d * a0["pairs"] / leaf_s / 1e12 if leaf_s > 0 else 0.0
+    roof_fp32 = {
+        "bound": "alu", "kernel": "leaf_pipe_kernel (ProcessAllBuffers, fp32)",
         "achieved": achieved, "peak": peak_ops, "unit": "Top/s",
-        "frac": achieved / peak_ops,
-        "traffic": traffic,
+        "frac": achieved / peak_ops, "traffic": leaf_traffic_per_launch(),
         "basis": (f"FP32 pipe operations: 2*d = {2 * d} per scored (query, "
                   f"point) pair (d subtractions + d multiply-adds); peak = "
                   f"128 FP32 lanes x {sm_count} SMs x {sm_max:.0f} MHz "
-                  f"(max SM clock of measured peaks); time = CUDA events "
-                  f"around every leaf-kernel launch on its stream"),
-        "leaf_share_of_step": leaf_s / (ms / 1000.0),
+                  f"(max SM clock of measured peaks), 'of measured'; time = "
+                  f"CUDA events around every leaf-kernel launch on its "
+                  f"stream"),
+        "leaf_share_of_step": leaf_s / (runs[0]["ms"] / 1000.0),
         "flop_view": {"flops_per_pair": 3 * d,
                       "achieved_tflops": 1.5 * achieved,
                       "peak_tflops_fma2": 2 * peak_ops},
     }
+    a1 = runs[1]["acc"]
+    kh = 1 if d <= 16 else 2
+    scr_s = a1["screen_ms"] / 1000.0
+    peak_bf16 = float(peaks.get("bf16_tflops") or 1900.0)
+    scr_tf = 2 * 16 * kh * a1["screen_pairs"] / scr_s / 1e12 if scr_s else 0.0
+    roof_bf16 = {
+        "bound": "tensor", "kernel": "screen_kernel (BF16 mma.sync screen)",
+        "achieved": scr_tf, "peak": peak_bf16, "unit": "TFLOP/s",
+        "frac": scr_tf / peak_bf16, "traffic": None,
+        "basis": (f"2 x {16 * kh} flops per screened (query, point) pair "
+                  f"(bf16 dot product padded to {16 * kh}); peak = measured "
+                  f"cuBLAS bf16 burst, 'of measured'"),
+        "screen_share_of_step": scr_s / (runs[1]["ms"] / 1000.0),
+        "pairs_per_s": a1["screen_pairs"] / scr_s if scr_s else 0.0,
+        "kept_fraction": (a1["screen_kept"] / a1["screen_pairs"]
+                          if a1["screen_pairs"] else None),
+        "alu_view": {"fp32_ops_per_pair_exact_path": 2 * d,
+                     "equivalent_exact_top_s":
+                         2 * d * a1["screen_pairs"] / scr_s / 1e12
+                         if scr_s else 0.0},
+    }
+    roofline = roof_bf16 if head == 1 else roof_fp32
+    names = {0: "fp32 exact path", 1: "bf16 tensor-core screen + fp32 rescore"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s",
         "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms_max / a.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16+f32" if head == 1 else "f32",
         "data": ("synthetic: seeded Gaussian mixture (32 isotropic "
                  "components, centres U[0,1]^10, sigma logU[0.02,0.2], "
                  "Dirichlet(1) weights); per-rank query sets"),
-        "config": dict(w.describe(), precision="fp32 exact path",
+        "config": dict(w.describe(), precision=names[head],
                        parallelism=f"replicas x{world}, queries sharded",
                        l2=("inputs larger than L2 (leaf structure 2.7 GB, "
                            "queries 0.67 GB) - no flush needed"),
@@ -329,6 +371,17 @@ def run_ours(a, w, rank, world, local_rank):
         "e2e": e2e,
         "gpu_launches": int(acc["kernel_launches"]),
         "roofline": roofline,
+        "roofline_fp32_leaf": roof_fp32,
+        "roofline_bf16_screen": roof_bf16,
+        "fp32_vs_bf16": {
+            "fp32": {"value": runs[0]["value"],
+                     "ms_per_step": runs[0]["ms_max"] / a.steps,
+                     "clocks": runs[0]["clk"]},
+            "bf16_screened": {"value": runs[1]["value"],
+                              "ms_per_step": runs[1]["ms_max"] / a.steps,
+                              "clocks": runs[1]["clk"]},
+            "identical_results": identical,
+            "headline": names[head]},
         "clocks": clk,
         "path": {"rounds_per_step": acc["rounds"] / a.steps,
                  "leaf_visits_per_query": (acc["leaf_visits"]
@@ -342,6 +395,9 @@ def run_ours(a, w, rank, world, local_rank):
                  "leaf_launches_per_step": acc["leaf_launches"] / a.steps,
                  "resorted_per_step": acc["resorted"] / a.steps,
                  "fallback_per_step": acc["fallback"] / a.steps,
+                 "screen_pairs_per_step": acc["screen_pairs"] / a.steps,
+                 "screen_kept_per_step": acc["screen_kept"] / a.steps,
+                 "screen_ms_per_step": acc["screen_ms"] / a.steps,
                  "e2e_matches_device_run": same},
     }
     bkd.bkd_free(tree)

@@ -87,7 +87,13 @@ enum bkd_option {
    * (one warp per query walks its remaining leaves) instead of one
    * LazySearch round per leaf.  -1 (default) = automatic (8192); 0 = never.
    * Results do not depend on it.  Any time. */
-  BKD_OPT_TAIL_QUERIES = 5
+  BKD_OPT_TAIL_QUERIES = 5,
+  /* Leaf scoring: 0 (default) = float32 for every (query, point) pair;
+   * 1 = a BF16 tensor-core screen rejects points that provably cannot enter
+   * a candidate list, the rest are scored in float32 -- results identical to
+   * 0.  1 at build also prepares the screen data (resident trees only;
+   * chunked: BKD_EUNSUPPORTED); afterwards 0 / 1 may be switched any time. */
+  BKD_OPT_PRECISION = 6
 };
 
 /* ------------------------------------------------------------------- stats
@@ -106,7 +112,10 @@ enum bkd_stat {
   BKD_STAT_TAIL_QUERIES = 11,  /* queries finished by the tail kernel        */
   BKD_STAT_TAIL_VISITS = 12,   /* (query, leaf) visits of the tail kernel    */
   BKD_STAT_TAIL_PAIRS = 13,    /* distances scored by the tail kernel        */
-  BKD_STAT_TAIL_MS = 14        /* device time of the tail kernel             */
+  BKD_STAT_TAIL_MS = 14,       /* device time of the tail kernel             */
+  BKD_STAT_SCREEN_KEPT = 15,   /* pairs the BF16 screen passed to float32    */
+  BKD_STAT_SCREEN_PAIRS = 16,  /* pairs the BF16 screen kernel examined      */
+  BKD_STAT_SCREEN_MS = 17      /* device time of the BF16 screen kernel      */
 };
 
 typedef struct bkd_tree bkd_tree; /* opaque; owned by the library */

@@ -35,11 +35,12 @@ BKD_STATIC_MAX_QUERIES = 4096
 BKD_STATIC_MAX_HEIGHT = 16
 
 OPTIONS = {"stream": 1, "device_mem_cap": 2, "chunks": 3, "max_active": 4,
-           "tail_queries": 5}
+           "tail_queries": 5, "precision": 6}
 STATS = {"rounds": 1, "leaf_visits": 2, "pairs": 3, "resorted": 4,
          "fallback": 5, "leaf_kernel_ms": 6, "chunk_bytes": 7, "copy_ms": 8,
          "leaf_launches": 9, "kernel_launches": 10, "tail_queries": 11,
-         "tail_visits": 12, "tail_pairs": 13, "tail_ms": 14}
+         "tail_visits": 12, "tail_pairs": 13, "tail_ms": 14,
+         "screen_kept": 15, "screen_pairs": 16, "screen_ms": 17}
 
 _lock = threading.Lock()
 _lib = None

@@ -115,6 +115,12 @@ struct bkd_tree {
   float* d_split = nullptr;
   int32_t* d_leaf_cnt = nullptr;
   float* d_box = nullptr;
+  // BF16 screen data (built on request, resident trees only)
+  uint32_t* d_scr_words = nullptr;
+  float *d_scr_pn = nullptr, *d_scr_center = nullptr, *d_scr_bmax = nullptr,
+        *d_scr_pnmax = nullptr;
+  ScreenData screen;
+  int precision = 0;
   // chunked storage
   bool chunked = false;
   int n_chunks = 0;
@@ -140,12 +146,14 @@ struct bkd_tree {
   // timing
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> leaf_ev, copy_ev, tail_ev;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> leaf_ev, copy_ev, tail_ev,
+      screen_ev;
   // stats of the last query
   double st_rounds = 0, st_visits = 0, st_pairs = 0, st_resorted = 0,
          st_fallback = 0, st_leaf_ms = 0, st_chunk_bytes = 0, st_copy_ms = 0,
          st_leaf_launches = 0, st_launches = 0, st_tail_queries = 0,
-         st_tail_visits = 0, st_tail_pairs = 0, st_tail_ms = 0;
+         st_tail_visits = 0, st_tail_pairs = 0, st_tail_ms = 0,
+         st_screen_kept = 0, st_screen_pairs = 0, st_screen_ms = 0;
 
   cudaEvent_t next_event() {
     if (ev_used == ev_pool.size()) {
@@ -169,6 +177,11 @@ void release(bkd_tree* t) {
   cudaFree(t->d_split);
   cudaFree(t->d_leaf_cnt);
   cudaFree(t->d_box);
+  cudaFree(t->d_scr_words);
+  cudaFree(t->d_scr_pn);
+  cudaFree(t->d_scr_center);
+  cudaFree(t->d_scr_bmax);
+  cudaFree(t->d_scr_pnmax);
   cudaFree(t->d_chunk_leaf);
   cudaFree(t->d_chunk_buf[0]);
   cudaFree(t->d_chunk_buf[1]);
@@ -244,7 +257,7 @@ int build_impl(const float* P, int64_t n, int d, int height,
                 (long long)((int64_t)1 << height), (long long)n);
   if (n_options < 0 || (n_options > 0 && !options))
     return fail(BKD_EINVAL, "bad options array");
-  int64_t cap = -1, chunks = 0;
+  int64_t cap = -1, chunks = 0, precision = 0;
   for (int i = 0; i < n_options; ++i) {
     const int64_t key = options[2 * i], val = options[2 * i + 1];
     if (key == BKD_OPT_DEVICE_MEM_CAP) {
@@ -254,6 +267,10 @@ int build_impl(const float* P, int64_t n, int d, int height,
       if (val < 0 || val > (1 << 20))
         return fail(BKD_EINVAL, "chunk count out of range");
       chunks = val;
+    } else if (key == BKD_OPT_PRECISION) {
+      if (val != 0 && val != 1)
+        return fail(BKD_EINVAL, "precision must be 0 or 1");
+      precision = val;
     } else if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE ||
                key == BKD_OPT_TAIL_QUERIES) {
       // applied after construction below
@@ -410,6 +427,50 @@ int build_impl(const float* P, int64_t n, int d, int height,
               cudaSuccess)
         return bail(fail(BKD_ECUDA, "event creation failed"));
   }
+  if (precision == 1) {
+    if (chunked)
+      return bail(fail(BKD_EUNSUPPORTED,
+                       "the BF16 screen needs a tree resident in device "
+                       "memory"));
+    const int kh = screen_halves(d);
+    std::vector<uint32_t> words;
+    std::vector<float> pn, center, bmax, pnmax;
+    try {
+      words.resize((size_t)L * kh * H.lcap * 8);
+      pn.resize((size_t)slots);
+      center.resize((size_t)L * d);
+      bmax.resize(L);
+      pnmax.resize(L);
+    } catch (...) {
+      return bail(fail(BKD_ENOMEM, "host staging of the screen data"));
+    }
+    fill_screen(Ph, H, words.data(), pn.data(), center.data(), bmax.data(),
+                pnmax.data());
+    if (cudaMalloc(&t->d_scr_words, words.size() * 4) != cudaSuccess ||
+        cudaMalloc(&t->d_scr_pn, pn.size() * 4) != cudaSuccess ||
+        cudaMalloc(&t->d_scr_center, center.size() * 4) != cudaSuccess ||
+        cudaMalloc(&t->d_scr_bmax, bmax.size() * 4) != cudaSuccess ||
+        cudaMalloc(&t->d_scr_pnmax, pnmax.size() * 4) != cudaSuccess)
+      return bail(fail(BKD_ENOMEM, "device allocation failed (screen data)"));
+    if (cudaMemcpy(t->d_scr_words, words.data(), words.size() * 4,
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t->d_scr_pn, pn.data(), pn.size() * 4,
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t->d_scr_center, center.data(), center.size() * 4,
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t->d_scr_bmax, bmax.data(), bmax.size() * 4,
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t->d_scr_pnmax, pnmax.data(), pnmax.size() * 4,
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(fail(BKD_ECUDA, "upload of the screen data failed"));
+    t->screen.words = t->d_scr_words;
+    t->screen.pn = t->d_scr_pn;
+    t->screen.center = t->d_scr_center;
+    t->screen.bmax = t->d_scr_bmax;
+    t->screen.pnmax = t->d_scr_pnmax;
+    t->screen.kh = kh;
+    t->precision = 1;
+  }
   if (cudaMalloc(&t->d_ctr, sizeof(Counters)) != cudaSuccess ||
       cudaHostAlloc(&t->h_ctr, sizeof(Counters), cudaHostAllocDefault) !=
           cudaSuccess ||
@@ -483,6 +544,9 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   uint32_t* nxt = t->act_b.p;
   int n_act = (int)m;
   const int grid_max = leaf_kernel_grid(Dp, cap, t->sm_count);
+  const int screen_max =
+      t->precision == 1 ? screen_grid(t->screen.kh, D.lcap, K, t->sm_count)
+                        : 0;
   const int tail = t->tail_queries >= 0 ? t->tail_queries : 8192;
   // A round: FindLeafBatch over the active queries (it also counts every
   // query into its next leaf), bucketing by leaf, ProcessAllBuffers.
@@ -528,8 +592,20 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
     }
     t->st_rounds += 1;
     t->st_visits += n_next;
-    t->st_pairs += (double)t->h_ctr->pairs;
-    if (!t->chunked) {
+    if (!t->chunked && t->precision == 1 && round > 0 && screen_max > 0) {
+      // BF16 tensor-core screen + exact float32 rescoring (the first round
+      // stays on the float32 kernel: every list is still empty there)
+      const int grid = std::min(screen_max, n_items);
+      cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
+      if (e0) cudaEventRecord(e0, s);
+      CU(launch_screen(D, t->screen, t->items.p, 0, n_items, t->d_ctr, nxt,
+                       t->qpad.p, t->lst_d.p, t->lst_i.p, K, grid, s));
+      if (e1) cudaEventRecord(e1, s);
+      if (e0 && e1) t->screen_ev.push_back({e0, e1});
+      t->st_screen_pairs += (double)t->h_ctr->pairs;  // whole round
+      t->st_launches += 1;
+    } else if (!t->chunked) {
+      t->st_pairs += (double)t->h_ctr->pairs;
       const int grid = std::min(grid_max, n_items);
       cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
       if (e0) cudaEventRecord(e0, s);
@@ -541,6 +617,7 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
       t->st_launches += 1;
     } else {
       // Brute / Copy / Wait over the chunks holding buffered queries
+      t->st_pairs += (double)t->h_ctr->pairs;
       const int N = t->n_chunks;
       const bool forward = (round % 2) == 0;
       int prev_b = -1;
@@ -605,6 +682,7 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   t->st_fallback += n_fb;
   t->st_tail_visits += (double)t->h_ctr->tail_visits;
   t->st_tail_pairs += (double)t->h_ctr->tail_pairs;
+  t->st_screen_kept += (double)t->h_ctr->screen_kept;
   t->st_resorted += t->h_ctr->n_resorted;
   if (n_fb > 0) {
     CU(launch_fallback(D, n_fb, t->fb_list.p, k, K, t->qpad.p, t->lst_d.p,
@@ -674,11 +752,13 @@ int bkd_query(bkd_tree* t, const float* Q, int64_t m, int k, int64_t* out_idx,
   t->st_rounds = t->st_visits = t->st_pairs = t->st_resorted =
       t->st_fallback = t->st_leaf_ms = t->st_chunk_bytes = t->st_copy_ms =
           t->st_leaf_launches = t->st_launches = t->st_tail_queries =
-              t->st_tail_visits = t->st_tail_pairs = t->st_tail_ms = 0;
+              t->st_tail_visits = t->st_tail_pairs = t->st_tail_ms =
+                  t->st_screen_kept = t->st_screen_pairs = t->st_screen_ms = 0;
   t->ev_used = 0;
   t->leaf_ev.clear();
   t->copy_ev.clear();
   t->tail_ev.clear();
+  t->screen_ev.clear();
   if (m == 0) return BKD_OK;
   const int d = t->dev.d;
   cudaStream_t s = t->stream;
@@ -724,6 +804,11 @@ int bkd_query(bkd_tree* t, const float* Q, int64_t m, int k, int64_t* out_idx,
     if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess)
       t->st_tail_ms += ms;
   }
+  for (auto& pr : t->screen_ev) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess)
+      t->st_screen_ms += ms;
+  }
   cudaGetLastError();
   return BKD_OK;
 }
@@ -739,6 +824,15 @@ int bkd_set_option(bkd_tree* t, int key, int64_t value) {
       if (value < 0 || value >= ((int64_t)1 << 31))
         return fail(BKD_EINVAL, "max active out of range");
       t->max_active = (int)value;
+      return BKD_OK;
+    case BKD_OPT_PRECISION:
+      if (value != 0 && value != 1)
+        return fail(BKD_EINVAL, "precision must be 0 or 1");
+      if (value == 1 && !t->screen.words)
+        return fail(BKD_EINVAL,
+                    "the tree was built without BF16 screen data (pass "
+                    "BKD_OPT_PRECISION=1 to bkd_build_with)");
+      t->precision = (int)value;
       return BKD_OK;
     case BKD_OPT_TAIL_QUERIES:
       if (value < -1 || value >= ((int64_t)1 << 31))
@@ -771,6 +865,9 @@ int bkd_get_stat(const bkd_tree* t, int key, double* value) {
     case BKD_STAT_TAIL_VISITS: *value = t->st_tail_visits; break;
     case BKD_STAT_TAIL_PAIRS: *value = t->st_tail_pairs; break;
     case BKD_STAT_TAIL_MS: *value = t->st_tail_ms; break;
+    case BKD_STAT_SCREEN_KEPT: *value = t->st_screen_kept; break;
+    case BKD_STAT_SCREEN_PAIRS: *value = t->st_screen_pairs; break;
+    case BKD_STAT_SCREEN_MS: *value = t->st_screen_ms; break;
     default: return fail(BKD_EINVAL, "unknown stat %d", key);
   }
   return BKD_OK;

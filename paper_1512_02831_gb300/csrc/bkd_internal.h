@@ -61,6 +61,7 @@ struct Counters {
   int32_t pad;
   unsigned long long tail_pairs;   // (query, point) pairs of the tail kernel
   unsigned long long tail_visits;  // (query, leaf) visits of the tail kernel
+  unsigned long long screen_kept;  // pairs the BF16 screen passed on
 };
 
 constexpr int kErrNonFinite = 1;   // a query holds a non-finite / huge value
@@ -120,6 +121,27 @@ cudaError_t launch_leaf(const DevTree& t, int cap, const Item* items,
                         int K, int grid, cudaStream_t s);
 
 int leaf_kernel_grid(int Dp, int cap, int sm_count);
+
+// BF16 screen data on the device (see fill_screen).
+struct ScreenData {
+  const uint32_t* words = nullptr;
+  const float* pn = nullptr;
+  const float* center = nullptr;
+  const float* bmax = nullptr;
+  const float* pnmax = nullptr;
+  int kh = 0;
+};
+
+// ProcessAllBuffers with the BF16 tensor-core screen and exact float32
+// rescoring (k_screen.cu); same items and results as launch_leaf on a
+// resident tree.  screen_grid: resident CTAs (0 if the shared memory does
+// not fit).
+int screen_grid(int kh, int64_t lcap, int K, int sm_count);
+cudaError_t launch_screen(const DevTree& t, const ScreenData& sd,
+                          const Item* items, int item_lo, int item_hi,
+                          Counters* ctr, const uint32_t* act,
+                          const float* qpad, float* lst_d, uint32_t* lst_i,
+                          int K, int grid, cudaStream_t s);
 
 // Runs the traversal of each of the n_act queries in `act` to its end (one
 // warp per query); state[q] is the query's pending (not yet scanned) leaf.

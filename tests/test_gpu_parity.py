@@ -267,3 +267,71 @@ def test_tail_kernel_in_chunked_mode():
     i1, d1, st = run(P, Q, 10, 8, chunks=3, tail_queries=1500)
     assert st["tail_queries"] > 0
     assert np.array_equal(i0, i1) and np.array_equal(d0, d1)
+
+
+def run_both_precisions(P, Q, k, h, **opts):
+    """One tree with BF16 screen data; the same queries scored with the
+    float32 kernel only and with the screen."""
+    opts.setdefault("tail_queries", 0)
+    tree = bkd.bkd_build(P, h, precision=1, **opts)
+    try:
+        bkd.bkd_set_option(tree, "precision", 0)
+        i0, d0 = bkd.bkd_query(tree, Q, k)
+        bkd.bkd_set_option(tree, "precision", 1)
+        i1, d1 = bkd.bkd_query(tree, Q, k)
+        st = {s: bkd.bkd_get_stat(tree, s) for s in bkd.STATS}
+    finally:
+        bkd.bkd_free(tree)
+    return i0, d0, i1, d1, st
+
+
+@pytest.mark.parametrize("d,k", [(2, 4), (3, 10), (10, 10), (10, 1), (10, 31),
+                                 (16, 10), (17, 10), (27, 5), (32, 10)])
+def test_bf16_screen_is_bit_identical(d, k):
+    """The BF16 tensor-core screen only skips points that provably cannot
+    enter a list; survivors are scored in float32, so results equal the
+    float32 path bit for bit."""
+    params = workloads.mixture_params(d, 16, 0.02, 0.2, 0)
+    P = workloads.mixture(60000, params, 1)
+    Q = workloads.mixture(4000, params, 2)
+    i0, d0, i1, d1, st = run_both_precisions(P, Q, k, 7)
+    assert np.array_equal(i0, i1) and np.array_equal(d0, d1)
+    assert st["screen_pairs"] > 0
+    assert st["screen_kept"] < 0.2 * st["screen_pairs"]
+    check(P, Q, k, i1, d1, oracle.brute_knn(P, Q[:600], k),
+          rows=np.arange(600))
+
+
+def test_bf16_screen_with_ties_and_duplicates():
+    rng = np.random.default_rng(4)
+    P = rng.integers(0, 6, (20000, 4)).astype(np.float32)
+    Q = (rng.integers(-2, 14, (2000, 4)) * 0.5).astype(np.float32)
+    i0, d0, i1, d1, _ = run_both_precisions(P, Q, 10, 6)
+    assert np.array_equal(i0, i1) and np.array_equal(d0, d1)
+    Pd = workloads.with_duplicates(workloads.uniform(30000, 10, 5), 0.05, 2)
+    Qd = np.concatenate([Pd[::50], workloads.uniform(1000, 10, 6)])
+    i0, d0, i1, d1, _ = run_both_precisions(Pd, Qd, 10, 7)
+    assert np.array_equal(i0, i1) and np.array_equal(d0, d1)
+    check(Pd, Qd, 10, i1, d1, oracle.brute_knn(Pd, Qd, 10))
+
+
+def test_bf16_screen_uniform_65536():
+    w = workloads.UNIFORM_64K
+    P, Q = w.points(), w.queries()
+    i0, d0, i1, d1, st = run_both_precisions(P, Q, w.k, w.height,
+                                             tail_queries=-1)
+    assert np.array_equal(i0, i1) and np.array_equal(d0, d1)
+    check(P, Q, w.k, i1, d1, oracle.brute_knn(P, Q, w.k))
+    print("screen kept fraction", st["screen_kept"] / st["screen_pairs"])
+
+
+def test_bf16_screen_option_errors():
+    P = workloads.uniform(5000, 4, 1)
+    tree = bkd.bkd_build(P, 4)
+    with pytest.raises(bkd.BkdError) as e:
+        bkd.bkd_set_option(tree, "precision", 1)
+    assert e.value.code == bkd.BKD_EINVAL
+    bkd.bkd_free(tree)
+    with pytest.raises(bkd.BkdError) as e:
+        bkd.bkd_build(P, 4, precision=1, chunks=2)
+    assert e.value.code == bkd.BKD_EUNSUPPORTED
