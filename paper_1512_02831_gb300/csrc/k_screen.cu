@@ -20,7 +20,8 @@
 // D32 >= D (1 - g) - eta, g = (d+3) 2^-24, eta = 2^-120.  Hence a point can
 // only enter the list (D32 < bound) if
 //   s < (sqrt((bound + eta) / (1 - g)) + A_q + B_max)^2 + E,
-// evaluated once per (query, leaf) in binary64 and rounded up to float.  Kept
+// evaluated once per (query, leaf) in float32 with every operation rounded
+// toward the larger threshold (divisors toward the smaller).  Kept
 // points are scored with the exact float32 chain of the leaf kernel and
 // inserted with the same strict rule, so the lists -- and the answers -- are
 // bit for bit those of the float32 path.
@@ -28,6 +29,7 @@
 
 #include "bkd.h"
 #include "bkd_internal.h"
+#include "k_leaf.cuh"
 
 namespace bkd {
 namespace {
@@ -83,11 +85,66 @@ struct ScreenArgs {
   int kh;                 // 16-dimension halves
 };
 
-}  // namespace
-}  // namespace bkd
-
-namespace bkd {
-namespace {
+// Per-warp setup of the warp's 16 query rows of item w: query ids, the
+// candidate lists (copied into shared memory), the bf16 offsets (A operand
+// record) and the screen thresholds.  Lanes 0..15, row = 16 * warp + lane.
+template <int KH>
+__device__ __forceinline__ void setup_rows(
+    const DevTree& t, const ScreenArgs& sc, const Item& w, int warp, int lane,
+    const uint32_t* __restrict__ act, const float* __restrict__ qpad,
+    const float* __restrict__ lst_d, const uint32_t* __restrict__ lst_i,
+    int K, float* s_ld, uint32_t* s_li, uint32_t* s_rows, float* s_thr,
+    uint32_t* s_q) {
+  if (lane >= 16) return;
+  const float inf = __int_as_float(0x7f800000);
+  const int r = warp * 16 + lane;
+  uint32_t* rec = s_rows + (size_t)warp * KH * 16 * 8;
+  float thr = -inf;  // empty rows keep nothing
+  if (r < w.count) {
+    const uint32_t q = act[w.start + r];
+    s_q[r] = q;
+    for (int j = 0; j < K; ++j) {
+      s_ld[r * K + j] = lst_d[(size_t)q * K + j];
+      s_li[r * K + j] = lst_i[(size_t)q * K + j];
+    }
+    const float* qp = qpad + (size_t)q * t.Dp;
+    const float* c = sc.center + (size_t)w.leaf * t.d;
+    float qn = 0.f, ss = 0.f;  // |v^|^2 rounded to nearest / upward
+    for (int h = 0; h < KH; ++h)
+      for (int j = 0; j < 8; ++j) {
+        const int k0 = 16 * h + 2 * j;
+        const float a0 = k0 < t.d ? __fsub_rn(qp[k0], c[k0]) : 0.f;
+        const float a1 = k0 + 1 < t.d ? __fsub_rn(qp[k0 + 1], c[k0 + 1]) : 0.f;
+        const uint32_t wd = pack_bf16(a0, a1);
+        rec[(h * 16 + lane) * 8 + (j < 4 ? 2 * j : 2 * (j - 4) + 1)] = wd;
+        const float v0 = bf16_lo(wd), v1 = bf16_hi(wd);
+        qn = __fmaf_rn(v0, v0, qn);
+        qn = __fmaf_rn(v1, v1, qn);
+        ss = __fmaf_ru(v0, v0, ss);
+        ss = __fmaf_ru(v1, v1, ss);
+      }
+    const float bound = s_ld[r * K + K - 1];
+    if (isinf(bound)) {
+      thr = inf;
+    } else {
+      // the bound of the header comment, every step rounded upward
+      // (divisors downward) so the float result is never too small
+      const float rho = 0x1p-9f * 1.0001f;
+      const float rr = __fdiv_ru(rho, __fsub_rd(1.f, rho));
+      const float one_m_g = __fsub_rd(1.f, (float)(t.d + 3) * 0x1p-24f);
+      const float aq = __fadd_ru(__fmul_ru(rr, __fsqrt_ru(ss)), 0x1p-123f);
+      const float R =
+          __fsqrt_ru(__fdiv_ru(__fadd_ru(bound, 0x1p-120f), one_m_g));
+      const float Rb = __fadd_ru(__fadd_ru(R, aq), sc.bmax[w.leaf]);
+      const float E = __fmul_ru(0x1p-15f, __fadd_ru(ss, sc.pnmax[w.leaf]));
+      thr = __fsub_ru(__fadd_ru(__fmul_ru(Rb, Rb), E), qn);
+    }
+  } else {
+    for (int h = 0; h < KH; ++h)
+      for (int j = 0; j < 8; ++j) rec[(h * 16 + lane) * 8 + j] = 0u;
+  }
+  s_thr[r] = thr;
+}
 
 // Shared memory of one CTA (lcap8 = slots per leaf rounded up to 8):
 //   words  KH * lcap8 * 8 u32   the leaf's packed bf16 offsets
@@ -96,6 +153,9 @@ namespace {
 //   rows   4 * KH * 16 * 8 u32  each warp's 16 query offsets (A operand)
 //   thr    64 f32               screen thresholds (minus |v^|^2)
 //   qid    64 u32               query ids
+// A CTA takes a contiguous range of items; consecutive items of the same
+// leaf reuse the staged leaf, a new leaf arrives by two TMA bulk copies
+// (offsets, norms) on one mbarrier while the warps set up their rows.
 template <int KH>
 __global__ void __launch_bounds__(kScrThreads)
     screen_kernel(DevTree t, ScreenArgs sc, const Item* __restrict__ items,
@@ -104,6 +164,7 @@ __global__ void __launch_bounds__(kScrThreads)
                   const float* __restrict__ qpad, float* __restrict__ lst_d,
                   uint32_t* __restrict__ lst_i, int K, int lcap8) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full;
   uint32_t* s_words = reinterpret_cast<uint32_t*>(smem);
   float* s_pn = reinterpret_cast<float*>(s_words + (size_t)KH * lcap8 * 8);
   float* s_ld = s_pn + lcap8;
@@ -115,76 +176,73 @@ __global__ void __launch_bounds__(kScrThreads)
   const int hi = item_hi >= 0 ? item_hi : ctr->n_items;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, tq = lane & 3;
-  const unsigned full = 0xffffffffu;
+  const unsigned full_mask = 0xffffffffu;
+  const int lcap = (int)t.lcap;
+  const uint32_t bar = smem_u32(&full);
+  // slots past the leaf: zero offsets, +inf norms (never kept)
+  for (int h = 0; h < KH; ++h)
+    for (int i = lcap * 8 + tid; i < lcap8 * 8; i += kScrThreads)
+      s_words[(size_t)h * lcap8 * 8 + i] = 0u;
+  for (int i = lcap + tid; i < lcap8; i += kScrThreads) s_pn[i] = inf;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  const int n = hi - item_lo;
+  const int per = (n + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int it0 = item_lo + (int)blockIdx.x * per;
+  const int it1 = min(hi, it0 + per);
+  int staged = -1;
+  uint32_t parity = 0;
   unsigned long long kept = 0;
-  for (int it = item_lo + blockIdx.x; it < hi; it += gridDim.x) {
+  for (int it = it0; it < it1; ++it) {
     const Item w = items[it];
-    const int leaf = w.leaf;
-    const int npt = t.leaf_cnt[leaf];
-    const int ntile = (npt + 7) >> 3;
-    __syncthreads();  // the previous item no longer reads shared memory
-    for (int h = 0; h < KH; ++h) {
-      const uint4* src = reinterpret_cast<const uint4*>(
-          sc.words + (((size_t)leaf * KH + h) * t.lcap) * 8);
-      uint4* dst = reinterpret_cast<uint4*>(s_words + (size_t)h * lcap8 * 8);
-      const int n_src = (int)t.lcap * 2, n_dst = lcap8 * 2;
-      for (int i = tid; i < n_dst; i += kScrThreads)
-        dst[i] = i < n_src ? src[i] : make_uint4(0u, 0u, 0u, 0u);
-    }
-    for (int i = tid; i < lcap8; i += kScrThreads)
-      s_pn[i] = i < t.lcap ? sc.pn[(size_t)leaf * t.lcap + i] : inf;
-    if (tid < 64) {
-      const int r = tid;
-      uint32_t* rec = s_rows + (size_t)(r >> 4) * KH * 16 * 8;
-      float thr = -inf;  // empty rows keep nothing
-      if (r < w.count) {
-        const uint32_t q = act[w.start + r];
-        s_q[r] = q;
-        for (int j = 0; j < K; ++j) {
-          s_ld[r * K + j] = lst_d[(size_t)q * K + j];
-          s_li[r * K + j] = lst_i[(size_t)q * K + j];
-        }
-        const float* qp = qpad + (size_t)q * t.Dp;
-        const float* c = sc.center + (size_t)leaf * t.d;
-        float qn = 0.f;
-        double ss = 0.0;
+    const bool fresh = w.leaf != staged;
+    if (fresh) {
+      __syncthreads();  // every warp is done with the previous leaf
+      if (tid == 0) {
+        async_proxy_fence();
+        const uint32_t wbytes = (uint32_t)lcap * 32u;
+        const uint32_t pbytes = (uint32_t)lcap * 4u;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::
+                         "r"(bar),
+                     "r"((uint32_t)KH * wbytes + pbytes)
+                     : "memory");
         for (int h = 0; h < KH; ++h)
-          for (int j = 0; j < 8; ++j) {
-            const int k0 = 16 * h + 2 * j;
-            const float a0 = k0 < t.d ? __fsub_rn(qp[k0], c[k0]) : 0.f;
-            const float a1 =
-                k0 + 1 < t.d ? __fsub_rn(qp[k0 + 1], c[k0 + 1]) : 0.f;
-            const uint32_t wd = pack_bf16(a0, a1);
-            rec[(h * 16 + (r & 15)) * 8 + (j < 4 ? 2 * j : 2 * (j - 4) + 1)] =
-                wd;
-            const float v0 = bf16_lo(wd), v1 = bf16_hi(wd);
-            qn = __fmaf_rn(v0, v0, qn);
-            qn = __fmaf_rn(v1, v1, qn);
-            ss += (double)v0 * v0 + (double)v1 * v1;
-          }
-        const float bound = s_ld[r * K + K - 1];
-        if (isinf(bound)) {
-          thr = inf;
-        } else {
-          const double rho = 0x1p-9 * (1.0 + 1e-4);
-          const double gam = (t.d + 3) * 0x1p-24;
-          const double aq =
-              rho / (1.0 - rho) * sqrt(ss) + 0x1p-126 * sqrt((double)t.d);
-          const double R =
-              sqrt(((double)bound + 0x1p-120) / (1.0 - gam)) * (1.0 + 0x1p-40) +
-              aq;
-          const double Rb = R + (double)sc.bmax[leaf];
-          const double T = Rb * Rb * (1.0 + 0x1p-40) +
-                           0x1p-15 * ((double)qn + (double)sc.pnmax[leaf]);
-          thr = __double2float_ru(T - (double)qn);
-        }
-      } else {
-        for (int h = 0; h < KH; ++h)
-          for (int j = 0; j < 8; ++j) rec[(h * 16 + (r & 15)) * 8 + j] = 0u;
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::"
+              "bytes [%0], [%1], %2, [%3];" ::"r"(
+                  smem_u32(s_words + (size_t)h * lcap8 * 8)),
+              "l"(__cvta_generic_to_global(
+                  sc.words + (((size_t)w.leaf * KH + h) * lcap) * 8)),
+              "r"(wbytes), "r"(bar)
+              : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::"
+            "bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(s_pn)),
+            "l"(__cvta_generic_to_global(sc.pn + (size_t)w.leaf * lcap)),
+            "r"(pbytes), "r"(bar)
+            : "memory");
       }
-      s_thr[r] = thr;
+      staged = w.leaf;
     }
-    __syncthreads();
+    setup_rows<KH>(t, sc, w, warp, lane, act, qpad, lst_d, lst_i, K, s_ld,
+                   s_li, s_rows, s_thr, s_q);
+    __syncwarp();
+    if (fresh) {
+      const bool ok = mbar_wait(bar, parity);
+      parity ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+          atomicOr(&ctr->err, kErrTimeout);
+          mbar_wait(bar, parity ^ 1u);  // bounded: let the copy land
+        }
+        return;
+      }
+    }
+    const int npt = t.leaf_cnt[w.leaf];
+    const int ntile = (npt + 7) >> 3;
     const int wr0 = warp * 16;
     if (wr0 < w.count) {  // warp-uniform
       uint32_t a[KH][4];
@@ -217,7 +275,7 @@ __global__ void __launch_bounds__(kScrThreads)
         y[3] = __fmaf_rn(-2.f, acc[3], p2.y);
         const bool keep =
             fminf(y[0], y[1]) < thr_g || fminf(y[2], y[3]) < thr_g8;
-        if (__any_sync(full, keep)) {
+        if (__any_sync(full_mask, keep)) {
           // exact rescoring; the four lanes of a group share rows g and
           // g + 8, so they take turns
           for (int turn = 0; turn < 4; ++turn) {
@@ -229,7 +287,7 @@ __global__ void __launch_bounds__(kScrThreads)
                 if (y[j] < (j < 2 ? thr_g : thr_g8) && col < npt) {
                   ++kept;
                   const uint32_t slot =
-                      (uint32_t)((int64_t)leaf * t.lcap + col);
+                      (uint32_t)((int64_t)w.leaf * t.lcap + col);
                   const float dv = exact_dist(qpad + (size_t)s_q[row] * t.Dp,
                                               t.pts, t.Dp, slot);
                   float* ld = s_ld + row * K;
@@ -252,14 +310,18 @@ __global__ void __launch_bounds__(kScrThreads)
         }
       }
     }
-    __syncthreads();
-    if (tid < w.count) {
-      const uint32_t q = s_q[tid];
-      for (int j = 0; j < K; ++j) {
-        lst_d[(size_t)q * K + j] = s_ld[tid * K + j];
-        lst_i[(size_t)q * K + j] = s_li[tid * K + j];
+    __syncwarp();
+    if (lane < 16) {  // write the warp's rows back
+      const int r = wr0 + lane;
+      if (r < w.count) {
+        const uint32_t q = s_q[r];
+        for (int j = 0; j < K; ++j) {
+          lst_d[(size_t)q * K + j] = s_ld[r * K + j];
+          lst_i[(size_t)q * K + j] = s_li[r * K + j];
+        }
       }
     }
+    __syncwarp();
   }
   if (kept) atomicAdd(&ctr->screen_kept, kept);
 }
