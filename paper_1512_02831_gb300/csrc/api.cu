@@ -433,19 +433,20 @@ int build_impl(const float* P, int64_t n, int d, int height,
                        "the BF16 screen needs a tree resident in device "
                        "memory"));
     const int kh = screen_halves(d);
+    const int64_t stride = screen_stride(H.lcap);
     std::vector<uint32_t> words;
     std::vector<float> pn, center, bmax, pnmax;
     try {
-      words.resize((size_t)L * kh * H.lcap * 8);
-      pn.resize((size_t)slots);
+      words.resize((size_t)L * kh * stride * 8);
+      pn.resize((size_t)L * stride);
       center.resize((size_t)L * d);
       bmax.resize(L);
       pnmax.resize(L);
     } catch (...) {
       return bail(fail(BKD_ENOMEM, "host staging of the screen data"));
     }
-    fill_screen(Ph, H, words.data(), pn.data(), center.data(), bmax.data(),
-                pnmax.data());
+    fill_screen(Ph, H, stride, words.data(), pn.data(), center.data(),
+                bmax.data(), pnmax.data());
     if (cudaMalloc(&t->d_scr_words, words.size() * 4) != cudaSuccess ||
         cudaMalloc(&t->d_scr_pn, pn.size() * 4) != cudaSuccess ||
         cudaMalloc(&t->d_scr_center, center.size() * 4) != cudaSuccess ||
@@ -464,7 +465,8 @@ int build_impl(const float* P, int64_t n, int d, int height,
                    cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(fail(BKD_ECUDA, "upload of the screen data failed"));
     t->screen.words = t->d_scr_words;
-    t->screen.pn = t->d_scr_pn;
+    t->screen.hpn = t->d_scr_pn;
+    t->screen.stride = stride;
     t->screen.center = t->d_scr_center;
     t->screen.bmax = t->d_scr_bmax;
     t->screen.pnmax = t->d_scr_pnmax;
@@ -513,7 +515,7 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   const int Dp = D.Dp;
   cudaStream_t s = t->stream;
   const int64_t L = t->n_leaves;
-  const int64_t max_items = m / kPipeTile + L + 1;
+  const int64_t max_items = m / kScreenTile + L + 1;  // kScreenTile <= kPipeTile
   CU(t->qpad.ensure(m * Dp));
   CU(t->lst_d.ensure(m * K));
   CU(t->lst_i.ensure(m * K));
@@ -552,11 +554,17 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   // query into its next leaf), bucketing by leaf, ProcessAllBuffers.
   int round = 0;
   for (;;) {
+    // a round that ends in the BF16 screen (the first round stays on the
+    // float32 kernel: every list is still empty there) buckets its queries
+    // into the screen's smaller items
+    const bool screened =
+        !t->chunked && t->precision == 1 && round > 0 && screen_max > 0;
     CU(cudaMemsetAsync(t->cnt.p, 0, sizeof(int32_t) * L, s));
     CU(launch_find_leaf(D, t->qpad.p, act, n_act, t->state.p, t->lst_d.p, K,
                         t->leaf_of.p, t->cnt.p, s));
     t->st_launches += 1;
-    CU(launch_bucket(t->leaf_of.p, act, n_act, (int)L, kPipeTile,
+    CU(launch_bucket(t->leaf_of.p, act, n_act, (int)L,
+                     screened ? kScreenTile : kPipeTile,
                      t->d_leaf_cnt, t->cnt.p, t->off.p, t->cursor.p,
                      t->toff.p, t->items.p, nxt, t->d_ctr, s));
     t->st_launches += 3;
@@ -592,14 +600,12 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
     }
     t->st_rounds += 1;
     t->st_visits += n_next;
-    if (!t->chunked && t->precision == 1 && round > 0 && screen_max > 0) {
-      // BF16 tensor-core screen + exact float32 rescoring (the first round
-      // stays on the float32 kernel: every list is still empty there)
-      const int grid = std::min(screen_max, n_items);
+    if (screened) {
+      // BF16 tensor-core screen + exact float32 rescoring
       cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
       if (e0) cudaEventRecord(e0, s);
       CU(launch_screen(D, t->screen, t->items.p, 0, n_items, t->d_ctr, nxt,
-                       t->qpad.p, t->lst_d.p, t->lst_i.p, K, grid, s));
+                       t->qpad.p, t->lst_d.p, t->lst_i.p, K, screen_max, s));
       if (e1) cudaEventRecord(e1, s);
       if (e0 && e1) t->screen_ev.push_back({e0, e1});
       t->st_screen_pairs += (double)t->h_ctr->pairs;  // whole round

@@ -125,17 +125,26 @@ int leaf_kernel_grid(int Dp, int cap, int sm_count);
 // BF16 screen data on the device (see fill_screen).
 struct ScreenData {
   const uint32_t* words = nullptr;
-  const float* pn = nullptr;
+  const float* hpn = nullptr;  // -pn / 2 per slot
   const float* center = nullptr;
   const float* bmax = nullptr;
   const float* pnmax = nullptr;
+  int64_t stride = 0;  // slots per leaf in words / hpn
   int kh = 0;
 };
 
+// Queries per work item of a screened round (up to four 8-query n-blocks
+// of one m16n8k16 tile column set, one warp per item).
+constexpr int kScreenTile = 32;
+// Slots per leaf of the screen arrays: the leaf capacity rounded up to the
+// 32-point super-tile (two 16-point m-tiles).
+inline int64_t screen_stride(int64_t lcap) { return (lcap + 31) / 32 * 32; }
+
 // ProcessAllBuffers with the BF16 tensor-core screen and exact float32
-// rescoring (k_screen.cu); same items and results as launch_leaf on a
-// resident tree.  screen_grid: resident CTAs (0 if the shared memory does
-// not fit).
+// rescoring (k_screen.cu); same candidate lists as launch_leaf on a
+// resident tree, over items of at most kScreenTile queries.  screen_grid:
+// resident CTAs (0 if the shared memory does not fit or the leaf capacity
+// is out of range).
 int screen_grid(int kh, int64_t lcap, int K, int sm_count);
 cudaError_t launch_screen(const DevTree& t, const ScreenData& sd,
                           const Item* items, int item_lo, int item_hi,
@@ -200,14 +209,16 @@ void fill_boxes(const float* P, const HostTree& t, float* box);
 // k-halves of 16 dimensions the BF16 screen uses (1 for d <= 16, else 2).
 inline int screen_halves(int d) { return d <= 16 ? 1 : 2; }
 
-// Data of the BF16 screen, per leaf: the centre c (midpoint of the leaf's
-// bounding box), every point's offset bf16(fl(x - c)) packed as bf16 pairs
-// (8 words per point and k-half, in m16n8k16 B-fragment order, see
-// build.cpp), its squared norm pn (binary64 sum rounded to float; +inf for
-// padding slots), and per leaf bmax (upper bound on the offset rounding
-// error norm) and pnmax (largest pn).
-void fill_screen(const float* P, const HostTree& t, uint32_t* words,
-                 float* pn, float* center, float* bmax, float* pnmax);
+// Data of the BF16 screen, per leaf (stride slots per leaf, see
+// screen_stride): the centre c (midpoint of the leaf's bounding box), every
+// point's offset bf16(fl(x - c)) packed as bf16 pairs (8 words per point and
+// k-half, in m16n8k16 A-fragment order, see build.cpp), hpn = -pn / 2 with pn
+// its squared norm (binary64 sum rounded to float; hpn = -inf and zero
+// words for padding slots), and per leaf bmax (upper bound on the offset
+// rounding error norm) and pnmax (largest pn).
+void fill_screen(const float* P, const HostTree& t, int64_t stride,
+                 uint32_t* words, float* hpn, float* center, float* bmax,
+                 float* pnmax);
 
 // Writes the quads and orig arrays for leaves [leaf_lo_id, leaf_hi_id)
 // into host buffers (`pts` and `orig` point at leaf leaf_lo_id's first slot).

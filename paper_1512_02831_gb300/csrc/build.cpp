@@ -224,11 +224,11 @@ inline float bf16_to_float(uint16_t h) {
 
 }  // namespace
 
-void fill_screen(const float* P, const HostTree& t, uint32_t* words,
-                 float* pn, float* center, float* bmax, float* pnmax) {
+void fill_screen(const float* P, const HostTree& t, int64_t stride,
+                 uint32_t* words, float* hpn, float* center, float* bmax,
+                 float* pnmax) {
   const int d = t.d;
   const int kh = screen_halves(d);
-  const int64_t lcap = t.lcap;
   const int64_t L = (int64_t)1 << t.h;
   // BF16 rounding error (relative, round to nearest) with margin, and its
   // effect on a norm: |w_hat - w| <= rho |w|, |w| <= |w_hat| / (1 - rho).
@@ -248,7 +248,7 @@ void fill_screen(const float* P, const HostTree& t, uint32_t* words,
     }
     double wmax = 0.0;
     float pmax = 0.f;
-    for (int64_t u = 0; u < lcap; ++u) {
+    for (int64_t u = 0; u < stride; ++u) {
       uint16_t hv[32] = {0};
       float pv = INFINITY;
       if (u < cnt) {
@@ -263,18 +263,24 @@ void fill_screen(const float* P, const HostTree& t, uint32_t* words,
         wmax = std::max(wmax, std::sqrt(ss));
         pmax = std::max(pmax, pv);
       }
-      pn[leaf * lcap + u] = pv;
+      // 32-point super-tiles S = u / 32 of two 16-point m-tiles a; in tile
+      // a the point is row 8 r + g (r = 0, 1; g = 0..7).  Lane (g, t) of a
+      // warp loads, with one 16-byte load per row half r, words (t, t + 4)
+      // of row 8 r + g of both tiles: its m16n8k16 A fragments.  hpn holds
+      // (a, r) = (0,0) (0,1) (1,0) (1,1) of row g as one float4.
+      const int64_t S = u / 32, a = (u % 32) / 16, r = (u % 16) / 8,
+                    g = u % 8;
+      hpn[leaf * stride + (S * 8 + g) * 4 + 2 * a + r] = -0.5f * pv;  // exact
       for (int h = 0; h < kh; ++h) {
-        // 8 words per point and k-half, word j = dims (2j, 2j+1) of the
-        // half, stored in the order w0 w4 w1 w5 w2 w6 w3 w7 so that lane
-        // (g, t) of an m16n8k16 B fragment reads words t, t+4 with one
-        // 8-byte load.
-        uint32_t* rec = words + ((leaf * kh + h) * lcap + u) * 8;
-        for (int j = 0; j < 8; ++j) {
-          const int k0 = 16 * h + 2 * j;
-          const uint32_t wj = (uint32_t)hv[k0] | ((uint32_t)hv[k0 + 1] << 16);
-          rec[j < 4 ? 2 * j : 2 * (j - 4) + 1] = wj;
-        }
+        // word j of a k-half = dims (2j, 2j+1) of the half
+        uint32_t* blk = words + (leaf * kh + h) * stride * 8 +
+                        ((S * 2 + r) * 8 + g) * 16 + 2 * a;
+        for (int tq = 0; tq < 4; ++tq)
+          for (int e = 0; e < 2; ++e) {
+            const int k0 = 16 * h + 2 * (tq + 4 * e);
+            blk[tq * 4 + e] =
+                (uint32_t)hv[k0] | ((uint32_t)hv[k0 + 1] << 16);
+          }
       }
     }
     bmax[leaf] = std::nextafter((float)(rho / (1.0 - rho) * wmax + tiny),
