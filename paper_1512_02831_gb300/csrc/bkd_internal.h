@@ -15,8 +15,9 @@
 //   queries    float qpad[m * Dp], zero-padded rows.
 //   k-best     float lst_d[m * K], uint32 lst_i[m * K] (K = k + 1 entries,
 //              ascending, lst_d[q*K + K-1] is the pruning bound); slots.
-//   boxes      float box[(2^(h+1) - 1) * 2d]: tight bounding box of the
-//              points under each heap node (min row, then max row).
+//   boxes      float box[(2^(h+1) - 1) * 2Dp]: tight bounding box of the
+//              points under each heap node (min row, then max row, each
+//              Dp floats; padding dimensions hold [0, 0]).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -35,6 +36,8 @@ constexpr uint32_t kNoSlot = 0xffffffffu;
 
 // Compiled dimensions of the leaf kernel and compiled list capacities.
 constexpr int kDims[] = {2, 4, 6, 8, 10, 12, 16, 24, 32};
+// X(Dp) for every entry of kDims (kernel instantiation lists).
+#define BKD_DIMS(X) X(2) X(4) X(6) X(8) X(10) X(12) X(16) X(24) X(32)
 constexpr int kCaps[] = {2, 4, 8, 12, 16, 32};
 
 int padded_dim(int d);       // smallest compiled dimension >= d (0: none)
@@ -75,7 +78,7 @@ struct DevTree {
                            // chunked mode; used by the binary64 checks)
   const int64_t* orig;     // slot -> original index (device or mapped host)
   const int32_t* leaf_cnt; // points per leaf (device)
-  const float* box;        // per-node bounding boxes, 2d floats each (device)
+  const float* box;        // per-node bounding boxes, 2Dp floats each (device)
   int64_t n;
   int d, Dp, h;
   int64_t lcap;            // slots per leaf (multiple of 4)
@@ -202,8 +205,8 @@ const char* build_host_tree(const float* P, int64_t n, int d, int h,
                             HostTree* out);
 
 // Bounding box of the points under every heap node (2^(h+1) - 1 nodes):
-// box[v*2d .. v*2d+d) = per-dimension minimum, box[v*2d+d .. v*2d+2d) =
-// maximum.
+// box[v*2Dp .. v*2Dp+Dp) = per-dimension minimum, box[v*2Dp+Dp .. v*2Dp+2Dp)
+// = maximum; dimensions d..Dp-1 are [0, 0].
 void fill_boxes(const float* P, const HostTree& t, float* box);
 
 // k-halves of 16 dimensions the BF16 screen uses (1 for d <= 16, else 2).

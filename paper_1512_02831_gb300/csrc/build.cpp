@@ -176,15 +176,16 @@ void fill_quads(const float* P, const HostTree& t, int64_t leaf_a,
 }
 
 void fill_boxes(const float* P, const HostTree& t, float* box) {
-  const int d = t.d;
+  const int d = t.d, Dp = t.Dp;
   const int64_t L = (int64_t)1 << t.h;
   const int64_t first_leaf = L - 1;
   parallel_items(L, [&](int64_t leaf) {
-    float* lo = box + (first_leaf + leaf) * 2 * d;
-    float* hi = lo + d;
-    for (int i = 0; i < d; ++i) {
-      lo[i] = INFINITY;
-      hi[i] = -INFINITY;
+    float* lo = box + (first_leaf + leaf) * 2 * Dp;
+    float* hi = lo + Dp;
+    for (int i = 0; i < Dp; ++i) {
+      // padding dimensions: q_i = 0 lies in [0, 0] and adds nothing
+      lo[i] = i < d ? INFINITY : 0.f;
+      hi[i] = i < d ? -INFINITY : 0.f;
     }
     for (int64_t p = t.leaf_lo[leaf]; p < t.leaf_lo[leaf + 1]; ++p) {
       const float* x = P + t.perm[p] * d;
@@ -195,12 +196,12 @@ void fill_boxes(const float* P, const HostTree& t, float* box) {
     }
   });
   for (int64_t v = first_leaf - 1; v >= 0; --v) {
-    float* b = box + v * 2 * d;
-    const float* l = box + (2 * v + 1) * 2 * d;
-    const float* r = box + (2 * v + 2) * 2 * d;
-    for (int i = 0; i < d; ++i) {
+    float* b = box + v * 2 * Dp;
+    const float* l = box + (2 * v + 1) * 2 * Dp;
+    const float* r = box + (2 * v + 2) * 2 * Dp;
+    for (int i = 0; i < Dp; ++i) {
       b[i] = std::min(l[i], r[i]);
-      b[d + i] = std::max(l[d + i], r[d + i]);
+      b[Dp + i] = std::max(l[Dp + i], r[Dp + i]);
     }
   }
 }

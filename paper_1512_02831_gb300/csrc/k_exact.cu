@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(32 * kFbWarps)
     int node = kStart;
     for (;;) {
       const double kd = __shfl_sync(0xffffffffu, myd, k - 1);
-      node = next_leaf<F64Bound>(t, qp, node, cnt == k ? fmin(kd, seed) : seed);
+      node = next_leaf(t, F64Bound{qp}, qp, node,
+                       cnt == k ? fmin(kd, seed) : seed);
       if (node == kDone) break;
       // ---- scan the leaf
       const int leaf = node - first_leaf;

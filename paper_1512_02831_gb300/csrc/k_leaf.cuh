@@ -327,7 +327,7 @@ BKD_LEAF_DECLARE(12)
 BKD_LEAF_DECLARE(16)
 BKD_LEAF_DECLARE(32)
 
-#define BKD_LEAF_DIMS(X) X(2) X(4) X(6) X(8) X(10) X(12) X(16) X(24) X(32)
+#define BKD_LEAF_DIMS(X) BKD_DIMS(X)
 
 #define BKD_LEAF_CASE_LAUNCH(DIM)                                             \
   case DIM:                                                                   \

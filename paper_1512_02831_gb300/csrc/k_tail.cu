@@ -50,10 +50,12 @@ __global__ void __launch_bounds__(kTailWarps * 32)
       myi = lst_i[(size_t)q * K + lane];
     }
     float bound = __shfl_sync(full, myd, K - 1);
+    F32Bound<D> bx;
+    bx.load(qp);
     // state holds the query's pending leaf: scan it, then walk on
     int node = state[q];
-    if (node == kStart) node = next_leaf<F32Bound>(t, qp, node, bound);
-    for (; node != kDone; node = next_leaf<F32Bound>(t, qp, node, bound)) {
+    if (node == kStart) node = next_leaf(t, bx, qp, node, bound);
+    for (; node != kDone; node = next_leaf(t, bx, qp, node, bound)) {
       const int leaf = node - first_leaf;
       const int np = t.leaf_cnt[leaf];
       const int nq = (np + 3) >> 2;

@@ -39,20 +39,24 @@ __global__ void init_kernel(const float* __restrict__ Q, int64_t m, int d,
   if (bad) atomicOr(&ctr->err, kErrNonFinite);
 }
 
-__global__ void find_leaf_kernel(DevTree t, const float* __restrict__ qpad,
-                                 const uint32_t* __restrict__ act, int n_act,
-                                 int32_t* __restrict__ state,
-                                 const float* __restrict__ lst_d, int K,
-                                 int32_t* __restrict__ leaf_of,
-                                 int32_t* __restrict__ cnt) {
+template <int D>
+__global__ void __launch_bounds__(256)
+    find_leaf_kernel(DevTree t, const float* __restrict__ qpad,
+                     const uint32_t* __restrict__ act, int n_act,
+                     int32_t* __restrict__ state,
+                     const float* __restrict__ lst_d, int K,
+                     int32_t* __restrict__ leaf_of,
+                     int32_t* __restrict__ cnt) {
   const int pos = blockIdx.x * blockDim.x + threadIdx.x;
   if (pos >= n_act) return;
   const uint32_t q = act[pos];
-  const float* qp = qpad + (size_t)q * t.Dp;
+  const float* qp = qpad + (size_t)q * D;
   const int node = state[q];
   const float bound = node == kStart ? __int_as_float(0x7f800000)
                                      : lst_d[(size_t)q * K + (K - 1)];
-  const int next = next_leaf<F32Bound>(t, qp, node, bound);
+  F32Bound<D> bx;
+  bx.load(qp);
+  const int next = next_leaf(t, bx, qp, node, bound);
   state[q] = next;
   if (next == kDone) {
     leaf_of[pos] = -1;
@@ -255,9 +259,14 @@ cudaError_t launch_find_leaf(const DevTree& t, const float* qpad,
                              const float* lst_d, int K, int32_t* leaf_of,
                              int32_t* cnt, cudaStream_t s) {
   if (n_act == 0) return cudaSuccess;
-  find_leaf_kernel<<<blocks(n_act, 256), 256, 0, s>>>(
-      t, qpad, act, n_act, state, lst_d, K, leaf_of, cnt);
-  return cudaGetLastError();
+#define BKD_FIND_CASE(DIM)                                          \
+  case DIM:                                                         \
+    find_leaf_kernel<DIM><<<blocks(n_act, 256), 256, 0, s>>>(       \
+        t, qpad, act, n_act, state, lst_d, K, leaf_of, cnt);        \
+    return cudaGetLastError();
+  switch (t.Dp) { BKD_DIMS(BKD_FIND_CASE) default: break; }
+#undef BKD_FIND_CASE
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_bucket(const int32_t* leaf_of, const uint32_t* act,

@@ -37,16 +37,35 @@ namespace bkd {
 
 __device__ __forceinline__ int heap_level(int v) { return 31 - __clz(v + 1); }
 
+// float32 pruning bound of one query; D = Dp (compile time), the query in
+// registers and each box read as 2D/4 16-byte loads.  Padding dimensions
+// (q_i = 0, box [0, 0]) add fma(0, 0, B) = B.
+template <int D>
 struct F32Bound {
   using T = float;
+  float x[D];
+  __device__ void load(const float* __restrict__ qp) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) x[i] = qp[i];
+  }
   __device__ static bool keep(float b, float bound) { return b < bound; }
-  __device__ static float box(const float* __restrict__ box, int d,
-                              const float* __restrict__ qp, int node) {
-    const float* lo = box + (size_t)node * 2 * d;
-    const float* hi = lo + d;
+  __device__ float box(const DevTree& t, int node) const {
+    static_assert(D % 2 == 0, "a box row pair is a whole number of float4");
+    const float4* p =
+        reinterpret_cast<const float4*>(t.box + (size_t)node * 2 * D);
+    float f[2 * D];
+#pragma unroll
+    for (int j = 0; j < D / 2; ++j) {
+      const float4 v = __ldg(p + j);
+      f[4 * j] = v.x;
+      f[4 * j + 1] = v.y;
+      f[4 * j + 2] = v.z;
+      f[4 * j + 3] = v.w;
+    }
     float b = 0.f;
-    for (int i = 0; i < d; ++i) {
-      const float q = qp[i], l = __ldg(lo + i), u = __ldg(hi + i);
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      const float q = x[i], l = f[i], u = f[D + i];
       const float o = q < l ? __fsub_rn(l, q) : (q > u ? __fsub_rn(q, u) : 0.f);
       b = i == 0 ? __fmul_rn(o, o) : __fmaf_rn(o, o, b);
     }
@@ -58,15 +77,16 @@ struct F32Bound {
   }
 };
 
+// binary64 pruning bound of one query (the oracle's sequence).
 struct F64Bound {
   using T = double;
+  const float* qp;
   __device__ static bool keep(double b, double bound) { return b <= bound; }
-  __device__ static double box(const float* __restrict__ box, int d,
-                               const float* __restrict__ qp, int node) {
-    const float* lo = box + (size_t)node * 2 * d;
-    const float* hi = lo + d;
+  __device__ double box(const DevTree& t, int node) const {
+    const float* lo = t.box + (size_t)node * 2 * t.Dp;
+    const float* hi = lo + t.Dp;
     double b = 0.0;
-    for (int i = 0; i < d; ++i) {
+    for (int i = 0; i < t.d; ++i) {
       const double q = qp[i], l = __ldg(lo + i), u = __ldg(hi + i);
       const double o = q < l ? __dsub_rn(l, q) : (q > u ? __dsub_rn(q, u) : 0.0);
       b = __dadd_rn(b, __dmul_rn(o, o));
@@ -80,34 +100,39 @@ struct F64Bound {
 };
 
 // Last leaf, in depth-first order, of the subtree of u (always the far side).
-__device__ __forceinline__ int last_leaf(const float* __restrict__ split,
-                                         int h, int d,
+// The split dimension of level l is l mod d, stepped incrementally.
+__device__ __forceinline__ int last_leaf(const DevTree& t,
                                          const float* __restrict__ qp, int u) {
-  const int first_leaf = (1 << h) - 1;
-  for (int level = heap_level(u); u < first_leaf; ++level)
-    u = 2 * u + (qp[level % d] < __ldg(split + u) ? 2 : 1);
+  const int first_leaf = (1 << t.h) - 1;
+  int dim = heap_level(u) % t.d;
+  while (u < first_leaf) {
+    u = 2 * u + (qp[dim] < __ldg(t.split + u) ? 2 : 1);
+    dim = dim + 1 == t.d ? 0 : dim + 1;
+  }
   return u;
 }
 
 // Deepest unvisited far child on the path of leaf `node` that survives
 // pruning, or -1.
 template <class B>
-__device__ __forceinline__ int climb(const DevTree& t,
+__device__ __forceinline__ int climb(const DevTree& t, const B& bx,
                                      const float* __restrict__ qp, int node,
                                      typename B::T bound) {
   const int h = t.h, d = t.d;
   if (node == 0) return -1;
   const unsigned path = (unsigned)(node + 1);
-  for (int level = h - 1; level >= 0; --level) {
+  int dim = (h - 1) % d;
+  for (int level = h - 1; level >= 0;
+       --level, dim = dim == 0 ? d - 1 : dim - 1) {
     const int anc = (int)(path >> (h - level)) - 1;
     const float sv = __ldg(t.split + anc);
-    const float qs = qp[level % d];
+    const float qs = qp[dim];
     const bool near_left = qs < sv;
     const bool went_left = ((path >> (h - 1 - level)) & 1u) == 0u;
     if (went_left != near_left) continue;  // far child already on the path
     if (!B::keep(B::plane(qs, sv), bound)) continue;  // box is beyond plane
     const int far = 2 * anc + (near_left ? 2 : 1);
-    if (B::keep(B::box(t.box, d, qp, far), bound)) return far;
+    if (B::keep(bx.box(t, far), bound)) return far;
   }
   return -1;
 }
@@ -115,32 +140,33 @@ __device__ __forceinline__ int climb(const DevTree& t,
 // Next leaf (heap index) to visit after leaf `node` (kStart: enter at the
 // root), or kDone.
 template <class B>
-__device__ __forceinline__ int next_leaf(const DevTree& t,
+__device__ __forceinline__ int next_leaf(const DevTree& t, const B& bx,
                                          const float* __restrict__ qp,
                                          int node, typename B::T bound) {
   const int first_leaf = (1 << t.h) - 1;
   int cand;
   if (node == kStart) {
-    if (!B::keep(B::box(t.box, t.d, qp, 0), bound)) return kDone;
+    if (!B::keep(bx.box(t, 0), bound)) return kDone;
     cand = 0;
   } else {
-    cand = climb<B>(t, qp, node, bound);
+    cand = climb<B>(t, bx, qp, node, bound);
   }
   while (cand >= 0) {
     int v = cand;
+    int dim = heap_level(v) % t.d;
     while (v < first_leaf) {
-      const int level = heap_level(v);
-      const int nc = 2 * v + (qp[level % t.d] < __ldg(t.split + v) ? 1 : 2);
-      if (B::keep(B::box(t.box, t.d, qp, nc), bound)) {
+      const int nc = 2 * v + (qp[dim] < __ldg(t.split + v) ? 1 : 2);
+      dim = dim + 1 == t.d ? 0 : dim + 1;
+      if (B::keep(bx.box(t, nc), bound)) {
         v = nc;
       } else {  // the near child holds nothing better: skip its subtree
-        node = last_leaf(t.split, t.h, t.d, qp, nc);
+        node = last_leaf(t, qp, nc);
         v = -1;
         break;
       }
     }
     if (v >= 0) return v;
-    cand = climb<B>(t, qp, node, bound);
+    cand = climb<B>(t, bx, qp, node, bound);
   }
   return kDone;
 }
