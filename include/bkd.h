@@ -115,7 +115,9 @@ enum bkd_stat {
   BKD_STAT_TAIL_MS = 14,       /* device time of the tail kernel             */
   BKD_STAT_SCREEN_KEPT = 15,   /* pairs the BF16 screen passed to float32    */
   BKD_STAT_SCREEN_PAIRS = 16,  /* pairs the BF16 screen kernel examined      */
-  BKD_STAT_SCREEN_MS = 17      /* device time of the BF16 screen kernel      */
+  BKD_STAT_SCREEN_MS = 17,     /* device time of the BF16 screen kernel      */
+  BKD_STAT_SCREEN_ITEMS = 18,  /* work items (one leaf, <= 32 queries) of it */
+  BKD_STAT_SCREEN_VISITS = 19  /* (query, leaf) pairs of the screened rounds */
 };
 
 typedef struct bkd_tree bkd_tree; /* opaque; owned by the library */

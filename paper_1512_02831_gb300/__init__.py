@@ -40,7 +40,8 @@ STATS = {"rounds": 1, "leaf_visits": 2, "pairs": 3, "resorted": 4,
          "fallback": 5, "leaf_kernel_ms": 6, "chunk_bytes": 7, "copy_ms": 8,
          "leaf_launches": 9, "kernel_launches": 10, "tail_queries": 11,
          "tail_visits": 12, "tail_pairs": 13, "tail_ms": 14,
-         "screen_kept": 15, "screen_pairs": 16, "screen_ms": 17}
+         "screen_kept": 15, "screen_pairs": 16, "screen_ms": 17,
+         "screen_items": 18, "screen_visits": 19}
 
 _lock = threading.Lock()
 _lib = None

@@ -153,7 +153,8 @@ struct bkd_tree {
          st_fallback = 0, st_leaf_ms = 0, st_chunk_bytes = 0, st_copy_ms = 0,
          st_leaf_launches = 0, st_launches = 0, st_tail_queries = 0,
          st_tail_visits = 0, st_tail_pairs = 0, st_tail_ms = 0,
-         st_screen_kept = 0, st_screen_pairs = 0, st_screen_ms = 0;
+         st_screen_kept = 0, st_screen_pairs = 0, st_screen_ms = 0,
+         st_screen_items = 0, st_screen_visits = 0;
 
   cudaEvent_t next_event() {
     if (ev_used == ev_pool.size()) {
@@ -609,6 +610,8 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
       if (e1) cudaEventRecord(e1, s);
       if (e0 && e1) t->screen_ev.push_back({e0, e1});
       t->st_screen_pairs += (double)t->h_ctr->pairs;  // whole round
+      t->st_screen_items += n_items;
+      t->st_screen_visits += n_next;
       t->st_launches += 1;
     } else if (!t->chunked) {
       t->st_pairs += (double)t->h_ctr->pairs;
@@ -760,6 +763,7 @@ int bkd_query(bkd_tree* t, const float* Q, int64_t m, int k, int64_t* out_idx,
           t->st_leaf_launches = t->st_launches = t->st_tail_queries =
               t->st_tail_visits = t->st_tail_pairs = t->st_tail_ms =
                   t->st_screen_kept = t->st_screen_pairs = t->st_screen_ms = 0;
+  t->st_screen_items = t->st_screen_visits = 0;
   t->ev_used = 0;
   t->leaf_ev.clear();
   t->copy_ev.clear();
@@ -874,6 +878,8 @@ int bkd_get_stat(const bkd_tree* t, int key, double* value) {
     case BKD_STAT_SCREEN_KEPT: *value = t->st_screen_kept; break;
     case BKD_STAT_SCREEN_PAIRS: *value = t->st_screen_pairs; break;
     case BKD_STAT_SCREEN_MS: *value = t->st_screen_ms; break;
+    case BKD_STAT_SCREEN_ITEMS: *value = t->st_screen_items; break;
+    case BKD_STAT_SCREEN_VISITS: *value = t->st_screen_visits; break;
     default: return fail(BKD_EINVAL, "unknown stat %d", key);
   }
   return BKD_OK;

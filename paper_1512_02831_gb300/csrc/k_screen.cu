@@ -95,6 +95,9 @@ __device__ __forceinline__ float exact_dist(const float* __restrict__ qp,
 }
 
 // Per-warp shared memory (32-bit words):
+//   ring   R x NC x 32 x 4  super-tiles in flight: stage, component, lane
+//                       (each lane copies, and later reads, only its own
+//                       fragments; NC = 2 KH + 1 16-byte components)
 //   rec    32 x KH x 8   bf16 offsets of the item's queries (B operand)
 //   tneg   32            -T'/2 per query column (+inf: unused column)
 //   qid    32            query ids
@@ -104,6 +107,7 @@ __device__ __forceinline__ float exact_dist(const float* __restrict__ qp,
 //   qd     kQueue        their exact float32 distances
 //   ld, li 32 x K each   candidate lists, read on first insertion
 struct WarpSmem {
+  uint4* ring;
   uint32_t* rec;
   float* tneg;
   uint32_t* qid;
@@ -115,8 +119,15 @@ struct WarpSmem {
   uint32_t* li;
 };
 
+// Ring depth (super-tiles per warp in the ring: one being read, the rest in
+// flight) and 16-byte components per stage.  Deeper rings measured slower:
+// the shared memory they take comes out of L1.
+__host__ __device__ constexpr int ring_depth(int) { return 4; }
+__host__ __device__ constexpr int ring_comps(int kh) { return 2 * kh + 1; }
+
 __host__ __device__ constexpr int warp_words(int kh, int K) {
-  return kh * 256 + 128 + 2 * kQueue + 64 * K;
+  return ring_depth(kh) * ring_comps(kh) * 128 + kh * 256 + 128 +
+         2 * kQueue + 64 * K;
 }
 
 template <int KH>
@@ -124,6 +135,8 @@ __device__ __forceinline__ WarpSmem warp_smem(uint32_t* base, int warp,
                                               int K) {
   uint32_t* p = base + (size_t)warp * warp_words(KH, K);
   WarpSmem w;
+  w.ring = reinterpret_cast<uint4*>(p);
+  p += ring_depth(KH) * ring_comps(KH) * 128;
   w.rec = p;
   w.tneg = reinterpret_cast<float*>(p + KH * 256);
   w.qid = p + KH * 256 + 32;
@@ -197,16 +210,47 @@ struct Super {
   float4 c;
 };
 
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(__cvta_generic_to_global(src))
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Copies this lane's fragments of super-tile S into ring stage `slot`.
 template <int KH>
-__device__ __forceinline__ void load_super(Super<KH>& x, const uint4* wb,
-                                           int64_t hstep, const float4* cb,
-                                           int S) {
+__device__ __forceinline__ void issue_super(const WarpSmem& ws, int slot,
+                                            int lane, const uint4* wb,
+                                            int64_t hstep, const float4* cb,
+                                            int S) {
+  uint4* dst = ws.ring + (size_t)slot * ring_comps(KH) * 32 + lane;
 #pragma unroll
   for (int h = 0; h < KH; ++h) {
-    x.a[h][0] = __ldg(wb + h * hstep + (int64_t)S * 64);
-    x.a[h][1] = __ldg(wb + h * hstep + (int64_t)S * 64 + 32);
+    cp_async16(dst + (2 * h) * 32, wb + h * hstep + (int64_t)S * 64);
+    cp_async16(dst + (2 * h + 1) * 32, wb + h * hstep + (int64_t)S * 64 + 32);
   }
-  x.c = __ldg(cb + (int64_t)S * 8);
+  cp_async16(dst + (2 * KH) * 32, cb + (int64_t)S * 8);
+}
+
+template <int KH>
+__device__ __forceinline__ void read_super(Super<KH>& x, const WarpSmem& ws,
+                                           int slot, int lane) {
+  const uint4* src = ws.ring + (size_t)slot * ring_comps(KH) * 32 + lane;
+#pragma unroll
+  for (int h = 0; h < KH; ++h) {
+    x.a[h][0] = src[(2 * h) * 32];
+    x.a[h][1] = src[(2 * h + 1) * 32];
+  }
+  const uint4 c = src[(2 * KH) * 32];
+  x.c = make_float4(__uint_as_float(c.x), __uint_as_float(c.y),
+                    __uint_as_float(c.z), __uint_as_float(c.w));
 }
 
 // acc[nb] = seeds + (m-tile a of x) . (column block nb of b).
@@ -232,8 +276,8 @@ __device__ __forceinline__ void super_mma(float (&acc)[NB][4],
 }
 
 // The screen over one leaf for NB 8-query column blocks, one 32-point
-// super-tile (two m16n8k16 m-tiles) per step, the next super-tile loaded
-// while the current one is multiplied.
+// super-tile (two m16n8k16 m-tiles) per step, with ring_depth - 1 further
+// super-tiles on their way into shared memory (cp.async).
 template <int KH, int NB>
 __device__ __forceinline__ void scan_leaf(
     const DevTree& t, const ScreenData& sc, int leaf, int npt,
@@ -263,12 +307,24 @@ __device__ __forceinline__ void scan_leaf(
   const float4* cb =
       reinterpret_cast<const float4*>(sc.hpn + (size_t)leaf * st) + g;
   const int nsup = (npt + 31) >> 5;
-  Super<KH> nx;
-  load_super<KH>(nx, wb, hstep, cb, 0);
+  constexpr int R = ring_depth(KH);
+#pragma unroll
+  for (int j = 0; j < R - 1; ++j) {
+    if (j < nsup) issue_super<KH>(ws, j, lane, wb, hstep, cb, j);
+    cp_async_commit();  // possibly empty: one group per super-tile
+  }
   int nq = 0;
+  int slot = 0, fill = R - 1;  // stage read now, stage refilled now
   for (int S = 0; S < nsup; ++S) {
-    const Super<KH> x = nx;
-    if (S + 1 < nsup) load_super<KH>(nx, wb, hstep, cb, S + 1);
+    // the stage refilled was read in the previous step (its values were
+    // consumed by the multiplications there)
+    if (S + R - 1 < nsup) issue_super<KH>(ws, fill, lane, wb, hstep, cb, S + R - 1);
+    cp_async_commit();
+    cp_async_wait<R - 1>();  // super-tile S has landed
+    Super<KH> x;
+    read_super<KH>(x, ws, slot, lane);
+    slot = slot + 1 == R ? 0 : slot + 1;
+    fill = fill + 1 == R ? 0 : fill + 1;
     // the hot path only asks whether any pair of the super-tile passes
     bool any = false;
 #pragma unroll
@@ -321,6 +377,7 @@ __device__ __forceinline__ void scan_leaf(
       }
     }
   }
+  cp_async_wait<0>();  // only empty groups remain; the ring is free
   if (nq) drain(t, leaf, qpad, lst_d, lst_i, K, ws, lane, nq, ncol);
 }
 
