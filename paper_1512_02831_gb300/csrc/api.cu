@@ -117,7 +117,7 @@ struct bkd_tree {
   float* d_box = nullptr;
   // BF16 screen data (built on request, resident trees only)
   uint32_t* d_scr_words = nullptr;
-  float *d_scr_pn = nullptr, *d_scr_center = nullptr, *d_scr_bmax = nullptr,
+  float *d_scr_center = nullptr, *d_scr_bmax = nullptr,
         *d_scr_pnmax = nullptr;
   ScreenData screen;
   int precision = 0;
@@ -179,7 +179,6 @@ void release(bkd_tree* t) {
   cudaFree(t->d_leaf_cnt);
   cudaFree(t->d_box);
   cudaFree(t->d_scr_words);
-  cudaFree(t->d_scr_pn);
   cudaFree(t->d_scr_center);
   cudaFree(t->d_scr_bmax);
   cudaFree(t->d_scr_pnmax);
@@ -436,27 +435,23 @@ int build_impl(const float* P, int64_t n, int d, int height,
     const int kh = screen_halves(d);
     const int64_t stride = screen_stride(H.lcap);
     std::vector<uint32_t> words;
-    std::vector<float> pn, center, bmax, pnmax;
+    std::vector<float> center, bmax, pnmax;
     try {
       words.resize((size_t)L * kh * stride * 8);
-      pn.resize((size_t)L * stride);
       center.resize((size_t)L * d);
       bmax.resize(L);
       pnmax.resize(L);
     } catch (...) {
       return bail(fail(BKD_ENOMEM, "host staging of the screen data"));
     }
-    fill_screen(Ph, H, stride, words.data(), pn.data(), center.data(),
-                bmax.data(), pnmax.data());
+    fill_screen(Ph, H, stride, words.data(), center.data(), bmax.data(),
+                pnmax.data());
     if (cudaMalloc(&t->d_scr_words, words.size() * 4) != cudaSuccess ||
-        cudaMalloc(&t->d_scr_pn, pn.size() * 4) != cudaSuccess ||
         cudaMalloc(&t->d_scr_center, center.size() * 4) != cudaSuccess ||
         cudaMalloc(&t->d_scr_bmax, bmax.size() * 4) != cudaSuccess ||
         cudaMalloc(&t->d_scr_pnmax, pnmax.size() * 4) != cudaSuccess)
       return bail(fail(BKD_ENOMEM, "device allocation failed (screen data)"));
     if (cudaMemcpy(t->d_scr_words, words.data(), words.size() * 4,
-                   cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(t->d_scr_pn, pn.data(), pn.size() * 4,
                    cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(t->d_scr_center, center.data(), center.size() * 4,
                    cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -466,7 +461,6 @@ int build_impl(const float* P, int64_t n, int d, int height,
                    cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(fail(BKD_ECUDA, "upload of the screen data failed"));
     t->screen.words = t->d_scr_words;
-    t->screen.hpn = t->d_scr_pn;
     t->screen.stride = stride;
     t->screen.center = t->d_scr_center;
     t->screen.bmax = t->d_scr_bmax;

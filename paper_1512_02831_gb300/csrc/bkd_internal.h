@@ -61,7 +61,7 @@ struct Counters {
   int32_t n_fallback;       // queries sent to the binary64 search
   int32_t n_resorted;       // queries re-ordered by binary64 distances
   int32_t err;              // device-detected input errors (bit mask)
-  int32_t pad;
+  int32_t screen_next;      // next work item of the running screen launch
   unsigned long long tail_pairs;   // (query, point) pairs of the tail kernel
   unsigned long long tail_visits;  // (query, leaf) visits of the tail kernel
   unsigned long long screen_kept;  // pairs the BF16 screen passed on
@@ -128,11 +128,10 @@ int leaf_kernel_grid(int Dp, int cap, int sm_count);
 // BF16 screen data on the device (see fill_screen).
 struct ScreenData {
   const uint32_t* words = nullptr;
-  const float* hpn = nullptr;  // -pn / 2 per slot
   const float* center = nullptr;
   const float* bmax = nullptr;
   const float* pnmax = nullptr;
-  int64_t stride = 0;  // slots per leaf in words / hpn
+  int64_t stride = 0;  // slots per leaf in words
   int kh = 0;
 };
 
@@ -209,19 +208,21 @@ const char* build_host_tree(const float* P, int64_t n, int d, int h,
 // = maximum; dimensions d..Dp-1 are [0, 0].
 void fill_boxes(const float* P, const HostTree& t, float* box);
 
-// k-halves of 16 dimensions the BF16 screen uses (1 for d <= 16, else 2).
-inline int screen_halves(int d) { return d <= 16 ? 1 : 2; }
+// k-halves of 16 bf16 slots the BF16 screen uses: the d offsets plus two
+// slots that carry the point's squared norm (1 for d <= 14, 2 for d <= 30,
+// else 3).
+inline int screen_halves(int d) { return (d + 2 + 15) / 16; }
 
 // Data of the BF16 screen, per leaf (stride slots per leaf, see
 // screen_stride): the centre c (midpoint of the leaf's bounding box), every
-// point's offset bf16(fl(x - c)) packed as bf16 pairs (8 words per point and
-// k-half, in m16n8k16 A-fragment order, see build.cpp), hpn = -pn / 2 with pn
-// its squared norm (binary64 sum rounded to float; hpn = -inf and zero
-// words for padding slots), and per leaf bmax (upper bound on the offset
-// rounding error norm) and pnmax (largest pn).
+// point's offset bf16(fl(x - c)) in slots 0..d-1 and its squared norm pn
+// (binary64 sum rounded to float) split as pn_hi = bf16(pn), pn_lo =
+// bf16(pn - pn_hi) in slots d, d+1 (padding slots: pn_hi = +inf), packed as
+// bf16 pairs (8 words per point and k-half, in m16n8k16 A-fragment order,
+// see build.cpp); per leaf bmax (upper bound on the offset rounding error
+// norm) and pnmax (largest pn).
 void fill_screen(const float* P, const HostTree& t, int64_t stride,
-                 uint32_t* words, float* hpn, float* center, float* bmax,
-                 float* pnmax);
+                 uint32_t* words, float* center, float* bmax, float* pnmax);
 
 // Writes the quads and orig arrays for leaves [leaf_lo_id, leaf_hi_id)
 // into host buffers (`pts` and `orig` point at leaf leaf_lo_id's first slot).

@@ -226,8 +226,7 @@ inline float bf16_to_float(uint16_t h) {
 }  // namespace
 
 void fill_screen(const float* P, const HostTree& t, int64_t stride,
-                 uint32_t* words, float* hpn, float* center, float* bmax,
-                 float* pnmax) {
+                 uint32_t* words, float* center, float* bmax, float* pnmax) {
   const int d = t.d;
   const int kh = screen_halves(d);
   const int64_t L = (int64_t)1 << t.h;
@@ -250,8 +249,7 @@ void fill_screen(const float* P, const HostTree& t, int64_t stride,
     double wmax = 0.0;
     float pmax = 0.f;
     for (int64_t u = 0; u < stride; ++u) {
-      uint16_t hv[32] = {0};
-      float pv = INFINITY;
+      uint16_t hv[48] = {0};
       if (u < cnt) {
         const float* x = P + t.perm[lo + u] * d;
         double ss = 0.0;
@@ -260,20 +258,23 @@ void fill_screen(const float* P, const HostTree& t, int64_t stride,
           const double w = bf16_to_float(hv[i]);
           ss += w * w;
         }
-        pv = (float)ss;
+        const float pv = (float)ss;
+        // pn = pn_hi + pn_lo up to 2^-18 pn; pv - pn_hi is exact
+        hv[d] = bf16_rn(pv);
+        hv[d + 1] = bf16_rn(pv - bf16_to_float(hv[d]));
         wmax = std::max(wmax, std::sqrt(ss));
         pmax = std::max(pmax, pv);
+      } else {
+        hv[d] = 0x7f80;  // +inf: the row's product is -inf, never kept
       }
       // 32-point super-tiles S = u / 32 of two 16-point m-tiles a; in tile
       // a the point is row 8 r + g (r = 0, 1; g = 0..7).  Lane (g, t) of a
       // warp loads, with one 16-byte load per row half r, words (t, t + 4)
-      // of row 8 r + g of both tiles: its m16n8k16 A fragments.  hpn holds
-      // (a, r) = (0,0) (0,1) (1,0) (1,1) of row g as one float4.
+      // of row 8 r + g of both tiles: its m16n8k16 A fragments.
       const int64_t S = u / 32, a = (u % 32) / 16, r = (u % 16) / 8,
                     g = u % 8;
-      hpn[leaf * stride + (S * 8 + g) * 4 + 2 * a + r] = -0.5f * pv;  // exact
       for (int h = 0; h < kh; ++h) {
-        // word j of a k-half = dims (2j, 2j+1) of the half
+        // word j of a k-half = slots (2j, 2j+1) of the half
         uint32_t* blk = words + (leaf * kh + h) * stride * 8 +
                         ((S * 2 + r) * 8 + g) * 16 + 2 * a;
         for (int tq = 0; tq < 4; ++tq)

@@ -7,24 +7,25 @@
 //   v = q - c, w = x - c (c: centre of the leaf), rounded to bf16 (v^, w^);
 //   s = |v^|^2 + |w^|^2 - 2 v^.w^.
 //
-// The tensor cores form D = -|w^|^2/2 + v^.w^ (mma.sync m16n8k16, bf16 in,
-// fp32 accumulate, the accumulator initialised with -|w^|^2/2): 16 points
-// (rows) x 8 queries (columns) per instruction and 16-dimension half, so
-// s = |v^|^2 - 2 D and the screen test s < T reads D > (|v^|^2 - T) / 2,
-// one comparison per (query, point) pair.
+// The tensor cores form D = v^.w^ - |w^|^2/2 (mma.sync m16n8k16, bf16 in,
+// fp32 accumulate from zero): 16 points (rows) x 8 queries (columns) per
+// instruction and k-half of 16 bf16 slots.  A point's slots hold w^ and,
+// after it, pn_hi and pn_lo (|w^|^2 = pn_hi + pn_lo up to 2^-18 of it); a
+// query's hold v^ and -1/2, -1/2.  So s = |v^|^2 - 2 D, and the screen test
+// s < T reads D > (|v^|^2 - T) / 2: one comparison per (query, point) pair.
+// Padding points carry pn_hi = +inf, so D = -inf there.
 //
 // Safety bound.  With rho = 2^-9 (1 + 1e-4) (bf16 round-to-nearest plus the
 // float32 subtraction), |v^ - v| <= rho |v| and |v| <= |v^| / (1 - rho), so
 //   |q - x| >= |v^ - w^| - A_q - B_x,  A_q = rho/(1-rho) |v^|,
 // and B_x <= B_max, the leaf's largest such term (prepared on the host).  The
-// computed s differs from |v^ - w^|^2 by at most E = 2^-15 (|v^|^2 + pn_max):
-// the fp32 accumulation inside the tensor core is taken to err by at most
-// 2^-22 of the largest magnitude per added term (17 terms, two chained
-// instructions for 32 dimensions), every magnitude is at most
-// |v^|^2 + |w^|^2, and the roundings of |v^|^2 and |w^|^2 add d 2^-24 of
-// those, which together stay below E.  The float32 distance of the exact path
-// obeys D32 >= D (1 - g) - eta, g = (d+3) 2^-24, eta = 2^-120.  Hence a point
-// can only enter the list (D32 < bound) if
+// computed s differs from |v^ - w^|^2 by at most E = 2^-14 (|v^|^2 + pn_max):
+// every product is exact, the sum of the absolute terms is at most
+// |v^|^2 + |w^|^2, the fp32 accumulation is taken to err by at most 2^-22 of
+// that per addition (16 per k-half, at most 3 halves), and the norm split and
+// the rounding of |v^|^2 add less than 2^-17 of it.  The float32 distance of
+// the exact path obeys D32 >= D (1 - g) - eta, g = (d+3) 2^-24,
+// eta = 2^-120.  Hence a point can only enter the list (D32 < bound) if
 //   s < T = (sqrt((bound + eta) / (1 - g)) + A_q + B_max)^2 + E,
 // evaluated once per (query, leaf) in float32 with every operation rounded
 // toward the larger threshold (divisors toward the smaller).  Kept points
@@ -33,13 +34,12 @@
 // answers -- are bit for bit those of the float32 path.
 //
 // Work layout.  One warp per item (one leaf, at most 32 buffered queries,
-// i.e. up to four 8-query column blocks); the warps of a CTA take
-// consecutive items, which mostly share a leaf, and read the leaf's offsets
-// straight from global memory (coalesced 256-byte rows, L1 shared by the
-// warps on the same leaf).  Kept pairs go to a per-warp queue; a full queue
-// is scored 32 pairs at a time and inserted per query in queue order.  A
-// query's list is read from global memory only when a point is inserted
-// into it, and written back only then.
+// i.e. up to four 8-query column blocks).  Each lane streams its own A
+// fragments of the leaf through a small shared-memory ring (cp.async, L2
+// only).  Kept pairs go to a per-warp queue; a full queue is scored 32
+// pairs at a time and inserted per query in queue order.  A query's list is
+// read from global memory only when a point is inserted into it, and
+// written back only then.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -79,6 +79,26 @@ __device__ __forceinline__ void mma_bf16(float (&acc)[4], uint32_t a0,
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// acc = a x b, accumulated from zero.
+__device__ __forceinline__ void mma_bf16_z(float (&acc)[4], uint32_t a0,
+                                           uint32_t a1, uint32_t a2,
+                                           uint32_t a3, uint32_t b0,
+                                           uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+      "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%10, %10, %10, %10};"
+      : "=f"(acc[0]), "=f"(acc[1]), "=f"(acc[2]), "=f"(acc[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1), "f"(0.f));
+}
+
+// max(a, b, c) (three-input float max of sm_100 and later).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
 // Exact float32 distance of query coordinates qp (Dp, zero-padded) to the
 // point in `slot`: the leaf kernel's chain, one dimension at a time.
 __device__ __forceinline__ float exact_dist(const float* __restrict__ qp,
@@ -97,7 +117,7 @@ __device__ __forceinline__ float exact_dist(const float* __restrict__ qp,
 // Per-warp shared memory (32-bit words):
 //   ring   R x NC x 32 x 4  super-tiles in flight: stage, component, lane
 //                       (each lane copies, and later reads, only its own
-//                       fragments; NC = 2 KH + 1 16-byte components)
+//                       fragments; NC = 2 KH 16-byte components)
 //   rec    32 x KH x 8   bf16 offsets of the item's queries (B operand)
 //   tneg   32            -T'/2 per query column (+inf: unused column)
 //   qid    32            query ids
@@ -123,7 +143,7 @@ struct WarpSmem {
 // flight) and 16-byte components per stage.  Deeper rings measured slower:
 // the shared memory they take comes out of L1.
 __host__ __device__ constexpr int ring_depth(int) { return 4; }
-__host__ __device__ constexpr int ring_comps(int kh) { return 2 * kh + 1; }
+__host__ __device__ constexpr int ring_comps(int kh) { return 2 * kh; }
 
 __host__ __device__ constexpr int warp_words(int kh, int K) {
   return ring_depth(kh) * ring_comps(kh) * 128 + kh * 256 + 128 +
@@ -203,11 +223,10 @@ __device__ __noinline__ void drain(const DevTree& t, int leaf,
 }
 
 // One 32-point super-tile in registers: per k-half the A fragments of rows
-// g and g + 8 of both m-tiles, and the four accumulator seeds -pn/2.
+// g and g + 8 of both m-tiles.
 template <int KH>
 struct Super {
   uint4 a[KH][2];
-  float4 c;
 };
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
@@ -228,15 +247,14 @@ __device__ __forceinline__ void cp_async_wait() {
 template <int KH>
 __device__ __forceinline__ void issue_super(const WarpSmem& ws, int slot,
                                             int lane, const uint4* wb,
-                                            int64_t hstep, const float4* cb,
-                                            int S) {
+                                            int64_t hstep, int S) {
   uint4* dst = ws.ring + (size_t)slot * ring_comps(KH) * 32 + lane;
+  const uint4* src = wb + (int64_t)S * 64;
 #pragma unroll
   for (int h = 0; h < KH; ++h) {
-    cp_async16(dst + (2 * h) * 32, wb + h * hstep + (int64_t)S * 64);
-    cp_async16(dst + (2 * h + 1) * 32, wb + h * hstep + (int64_t)S * 64 + 32);
+    cp_async16(dst + (2 * h) * 32, src + h * hstep);
+    cp_async16(dst + (2 * h + 1) * 32, src + h * hstep + 32);
   }
-  cp_async16(dst + (2 * KH) * 32, cb + (int64_t)S * 8);
 }
 
 template <int KH>
@@ -248,29 +266,25 @@ __device__ __forceinline__ void read_super(Super<KH>& x, const WarpSmem& ws,
     x.a[h][0] = src[(2 * h) * 32];
     x.a[h][1] = src[(2 * h + 1) * 32];
   }
-  const uint4 c = src[(2 * KH) * 32];
-  x.c = make_float4(__uint_as_float(c.x), __uint_as_float(c.y),
-                    __uint_as_float(c.z), __uint_as_float(c.w));
 }
 
-// acc[nb] = seeds + (m-tile a of x) . (column block nb of b).
+// acc[nb] = (m-tile a of x) . (column block nb of b) = v^.w^ - |w^|^2 / 2.
 template <int KH, int NB>
 __device__ __forceinline__ void super_mma(float (&acc)[NB][4],
                                           const Super<KH>& x,
                                           const uint32_t (&b)[NB][KH][2],
                                           int a) {
-  const float cg = a ? x.c.z : x.c.x, cg8 = a ? x.c.w : x.c.y;
 #pragma unroll
   for (int nb = 0; nb < NB; ++nb) {
-    acc[nb][0] = cg;
-    acc[nb][1] = cg;
-    acc[nb][2] = cg8;
-    acc[nb][3] = cg8;
 #pragma unroll
     for (int h = 0; h < KH; ++h) {
       const uint4 r0 = x.a[h][0], r1 = x.a[h][1];
-      mma_bf16(acc[nb], a ? r0.z : r0.x, a ? r1.z : r1.x, a ? r0.w : r0.y,
-               a ? r1.w : r1.y, b[nb][h][0], b[nb][h][1]);
+      const uint32_t a0 = a ? r0.z : r0.x, a1 = a ? r1.z : r1.x,
+                     a2 = a ? r0.w : r0.y, a3 = a ? r1.w : r1.y;
+      if (h == 0)
+        mma_bf16_z(acc[nb], a0, a1, a2, a3, b[nb][h][0], b[nb][h][1]);
+      else
+        mma_bf16(acc[nb], a0, a1, a2, a3, b[nb][h][0], b[nb][h][1]);
     }
   }
 }
@@ -304,13 +318,11 @@ __device__ __forceinline__ void scan_leaf(
   const int64_t hstep = st * 2;  // uint4 per k-half of a leaf
   const uint4* wb = reinterpret_cast<const uint4*>(sc.words) +
                     (size_t)leaf * KH * hstep + g * 4 + tq;
-  const float4* cb =
-      reinterpret_cast<const float4*>(sc.hpn + (size_t)leaf * st) + g;
   const int nsup = (npt + 31) >> 5;
   constexpr int R = ring_depth(KH);
 #pragma unroll
   for (int j = 0; j < R - 1; ++j) {
-    if (j < nsup) issue_super<KH>(ws, j, lane, wb, hstep, cb, j);
+    if (j < nsup) issue_super<KH>(ws, j, lane, wb, hstep, j);
     cp_async_commit();  // possibly empty: one group per super-tile
   }
   int nq = 0;
@@ -318,24 +330,35 @@ __device__ __forceinline__ void scan_leaf(
   for (int S = 0; S < nsup; ++S) {
     // the stage refilled was read in the previous step (its values were
     // consumed by the multiplications there)
-    if (S + R - 1 < nsup) issue_super<KH>(ws, fill, lane, wb, hstep, cb, S + R - 1);
+    if (S + R - 1 < nsup) issue_super<KH>(ws, fill, lane, wb, hstep, S + R - 1);
     cp_async_commit();
     cp_async_wait<R - 1>();  // super-tile S has landed
     Super<KH> x;
     read_super<KH>(x, ws, slot, lane);
     slot = slot + 1 == R ? 0 : slot + 1;
     fill = fill + 1 == R ? 0 : fill + 1;
-    // the hot path only asks whether any pair of the super-tile passes
+    // the hot path only asks whether any pair of the super-tile passes:
+    // per query column the largest D over its 4 rows (2 per m-tile)
+    float cm[NB][2];
+    {
+      float acc[NB][4];
+      super_mma<KH, NB>(acc, x, b, 0);
+#pragma unroll
+      for (int nb = 0; nb < NB; ++nb) {
+        cm[nb][0] = fmaxf(acc[nb][0], acc[nb][2]);
+        cm[nb][1] = fmaxf(acc[nb][1], acc[nb][3]);
+      }
+      super_mma<KH, NB>(acc, x, b, 1);
+#pragma unroll
+      for (int nb = 0; nb < NB; ++nb) {
+        cm[nb][0] = fmax3(cm[nb][0], acc[nb][0], acc[nb][2]);
+        cm[nb][1] = fmax3(cm[nb][1], acc[nb][1], acc[nb][3]);
+      }
+    }
     bool any = false;
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      float acc[NB][4];
-      super_mma<KH, NB>(acc, x, b, a);
-#pragma unroll
-      for (int nb = 0; nb < NB; ++nb)
-        any = any | (acc[nb][0] > tn[nb][0]) | (acc[nb][1] > tn[nb][1]) |
-              (acc[nb][2] > tn[nb][0]) | (acc[nb][3] > tn[nb][1]);
-    }
+    for (int nb = 0; nb < NB; ++nb)
+      any = any || cm[nb][0] > tn[nb][0] || cm[nb][1] > tn[nb][1];
     if (__any_sync(full, any)) {
       // rare: multiply again and collect the passing pairs; bit
       // 16 a + 8 r + 2 nb + p = row 8 r + g of m-tile a, column
@@ -404,12 +427,16 @@ __device__ __forceinline__ void setup_column(
     for (int h = 0; h < KH; ++h)
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        const int k0 = 16 * h + 2 * j;
-        const float a0 = k0 < t.d ? __fsub_rn(qp[k0], c[k0]) : 0.f;
-        const float a1 = k0 + 1 < t.d ? __fsub_rn(qp[k0 + 1], c[k0 + 1]) : 0.f;
+        // slots: v^ (0..d-1), then -1/2 twice against the point's norm
+        const int k0 = 16 * h + 2 * j, d = t.d;
+        const float a0 = k0 < d ? __fsub_rn(qp[k0], c[k0])
+                                : (k0 < d + 2 ? -0.5f : 0.f);
+        const float a1 = k0 + 1 < d ? __fsub_rn(qp[k0 + 1], c[k0 + 1])
+                                    : (k0 + 1 < d + 2 ? -0.5f : 0.f);
         const uint32_t wd = pack_bf16(a0, a1);
         rec[h * 8 + (j < 4 ? 2 * j : 2 * (j - 4) + 1)] = wd;
-        const float v0 = bf16_lo(wd), v1 = bf16_hi(wd);
+        const float v0 = k0 < d ? bf16_lo(wd) : 0.f;
+        const float v1 = k0 + 1 < d ? bf16_hi(wd) : 0.f;
         qn = __fmaf_rn(v0, v0, qn);
         qn = __fmaf_rn(v1, v1, qn);
         ss = __fmaf_ru(v0, v0, ss);
@@ -427,7 +454,7 @@ __device__ __forceinline__ void setup_column(
       const float R =
           __fsqrt_ru(__fdiv_ru(__fadd_ru(bound, 0x1p-120f), one_m_g));
       const float Rb = __fadd_ru(__fadd_ru(R, aq), sc.bmax[w.leaf]);
-      const float E = __fmul_ru(0x1p-15f, __fadd_ru(ss, sc.pnmax[w.leaf]));
+      const float E = __fmul_ru(0x1p-14f, __fadd_ru(ss, sc.pnmax[w.leaf]));
       const float thr = __fsub_ru(__fadd_ru(__fmul_ru(Rb, Rb), E), qn);
       tneg = -0.5f * thr;  // exact scale
     }
@@ -448,12 +475,15 @@ __global__ void __launch_bounds__(kScrThreads, 2)
   extern __shared__ __align__(16) uint32_t smem_words[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const WarpSmem ws = warp_smem<KH>(smem_words, warp, K);
-  const int n = item_hi - item_lo;
-  const int per = (n + (int)gridDim.x - 1) / (int)gridDim.x;
-  const int it0 = item_lo + (int)blockIdx.x * per;
-  const int it1 = min(item_hi, it0 + per);
   unsigned long long kept = 0;
-  for (int it = it0 + warp; it < it1; it += kScrWarps) {
+  // items are taken one at a time from a launch-wide counter: their costs
+  // differ (leaf size, column blocks, rescoring), a static split leaves SMs
+  // idle at the end of the launch
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(&ctr->screen_next, 1);
+    it = __shfl_sync(0xffffffffu, it, 0) + item_lo;
+    if (it >= item_hi) break;
     const Item w = items[it];
     setup_column<KH>(t, sc, w, lane, act, qpad, lst_d, K, ws);
     __syncwarp();
@@ -494,15 +524,19 @@ size_t screen_smem(int kh, int K) {
 }
 
 const void* screen_kernel_for(int kh) {
-  return kh == 1 ? (const void*)screen_kernel<1>
-                 : (const void*)screen_kernel<2>;
+  switch (kh) {
+    case 1: return (const void*)screen_kernel<1>;
+    case 2: return (const void*)screen_kernel<2>;
+    case 3: return (const void*)screen_kernel<3>;
+    default: return nullptr;
+  }
 }
 
 }  // namespace
 
 int screen_grid(int kh, int64_t lcap, int K, int sm_count) {
   // slots in a queue entry: 27 bits
-  if (kh < 1 || kh > 2 || K < 1 || K > 32 || lcap >= ((int64_t)1 << 27))
+  if (kh < 1 || kh > 3 || K < 1 || K > 32 || lcap >= ((int64_t)1 << 27))
     return 0;
   const size_t smem = screen_smem(kh, K);
   const void* k = screen_kernel_for(kh);
@@ -526,12 +560,24 @@ cudaError_t launch_screen(const DevTree& t, const ScreenData& sd,
   if (n <= 0 || grid <= 0) return cudaSuccess;
   grid = std::min(grid, (n + kScrWarps - 1) / kScrWarps);
   const size_t smem = screen_smem(sd.kh, K);
-  if (sd.kh == 1)
-    screen_kernel<1><<<grid, kScrThreads, smem, s>>>(
-        t, sd, items, item_lo, item_hi, ctr, act, qpad, lst_d, lst_i, K);
-  else
-    screen_kernel<2><<<grid, kScrThreads, smem, s>>>(
-        t, sd, items, item_lo, item_hi, ctr, act, qpad, lst_d, lst_i, K);
+  cudaError_t e = cudaMemsetAsync(&ctr->screen_next, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
+  switch (sd.kh) {
+    case 1:
+      screen_kernel<1><<<grid, kScrThreads, smem, s>>>(
+          t, sd, items, item_lo, item_hi, ctr, act, qpad, lst_d, lst_i, K);
+      break;
+    case 2:
+      screen_kernel<2><<<grid, kScrThreads, smem, s>>>(
+          t, sd, items, item_lo, item_hi, ctr, act, qpad, lst_d, lst_i, K);
+      break;
+    case 3:
+      screen_kernel<3><<<grid, kScrThreads, smem, s>>>(
+          t, sd, items, item_lo, item_hi, ctr, act, qpad, lst_d, lst_i, K);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
