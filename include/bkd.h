@@ -117,7 +117,11 @@ enum bkd_stat {
   BKD_STAT_SCREEN_PAIRS = 16,  /* pairs the BF16 screen kernel examined      */
   BKD_STAT_SCREEN_MS = 17,     /* device time of the BF16 screen kernel      */
   BKD_STAT_SCREEN_ITEMS = 18,  /* work items (one leaf, <= 32 queries) of it */
-  BKD_STAT_SCREEN_VISITS = 19  /* (query, leaf) pairs of the screened rounds */
+  BKD_STAT_SCREEN_VISITS = 19, /* (query, leaf) pairs of the screened rounds */
+  BKD_STAT_FIND_MS = 20,       /* device time of FindLeafBatch (all rounds)  */
+  BKD_STAT_BUCKET_MS = 21,     /* device time of the bucketing (all rounds)  */
+  BKD_STAT_EXACT_MS = 22       /* device time of the binary64 re-check and
+                                  fallback search                           */
 };
 
 typedef struct bkd_tree bkd_tree; /* opaque; owned by the library */

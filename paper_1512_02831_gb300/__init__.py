@@ -41,7 +41,8 @@ STATS = {"rounds": 1, "leaf_visits": 2, "pairs": 3, "resorted": 4,
          "leaf_launches": 9, "kernel_launches": 10, "tail_queries": 11,
          "tail_visits": 12, "tail_pairs": 13, "tail_ms": 14,
          "screen_kept": 15, "screen_pairs": 16, "screen_ms": 17,
-         "screen_items": 18, "screen_visits": 19}
+         "screen_items": 18, "screen_visits": 19, "find_ms": 20,
+         "bucket_ms": 21, "exact_ms": 22}
 
 _lock = threading.Lock()
 _lib = None

@@ -134,7 +134,8 @@ struct bkd_tree {
   // query workspace
   DevBuf<float> qdev, qpad, lst_d;
   DevBuf<uint32_t> lst_i, act_a, act_b, fb_list;
-  DevBuf<int32_t> state, leaf_of, cnt, off, cursor, toff, chunk_item;
+  DevBuf<uint64_t> state;  // per query: TravState
+  DevBuf<int32_t> leaf_of, cnt, off, cursor, toff, chunk_item;
   DevBuf<Item> items;
   DevBuf<int64_t> out_idx;
   DevBuf<float> out_dist;
@@ -147,14 +148,15 @@ struct bkd_tree {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> leaf_ev, copy_ev, tail_ev,
-      screen_ev;
+      screen_ev, find_ev, bucket_ev, exact_ev;
   // stats of the last query
   double st_rounds = 0, st_visits = 0, st_pairs = 0, st_resorted = 0,
          st_fallback = 0, st_leaf_ms = 0, st_chunk_bytes = 0, st_copy_ms = 0,
          st_leaf_launches = 0, st_launches = 0, st_tail_queries = 0,
          st_tail_visits = 0, st_tail_pairs = 0, st_tail_ms = 0,
          st_screen_kept = 0, st_screen_pairs = 0, st_screen_ms = 0,
-         st_screen_items = 0, st_screen_visits = 0;
+         st_screen_items = 0, st_screen_visits = 0, st_find_ms = 0,
+         st_bucket_ms = 0, st_exact_ms = 0;
 
   cudaEvent_t next_event() {
     if (ev_used == ev_pool.size()) {
@@ -554,14 +556,22 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
     // into the screen's smaller items
     const bool screened =
         !t->chunked && t->precision == 1 && round > 0 && screen_max > 0;
+    cudaEvent_t f0 = t->next_event(), f1 = t->next_event();
+    if (f0) cudaEventRecord(f0, s);
     CU(cudaMemsetAsync(t->cnt.p, 0, sizeof(int32_t) * L, s));
     CU(launch_find_leaf(D, t->qpad.p, act, n_act, t->state.p, t->lst_d.p, K,
                         t->leaf_of.p, t->cnt.p, s));
+    if (f1) cudaEventRecord(f1, s);
+    if (f0 && f1) t->find_ev.push_back({f0, f1});
     t->st_launches += 1;
+    cudaEvent_t b0 = t->next_event(), b1 = t->next_event();
+    if (b0) cudaEventRecord(b0, s);
     CU(launch_bucket(t->leaf_of.p, act, n_act, (int)L,
                      screened ? kScreenTile : kPipeTile,
                      t->d_leaf_cnt, t->cnt.p, t->off.p, t->cursor.p,
                      t->toff.p, t->items.p, nxt, t->d_ctr, s));
+    if (b1) cudaEventRecord(b1, s);
+    if (b0 && b1) t->bucket_ev.push_back({b0, b1});
     t->st_launches += 3;
     if (t->chunked) {
       CU(launch_chunk_items(t->toff.p, t->d_chunk_leaf, t->n_chunks,
@@ -670,6 +680,8 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
     n_act = n_next;
     ++round;
   }
+  cudaEvent_t x0 = t->next_event();
+  if (x0) cudaEventRecord(x0, s);
   CU(launch_recheck(D, m, k, K, t->qpad.p, t->lst_d.p, t->lst_i.p, out_idx,
                     out_dist, t->fb_list.p, t->d_ctr, s));
   CU(cudaMemcpyAsync(t->h_ctr, t->d_ctr, sizeof(Counters),
@@ -692,6 +704,9 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
                        out_idx, out_dist, s));
     t->st_launches += 1;
   }
+  cudaEvent_t x1 = t->next_event();
+  if (x1) cudaEventRecord(x1, s);
+  if (x0 && x1) t->exact_ev.push_back({x0, x1});
   return BKD_OK;
 }
 
@@ -758,7 +773,11 @@ int bkd_query(bkd_tree* t, const float* Q, int64_t m, int k, int64_t* out_idx,
               t->st_tail_visits = t->st_tail_pairs = t->st_tail_ms =
                   t->st_screen_kept = t->st_screen_pairs = t->st_screen_ms = 0;
   t->st_screen_items = t->st_screen_visits = 0;
+  t->st_find_ms = t->st_bucket_ms = t->st_exact_ms = 0;
   t->ev_used = 0;
+  t->find_ev.clear();
+  t->bucket_ev.clear();
+  t->exact_ev.clear();
   t->leaf_ev.clear();
   t->copy_ev.clear();
   t->tail_ev.clear();
@@ -813,6 +832,17 @@ int bkd_query(bkd_tree* t, const float* Q, int64_t m, int k, int64_t* out_idx,
     if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess)
       t->st_screen_ms += ms;
   }
+  const std::pair<std::vector<std::pair<cudaEvent_t, cudaEvent_t>>*,
+                  double*>
+      phases[] = {{&t->find_ev, &t->st_find_ms},
+                  {&t->bucket_ev, &t->st_bucket_ms},
+                  {&t->exact_ev, &t->st_exact_ms}};
+  for (const auto& ph : phases)
+    for (auto& pr : *ph.first) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess)
+        *ph.second += ms;
+    }
   cudaGetLastError();
   return BKD_OK;
 }
@@ -874,6 +904,9 @@ int bkd_get_stat(const bkd_tree* t, int key, double* value) {
     case BKD_STAT_SCREEN_MS: *value = t->st_screen_ms; break;
     case BKD_STAT_SCREEN_ITEMS: *value = t->st_screen_items; break;
     case BKD_STAT_SCREEN_VISITS: *value = t->st_screen_visits; break;
+    case BKD_STAT_FIND_MS: *value = t->st_find_ms; break;
+    case BKD_STAT_BUCKET_MS: *value = t->st_bucket_ms; break;
+    case BKD_STAT_EXACT_MS: *value = t->st_exact_ms; break;
     default: return fail(BKD_EINVAL, "unknown stat %d", key);
   }
   return BKD_OK;

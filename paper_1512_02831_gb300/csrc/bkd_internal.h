@@ -54,6 +54,20 @@ struct Item {
 };
 
 // Device-side round counters, copied to the host once per round.
+// Traversal state of one query between rounds: the heap index of its last
+// (or pending) leaf, or kStart / kDone, in the low 32 bits; in the high 32
+// bits the mask of path levels whose off-path child is finished (see
+// traverse.cuh).
+__host__ __device__ inline uint64_t trav_state(int node, uint32_t mask) {
+  return ((uint64_t)mask << 32) | (uint32_t)node;
+}
+__host__ __device__ inline int state_node(uint64_t s) {
+  return (int)(uint32_t)s;
+}
+__host__ __device__ inline uint32_t state_mask(uint64_t s) {
+  return (uint32_t)(s >> 32);
+}
+
 struct Counters {
   int32_t n_next;           // queries bucketed into some leaf this round
   int32_t n_items;          // work items this round
@@ -86,14 +100,14 @@ struct DevTree {
 
 // ------------------------------------------------------------- launchers
 cudaError_t launch_init(const float* Q, int64_t m, int d, int Dp, float* qpad,
-                        float* lst_d, uint32_t* lst_i, int K, int32_t* state,
+                        float* lst_d, uint32_t* lst_i, int K, uint64_t* state,
                         uint32_t* act, Counters* ctr, cudaStream_t s);
 
 // FindLeafBatch from the traversal states in `state` (kStart for the first
 // round): next leaf per position of `act` in leaf_of (-1: done), the new
 // pending leaf in state, and +1 in cnt[leaf] for every query that goes on.
 cudaError_t launch_find_leaf(const DevTree& t, const float* qpad,
-                             const uint32_t* act, int n_act, int32_t* state,
+                             const uint32_t* act, int n_act, uint64_t* state,
                              const float* lst_d, int K, int32_t* leaf_of,
                              int32_t* cnt, cudaStream_t s);
 
@@ -158,7 +172,7 @@ cudaError_t launch_screen(const DevTree& t, const ScreenData& sd,
 // warp per query); state[q] is the query's pending (not yet scanned) leaf.
 // `pts` is the leaf structure (device or mapped host).
 cudaError_t launch_tail(const DevTree& t, const float* pts,
-                        const uint32_t* act, int n_act, int32_t* state,
+                        const uint32_t* act, int n_act, uint64_t* state,
                         const float* qpad, float* lst_d, uint32_t* lst_i,
                         int K, Counters* ctr, int sm_count, cudaStream_t s);
 

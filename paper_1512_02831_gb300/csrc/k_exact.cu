@@ -21,7 +21,11 @@
 //     k-d tree search (Sec. 2.3) with the exact key, skipping subtrees whose
 //     binary64 bounding-box distance exceeds min(current k-th D64,
 //     hi(v_{k-1})) -- hi(v_{k-1}) bounds the true k-th distance from above
-//     because k points score at most v_{k-1}.
+//     because k points score at most v_{k-1}.  A point's binary64 distance
+//     is formed only when lo of its float32 distance does not exceed that
+//     seed bound.
+#include <cmath>
+
 #include "bkd.h"
 #include "bkd_internal.h"
 #include "traverse.cuh"
@@ -29,11 +33,17 @@
 namespace bkd {
 namespace {
 
-__device__ __forceinline__ double lo_bound(float v, double gam, double eta) {
-  return ((double)v - eta) / (1.0 + gam);
+// The interval [lo(v), hi(v)] with directed roundings: `rlo` <= 1/(1+gam)
+// and `rhi` >= 1/(1-gam) are prepared on the host (Bounds), so the interval
+// only widens.
+struct Bounds {
+  double eta, rlo, rhi;
+};
+__device__ __forceinline__ double lo_bound(float v, const Bounds& b) {
+  return __dmul_rd(__dsub_rd((double)v, b.eta), b.rlo);
 }
-__device__ __forceinline__ double hi_bound(float v, double gam, double eta) {
-  return ((double)v + eta) / (1.0 - gam);
+__device__ __forceinline__ double hi_bound(float v, const Bounds& b) {
+  return __dmul_ru(__dadd_ru((double)v, b.eta), b.rhi);
 }
 
 __device__ __forceinline__ float coord(const float* pts, int Dp, uint64_t slot,
@@ -53,6 +63,19 @@ __device__ double dist64(const float* qp, const float* pts, int Dp, int d,
   return acc;
 }
 
+// float32 squared distance by the leaf kernel's chain (the value v above):
+// e = fl(t_0^2), e = fma(t_i, t_i, e), t_i = fl(q_i - x_i).
+__device__ float dist32(const float* qp, const float* pts, int Dp, int d,
+                        uint64_t slot) {
+  float t = __fsub_rn(qp[0], coord(pts, Dp, slot, 0));
+  float e = __fmul_rn(t, t);
+  for (int i = 1; i < d; ++i) {
+    t = __fsub_rn(qp[i], coord(pts, Dp, slot, i));
+    e = __fmaf_rn(t, t, e);
+  }
+  return e;
+}
+
 __device__ __forceinline__ bool key_less(double da, int64_t ia, double db,
                                          int64_t ib) {
   return da < db || (da == db && ia < ib);
@@ -65,7 +88,7 @@ __global__ void recheck_kernel(DevTree t, int64_t m, int k, int K,
                                int64_t* __restrict__ out_idx,
                                float* __restrict__ out_dist,
                                uint32_t* __restrict__ fb_list, Counters* ctr,
-                               double gam, double eta) {
+                               Bounds bd) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= m) return;
   const float* v = lst_d + q * K;
@@ -85,7 +108,7 @@ __global__ void recheck_kernel(DevTree t, int64_t m, int k, int K,
   }
   const float vk = v[k];
   const bool member_ok =
-      isinf(vk) || hi_bound(v[k - 1], gam, eta) < lo_bound(vk, gam, eta);
+      isinf(vk) || hi_bound(v[k - 1], bd) < lo_bound(vk, bd);
   if (!member_ok) {
     const int j = atomicAdd(&ctr->n_fallback, 1);
     fb_list[j] = (uint32_t)q;
@@ -93,7 +116,7 @@ __global__ void recheck_kernel(DevTree t, int64_t m, int k, int K,
   }
   bool order_ok = true;
   for (int j = 0; j + 1 < k; ++j)
-    order_ok &= hi_bound(v[j], gam, eta) < lo_bound(v[j + 1], gam, eta);
+    order_ok &= hi_bound(v[j], bd) < lo_bound(v[j + 1], bd);
   if (order_ok) {
     for (int j = 0; j < k; ++j) {
       out_idx[q * k + j] = t.orig[sl[j]];
@@ -131,21 +154,22 @@ __global__ void __launch_bounds__(32 * kFbWarps)
                     int k, int K, const float* __restrict__ qpad,
                     const float* __restrict__ lst_d,
                     int64_t* __restrict__ out_idx,
-                    float* __restrict__ out_dist, double gam, double eta) {
+                    float* __restrict__ out_dist, Bounds bd) {
   const int lane = threadIdx.x & 31;
   const int first_leaf = (1 << t.h) - 1;
   for (int f = blockIdx.x * kFbWarps + (threadIdx.x >> 5); f < n_fb;
        f += gridDim.x * kFbWarps) {
     const int64_t q = fb_list[f];
     const float* qp = qpad + q * t.Dp;
-    const double seed = hi_bound(lst_d[q * K + (k - 1)], gam, eta);
+    const double seed = hi_bound(lst_d[q * K + (k - 1)], bd);
     double myd = __longlong_as_double(0x7ff0000000000000ll);  // +inf
     int64_t myi = INT64_MAX;
     int cnt = 0;  // warp-uniform
     int node = kStart;
+    uint32_t mask = 0;
     for (;;) {
       const double kd = __shfl_sync(0xffffffffu, myd, k - 1);
-      node = next_leaf(t, F64Bound{qp}, qp, node,
+      node = next_leaf(t, F64Bound{qp}, qp, node, mask,
                        cnt == k ? fmin(kd, seed) : seed);
       if (node == kDone) break;
       // ---- scan the leaf
@@ -157,7 +181,11 @@ __global__ void __launch_bounds__(32 * kFbWarps)
         double dv = 0.0;
         int64_t iv = 0;
         bool cand = false;
-        if (u < np) {
+        // D64 >= lo(v): the binary64 distance is formed only where the
+        // float32 one leaves room for D64 <= seed (binary64 is slow here)
+        if (u < np &&
+            lo_bound(dist32(qp, t.pts, t.Dp, t.d, base + u), bd) <=
+                seed) {
           dv = dist64(qp, t.pts, t.Dp, t.d, base + u);
           iv = t.orig[base + u];
           cand = dv <= seed;
@@ -193,6 +221,16 @@ __global__ void __launch_bounds__(32 * kFbWarps)
   }
 }
 
+// gam = (d + 3) 2^-24, eta = 2^-120; the reciprocals rounded outward.
+Bounds bounds_for(int d) {
+  const double gam = (d + 3) * 5.9604644775390625e-08;
+  Bounds b;
+  b.eta = 7.52316384526264e-37;
+  b.rlo = std::nextafter(1.0 / (1.0 + gam), 0.0);
+  b.rhi = std::nextafter(1.0 / (1.0 - gam), 2.0);
+  return b;
+}
+
 }  // namespace
 
 cudaError_t launch_recheck(const DevTree& t, int64_t m, int k, int K,
@@ -201,11 +239,9 @@ cudaError_t launch_recheck(const DevTree& t, int64_t m, int k, int K,
                            float* out_dist, uint32_t* fb_list, Counters* ctr,
                            cudaStream_t s) {
   if (m == 0) return cudaSuccess;
-  const double gam = (t.d + 3) * 5.9604644775390625e-08;  // (d+3) 2^-24
-  const double eta = 7.52316384526264e-37;                // 2^-120
   recheck_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(
-      t, m, k, K, qpad, lst_d, lst_i, out_idx, out_dist, fb_list, ctr, gam,
-      eta);
+      t, m, k, K, qpad, lst_d, lst_i, out_idx, out_dist, fb_list, ctr,
+      bounds_for(t.d));
   return cudaGetLastError();
 }
 
@@ -213,11 +249,10 @@ cudaError_t launch_fallback(const DevTree& t, int n_fb, const uint32_t* fb_list,
                             int k, int K, const float* qpad, const float* lst_d,
                             int64_t* out_idx, float* out_dist, cudaStream_t s) {
   if (n_fb == 0) return cudaSuccess;
-  const double gam = (t.d + 3) * 5.9604644775390625e-08;
-  const double eta = 7.52316384526264e-37;
   const int grid = (n_fb + kFbWarps - 1) / kFbWarps;
   fallback_kernel<<<grid < 4096 ? grid : 4096, 32 * kFbWarps, 0, s>>>(
-      t, n_fb, fb_list, k, K, qpad, lst_d, out_idx, out_dist, gam, eta);
+      t, n_fb, fb_list, k, K, qpad, lst_d, out_idx, out_dist,
+      bounds_for(t.d));
   return cudaGetLastError();
 }
 

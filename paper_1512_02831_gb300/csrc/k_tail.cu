@@ -25,7 +25,7 @@ template <int D>
 __global__ void __launch_bounds__(kTailWarps * 32)
     tail_kernel(DevTree t, const float4* __restrict__ pts,
                 const uint32_t* __restrict__ act, int n_act,
-                int32_t* __restrict__ state, const float* __restrict__ qpad,
+                uint64_t* __restrict__ state, const float* __restrict__ qpad,
                 float* __restrict__ lst_d, uint32_t* __restrict__ lst_i, int K,
                 Counters* ctr) {
   const int lane = threadIdx.x & 31;
@@ -53,9 +53,11 @@ __global__ void __launch_bounds__(kTailWarps * 32)
     F32Bound<D> bx;
     bx.load(qp);
     // state holds the query's pending leaf: scan it, then walk on
-    int node = state[q];
-    if (node == kStart) node = next_leaf(t, bx, qp, node, bound);
-    for (; node != kDone; node = next_leaf(t, bx, qp, node, bound)) {
+    const uint64_t st = state[q];
+    int node = state_node(st);
+    uint32_t mask = state_mask(st);
+    if (node == kStart) node = next_leaf(t, bx, qp, node, mask, bound);
+    for (; node != kDone; node = next_leaf(t, bx, qp, node, mask, bound)) {
       const int leaf = node - first_leaf;
       const int np = t.leaf_cnt[leaf];
       const int nq = (np + 3) >> 2;
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(kTailWarps * 32)
       lst_d[(size_t)q * K + lane] = myd;
       lst_i[(size_t)q * K + lane] = myi;
     }
-    if (lane == 0) state[q] = kDone;
+    if (lane == 0) state[q] = trav_state(kDone, 0u);
   }
   if (lane == 0 && visits) {
     atomicAdd(&ctr->tail_pairs, pairs);
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(kTailWarps * 32)
 }  // namespace
 
 cudaError_t launch_tail(const DevTree& t, const float* pts,
-                        const uint32_t* act, int n_act, int32_t* state,
+                        const uint32_t* act, int n_act, uint64_t* state,
                         const float* qpad, float* lst_d, uint32_t* lst_i,
                         int K, Counters* ctr, int sm_count, cudaStream_t s) {
   if (n_act <= 0) return cudaSuccess;

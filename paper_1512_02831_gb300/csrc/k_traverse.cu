@@ -9,6 +9,8 @@
 //
 // The traversal step itself (stackless, exact bounding-box pruning) is
 // next_leaf() in traverse.cuh, shared with the tail and fallback kernels.
+#include <algorithm>
+
 #include "bkd_internal.h"
 #include "traverse.cuh"
 
@@ -19,7 +21,7 @@ __global__ void init_kernel(const float* __restrict__ Q, int64_t m, int d,
                             int Dp, float* __restrict__ qpad,
                             float* __restrict__ lst_d,
                             uint32_t* __restrict__ lst_i, int K,
-                            int32_t* __restrict__ state,
+                            uint64_t* __restrict__ state,
                             uint32_t* __restrict__ act, Counters* ctr) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= m) return;
@@ -34,16 +36,23 @@ __global__ void init_kernel(const float* __restrict__ Q, int64_t m, int d,
     lst_d[q * K + j] = __int_as_float(0x7f800000);  // +inf
     lst_i[q * K + j] = kNoSlot;
   }
-  state[q] = kStart;
+  state[q] = trav_state(kStart, 0u);
   act[q] = (uint32_t)q;
   if (bad) atomicOr(&ctr->err, kErrNonFinite);
 }
 
+constexpr int kFindThreads = 256;
+
+// One thread per active query.  The active list is ordered by leaf (the
+// previous round's scatter), so the lanes of a warp start from the same
+// leaf and mostly test the same boxes at the same time.  (Persistent lanes
+// that take a new query as soon as theirs is done were measured slower:
+// they lose that locality.)
 template <int D>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kFindThreads)
     find_leaf_kernel(DevTree t, const float* __restrict__ qpad,
                      const uint32_t* __restrict__ act, int n_act,
-                     int32_t* __restrict__ state,
+                     uint64_t* __restrict__ state,
                      const float* __restrict__ lst_d, int K,
                      int32_t* __restrict__ leaf_of,
                      int32_t* __restrict__ cnt) {
@@ -51,13 +60,15 @@ __global__ void __launch_bounds__(256)
   if (pos >= n_act) return;
   const uint32_t q = act[pos];
   const float* qp = qpad + (size_t)q * D;
-  const int node = state[q];
+  const uint64_t st = state[q];
+  const int node = state_node(st);
+  uint32_t mask = state_mask(st);
   const float bound = node == kStart ? __int_as_float(0x7f800000)
                                      : lst_d[(size_t)q * K + (K - 1)];
   F32Bound<D> bx;
   bx.load(qp);
-  const int next = next_leaf(t, bx, qp, node, bound);
-  state[q] = next;
+  const int next = next_leaf(t, bx, qp, node, mask, bound);
+  state[q] = trav_state(next, mask);
   if (next == kDone) {
     leaf_of[pos] = -1;
   } else {
@@ -246,7 +257,7 @@ inline int blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 }  // namespace
 
 cudaError_t launch_init(const float* Q, int64_t m, int d, int Dp, float* qpad,
-                        float* lst_d, uint32_t* lst_i, int K, int32_t* state,
+                        float* lst_d, uint32_t* lst_i, int K, uint64_t* state,
                         uint32_t* act, Counters* ctr, cudaStream_t s) {
   if (m == 0) return cudaSuccess;
   init_kernel<<<blocks(m, 256), 256, 0, s>>>(Q, m, d, Dp, qpad, lst_d, lst_i,
@@ -255,14 +266,15 @@ cudaError_t launch_init(const float* Q, int64_t m, int d, int Dp, float* qpad,
 }
 
 cudaError_t launch_find_leaf(const DevTree& t, const float* qpad,
-                             const uint32_t* act, int n_act, int32_t* state,
+                             const uint32_t* act, int n_act, uint64_t* state,
                              const float* lst_d, int K, int32_t* leaf_of,
                              int32_t* cnt, cudaStream_t s) {
   if (n_act == 0) return cudaSuccess;
-#define BKD_FIND_CASE(DIM)                                          \
-  case DIM:                                                         \
-    find_leaf_kernel<DIM><<<blocks(n_act, 256), 256, 0, s>>>(       \
-        t, qpad, act, n_act, state, lst_d, K, leaf_of, cnt);        \
+#define BKD_FIND_CASE(DIM)                                                  \
+  case DIM:                                                                 \
+    find_leaf_kernel<DIM><<<blocks(n_act, kFindThreads), kFindThreads, 0,   \
+                            s>>>(t, qpad, act, n_act, state, lst_d, K,      \
+                                 leaf_of, cnt);                             \
     return cudaGetLastError();
   switch (t.Dp) { BKD_DIMS(BKD_FIND_CASE) default: break; }
 #undef BKD_FIND_CASE

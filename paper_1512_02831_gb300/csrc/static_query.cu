@@ -40,7 +40,7 @@ constexpr int64_t kOffQpad = 0;
 constexpr int64_t kOffLstD = kOffQpad + align_up(kQ * kDc * 4);
 constexpr int64_t kOffLstI = kOffLstD + align_up(kQ * kKc * 4);
 constexpr int64_t kOffState = kOffLstI + align_up(kQ * kKc * 4);
-constexpr int64_t kOffActA = kOffState + align_up(kQ * 4);
+constexpr int64_t kOffActA = kOffState + align_up(kQ * 8);
 constexpr int64_t kOffActB = kOffActA + align_up(kQ * 4);
 constexpr int64_t kOffLeafOf = kOffActB + align_up(kQ * 4);
 constexpr int64_t kOffFb = kOffLeafOf + align_up(kQ * 4);
@@ -117,7 +117,7 @@ int run_static(const TreeView& v, char* base, const float* Q, int64_t m, int k,
   float* qpad = reinterpret_cast<float*>(base + kOffQpad);
   float* lst_d = reinterpret_cast<float*>(base + kOffLstD);
   uint32_t* lst_i = reinterpret_cast<uint32_t*>(base + kOffLstI);
-  int32_t* state = reinterpret_cast<int32_t*>(base + kOffState);
+  uint64_t* state = reinterpret_cast<uint64_t*>(base + kOffState);
   uint32_t* act = reinterpret_cast<uint32_t*>(base + kOffActA);
   uint32_t* nxt = reinterpret_cast<uint32_t*>(base + kOffActB);
   int32_t* leaf_of = reinterpret_cast<int32_t*>(base + kOffLeafOf);

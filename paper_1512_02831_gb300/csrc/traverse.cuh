@@ -3,12 +3,15 @@
 // visit, or kDone once the traversal has reached the root twice.
 //
 // Order: the depth-first order of the classical search -- near child (the
-// side of the split that holds q) before far child.  Stackless: the state is
-// the heap index of the last leaf.  The path from the root to it is encoded
-// in the index bits, so a pass over the path recovers every ancestor whose
-// far child is still unvisited (the path went through its near child) -- the
-// recursive search's backtracking stack -- and the next subtree to enter is
-// the far child of the DEEPEST such ancestor that survives pruning.
+// side of the split that holds q) before far child.  State: the heap index
+// of the last leaf (its bits encode the path from the root) and a mask with
+// bit l set when the child of the level-l ancestor that is NOT on the path
+// needs no further visit: the path went through the far child there (the
+// near child was visited before), or the far child was pruned.  The mask is
+// the recursive search's backtracking stack in 32 bits: the next subtree to
+// enter is the far child at the deepest level whose bit is clear and that
+// survives pruning.  A far child is tested at most once: pruned, it stays
+// pruned (the bound only shrinks); entered, it is on the path.
 //
 // Pruning: a subtree is skipped when the distance from q to the bounding box
 // of its points cannot beat the query's current bound.  This refines the
@@ -27,8 +30,8 @@
 //     B = sum of o_i^2 in dimension order from 0.0 -- the oracle's sequence --
 //     so B <= the binary64 distance of every point below; points enter on the
 //     key (D, index), so a subtree is visited while B <= bound.
-// A subtree whose near child is skipped is left through its last leaf in
-// depth-first order (always taking the far side), which marks it visited.
+// A near child that is pruned counts as visited: the walk continues with the
+// far child of its parent.
 #pragma once
 
 #include "bkd_internal.h"
@@ -71,10 +74,6 @@ struct F32Bound {
     }
     return b;
   }
-  __device__ static float plane(float q, float t) {
-    const float g = q < t ? __fsub_rn(t, q) : __fsub_rn(q, t);
-    return __fmul_rn(g, g);
-  }
 };
 
 // binary64 pruning bound of one query (the oracle's sequence).
@@ -93,82 +92,63 @@ struct F64Bound {
     }
     return b;
   }
-  __device__ static double plane(float q, float t) {
-    const double g = __dsub_rn((double)q, (double)t);
-    return __dmul_rn(g, g);
-  }
 };
 
-// Last leaf, in depth-first order, of the subtree of u (always the far side).
-// The split dimension of level l is l mod d, stepped incrementally.
-__device__ __forceinline__ int last_leaf(const DevTree& t,
-                                         const float* __restrict__ qp, int u) {
-  const int first_leaf = (1 << t.h) - 1;
-  int dim = heap_level(u) % t.d;
-  while (u < first_leaf) {
-    u = 2 * u + (qp[dim] < __ldg(t.split + u) ? 2 : 1);
-    dim = dim + 1 == t.d ? 0 : dim + 1;
-  }
-  return u;
+// Ancestor of heap node u (at level lu) at level l <= lu.
+__device__ __forceinline__ int ancestor(int u, int lu, int l) {
+  return (int)(((unsigned)u + 1u) >> (lu - l)) - 1;
 }
 
-// Deepest unvisited far child on the path of leaf `node` that survives
-// pruning, or -1.
-template <class B>
-__device__ __forceinline__ int climb(const DevTree& t, const B& bx,
-                                     const float* __restrict__ qp, int node,
-                                     typename B::T bound) {
-  const int h = t.h, d = t.d;
-  if (node == 0) return -1;
-  const unsigned path = (unsigned)(node + 1);
-  int dim = (h - 1) % d;
-  for (int level = h - 1; level >= 0;
-       --level, dim = dim == 0 ? d - 1 : dim - 1) {
-    const int anc = (int)(path >> (h - level)) - 1;
-    const float sv = __ldg(t.split + anc);
-    const float qs = qp[dim];
-    const bool near_left = qs < sv;
-    const bool went_left = ((path >> (h - 1 - level)) & 1u) == 0u;
-    if (went_left != near_left) continue;  // far child already on the path
-    if (!B::keep(B::plane(qs, sv), bound)) continue;  // box is beyond plane
-    const int far = 2 * anc + (near_left ? 2 : 1);
-    if (B::keep(bx.box(t, far), bound)) return far;
-  }
-  return -1;
-}
-
-// Next leaf (heap index) to visit after leaf `node` (kStart: enter at the
-// root), or kDone.
+// Next leaf (heap index) to visit after `node` (kStart: enter at the root),
+// or kDone; `mask` (see the header) is updated to the returned leaf's path.
+// One loop for both directions, one box test per iteration, so that the
+// lanes of a warp -- each on its own query -- stay in step as far as their
+// paths allow.  (The paper's hyperplane test needs no separate pass: the box
+// of a far child lies beyond the plane, so its bound is never smaller, in
+// either precision, and it prunes everything the plane test would.)
 template <class B>
 __device__ __forceinline__ int next_leaf(const DevTree& t, const B& bx,
                                          const float* __restrict__ qp,
-                                         int node, typename B::T bound) {
-  const int first_leaf = (1 << t.h) - 1;
-  int cand;
+                                         int node, uint32_t& mask,
+                                         typename B::T bound) {
+  const int h = t.h, d = t.d;
+  int u;      // descending: the node entered last; climbing: a finished node
+  bool down;  // descending (near child next) or climbing (open far child)
   if (node == kStart) {
+    mask = 0u;
     if (!B::keep(bx.box(t, 0), bound)) return kDone;
-    cand = 0;
+    u = 0;
+    down = true;
   } else {
-    cand = climb<B>(t, bx, qp, node, bound);
+    u = node;
+    down = false;
   }
-  while (cand >= 0) {
-    int v = cand;
-    int dim = heap_level(v) % t.d;
-    while (v < first_leaf) {
-      const int nc = 2 * v + (qp[dim] < __ldg(t.split + v) ? 1 : 2);
-      dim = dim + 1 == t.d ? 0 : dim + 1;
-      if (B::keep(bx.box(t, nc), bound)) {
-        v = nc;
-      } else {  // the near child holds nothing better: skip its subtree
-        node = last_leaf(t, qp, nc);
-        v = -1;
-        break;
-      }
+  for (;;) {
+    const int lu = heap_level(u);
+    int c, l = 0;
+    if (down) {
+      if (lu == h) return u;  // a leaf: visit it
+      c = 2 * u + (qp[lu % d] < __ldg(t.split + u) ? 1 : 2);  // near child
+    } else {
+      // the far child at the deepest level with a clear bit
+      const uint32_t open = ~mask & ((1u << lu) - 1u);
+      if (open == 0u) return kDone;
+      l = 31 - __clz(open);
+      const int p = ancestor(u, lu, l + 1);  // path node at level l + 1
+      c = 4 * ((p - 1) >> 1) + 3 - p;        // its sibling
+      mask |= 1u << l;  // finished from here on: pruned now, or entered now
+                        // (then it is on the path)
     }
-    if (v >= 0) return v;
-    cand = climb<B>(t, bx, qp, node, bound);
+    const bool pass = B::keep(bx.box(t, c), bound);
+    if (down) {
+      u = c;  // a pruned near child is finished without a visit; its far
+      down = pass;  // sibling (clear bit) is next in line
+    } else if (pass) {
+      u = c;
+      mask &= (2u << l) - 1u;  // levels below l: a new path
+      down = true;
+    }
   }
-  return kDone;
 }
 
 }  // namespace bkd
