@@ -21,9 +21,11 @@
 //     k-d tree search (Sec. 2.3) with the exact key, skipping subtrees whose
 //     binary64 bounding-box distance exceeds min(current k-th D64,
 //     hi(v_{k-1})) -- hi(v_{k-1}) bounds the true k-th distance from above
-//     because k points score at most v_{k-1}.  A point's binary64 distance
-//     is formed only when lo of its float32 distance does not exceed that
-//     seed bound.
+//     because k points score at most v_{k-1}.  The traversal and the point
+//     filter compare float32 values against that bound widened to
+//     r (1 + gam) + eta (every point or box with D64 <= r scores at most
+//     that in float32); a point's binary64 distance is formed only when it
+//     passes.
 #include <cmath>
 
 #include "bkd.h"
@@ -38,6 +40,7 @@ namespace {
 // only widens.
 struct Bounds {
   double eta, rlo, rhi;
+  double gup;  // >= 1 + gam
 };
 __device__ __forceinline__ double lo_bound(float v, const Bounds& b) {
   return __dmul_rd(__dsub_rd((double)v, b.eta), b.rlo);
@@ -146,10 +149,23 @@ __global__ void recheck_kernel(DevTree t, int64_t m, int k, int K,
   }
 }
 
-constexpr int kFbWarps = 4;
+// A binary64 distance bound r as a float32 bound on the float32 chain: a
+// point or box with D64 <= r scores v <= r (1 + gam) + eta, rounded up here;
+// returned as the next float above it, for the strict test of F32Bound.
+__device__ __forceinline__ float f32_bound(double r, const Bounds& b) {
+  if (isinf(r)) return __int_as_float(0x7f800000);
+  const float v = __double2float_ru(__dadd_ru(__dmul_ru(r, b.gup), b.eta));
+  if (isinf(v)) return v;
+  return __int_as_float(__float_as_int(v) + 1);  // v >= 0: the next float
+}
 
-// One warp per query.  Lane j < k owns entry j of the sorted binary64 list.
-__global__ void __launch_bounds__(32 * kFbWarps)
+// One warp per query (one warp per CTA, so that the few fallback queries
+// spread over the SMs).  Lane j < k owns entry j of the sorted binary64
+// list.  The traversal and the point filter run on float32 values with the
+// bound widened by f32_bound (the binary64 pipe is narrow); only points that
+// pass get their binary64 distance.
+template <int D>
+__global__ void __launch_bounds__(32)
     fallback_kernel(DevTree t, int n_fb, const uint32_t* __restrict__ fb_list,
                     int k, int K, const float* __restrict__ qpad,
                     const float* __restrict__ lst_d,
@@ -157,11 +173,13 @@ __global__ void __launch_bounds__(32 * kFbWarps)
                     float* __restrict__ out_dist, Bounds bd) {
   const int lane = threadIdx.x & 31;
   const int first_leaf = (1 << t.h) - 1;
-  for (int f = blockIdx.x * kFbWarps + (threadIdx.x >> 5); f < n_fb;
-       f += gridDim.x * kFbWarps) {
+  for (int f = blockIdx.x; f < n_fb; f += gridDim.x) {
     const int64_t q = fb_list[f];
-    const float* qp = qpad + q * t.Dp;
+    const float* qp = qpad + q * D;
+    F32Bound<D> bx;
+    bx.load(qp);
     const double seed = hi_bound(lst_d[q * K + (k - 1)], bd);
+    const float seed32 = f32_bound(seed, bd);
     double myd = __longlong_as_double(0x7ff0000000000000ll);  // +inf
     int64_t myi = INT64_MAX;
     int cnt = 0;  // warp-uniform
@@ -169,8 +187,8 @@ __global__ void __launch_bounds__(32 * kFbWarps)
     uint32_t mask = 0;
     for (;;) {
       const double kd = __shfl_sync(0xffffffffu, myd, k - 1);
-      node = next_leaf(t, F64Bound{qp}, qp, node, mask,
-                       cnt == k ? fmin(kd, seed) : seed);
+      node = next_leaf(t, bx, qp, node, mask,
+                       f32_bound(cnt == k ? fmin(kd, seed) : seed, bd));
       if (node == kDone) break;
       // ---- scan the leaf
       const int leaf = node - first_leaf;
@@ -181,12 +199,8 @@ __global__ void __launch_bounds__(32 * kFbWarps)
         double dv = 0.0;
         int64_t iv = 0;
         bool cand = false;
-        // D64 >= lo(v): the binary64 distance is formed only where the
-        // float32 one leaves room for D64 <= seed (binary64 is slow here)
-        if (u < np &&
-            lo_bound(dist32(qp, t.pts, t.Dp, t.d, base + u), bd) <=
-                seed) {
-          dv = dist64(qp, t.pts, t.Dp, t.d, base + u);
+        if (u < np && dist32(qp, t.pts, D, t.d, base + u) < seed32) {
+          dv = dist64(qp, t.pts, D, t.d, base + u);
           iv = t.orig[base + u];
           cand = dv <= seed;
         }
@@ -228,6 +242,7 @@ Bounds bounds_for(int d) {
   b.eta = 7.52316384526264e-37;
   b.rlo = std::nextafter(1.0 / (1.0 + gam), 0.0);
   b.rhi = std::nextafter(1.0 / (1.0 - gam), 2.0);
+  b.gup = std::nextafter(1.0 + gam, 2.0);
   return b;
 }
 
@@ -249,11 +264,16 @@ cudaError_t launch_fallback(const DevTree& t, int n_fb, const uint32_t* fb_list,
                             int k, int K, const float* qpad, const float* lst_d,
                             int64_t* out_idx, float* out_dist, cudaStream_t s) {
   if (n_fb == 0) return cudaSuccess;
-  const int grid = (n_fb + kFbWarps - 1) / kFbWarps;
-  fallback_kernel<<<grid < 4096 ? grid : 4096, 32 * kFbWarps, 0, s>>>(
-      t, n_fb, fb_list, k, K, qpad, lst_d, out_idx, out_dist,
-      bounds_for(t.d));
-  return cudaGetLastError();
+  const int grid = n_fb < 65536 ? n_fb : 65536;
+#define BKD_FB_CASE(DIM)                                                  \
+  case DIM:                                                               \
+    fallback_kernel<DIM><<<grid, 32, 0, s>>>(t, n_fb, fb_list, k, K, qpad, \
+                                             lst_d, out_idx, out_dist,     \
+                                             bounds_for(t.d));             \
+    return cudaGetLastError();
+  switch (t.Dp) { BKD_DIMS(BKD_FB_CASE) default: break; }
+#undef BKD_FB_CASE
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace bkd

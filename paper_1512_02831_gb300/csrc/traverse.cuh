@@ -18,18 +18,15 @@
 // paper's hyperplane test (the box lies beyond the hyperplane, so its
 // distance is never smaller) and changes only how many leaves are visited,
 // never the result:
-//   * float32 pass: per dimension o_i = fl(lo_i - q_i) or fl(q_i - hi_i)
-//     (0 inside the box) and B = fl(o_0^2), B = fma(o_i, o_i, B) for
-//     i = 1..d-1 -- the same float32 chain that scores a point.  For every
-//     point x in the box |fl(q_i - x_i)| >= o_i (rounding is monotone) and
-//     each chain step is monotone in both arguments, so B <= the float32
-//     distance of every point below the node.  A point enters a list only if
-//     its distance is strictly below the list's last entry `bound`, so
-//     skipping when B >= bound is exact.
-//   * binary64 search: o_i in binary64 (exact differences of floats) and
-//     B = sum of o_i^2 in dimension order from 0.0 -- the oracle's sequence --
-//     so B <= the binary64 distance of every point below; points enter on the
-//     key (D, index), so a subtree is visited while B <= bound.
+// per dimension o_i = fl(lo_i - q_i) or fl(q_i - hi_i) (0 inside the box)
+// and B = fl(o_0^2), B = fma(o_i, o_i, B) for i = 1..d-1 -- the same float32
+// chain that scores a point.  For every point x in the box
+// |fl(q_i - x_i)| >= o_i (rounding is monotone) and each chain step is
+// monotone in both arguments, so B <= the float32 distance of every point
+// below the node.  A point enters a list only if its distance is strictly
+// below the list's last entry `bound`, so skipping when B >= bound is exact.
+// (The binary64 fallback search passes a bound widened to cover its
+// binary64 key, see k_exact.cu.)
 // A near child that is pruned counts as visited: the walk continues with the
 // far child of its parent.
 #pragma once
@@ -71,24 +68,6 @@ struct F32Bound {
       const float q = x[i], l = f[i], u = f[D + i];
       const float o = q < l ? __fsub_rn(l, q) : (q > u ? __fsub_rn(q, u) : 0.f);
       b = i == 0 ? __fmul_rn(o, o) : __fmaf_rn(o, o, b);
-    }
-    return b;
-  }
-};
-
-// binary64 pruning bound of one query (the oracle's sequence).
-struct F64Bound {
-  using T = double;
-  const float* qp;
-  __device__ static bool keep(double b, double bound) { return b <= bound; }
-  __device__ double box(const DevTree& t, int node) const {
-    const float* lo = t.box + (size_t)node * 2 * t.Dp;
-    const float* hi = lo + t.Dp;
-    double b = 0.0;
-    for (int i = 0; i < t.d; ++i) {
-      const double q = qp[i], l = __ldg(lo + i), u = __ldg(hi + i);
-      const double o = q < l ? __dsub_rn(l, q) : (q > u ? __dsub_rn(q, u) : 0.0);
-      b = __dadd_rn(b, __dmul_rn(o, o));
     }
     return b;
   }
