@@ -135,7 +135,8 @@ struct bkd_tree {
   DevBuf<float> qdev, qpad, lst_d;
   DevBuf<uint32_t> lst_i, act_a, act_b, fb_list;
   DevBuf<uint64_t> state;  // per query: TravState
-  DevBuf<int32_t> leaf_of, cnt, off, cursor, toff, chunk_item;
+  DevBuf<int2> placed;  // per active position: (next leaf, rank in its buffer)
+  DevBuf<int32_t> cnt, off, cursor, toff, chunk_item;
   DevBuf<Item> items;
   DevBuf<int64_t> out_idx;
   DevBuf<float> out_dist;
@@ -197,7 +198,7 @@ void release(bkd_tree* t) {
   t->act_b.release();
   t->fb_list.release();
   t->state.release();
-  t->leaf_of.release();
+  t->placed.release();
   t->cnt.release();
   t->off.release();
   t->cursor.release();
@@ -519,7 +520,7 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   CU(t->state.ensure(m));
   CU(t->act_a.ensure(m));
   CU(t->act_b.ensure(m));
-  CU(t->leaf_of.ensure(m));
+  CU(t->placed.ensure(m));
   CU(t->fb_list.ensure(m));
   CU(t->cnt.ensure(L));
   CU(t->cursor.ensure(std::max<int64_t>(L, 4)));  // also holds the scan's tile sums
@@ -560,13 +561,13 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
     if (f0) cudaEventRecord(f0, s);
     CU(cudaMemsetAsync(t->cnt.p, 0, sizeof(int32_t) * L, s));
     CU(launch_find_leaf(D, t->qpad.p, act, n_act, t->state.p, t->lst_d.p, K,
-                        t->leaf_of.p, t->cnt.p, s));
+                        t->placed.p, t->cnt.p, s));
     if (f1) cudaEventRecord(f1, s);
     if (f0 && f1) t->find_ev.push_back({f0, f1});
     t->st_launches += 1;
     cudaEvent_t b0 = t->next_event(), b1 = t->next_event();
     if (b0) cudaEventRecord(b0, s);
-    CU(launch_bucket(t->leaf_of.p, act, n_act, (int)L,
+    CU(launch_bucket(t->placed.p, act, n_act, (int)L,
                      screened ? kScreenTile : kPipeTile,
                      t->d_leaf_cnt, t->cnt.p, t->off.p, t->cursor.p,
                      t->toff.p, t->items.p, nxt, t->d_ctr, s));

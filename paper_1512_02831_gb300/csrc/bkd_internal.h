@@ -104,19 +104,20 @@ cudaError_t launch_init(const float* Q, int64_t m, int d, int Dp, float* qpad,
                         uint32_t* act, Counters* ctr, cudaStream_t s);
 
 // FindLeafBatch from the traversal states in `state` (kStart for the first
-// round): next leaf per position of `act` in leaf_of (-1: done), the new
-// pending leaf in state, and +1 in cnt[leaf] for every query that goes on.
+// round): per position of `act`, placed = (next leaf, rank among the
+// queries that go to it) or (-1, 0) when done; the new pending leaf in
+// state; cnt[leaf] counts the queries that go on (cnt must start at 0).
 cudaError_t launch_find_leaf(const DevTree& t, const float* qpad,
                              const uint32_t* act, int n_act, uint64_t* state,
-                             const float* lst_d, int K, int32_t* leaf_of,
+                             const float* lst_d, int K, int2* placed,
                              int32_t* cnt, cudaStream_t s);
 
-// Buffer insertion from per-leaf counts `cnt` (filled by FindLeafBatch):
-// offsets, work items of `tile` queries, round totals, and the active list
-// bucketed by leaf into `next`.  cursor must hold max(n_leaves, 4) int32:
-// between the two scan passes it carries one 16-byte partial sum per 2,048
-// leaves.
-cudaError_t launch_bucket(const int32_t* leaf_of, const uint32_t* act,
+// Buffer insertion from per-leaf counts `cnt` and the placements of
+// FindLeafBatch: offsets, work items of `tile` queries, round totals, and
+// the active list bucketed by leaf into `next`.  cursor must hold
+// max(n_leaves, 4) int32: between the two scan passes it carries one
+// 16-byte partial sum per 2,048 leaves.
+cudaError_t launch_bucket(const int2* placed, const uint32_t* act,
                           int n_act, int n_leaves, int tile,
                           const int32_t* leaf_cnt, const int32_t* cnt,
                           int32_t* off, int32_t* cursor, int32_t* toff,

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kFindThreads)
                      const uint32_t* __restrict__ act, int n_act,
                      uint64_t* __restrict__ state,
                      const float* __restrict__ lst_d, int K,
-                     int32_t* __restrict__ leaf_of,
+                     int2* __restrict__ placed,
                      int32_t* __restrict__ cnt) {
   const int pos = blockIdx.x * blockDim.x + threadIdx.x;
   if (pos >= n_act) return;
@@ -70,11 +70,11 @@ __global__ void __launch_bounds__(kFindThreads)
   const int next = next_leaf(t, bx, qp, node, mask, bound);
   state[q] = trav_state(next, mask);
   if (next == kDone) {
-    leaf_of[pos] = -1;
+    placed[pos] = make_int2(-1, 0);
   } else {
+    // the count before this query is its rank in the leaf's buffer
     const int leaf = next - ((1 << t.h) - 1);
-    leaf_of[pos] = leaf;
-    atomicAdd(cnt + leaf, 1);
+    placed[pos] = make_int2(leaf, atomicAdd(cnt + leaf, 1));
   }
 }
 
@@ -233,16 +233,15 @@ __global__ void __launch_bounds__(kScanBlock)
   }
 }
 
-__global__ void scatter_kernel(const int32_t* __restrict__ leaf_of,
+__global__ void scatter_kernel(const int2* __restrict__ placed,
                                const uint32_t* __restrict__ act, int n,
                                const int32_t* __restrict__ off,
-                               int32_t* __restrict__ cursor,
                                uint32_t* __restrict__ next) {
   const int pos = blockIdx.x * blockDim.x + threadIdx.x;
   if (pos >= n) return;
-  const int l = leaf_of[pos];
-  if (l < 0) return;
-  next[off[l] + atomicAdd(cursor + l, 1)] = act[pos];
+  const int2 p = placed[pos];
+  if (p.x < 0) return;
+  next[off[p.x] + p.y] = act[pos];
 }
 
 __global__ void chunk_items_kernel(const int32_t* __restrict__ toff,
@@ -267,28 +266,28 @@ cudaError_t launch_init(const float* Q, int64_t m, int d, int Dp, float* qpad,
 
 cudaError_t launch_find_leaf(const DevTree& t, const float* qpad,
                              const uint32_t* act, int n_act, uint64_t* state,
-                             const float* lst_d, int K, int32_t* leaf_of,
+                             const float* lst_d, int K, int2* placed,
                              int32_t* cnt, cudaStream_t s) {
   if (n_act == 0) return cudaSuccess;
 #define BKD_FIND_CASE(DIM)                                                  \
   case DIM:                                                                 \
     find_leaf_kernel<DIM><<<blocks(n_act, kFindThreads), kFindThreads, 0,   \
                             s>>>(t, qpad, act, n_act, state, lst_d, K,      \
-                                 leaf_of, cnt);                             \
+                                 placed, cnt);                              \
     return cudaGetLastError();
   switch (t.Dp) { BKD_DIMS(BKD_FIND_CASE) default: break; }
 #undef BKD_FIND_CASE
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_bucket(const int32_t* leaf_of, const uint32_t* act,
+cudaError_t launch_bucket(const int2* placed, const uint32_t* act,
                           int n_act, int n_leaves, int tile,
                           const int32_t* leaf_cnt, const int32_t* cnt,
                           int32_t* off, int32_t* cursor, int32_t* toff,
                           Item* items, uint32_t* next, Counters* ctr,
                           cudaStream_t s) {
   // the cursor array (4 bytes per leaf) holds the 16-byte tile sums (one per
-  // 2,048 leaves) until the scan is done, then is cleared for the scatter
+  // 2,048 leaves)
   ScanPart* parts = reinterpret_cast<ScanPart*>(cursor);
   const int nparts = blocks(n_leaves, kScanTile);
   scan_parts_kernel<<<nparts, kScanBlock, 0, s>>>(cnt, n_leaves, tile,
@@ -296,11 +295,9 @@ cudaError_t launch_bucket(const int32_t* leaf_of, const uint32_t* act,
   scan_write_kernel<<<nparts, kScanBlock, 0, s>>>(cnt, n_leaves, tile,
                                                   leaf_cnt, parts, off, toff,
                                                   items, ctr);
-  cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(int32_t) * n_leaves, s);
-  if (e != cudaSuccess) return e;
   if (n_act > 0)
-    scatter_kernel<<<blocks(n_act, 256), 256, 0, s>>>(leaf_of, act, n_act, off,
-                                                      cursor, next);
+    scatter_kernel<<<blocks(n_act, 256), 256, 0, s>>>(placed, act, n_act, off,
+                                                      next);
   return cudaGetLastError();
 }
 

@@ -42,8 +42,8 @@ constexpr int64_t kOffLstI = kOffLstD + align_up(kQ * kKc * 4);
 constexpr int64_t kOffState = kOffLstI + align_up(kQ * kKc * 4);
 constexpr int64_t kOffActA = kOffState + align_up(kQ * 8);
 constexpr int64_t kOffActB = kOffActA + align_up(kQ * 4);
-constexpr int64_t kOffLeafOf = kOffActB + align_up(kQ * 4);
-constexpr int64_t kOffFb = kOffLeafOf + align_up(kQ * 4);
+constexpr int64_t kOffPlaced = kOffActB + align_up(kQ * 4);
+constexpr int64_t kOffFb = kOffPlaced + align_up(kQ * 8);
 constexpr int64_t kOffCnt = kOffFb + align_up(kQ * 4);
 constexpr int64_t kOffCursor = kOffCnt + align_up(kL * 4);
 constexpr int64_t kOffOff = kOffCursor + align_up(kL * 4);
@@ -120,7 +120,7 @@ int run_static(const TreeView& v, char* base, const float* Q, int64_t m, int k,
   uint64_t* state = reinterpret_cast<uint64_t*>(base + kOffState);
   uint32_t* act = reinterpret_cast<uint32_t*>(base + kOffActA);
   uint32_t* nxt = reinterpret_cast<uint32_t*>(base + kOffActB);
-  int32_t* leaf_of = reinterpret_cast<int32_t*>(base + kOffLeafOf);
+  int2* placed = reinterpret_cast<int2*>(base + kOffPlaced);
   uint32_t* fb = reinterpret_cast<uint32_t*>(base + kOffFb);
   int32_t* cnt = reinterpret_cast<int32_t*>(base + kOffCnt);
   int32_t* cursor = reinterpret_cast<int32_t*>(base + kOffCursor);
@@ -132,7 +132,7 @@ int run_static(const TreeView& v, char* base, const float* Q, int64_t m, int k,
 
   // The counters keep the previous call's values: clear them.  Everything
   // else is fully written before it is read (init writes lists, state and the
-  // active list; the bucketing pass clears cnt / cursor itself).
+  // active list; every round clears cnt before FindLeafBatch).
   SQ_CU(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
   SQ_CU(launch_init(Q, m, D.d, D.Dp, qpad, lst_d, lst_i, K, state, act, ctr,
                     s));
@@ -140,9 +140,9 @@ int run_static(const TreeView& v, char* base, const float* Q, int64_t m, int k,
   int n_act = (int)m;
   for (;;) {
     SQ_CU(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * v.n_leaves, s));
-    SQ_CU(launch_find_leaf(D, qpad, act, n_act, state, lst_d, K, leaf_of,
+    SQ_CU(launch_find_leaf(D, qpad, act, n_act, state, lst_d, K, placed,
                            cnt, s));
-    SQ_CU(launch_bucket(leaf_of, act, n_act, (int)v.n_leaves, kPipeTile,
+    SQ_CU(launch_bucket(placed, act, n_act, (int)v.n_leaves, kPipeTile,
                         D.leaf_cnt, cnt, off, cursor, toff, items, nxt, ctr,
                         s));
     SQ_CU(cudaMemcpyAsync(h, ctr, sizeof(Counters), cudaMemcpyDeviceToHost,
