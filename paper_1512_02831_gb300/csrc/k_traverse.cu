@@ -41,7 +41,7 @@ __global__ void init_kernel(const float* __restrict__ Q, int64_t m, int d,
   if (bad) atomicOr(&ctr->err, kErrNonFinite);
 }
 
-constexpr int kFindThreads = 256;
+constexpr int kFindThreads = 128;
 
 // One thread per active query.  The active list is ordered by leaf (the
 // previous round's scatter), so the lanes of a warp start from the same
