@@ -57,11 +57,11 @@ extern "C" {
 
 /* ------------------------------------------------------------------ limits */
 #define BKD_MAX_DIM 32        /* d <= BKD_MAX_DIM                              */
-#define BKD_MAX_K 31          /* k <= BKD_MAX_K                                */
+#define BKD_MAX_K 63          /* k <= BKD_MAX_K                                */
 #define BKD_MAX_HEIGHT 24     /* height <= BKD_MAX_HEIGHT                      */
 #define BKD_STATIC_MAX_QUERIES 4096      /* m limit of bkd_query_static      */
 #define BKD_STATIC_MAX_HEIGHT 16         /* tree height limit of it          */
-#define BKD_STATIC_SCRATCH_BYTES 4194304 /* its static device scratch area   */
+#define BKD_STATIC_SCRATCH_BYTES 8388608 /* its static device scratch area   */
 
 /* ----------------------------------------------------------------- options
  * Set with bkd_set_option (after build) or passed as (key, value) pairs to
@@ -86,7 +86,7 @@ enum bkd_option {
   /* When at most this many queries remain active, they finish in one launch
    * (one warp per query walks its remaining leaves) instead of one
    * LazySearch round per leaf.  -1 (default) = automatic (8192); 0 = never.
-   * Results do not depend on it.  Any time. */
+   * Used for k <= 31 only.  Results do not depend on it.  Any time. */
   BKD_OPT_TAIL_QUERIES = 5,
   /* Leaf scoring: 0 (default) = float32 for every (query, point) pair;
    * 1 = a BF16 tensor-core screen rejects points that provably cannot enter

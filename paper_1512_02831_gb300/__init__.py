@@ -29,7 +29,7 @@ BKD_ECUDA = -3
 BKD_ETIMEOUT = -4
 BKD_EUNSUPPORTED = -5
 BKD_MAX_DIM = 32
-BKD_MAX_K = 31
+BKD_MAX_K = 63
 BKD_MAX_HEIGHT = 24
 BKD_STATIC_MAX_QUERIES = 4096
 BKD_STATIC_MAX_HEIGHT = 16

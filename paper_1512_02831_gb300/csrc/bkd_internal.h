@@ -38,7 +38,7 @@ constexpr uint32_t kNoSlot = 0xffffffffu;
 constexpr int kDims[] = {2, 4, 6, 8, 10, 12, 16, 24, 32};
 // X(Dp) for every entry of kDims (kernel instantiation lists).
 #define BKD_DIMS(X) X(2) X(4) X(6) X(8) X(10) X(12) X(16) X(24) X(32)
-constexpr int kCaps[] = {2, 4, 8, 12, 16, 32};
+constexpr int kCaps[] = {2, 4, 8, 12, 16, 32, 64};
 
 int padded_dim(int d);       // smallest compiled dimension >= d (0: none)
 int list_capacity(int K);    // smallest compiled capacity >= K (0: none)

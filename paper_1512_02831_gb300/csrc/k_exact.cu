@@ -160,10 +160,12 @@ __device__ __forceinline__ float f32_bound(double r, const Bounds& b) {
 }
 
 // One warp per query (one warp per CTA, so that the few fallback queries
-// spread over the SMs).  Lane j < k owns entry j of the sorted binary64
-// list.  The traversal and the point filter run on float32 values with the
-// bound widened by f32_bound (the binary64 pipe is narrow); only points that
-// pass get their binary64 distance.
+// spread over the SMs).  The sorted binary64 list (k entries) lives in
+// shared memory; candidates -- rare: only points that pass the float32
+// filter -- are inserted by lane 0 one at a time.  The traversal and the
+// point filter run on float32 values with the bound widened by f32_bound
+// (the binary64 pipe is narrow); only points that pass get their binary64
+// distance.
 template <int D>
 __global__ void __launch_bounds__(32)
     fallback_kernel(DevTree t, int n_fb, const uint32_t* __restrict__ fb_list,
@@ -171,6 +173,8 @@ __global__ void __launch_bounds__(32)
                     const float* __restrict__ lst_d,
                     int64_t* __restrict__ out_idx,
                     float* __restrict__ out_dist, Bounds bd) {
+  __shared__ double s_d[BKD_MAX_K];
+  __shared__ int64_t s_i[BKD_MAX_K];
   const int lane = threadIdx.x & 31;
   const int first_leaf = (1 << t.h) - 1;
   for (int f = blockIdx.x; f < n_fb; f += gridDim.x) {
@@ -180,15 +184,13 @@ __global__ void __launch_bounds__(32)
     bx.load(qp);
     const double seed = hi_bound(lst_d[q * K + (k - 1)], bd);
     const float seed32 = f32_bound(seed, bd);
-    double myd = __longlong_as_double(0x7ff0000000000000ll);  // +inf
-    int64_t myi = INT64_MAX;
-    int cnt = 0;  // warp-uniform
+    int cnt = 0;  // entries in the list (warp-uniform)
     int node = kStart;
     uint32_t mask = 0;
     for (;;) {
-      const double kd = __shfl_sync(0xffffffffu, myd, k - 1);
-      node = next_leaf(t, bx, qp, node, mask,
-                       f32_bound(cnt == k ? fmin(kd, seed) : seed, bd));
+      // the bound: min(k-th D64, seed) once the list is full
+      const double r = cnt == k ? fmin(s_d[k - 1], seed) : seed;
+      node = next_leaf(t, bx, qp, node, mask, f32_bound(r, bd));
       if (node == kDone) break;
       // ---- scan the leaf
       const int leaf = node - first_leaf;
@@ -204,34 +206,33 @@ __global__ void __launch_bounds__(32)
           iv = t.orig[base + u];
           cand = dv <= seed;
         }
-        unsigned mask = __ballot_sync(0xffffffffu, cand);
-        while (mask) {
-          const int src = __ffs(mask) - 1;
-          mask &= mask - 1;
+        unsigned m = __ballot_sync(0xffffffffu, cand);
+        while (m) {
+          const int src = __ffs(m) - 1;
+          m &= m - 1;
           const double cd = __shfl_sync(0xffffffffu, dv, src);
           const int64_t ci = __shfl_sync(0xffffffffu, iv, src);
-          const double kd2 = __shfl_sync(0xffffffffu, myd, k - 1);
-          const int64_t ki = __shfl_sync(0xffffffffu, myi, k - 1);
-          if (cnt == k && !key_less(cd, ci, kd2, ki)) continue;
-          const bool less = lane < cnt && key_less(myd, myi, cd, ci);
-          const int pos = __popc(__ballot_sync(0xffffffffu, less));
-          const double upd = __shfl_up_sync(0xffffffffu, myd, 1);
-          const int64_t upi = __shfl_up_sync(0xffffffffu, myi, 1);
-          if (lane > pos) {
-            myd = upd;
-            myi = upi;
-          } else if (lane == pos) {
-            myd = cd;
-            myi = ci;
+          if (lane == 0 &&
+              (cnt < k || key_less(cd, ci, s_d[k - 1], s_i[k - 1]))) {
+            int p = cnt < k ? cnt : k - 1;
+            while (p > 0 && key_less(cd, ci, s_d[p - 1], s_i[p - 1])) {
+              s_d[p] = s_d[p - 1];
+              s_i[p] = s_i[p - 1];
+              --p;
+            }
+            s_d[p] = cd;
+            s_i[p] = ci;
           }
           cnt = min(cnt + 1, k);
+          __syncwarp();
         }
       }
     }
-    if (lane < k) {
-      out_idx[q * k + lane] = myi;
-      out_dist[q * k + lane] = (float)myd;
+    for (int j = lane; j < k; j += 32) {
+      out_idx[q * k + j] = s_i[j];
+      out_dist[q * k + j] = (float)s_d[j];
     }
+    __syncwarp();
   }
 }
 

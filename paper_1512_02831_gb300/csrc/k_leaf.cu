@@ -15,6 +15,7 @@ const void* kernel_for(int Dp, int cap) {
     case 12: return leaf_kernel_c12(Dp);
     case 16: return leaf_kernel_c16(Dp);
     case 32: return leaf_kernel_c32(Dp);
+    case 64: return leaf_kernel_c64(Dp);
     default: return nullptr;
   }
 }
@@ -48,6 +49,7 @@ cudaError_t launch_leaf(const DevTree& t, int cap, const Item* items,
     case 12: return leaf_launch_c12(BKD_ARGS);
     case 16: return leaf_launch_c16(BKD_ARGS);
     case 32: return leaf_launch_c32(BKD_ARGS);
+    case 64: return leaf_launch_c64(BKD_ARGS);
     default: return cudaErrorInvalidValue;
   }
 #undef BKD_ARGS

@@ -326,6 +326,7 @@ BKD_LEAF_DECLARE(8)
 BKD_LEAF_DECLARE(12)
 BKD_LEAF_DECLARE(16)
 BKD_LEAF_DECLARE(32)
+BKD_LEAF_DECLARE(64)
 
 #define BKD_LEAF_DIMS(X) BKD_DIMS(X)
 

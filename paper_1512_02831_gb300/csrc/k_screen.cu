@@ -536,7 +536,8 @@ const void* screen_kernel_for(int kh) {
 
 int screen_grid(int kh, int64_t lcap, int K, int sm_count) {
   // slots in a queue entry: 27 bits
-  if (kh < 1 || kh > 3 || K < 1 || K > 32 || lcap >= ((int64_t)1 << 27))
+  if (kh < 1 || kh > 3 || K < 1 || K > BKD_MAX_K + 1 ||
+      lcap >= ((int64_t)1 << 27))
     return 0;
   const size_t smem = screen_smem(kh, K);
   const void* k = screen_kernel_for(kh);

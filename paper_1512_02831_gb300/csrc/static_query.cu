@@ -32,7 +32,7 @@ constexpr int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlig
 
 constexpr int64_t kQ = BKD_STATIC_MAX_QUERIES;
 constexpr int64_t kL = (int64_t)1 << BKD_STATIC_MAX_HEIGHT;
-constexpr int64_t kKc = 32;              // largest list capacity (k+1 <= 32)
+constexpr int64_t kKc = BKD_MAX_K + 1;   // largest list length k + 1
 constexpr int64_t kDc = BKD_MAX_DIM;     // largest compiled dimension
 
 // Byte offsets of the pieces carved out of the scratch array.

@@ -61,7 +61,7 @@ def test_every_dimension(d):
     check(P, Q, k, idx, dist, oracle.brute_knn(P, Q, k))
 
 
-@pytest.mark.parametrize("k", [1, 2, 3, 4, 7, 8, 11, 15, 16, 31])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 7, 8, 11, 15, 16, 31, 32, 50, 63])
 def test_every_list_capacity(k):
     P = workloads.uniform(5000, 6, 7)
     Q = workloads.uniform(700, 6, 8)
@@ -87,14 +87,15 @@ def test_k_equals_n():
     check(P, Q, 29, idx, dist, oracle.brute_knn(P, Q, 29))
 
 
-def test_all_points_identical():
+@pytest.mark.parametrize("k", [9, 50])
+def test_all_points_identical(k):
     P = np.full((600, 5), 0.25, np.float32)
     Q = np.concatenate([np.full((3, 5), 0.25, np.float32),
                         workloads.uniform(40, 5, 1)])
-    idx, dist, stats = run(P, Q, 9, 4)
-    ref = oracle.brute_knn(P, Q, 9)
-    check(P, Q, 9, idx, dist, ref)
-    assert (idx == np.arange(9)).all()   # all tie: smallest indices win
+    idx, dist, stats = run(P, Q, k, 4)
+    ref = oracle.brute_knn(P, Q, k)
+    check(P, Q, k, idx, dist, ref)
+    assert (idx == np.arange(k)).all()   # all tie: smallest indices win
     assert stats["fallback"] == Q.shape[0]
 
 
@@ -286,7 +287,8 @@ def run_both_precisions(P, Q, k, h, **opts):
 
 
 @pytest.mark.parametrize("d,k", [(2, 4), (3, 10), (10, 10), (10, 1), (10, 31),
-                                 (16, 10), (17, 10), (27, 5), (32, 10)])
+                                 (16, 10), (17, 10), (27, 5), (32, 10),
+                                 (27, 50), (10, 63)])
 def test_bf16_screen_is_bit_identical(d, k):
     """The BF16 tensor-core screen only skips points that provably cannot
     enter a list; survivors are scored in float32, so results equal the
@@ -335,3 +337,22 @@ def test_bf16_screen_option_errors():
     with pytest.raises(bkd.BkdError) as e:
         bkd.bkd_build(P, 4, precision=1, chunks=2)
     assert e.value.code == bkd.BKD_EUNSUPPORTED
+
+
+def test_d27_k50_duplicates_workload():
+    """The d = 27, k = 50 workload (64-component mixture, 1% of the rows
+    exact copies of others) at a size the oracle finishes: default options
+    (tail kernel automatic, which lists of k + 1 > 32 entries do not use)
+    and the BF16 screen, both against the oracle."""
+    w = workloads.scaled(workloads.MIXTURE_D27, 1 << 16, 2000, 8)
+    P, Q = w.points(), w.queries()
+    ref = oracle.brute_knn(P, Q, 50)
+    tree = bkd.bkd_build(P, w.height, precision=1)
+    try:
+        for prec in (0, 1):
+            bkd.bkd_set_option(tree, "precision", prec)
+            idx, dist = bkd.bkd_query(tree, Q, 50)
+            check(P, Q, 50, idx, dist, ref)
+            assert bkd.bkd_get_stat(tree, "tail_queries") == 0
+    finally:
+        bkd.bkd_free(tree)
