@@ -61,6 +61,10 @@ def args_():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--latency-seconds", type=float, default=4.0,
+                    help="time budget of the per-batch latency sample")
+    ap.add_argument("--streamer", action="store_true",
+                    help="measure the chunk streamer (bigger mode) instead")
     return ap.parse_args()
 
 
@@ -209,6 +213,43 @@ def run_reference(a, w):
     print(json.dumps(line), flush=True)
 
 
+def latency_sample(bkd, tree, Q, seconds: float, barrier) -> dict:
+    """p50 / p99 wall latency of single bkd_query calls on a seeded sequence
+    of batches (host buffers, pinned), until `seconds` have passed."""
+    import torch
+    rng = np.random.default_rng(12345)
+    m = Q.shape[0]
+    Qh = torch.from_numpy(Q).pin_memory()
+    kmax = 50
+    oi = torch.empty((1 << 20) * kmax, dtype=torch.int64).pin_memory()
+    od = torch.empty((1 << 20) * kmax, dtype=torch.float32).pin_memory()
+    lat, sizes, ks = [], [], []
+    barrier()
+    t_end = time.perf_counter() + seconds
+    while time.perf_counter() < t_end and len(lat) < 2000:
+        b = int(min(m, np.exp(rng.uniform(0.0, np.log(1 << 20)))))
+        k = int(rng.choice([1, 10, 50]))
+        s0 = int(rng.integers(0, m - b + 1))
+        t0 = time.perf_counter()
+        bkd.bkd_query(tree, Qh[s0:s0 + b], k, oi[:b * k].view(b, k),
+                      od[:b * k].view(b, k))
+        lat.append(time.perf_counter() - t0)
+        sizes.append(b)
+        ks.append(k)
+    lat_ms = np.array(lat) * 1e3
+    return {"batches": len(lat), "p50_ms": float(np.percentile(lat_ms, 50)),
+            "p99_ms": float(np.percentile(lat_ms, 99)),
+            "mean_batch": float(np.mean(sizes)),
+            "queries_per_s": float(np.sum(sizes) / np.sum(lat)),
+            "p50_ms_batches_le_1024": float(np.percentile(
+                lat_ms[np.array(sizes) <= 1024], 50))
+            if (np.array(sizes) <= 1024).any() else None,
+            "recipe": ("sizes logU[1, 2^20] (capped at m), k uniform in "
+                       "{1, 10, 50}, queries sliced from the query set, "
+                       "pinned host in / out, one call at a time, seed "
+                       "12345")}
+
+
 def run_ours(a, w, rank, world, local_rank):
     import torch
     import paper_1512_02831_gb300 as bkd
@@ -246,7 +287,8 @@ def run_ours(a, w, rank, world, local_rank):
     stats_keys = ("rounds", "leaf_visits", "pairs", "resorted", "fallback",
                   "leaf_kernel_ms", "kernel_launches", "leaf_launches",
                   "tail_queries", "tail_visits", "tail_pairs", "tail_ms",
-                  "screen_kept", "screen_pairs", "screen_ms")
+                  "screen_kept", "screen_pairs", "screen_ms", "screen_items",
+                  "screen_visits", "find_ms", "bucket_ms", "exact_ms")
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     vis = [v for v in vis.split(",") if v.strip()]
     smi_index = (vis[local_rank] if local_rank < len(vis)
@@ -306,6 +348,11 @@ def run_ours(a, w, rank, world, local_rank):
            "buffers": "pinned host, bkd_query copies in and out"}
     same = bool(torch.equal(oi_h, out_i.cpu()))
 
+    # per-batch latency: a seeded sequence of batches (sizes log-uniform in
+    # [1, 2^20], k in {1, 10, 50}) through the same public call with pinned
+    # host buffers, one after the other on the resident tree
+    lat = latency_sample(bkd, tree, Q, a.latency_seconds, barrier)
+
     # rooflines: the float32 leaf kernel (from the float32 run) and the BF16
     # screen kernel (from the screened run)
     peaks = measured_peaks()
@@ -331,7 +378,7 @@ def run_ours(a, w, rank, world, local_rank):
                       "peak_tflops_fma2": 2 * peak_ops},
     }
     a1 = runs[1]["acc"]
-    kh = 1 if d <= 16 else 2
+    kh = (d + 2 + 15) // 16  # k-halves: d offsets + 2 norm slots
     scr_s = a1["screen_ms"] / 1000.0
     peak_bf16 = float(peaks.get("bf16_tflops") or 1900.0)
     scr_tf = 2 * 16 * kh * a1["screen_pairs"] / scr_s / 1e12 if scr_s else 0.0
@@ -340,8 +387,9 @@ def run_ours(a, w, rank, world, local_rank):
         "achieved": scr_tf, "peak": peak_bf16, "unit": "TFLOP/s",
         "frac": scr_tf / peak_bf16, "traffic": None,
         "basis": (f"2 x {16 * kh} flops per screened (query, point) pair "
-                  f"(bf16 dot product padded to {16 * kh}); peak = measured "
-                  f"cuBLAS bf16 burst, 'of measured'"),
+                  f"(bf16 dot product over {16 * kh} slots: d offsets, 2 "
+                  f"norm slots, zero padding); peak = measured cuBLAS bf16 "
+                  f"burst, 'of measured'"),
         "screen_share_of_step": scr_s / (runs[1]["ms"] / 1000.0),
         "pairs_per_s": a1["screen_pairs"] / scr_s if scr_s else 0.0,
         "kept_fraction": (a1["screen_kept"] / a1["screen_pairs"]
@@ -369,6 +417,7 @@ def run_ours(a, w, rank, world, local_rank):
                            "queries 0.67 GB) - no flush needed"),
                        tree_build_s=round(build_s, 2)),
         "e2e": e2e,
+        "latency": lat,
         "gpu_launches": int(acc["kernel_launches"]),
         "roofline": roofline,
         "roofline_fp32_leaf": roof_fp32,
@@ -398,6 +447,12 @@ def run_ours(a, w, rank, world, local_rank):
                  "screen_pairs_per_step": acc["screen_pairs"] / a.steps,
                  "screen_kept_per_step": acc["screen_kept"] / a.steps,
                  "screen_ms_per_step": acc["screen_ms"] / a.steps,
+                 "screen_queries_per_item": (acc["screen_visits"]
+                                             / acc["screen_items"]
+                                             if acc["screen_items"] else None),
+                 "find_leaf_ms_per_step": acc["find_ms"] / a.steps,
+                 "bucket_ms_per_step": acc["bucket_ms"] / a.steps,
+                 "recheck_fallback_ms_per_step": acc["exact_ms"] / a.steps,
                  "e2e_matches_device_run": same},
     }
     bkd.bkd_free(tree)
@@ -419,6 +474,65 @@ def run_ours(a, w, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_streamer(a):
+    """Bigger mode: the leaf structure in pinned host memory, streamed in N
+    leaf-aligned chunks through two device buffers on a copy stream (the
+    chunk streamer).  Per N: queries/s, bytes copied, copy-stream bandwidth
+    against a pinned host-to-device copy measured here, and equality with the
+    resident tree's results."""
+    import torch
+    import paper_1512_02831_gb300 as bkd
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    w = WORKLOADS["mixture16M"]
+    P, Q = w.points(), w.queries()
+    m, k = Q.shape[0], w.k
+    Qd = torch.from_numpy(Q).to(dev)
+    # host-to-device peak: 1 GiB from pinned memory, best of 5
+    src = torch.empty(1 << 28, dtype=torch.float32).pin_memory()
+    dst = torch.empty(1 << 28, dtype=torch.float32, device=dev)
+    best = 0.0
+    for _ in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dst.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, src.numel() * 4 / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    del src, dst
+    out = {"metric": "chunk streamer (bigger mode)", "workload": w.describe(),
+           "h2d_peak_gbs": best, "modes": {}}
+    ref = None
+    for n_chunks in (0, 1, 3, 10):
+        opts = {"chunks": n_chunks} if n_chunks else {}
+        tree = bkd.bkd_build(P, w.height, **opts)
+        bkd.bkd_query(tree, Qd, k)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        idx, dist = bkd.bkd_query(tree, Qd, k)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st = {x: bkd.bkd_get_stat(tree, x)
+              for x in ("chunk_bytes", "copy_ms", "rounds", "leaf_kernel_ms")}
+        shape = bkd.bkd_tree_shape(tree)
+        bkd.bkd_free(tree)
+        if ref is None:
+            ref = (idx.clone(), dist.clone())
+        gbs = (st["chunk_bytes"] / (st["copy_ms"] / 1e3) / 1e9
+               if st["copy_ms"] > 0 else None)
+        out["modes"]["resident" if not n_chunks else f"chunks={n_chunks}"] = {
+            "chunked": shape["chunked"], "queries_per_s": m / dt,
+            "ms": dt * 1e3, "rounds": st["rounds"],
+            "copied_gb": st["chunk_bytes"] / 1e9, "copy_ms": st["copy_ms"],
+            "copy_gbs": gbs,
+            "copy_frac_of_h2d_peak": gbs / best if gbs else None,
+            "leaf_kernel_ms": st["leaf_kernel_ms"],
+            "identical_to_resident": bool(torch.equal(idx, ref[0])
+                                          and torch.equal(dist, ref[1]))}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = args_()
     w = WORKLOADS[a.workload]
@@ -428,6 +542,10 @@ def main():
     if a.impl == "reference":
         if rank == 0:
             run_reference(a, w)
+        return
+    if a.streamer:
+        if rank == 0:
+            run_streamer(a)
         return
     run_ours(a, w, rank, world, local_rank)
 
