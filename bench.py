@@ -217,6 +217,8 @@ def latency_sample(bkd, tree, Q, seconds: float, barrier) -> dict:
     """p50 / p99 wall latency of single bkd_query calls on a seeded sequence
     of batches (host buffers, pinned), until `seconds` have passed."""
     import torch
+    if seconds <= 0:
+        return None
     rng = np.random.default_rng(12345)
     m = Q.shape[0]
     Qh = torch.from_numpy(Q).pin_memory()

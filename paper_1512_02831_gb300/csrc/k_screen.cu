@@ -466,7 +466,7 @@ __device__ __forceinline__ void setup_column(
 }
 
 template <int KH>
-__global__ void __launch_bounds__(kScrThreads, 2)
+__global__ void __launch_bounds__(kScrThreads, KH == 1 ? 3 : 2)
     screen_kernel(DevTree t, ScreenData sc, const Item* __restrict__ items,
                   int item_lo, int item_hi, Counters* ctr,
                   const uint32_t* __restrict__ act,
