@@ -37,6 +37,13 @@ namespace bkd {
 
 __device__ __forceinline__ int heap_level(int v) { return 31 - __clz(v + 1); }
 
+// max(a, b, c) (three-input float max of sm_100 and later).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
 // float32 pruning bound of one query; D = Dp (compile time), the query in
 // registers and each box read as 2D/4 16-byte loads.  Padding dimensions
 // (q_i = 0, box [0, 0]) add fma(0, 0, B) = B.
@@ -65,8 +72,10 @@ struct F32Bound {
     float b = 0.f;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
-      const float q = x[i], l = f[i], u = f[D + i];
-      const float o = q < l ? __fsub_rn(l, q) : (q > u ? __fsub_rn(q, u) : 0.f);
+      // fl(l - q) if q < l, fl(q - u) if q > u, else 0 (the other
+      // difference is then <= 0): one three-input max
+      const float q = x[i];
+      const float o = fmax3(__fsub_rn(f[i], q), __fsub_rn(q, f[D + i]), 0.f);
       b = i == 0 ? __fmul_rn(o, o) : __fmaf_rn(o, o, b);
     }
     return b;
@@ -90,7 +99,7 @@ __device__ __forceinline__ int next_leaf(const DevTree& t, const B& bx,
                                          const float* __restrict__ qp,
                                          int node, uint32_t& mask,
                                          typename B::T bound) {
-  const int h = t.h, d = t.d;
+  const int h = t.h;
   int u;      // descending: the node entered last; climbing: a finished node
   bool down;  // descending (near child next) or climbing (open far child)
   if (node == kStart) {
@@ -107,7 +116,7 @@ __device__ __forceinline__ int next_leaf(const DevTree& t, const B& bx,
     int c, l = 0;
     if (down) {
       if (lu == h) return u;  // a leaf: visit it
-      c = 2 * u + (qp[lu % d] < __ldg(t.split + u) ? 1 : 2);  // near child
+      c = 2 * u + (qp[t.dim_of[lu]] < __ldg(t.split + u) ? 1 : 2);  // near
     } else {
       // the far child at the deepest level with a clear bit
       const uint32_t open = ~mask & ((1u << lu) - 1u);
