@@ -550,7 +550,7 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
                         : 0;
   // the tail kernel spreads a list over the 32 lanes of a warp
   const int tail =
-      K > 32 ? 0 : (t->tail_queries >= 0 ? t->tail_queries : 8192);
+      K > 32 ? 0 : (t->tail_queries >= 0 ? t->tail_queries : 32768);
   // A round: FindLeafBatch over the active queries (it also counts every
   // query into its next leaf), bucketing by leaf, ProcessAllBuffers.
   int round = 0;
