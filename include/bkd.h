@@ -85,7 +85,8 @@ enum bkd_option {
   BKD_OPT_MAX_ACTIVE = 4,
   /* When at most this many queries remain active, they finish in one launch
    * (one warp per query walks its remaining leaves) instead of one
-   * LazySearch round per leaf.  -1 (default) = automatic (32768); 0 = never.
+   * LazySearch round per leaf.  -1 (default) = automatic (8192, growing to
+   * 32768 for query sets of 2^24); 0 = never.
    * Used for k <= 31 only.  Results do not depend on it.  Any time. */
   BKD_OPT_TAIL_QUERIES = 5,
   /* Leaf scoring: 0 (default) = float32 for every (query, point) pair;

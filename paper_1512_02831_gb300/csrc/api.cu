@@ -548,9 +548,14 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   const int screen_max =
       t->precision == 1 ? screen_grid(t->screen.kh, D.lcap, K, t->sm_count)
                         : 0;
-  // the tail kernel spreads a list over the 32 lanes of a warp
-  const int tail =
-      K > 32 ? 0 : (t->tail_queries >= 0 ? t->tail_queries : 32768);
+  // the tail kernel spreads a list over the 32 lanes of a warp; automatic
+  // threshold: 8,192 active queries, up to 32,768 for the largest query
+  // sets (measured on 2^24 queries)
+  const int64_t tail_auto =
+      std::max<int64_t>(8192, std::min<int64_t>(32768, m / 512));
+  const int tail = K > 32 ? 0
+                          : (int)(t->tail_queries >= 0 ? t->tail_queries
+                                                       : tail_auto);
   // A round: FindLeafBatch over the active queries (it also counts every
   // query into its next leaf), bucketing by leaf, ProcessAllBuffers.
   int round = 0;
