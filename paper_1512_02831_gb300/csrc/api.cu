@@ -489,7 +489,6 @@ int build_impl(const float* P, int64_t n, int d, int height,
   D.Dp = H.Dp;
   D.h = height;
   D.lcap = H.lcap;
-  for (int l = 0; l < 32; ++l) D.dim_of[l] = (uint8_t)(l % d);
   for (int i = 0; i < n_options; ++i) {
     const int64_t key = options[2 * i], val = options[2 * i + 1];
     if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE ||

@@ -96,7 +96,6 @@ struct DevTree {
   int64_t n;
   int d, Dp, h;
   int64_t lcap;            // slots per leaf (multiple of 4)
-  uint8_t dim_of[32];      // split dimension of each level: level mod d
 };
 
 // ------------------------------------------------------------- launchers

@@ -116,7 +116,7 @@ __device__ __forceinline__ int next_leaf(const DevTree& t, const B& bx,
     int c, l = 0;
     if (down) {
       if (lu == h) return u;  // a leaf: visit it
-      c = 2 * u + (qp[t.dim_of[lu]] < __ldg(t.split + u) ? 1 : 2);  // near
+      c = 2 * u + (qp[lu % t.d] < __ldg(t.split + u) ? 1 : 2);  // near
     } else {
       // the far child at the deepest level with a clear bit
       const uint32_t open = ~mask & ((1u << lu) - 1u);
