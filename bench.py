@@ -405,24 +405,37 @@ def run_ours(a, w, rank, world, local_rank):
     a1 = runs[1]["acc"]
     kh = (d + 2 + 15) // 16  # k-halves: d offsets + 2 norm slots
     scr_s = a1["screen_ms"] / 1000.0
+    pairs_s = a1["screen_pairs"] / scr_s if scr_s else 0.0
     peak_bf16 = float(peaks.get("bf16_tflops") or 1900.0)
-    scr_tf = 2 * 16 * kh * a1["screen_pairs"] / scr_s / 1e12 if scr_s else 0.0
+    scr_tf = 2 * 16 * kh * pairs_s / 1e12
+    # the screen's per-pair work (SURVEY's per-unit figures): a 16*KH-slot
+    # bf16 contraction on the tensor pipe and ~3 ALU operations of epilogue
+    # (form, combine, compare); the binding fraction is the roofline
+    epi_ops = 3
+    epi = epi_ops * pairs_s / 1e12
+    tensor_view = {"achieved": scr_tf, "peak": peak_bf16, "unit": "TFLOP/s",
+                   "frac": scr_tf / peak_bf16,
+                   "basis": (f"2 x {16 * kh} flops per screened pair; peak = "
+                             f"measured cuBLAS bf16 burst, 'of measured'")}
     roof_bf16 = {
-        "bound": "tensor", "kernel": "screen_kernel (BF16 mma.sync screen)",
-        "achieved": scr_tf, "peak": peak_bf16, "unit": "TFLOP/s",
-        "frac": scr_tf / peak_bf16, "traffic": None,
-        "basis": (f"2 x {16 * kh} flops per screened (query, point) pair "
-                  f"(bf16 dot product over {16 * kh} slots: d offsets, 2 "
-                  f"norm slots, zero padding); peak = measured cuBLAS bf16 "
-                  f"burst, 'of measured'"),
+        "bound": "alu", "kernel": "screen_kernel (BF16 mma.sync screen)",
+        "achieved": epi, "peak": peak_ops, "unit": "Top/s",
+        "frac": epi / peak_ops, "traffic": None,
+        "basis": (f"ALU epilogue: {epi_ops} operations per screened (query, "
+                  f"point) pair against 128 lanes x {sm_count} SMs x "
+                  f"{sm_max:.0f} MHz (the FP32/ALU issue width of measured "
+                  f"peaks); the tensor view is far from its peak (one "
+                  f"mma.sync covers 128 pairs), so the epilogue binds; time = "
+                  f"CUDA events around every screen launch on its stream"),
+        "tensor_view": tensor_view,
         "screen_share_of_step": scr_s / (runs[1]["ms"] / 1000.0),
-        "pairs_per_s": a1["screen_pairs"] / scr_s if scr_s else 0.0,
+        "pairs_per_s": pairs_s,
         "kept_fraction": (a1["screen_kept"] / a1["screen_pairs"]
                           if a1["screen_pairs"] else None),
-        "alu_view": {"fp32_ops_per_pair_exact_path": 2 * d,
-                     "equivalent_exact_top_s":
-                         2 * d * a1["screen_pairs"] / scr_s / 1e12
-                         if scr_s else 0.0},
+        "exact_equivalent": {
+            "fp32_ops_per_pair_exact_path": 2 * d,
+            "top_s": 2 * d * pairs_s / 1e12,
+            "frac_of_fp32_peak": 2 * d * pairs_s / 1e12 / peak_ops},
     }
     roofline = roof_bf16 if head == 1 else roof_fp32
     names = {0: "fp32 exact path", 1: "bf16 tensor-core screen + fp32 rescore"}
