@@ -65,16 +65,43 @@ __global__ void __launch_bounds__(kTailWarps * 32)
       const uint32_t slot0 = (uint32_t)((int64_t)leaf * t.lcap);
       ++visits;
       pairs += (unsigned long long)np;
+      // up to 16 dimensions, the quads of the next 32-quad chunk are loaded
+      // while this one is scored (one warp on one query: a visit is
+      // latency-bound); above, the registers would not hold two chunks
+      constexpr bool kPipe = D <= 16;
+      float4 nb[kPipe ? D : 1];
+      if constexpr (kPipe) {
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+          nb[i] = lane < nq ? lq[(int64_t)lane * D + i]
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
       for (int g0 = 0; g0 < nq; g0 += 32) {
         const int g = g0 + lane;
+        float4 cb[D];
+        if constexpr (kPipe) {
+#pragma unroll
+          for (int i = 0; i < D; ++i) cb[i] = nb[i];
+          if (g0 + 32 < nq) {
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+              nb[i] = g + 32 < nq ? lq[(int64_t)(g + 32) * D + i]
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < D; ++i)
+            cb[i] = g < nq ? lq[(int64_t)g * D + i]
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         float e[4] = {__int_as_float(0x7f800000), __int_as_float(0x7f800000),
                       __int_as_float(0x7f800000), __int_as_float(0x7f800000)};
-        if (g < nq) quad_dist<D>(lq + (int64_t)g * D, qq, e[0], e[1], e[2], e[3]);
-        unsigned mask = __ballot_sync(
+        if (g < nq) quad_dist<D>(cb, qq, e[0], e[1], e[2], e[3]);
+        unsigned cand = __ballot_sync(
             full, fminf(fminf(e[0], e[1]), fminf(e[2], e[3])) < bound);
-        while (mask) {
-          const int src = __ffs(mask) - 1;
-          mask &= mask - 1;
+        while (cand) {
+          const int src = __ffs(cand) - 1;
+          cand &= cand - 1;
           const uint32_t id = slot0 + (uint32_t)(g0 + src) * 4u;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
