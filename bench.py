@@ -408,7 +408,7 @@ def run_ours(a, w, rank, world, local_rank):
     pairs_s = a1["screen_pairs"] / scr_s if scr_s else 0.0
     peak_bf16 = float(peaks.get("bf16_tflops") or 1900.0)
     scr_tf = 2 * 16 * kh * pairs_s / 1e12
-    # the screen's per-pair work (SURVEY's per-unit figures): a 16*KH-slot
+    # the screen's per-pair work: a 16*KH-slot
     # bf16 contraction on the tensor pipe and ~3 ALU operations of epilogue
     # (form, combine, compare); the binding fraction is the roofline
     epi_ops = 3

@@ -53,7 +53,7 @@ extern "C" {
 #define BKD_ENOMEM (-2)       /* device or pinned host allocation failed      */
 #define BKD_ECUDA (-3)        /* CUDA runtime error; the handle should be freed */
 #define BKD_ETIMEOUT (-4)     /* a bounded device-side wait ran out           */
-#define BKD_EUNSUPPORTED (-5) /* valid request outside this build's limits    */
+#define BKD_EUNSUPPORTED (-5) /* valid request outside the library's limits   */
 
 /* ------------------------------------------------------------------ limits */
 #define BKD_MAX_DIM 32        /* d <= BKD_MAX_DIM                              */
