@@ -218,6 +218,69 @@ void bkd_free(bkd_tree* t);
  * none).  The string stays valid until the thread's next bkd_* call. */
 const char* bkd_last_error(void);
 
+/* ------------------------------------------------------------------ serving
+ * Continuous batching over a resident tree.  The paper's on-the-fly querying
+ * (Sec. 3.2: new queries are fetched from the input queue while others are
+ * still in flight) made into a request loop: batches of any size and k are
+ * queued, admitted into free query slots as earlier batches finish, and every
+ * admitted query advances in the SAME LazySearch rounds (FindLeafBatch,
+ * buffer insertion, ProcessAllBuffers) -- work of different batches shares
+ * every launch.  A batch's results equal a bkd_query of it alone. */
+typedef struct bkd_server bkd_server; /* opaque; owned by the library */
+
+enum bkd_batch_status {
+  BKD_BATCH_QUEUED = 0,   /* waiting for free query slots                    */
+  BKD_BATCH_RUNNING = 1,  /* admitted; its queries are in the rounds         */
+  BKD_BATCH_DONE = 2      /* results written to its output buffers           */
+  /* a negative status is the error code the batch failed with */
+};
+
+/* bkd_serve_open -- a server on tree t (resident, not chunked).
+ *   k_max        largest k a batch may ask for, 1 <= k_max <= min(n,
+ *                BKD_MAX_K); every query carries a list of k_max + 1
+ *                entries (a smaller k only reads a prefix of its result).
+ *   max_queries  query slots: the most queries in flight at once (device
+ *                memory ~ max_queries x (4 Dp + 8 k_max + 60) bytes).
+ *   out          receives the server (NULL on failure).
+ * The server uses the tree's stream; do not run bkd_query on the same tree
+ * while the server has batches in flight.
+ * Errors: BKD_EINVAL, BKD_ENOMEM, BKD_ECUDA, BKD_EUNSUPPORTED. */
+int bkd_serve_open(bkd_tree* t, int k_max, int64_t max_queries,
+                   bkd_server** out);
+
+/* bkd_serve_submit -- queues a batch (no GPU work).
+ *   Q         m x d float32 queries, host or device; must stay valid and
+ *             unchanged until the batch is DONE (or failed).
+ *   m         0 <= m <= max_queries (m == 0 is DONE at once).
+ *   k         1 <= k <= k_max.
+ *   out_idx, out_dist  m x k int64 / float32, host or device, written when
+ *             the batch completes (same meaning as bkd_query).
+ *   ticket    receives the batch's ticket (>= 1).
+ * Errors: BKD_EINVAL. */
+int bkd_serve_submit(bkd_server* s, const float* Q, int64_t m, int k,
+                     int64_t* out_idx, float* out_dist, int64_t* ticket);
+
+/* bkd_serve_step -- admits queued batches (first come, first served) while
+ * contiguous free slots fit them, runs ONE LazySearch round over every
+ * admitted query, and completes the batches whose queries all finished
+ * (binary64 re-check, fallback, results to the caller's buffers).
+ *   pending  receives the number of batches not yet completed (queued or
+ *            running); may be NULL.
+ * A batch whose queries hold a non-finite value fails with BKD_EINVAL
+ * (its status) without affecting the others.
+ * Errors: BKD_EINVAL (NULL server), BKD_ECUDA, BKD_ETIMEOUT. */
+int bkd_serve_step(bkd_server* s, int64_t* pending);
+
+/* bkd_serve_status -- status of a ticket (enum bkd_batch_status, or the
+ * negative error code the batch failed with).  A terminal status (DONE or
+ * failed) is reported once; afterwards the ticket is unknown (BKD_EINVAL). */
+int bkd_serve_status(bkd_server* s, int64_t ticket, int* status);
+
+/* bkd_serve_close -- waits for the device, releases the server (queued and
+ * running batches are dropped without results).  Close servers before
+ * freeing their tree.  NULL is ignored. */
+void bkd_serve_close(bkd_server* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,6 +33,7 @@ BKD_MAX_K = 63
 BKD_MAX_HEIGHT = 24
 BKD_STATIC_MAX_QUERIES = 4096
 BKD_STATIC_MAX_HEIGHT = 16
+BKD_BATCH_QUEUED, BKD_BATCH_RUNNING, BKD_BATCH_DONE = 0, 1, 2
 
 OPTIONS = {"stream": 1, "device_mem_cap": 2, "chunks": 3, "max_active": 4,
            "tail_queries": 5, "precision": 6}
@@ -77,10 +78,19 @@ def load():
         lib.bkd_export_tree.argtypes = [vp, vp, vp, vp]
         lib.bkd_free.argtypes = [vp]
         lib.bkd_free.restype = None
+        lib.bkd_serve_open.argtypes = [vp, i32, i64, ctypes.POINTER(vp)]
+        lib.bkd_serve_submit.argtypes = [vp, vp, i64, i32, vp, vp,
+                                         ctypes.POINTER(ctypes.c_int64)]
+        lib.bkd_serve_step.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+        lib.bkd_serve_status.argtypes = [vp, i64, ctypes.POINTER(i32)]
+        lib.bkd_serve_close.argtypes = [vp]
+        lib.bkd_serve_close.restype = None
         lib.bkd_last_error.restype = ctypes.c_char_p
         for f in ("bkd_build", "bkd_build_with", "bkd_query",
                   "bkd_query_static", "bkd_set_option",
-                  "bkd_get_stat", "bkd_tree_shape", "bkd_export_tree"):
+                  "bkd_get_stat", "bkd_tree_shape", "bkd_export_tree",
+                  "bkd_serve_open", "bkd_serve_submit", "bkd_serve_step",
+                  "bkd_serve_status"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -244,3 +254,99 @@ def bkd_free(tree: Tree):
 
 def bkd_last_error() -> str:
     return load().bkd_last_error().decode()
+
+
+class Server:
+    """``bkd_serve_*``: continuous batching over a resident tree.
+
+        srv = Server(tree, k_max=50, max_queries=1 << 20)
+        t = srv.submit(Q, k)          # queued; outputs allocated here
+        while srv.step():             # one shared LazySearch round
+            ...                       # submit more at any time
+        idx, dist = srv.result(t)     # after status(t) == BKD_BATCH_DONE
+    """
+
+    def __init__(self, tree: Tree, k_max: int, max_queries: int):
+        lib = load()
+        out = ctypes.c_void_p()
+        _check(lib.bkd_serve_open(tree.handle, k_max, max_queries,
+                                  ctypes.byref(out)))
+        self.handle = out
+        self.tree = tree
+        self._io = {}  # ticket -> (Q, out_idx, out_dist), kept alive
+
+    def submit(self, Q, k: int, out_idx=None, out_dist=None) -> int:
+        lib = load()
+        q, shape = _ptr(Q, "f32")
+        m = shape[0]
+        if out_idx is None or out_dist is None:
+            if _is_torch(Q):
+                import torch
+                out_idx = torch.empty((m, k), dtype=torch.int64,
+                                      device=Q.device)
+                out_dist = torch.empty((m, k), dtype=torch.float32,
+                                       device=Q.device)
+            else:
+                out_idx = np.empty((m, k), np.int64)
+                out_dist = np.empty((m, k), np.float32)
+        oi, _ = _ptr(out_idx, "i64")
+        od, _ = _ptr(out_dist, "f32")
+        ticket = ctypes.c_int64()
+        _check(lib.bkd_serve_submit(self.handle, q, m, k, oi, od,
+                                    ctypes.byref(ticket)))
+        self._io[ticket.value] = (Q, out_idx, out_dist)
+        return ticket.value
+
+    def step(self) -> int:
+        """One admission + round + completion pass; returns the number of
+        batches not yet completed."""
+        pending = ctypes.c_int64()
+        _check(load().bkd_serve_step(self.handle, ctypes.byref(pending)))
+        return pending.value
+
+    def status(self, ticket: int) -> int:
+        st = ctypes.c_int()
+        _check(load().bkd_serve_status(self.handle, ticket, ctypes.byref(st)))
+        return st.value
+
+    def result(self, ticket: int):
+        """(out_idx, out_dist) of a ticket whose status was DONE."""
+        _, oi, od = self._io.pop(ticket)
+        return oi, od
+
+    def close(self):
+        if self.handle and self.handle.value:
+            load().bkd_serve_close(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bkd_serve_open(tree: Tree, k_max: int, max_queries: int) -> Server:
+    """``bkd_serve_open``."""
+    return Server(tree, k_max, max_queries)
+
+
+def bkd_serve_submit(server: Server, Q, k: int, out_idx=None,
+                     out_dist=None) -> int:
+    """``bkd_serve_submit``: returns the ticket."""
+    return server.submit(Q, k, out_idx, out_dist)
+
+
+def bkd_serve_step(server: Server) -> int:
+    """``bkd_serve_step``: returns the batches not yet completed."""
+    return server.step()
+
+
+def bkd_serve_status(server: Server, ticket: int) -> int:
+    """``bkd_serve_status``."""
+    return server.status(ticket)
+
+
+def bkd_serve_close(server: Server):
+    """``bkd_serve_close``."""
+    server.close()

@@ -531,7 +531,7 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
 
   CU(cudaMemsetAsync(t->d_ctr, 0, sizeof(Counters), s));
   CU(launch_init(t->qdev.p, m, D.d, Dp, t->qpad.p, t->lst_d.p, t->lst_i.p, K,
-                 t->state.p, t->act_a.p, t->d_ctr, s));
+                 t->state.p, t->act_a.p, 0u, t->d_ctr, s));
   t->st_launches += 1;
   // reject non-finite queries before any traversal (the tail kernel may take
   // every query without a single round)
@@ -732,6 +732,8 @@ TreeView view_of(const bkd_tree* t) {
   v.chunked = t->chunked;
   v.d_pts = t->d_pts;
   v.h_ctr = t->h_ctr;
+  v.screen = t->screen;
+  v.precision = t->precision;
   return v;
 }
 

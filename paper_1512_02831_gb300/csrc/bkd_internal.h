@@ -99,9 +99,21 @@ struct DevTree {
 };
 
 // ------------------------------------------------------------- launchers
+// Queries Q (m x d, device) padded into qpad, lists +inf, state "start",
+// act[q] = act_base + q (the slot numbers of the queries); non-finite or
+// huge inputs set kErrNonFinite in ctr->err.
 cudaError_t launch_init(const float* Q, int64_t m, int d, int Dp, float* qpad,
                         float* lst_d, uint32_t* lst_i, int K, uint64_t* state,
-                        uint32_t* act, Counters* ctr, cudaStream_t s);
+                        uint32_t* act, uint32_t act_base, Counters* ctr,
+                        cudaStream_t s);
+
+// Continuous batching helpers (serve.cu): v[0..n) = value; for every
+// position of `act` whose query finished (placed.x < 0) one less in
+// batch_left[slot_batch[slot]].
+cudaError_t launch_fill(int32_t* v, int64_t n, int32_t value, cudaStream_t s);
+cudaError_t launch_retire(const int2* placed, const uint32_t* act, int n_act,
+                          const int32_t* slot_batch, int32_t* batch_left,
+                          cudaStream_t s);
 
 // FindLeafBatch from the traversal states in `state` (kStart for the first
 // round): per position of `act`, placed = (next leaf, rank among the
@@ -197,6 +209,8 @@ struct TreeView {
   bool chunked;
   const float* d_pts;        // resident leaf structure (nullptr if chunked)
   Counters* h_ctr;           // pinned host counter block of the handle
+  ScreenData screen;         // BF16 screen data (words == nullptr: none)
+  int precision;             // current leaf-scoring option (0 / 1)
 };
 TreeView view_of(const struct ::bkd_tree* t);
 

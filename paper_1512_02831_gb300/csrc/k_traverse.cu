@@ -22,7 +22,8 @@ __global__ void init_kernel(const float* __restrict__ Q, int64_t m, int d,
                             float* __restrict__ lst_d,
                             uint32_t* __restrict__ lst_i, int K,
                             uint64_t* __restrict__ state,
-                            uint32_t* __restrict__ act, Counters* ctr) {
+                            uint32_t* __restrict__ act, uint32_t act_base,
+                            Counters* ctr) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= m) return;
   bool bad = false;
@@ -37,7 +38,7 @@ __global__ void init_kernel(const float* __restrict__ Q, int64_t m, int d,
     lst_i[q * K + j] = kNoSlot;
   }
   state[q] = trav_state(kStart, 0u);
-  act[q] = (uint32_t)q;
+  act[q] = act_base + (uint32_t)q;
   if (bad) atomicOr(&ctr->err, kErrNonFinite);
 }
 
@@ -251,16 +252,48 @@ __global__ void chunk_items_kernel(const int32_t* __restrict__ toff,
   if (c <= n_chunks) out[c] = toff[chunk_leaf[c]];
 }
 
+__global__ void fill_kernel(int32_t* __restrict__ v, int64_t n,
+                            int32_t value) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = value;
+}
+
+// One less in its batch's count for every query that finished this round.
+__global__ void retire_kernel(const int2* __restrict__ placed,
+                              const uint32_t* __restrict__ act, int n,
+                              const int32_t* __restrict__ slot_batch,
+                              int32_t* __restrict__ batch_left) {
+  const int pos = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= n || placed[pos].x >= 0) return;
+  atomicSub(batch_left + slot_batch[act[pos]], 1);
+}
+
 inline int blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
+cudaError_t launch_fill(int32_t* v, int64_t n, int32_t value, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  fill_kernel<<<blocks(n, 256), 256, 0, s>>>(v, n, value);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_retire(const int2* placed, const uint32_t* act, int n_act,
+                          const int32_t* slot_batch, int32_t* batch_left,
+                          cudaStream_t s) {
+  if (n_act <= 0) return cudaSuccess;
+  retire_kernel<<<blocks(n_act, 256), 256, 0, s>>>(placed, act, n_act,
+                                                   slot_batch, batch_left);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_init(const float* Q, int64_t m, int d, int Dp, float* qpad,
                         float* lst_d, uint32_t* lst_i, int K, uint64_t* state,
-                        uint32_t* act, Counters* ctr, cudaStream_t s) {
+                        uint32_t* act, uint32_t act_base, Counters* ctr,
+                        cudaStream_t s) {
   if (m == 0) return cudaSuccess;
   init_kernel<<<blocks(m, 256), 256, 0, s>>>(Q, m, d, Dp, qpad, lst_d, lst_i,
-                                             K, state, act, ctr);
+                                             K, state, act, act_base, ctr);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,500 @@
+// serve.cu -- continuous batching over a resident tree (bkd_serve_*).
+//
+// The paper's querying phase fetches new queries from the input queue while
+// earlier ones are still in flight (Algorithm 1; Sec. 3.2 on-the-fly
+// querying).  Here that queue takes whole batches of any size and k:
+//
+//   admit     queued batches, first come first served, get contiguous query
+//             slots while free slots fit them; their queries are padded into
+//             the slots, their lists set to +inf, their traversal to "start",
+//             and their slot numbers appended to the active list;
+//   round     one LazySearch round over every active query, whatever its
+//             batch: FindLeafBatch, buffer insertion, ProcessAllBuffers (the
+//             same kernels as bkd_query);
+//   complete  a batch whose queries have all finished gets the binary64
+//             re-check and fallback and its results, and frees its slots.
+//
+// Every query carries a list of k_max + 1 entries.  After the rounds a
+// query's list holds its k_max + 1 smallest float32 distances, so its
+// first k + 1 entries are the k + 1 smallest: the re-check and fallback of a
+// batch with k <= k_max see exactly what a bkd_query with that k sees, and
+// the results are the same (both equal the binary64 definition).
+//
+// Queries admitted in a step take their first leaf in a round of their own
+// on the float32 leaf kernel (their lists are still empty, so the BF16
+// screen could reject nothing); the shared round of the step then follows
+// the tree's precision option for everyone.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <deque>
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "bkd.h"
+#include "bkd_internal.h"
+
+using namespace bkd;
+
+namespace {
+
+constexpr int kMaxBatches = 4096;  // batches admitted at once
+
+#define SV_CU(call)                                                        \
+  do {                                                                     \
+    cudaError_t e_ = (call);                                               \
+    if (e_ != cudaSuccess)                                                 \
+      return set_error(e_ == cudaErrorMemoryAllocation ? BKD_ENOMEM        \
+                                                       : BKD_ECUDA,        \
+                       "%s failed: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
+
+bool device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceScope() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev)
+      cudaSetDevice(prev);
+  }
+};
+
+struct Batch {
+  int64_t ticket = 0;
+  const float* Q = nullptr;
+  int64_t m = 0;
+  int k = 0;
+  int64_t* out_idx = nullptr;
+  float* out_dist = nullptr;
+  bool q_dev = false, o_dev = false;
+  int64_t s0 = -1;  // first slot
+  int bid = -1;     // index into batch_left
+  int status = BKD_BATCH_QUEUED;
+};
+
+// First-fit allocator of contiguous slot ranges.
+struct Slots {
+  std::map<int64_t, int64_t> free_;  // start -> length
+  void reset(int64_t n) {
+    free_.clear();
+    if (n > 0) free_[0] = n;
+  }
+  int64_t take(int64_t len) {
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < len) continue;
+      const int64_t s = it->first, rest = it->second - len;
+      free_.erase(it);
+      if (rest > 0) free_[s + len] = rest;
+      return s;
+    }
+    return -1;
+  }
+  void give(int64_t s, int64_t len) {
+    auto it = free_.emplace(s, len).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
+template <class T>
+cudaError_t dev_alloc(T** p, int64_t n) {
+  return cudaMalloc(p, std::max<int64_t>(n, 1) * sizeof(T));
+}
+
+}  // namespace
+
+struct bkd_server {
+  bkd_tree* tree = nullptr;
+  TreeView v{};  // refreshed every step (stream, precision option)
+  int kmax = 0, K = 0, cap = 0;
+  int64_t max_q = 0;
+  int grid_max = 0, screen_max = 0;
+  // per slot
+  float *qstage = nullptr, *qpad = nullptr, *lst_d = nullptr;
+  uint32_t *lst_i = nullptr, *act_a = nullptr, *act_b = nullptr,
+           *fb = nullptr;
+  uint64_t* state = nullptr;
+  int2* placed = nullptr;
+  int32_t* slot_batch = nullptr;
+  int64_t* out_i = nullptr;
+  float* out_d = nullptr;
+  // per leaf / per round
+  int32_t *cnt = nullptr, *off = nullptr, *cursor = nullptr, *toff = nullptr;
+  Item* items = nullptr;
+  int32_t* batch_left = nullptr;  // device, kMaxBatches
+  Counters *d_ctr = nullptr, *d_fin = nullptr;
+  Counters *h_ctr = nullptr, *h_fin = nullptr;  // pinned
+  int32_t* h_left = nullptr;                    // pinned, kMaxBatches
+  // host state
+  uint32_t* act = nullptr;
+  uint32_t* nxt = nullptr;
+  int n_act = 0;
+  Slots slots;
+  std::vector<int> free_bids;
+  std::deque<Batch*> queue;
+  std::vector<Batch*> running;  // by batch id
+  std::map<int64_t, std::unique_ptr<Batch>> batches;
+  int64_t next_ticket = 1;
+
+  ~bkd_server() {
+    cudaFree(qstage);
+    cudaFree(qpad);
+    cudaFree(lst_d);
+    cudaFree(lst_i);
+    cudaFree(act_a);
+    cudaFree(act_b);
+    cudaFree(fb);
+    cudaFree(state);
+    cudaFree(placed);
+    cudaFree(slot_batch);
+    cudaFree(out_i);
+    cudaFree(out_d);
+    cudaFree(cnt);
+    cudaFree(off);
+    cudaFree(cursor);
+    cudaFree(toff);
+    cudaFree(items);
+    cudaFree(batch_left);
+    cudaFree(d_ctr);
+    cudaFree(d_fin);
+    cudaFreeHost(h_ctr);
+    cudaFreeHost(h_fin);
+    cudaFreeHost(h_left);
+  }
+
+  void finish(Batch* b, int status) {
+    b->status = status;
+    if (b->s0 >= 0) slots.give(b->s0, b->m);
+    if (b->bid >= 0) {
+      running[b->bid] = nullptr;
+      free_bids.push_back(b->bid);
+    }
+    b->s0 = -1;
+    b->bid = -1;
+  }
+
+  int admit(Batch* b, int64_t s0, int bid, bool* ok);
+  int complete(Batch* b);
+  int first_round(int n_old);
+  int round();
+};
+
+// Copies a batch's queries into its slots and appends them to the active
+// list; a non-finite query fails the batch (ok = false).
+int bkd_server::admit(Batch* b, int64_t s0, int bid, bool* ok) {
+  const DevTree& D = v.dev;
+  cudaStream_t s = v.stream;
+  const int64_t m = b->m;
+  SV_CU(cudaMemcpyAsync(qstage + s0 * D.d, b->Q, sizeof(float) * m * D.d,
+                        b->q_dev ? cudaMemcpyDeviceToDevice
+                                 : cudaMemcpyHostToDevice,
+                        s));
+  SV_CU(cudaMemsetAsync(d_fin, 0, sizeof(Counters), s));
+  SV_CU(launch_init(qstage + s0 * D.d, m, D.d, D.Dp, qpad + s0 * D.Dp,
+                    lst_d + s0 * K, lst_i + s0 * K, K, state + s0,
+                    act + n_act, (uint32_t)s0, d_fin, s));
+  SV_CU(launch_fill(slot_batch + s0, m, bid, s));
+  SV_CU(launch_fill(batch_left + bid, 1, (int32_t)m, s));
+  SV_CU(cudaMemcpyAsync(h_fin, d_fin, sizeof(Counters),
+                        cudaMemcpyDeviceToHost, s));
+  SV_CU(cudaStreamSynchronize(s));
+  *ok = !(h_fin->err & kErrNonFinite);
+  return BKD_OK;
+}
+
+// The first leaf of the queries admitted in this step (active positions
+// [n_old, n_act)): FindLeafBatch, bucketing and the float32 leaf kernel over
+// them alone.  Their processed list goes to the scratch `nxt`; they stay in
+// the active list for the shared round.
+int bkd_server::first_round(int n_old) {
+  const DevTree& D = v.dev;
+  cudaStream_t s = v.stream;
+  const int64_t L = v.n_leaves;
+  const int n_new = n_act - n_old;
+  SV_CU(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * L, s));
+  SV_CU(launch_find_leaf(D, qpad, act + n_old, n_new, state, lst_d, K,
+                         placed + n_old, cnt, s));
+  SV_CU(launch_retire(placed + n_old, act + n_old, n_new, slot_batch,
+                      batch_left, s));
+  SV_CU(launch_bucket(placed + n_old, act + n_old, n_new, (int)L, kPipeTile,
+                      D.leaf_cnt, cnt, off, cursor, toff, items, nxt, d_ctr,
+                      s));
+  SV_CU(cudaMemcpyAsync(h_ctr, d_ctr, sizeof(Counters),
+                        cudaMemcpyDeviceToHost, s));
+  SV_CU(cudaStreamSynchronize(s));
+  if (h_ctr->n_next > 0)
+    SV_CU(launch_leaf(D, cap, items, 0, h_ctr->n_items, d_ctr, v.d_pts, 0,
+                      nxt, qpad, lst_d, lst_i, K,
+                      std::min(grid_max, h_ctr->n_items), s));
+  return BKD_OK;
+}
+
+// One LazySearch round over the whole active list.
+int bkd_server::round() {
+  const DevTree& D = v.dev;
+  cudaStream_t s = v.stream;
+  const int64_t L = v.n_leaves;
+  const bool screened = v.precision == 1 && screen_max > 0;
+  SV_CU(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * L, s));
+  SV_CU(launch_find_leaf(D, qpad, act, n_act, state, lst_d, K, placed, cnt,
+                         s));
+  SV_CU(launch_retire(placed, act, n_act, slot_batch, batch_left, s));
+  SV_CU(launch_bucket(placed, act, n_act, (int)L,
+                      screened ? kScreenTile : kPipeTile, D.leaf_cnt, cnt, off,
+                      cursor, toff, items, nxt, d_ctr, s));
+  SV_CU(cudaMemcpyAsync(h_ctr, d_ctr, sizeof(Counters),
+                        cudaMemcpyDeviceToHost, s));
+  SV_CU(cudaMemcpyAsync(h_left, batch_left, sizeof(int32_t) * kMaxBatches,
+                        cudaMemcpyDeviceToHost, s));
+  SV_CU(cudaStreamSynchronize(s));
+  if (h_ctr->err & kErrTimeout)
+    return set_error(BKD_ETIMEOUT, "a leaf-segment copy did not complete");
+  const int n_next = h_ctr->n_next, n_items = h_ctr->n_items;
+  if (n_next > 0) {
+    if (screened)
+      SV_CU(launch_screen(D, v.screen, items, 0, n_items, d_ctr, nxt, qpad,
+                          lst_d, lst_i, K, screen_max, s));
+    else
+      SV_CU(launch_leaf(D, cap, items, 0, n_items, d_ctr, v.d_pts, 0, nxt,
+                        qpad, lst_d, lst_i, K, std::min(grid_max, n_items),
+                        s));
+  }
+  std::swap(act, nxt);
+  n_act = n_next;
+  return BKD_OK;
+}
+
+// Re-check, fallback and results of a batch whose queries all finished.
+int bkd_server::complete(Batch* b) {
+  const DevTree& D = v.dev;
+  cudaStream_t s = v.stream;
+  const int64_t s0 = b->s0, m = b->m;
+  const int k = b->k;
+  int64_t* oi = b->o_dev ? b->out_idx : out_i + s0 * kmax;
+  float* od = b->o_dev ? b->out_dist : out_d + s0 * kmax;
+  SV_CU(cudaMemsetAsync(d_fin, 0, sizeof(Counters), s));
+  SV_CU(launch_recheck(D, m, k, K, qpad + s0 * D.Dp, lst_d + s0 * K,
+                       lst_i + s0 * K, oi, od, fb + s0, d_fin, s));
+  SV_CU(cudaMemcpyAsync(h_fin, d_fin, sizeof(Counters),
+                        cudaMemcpyDeviceToHost, s));
+  SV_CU(cudaStreamSynchronize(s));
+  if (h_fin->err & kErrBadList)
+    return set_error(BKD_ECUDA, "internal error: a finished candidate list "
+                                "holds an empty entry");
+  if (h_fin->n_fallback > 0)
+    SV_CU(launch_fallback(D, h_fin->n_fallback, fb + s0, k, K,
+                          qpad + s0 * D.Dp, lst_d + s0 * K, oi, od, s));
+  if (!b->o_dev) {
+    SV_CU(cudaMemcpyAsync(b->out_idx, oi, sizeof(int64_t) * m * k,
+                          cudaMemcpyDeviceToHost, s));
+    SV_CU(cudaMemcpyAsync(b->out_dist, od, sizeof(float) * m * k,
+                          cudaMemcpyDeviceToHost, s));
+  }
+  SV_CU(cudaStreamSynchronize(s));
+  finish(b, BKD_BATCH_DONE);
+  return BKD_OK;
+}
+
+extern "C" {
+
+int bkd_serve_open(bkd_tree* t, int k_max, int64_t max_queries,
+                   bkd_server** out) {
+  set_error(BKD_OK, "");
+  if (!out) return set_error(BKD_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!t) return set_error(BKD_EINVAL, "tree is NULL");
+  const TreeView v = view_of(t);
+  if (v.chunked)
+    return set_error(BKD_EUNSUPPORTED,
+                     "serving needs a tree resident in device memory");
+  if (k_max < 1 || k_max > v.dev.n)
+    return set_error(BKD_EINVAL, "k_max must be in [1, n] (got %d)", k_max);
+  if (k_max > BKD_MAX_K)
+    return set_error(BKD_EUNSUPPORTED, "k_max = %d exceeds BKD_MAX_K = %d",
+                     k_max, BKD_MAX_K);
+  if (max_queries < 1 || max_queries >= ((int64_t)1 << 31))
+    return set_error(BKD_EINVAL, "max_queries must be in [1, 2^31)");
+  DeviceScope guard(v.device);
+  auto sv = std::make_unique<bkd_server>();
+  sv->tree = t;
+  sv->v = v;
+  sv->kmax = k_max;
+  sv->K = k_max + 1;
+  sv->cap = list_capacity(sv->K);
+  sv->max_q = max_queries;
+  const int64_t Q = max_queries, L = v.n_leaves;
+  const DevTree& D = v.dev;
+  SV_CU(dev_alloc(&sv->qstage, Q * D.d));
+  SV_CU(dev_alloc(&sv->qpad, Q * D.Dp));
+  SV_CU(dev_alloc(&sv->lst_d, Q * sv->K));
+  SV_CU(dev_alloc(&sv->lst_i, Q * sv->K));
+  SV_CU(dev_alloc(&sv->act_a, Q));
+  SV_CU(dev_alloc(&sv->act_b, Q));
+  SV_CU(dev_alloc(&sv->fb, Q));
+  SV_CU(dev_alloc(&sv->state, Q));
+  SV_CU(dev_alloc(&sv->placed, Q));
+  SV_CU(dev_alloc(&sv->slot_batch, Q));
+  SV_CU(dev_alloc(&sv->out_i, Q * k_max));
+  SV_CU(dev_alloc(&sv->out_d, Q * k_max));
+  SV_CU(dev_alloc(&sv->cnt, L));
+  SV_CU(dev_alloc(&sv->off, L + 1));
+  SV_CU(dev_alloc(&sv->cursor, std::max<int64_t>(L, 4)));
+  SV_CU(dev_alloc(&sv->toff, L + 1));
+  SV_CU(dev_alloc(&sv->items, Q / kScreenTile + L + 1));
+  SV_CU(dev_alloc(&sv->batch_left, kMaxBatches));
+  SV_CU(dev_alloc(&sv->d_ctr, 1));
+  SV_CU(dev_alloc(&sv->d_fin, 1));
+  SV_CU(cudaHostAlloc(&sv->h_ctr, sizeof(Counters), cudaHostAllocDefault));
+  SV_CU(cudaHostAlloc(&sv->h_fin, sizeof(Counters), cudaHostAllocDefault));
+  SV_CU(cudaHostAlloc(&sv->h_left, sizeof(int32_t) * kMaxBatches,
+                      cudaHostAllocDefault));
+  SV_CU(cudaMemsetAsync(sv->d_ctr, 0, sizeof(Counters), v.stream));
+  SV_CU(cudaMemsetAsync(sv->batch_left, 0, sizeof(int32_t) * kMaxBatches,
+                        v.stream));
+  SV_CU(cudaStreamSynchronize(v.stream));
+  sv->grid_max = leaf_kernel_grid(D.Dp, sv->cap, v.sm_count);
+  sv->screen_max = v.screen.words
+                       ? screen_grid(v.screen.kh, D.lcap, sv->K, v.sm_count)
+                       : 0;
+  if (sv->grid_max <= 0)
+    return set_error(BKD_EUNSUPPORTED, "no leaf kernel for d = %d, k = %d",
+                     D.d, k_max);
+  sv->act = sv->act_a;
+  sv->nxt = sv->act_b;
+  sv->slots.reset(Q);
+  sv->running.assign(kMaxBatches, nullptr);
+  for (int i = kMaxBatches - 1; i >= 0; --i) sv->free_bids.push_back(i);
+  *out = sv.release();
+  return BKD_OK;
+}
+
+int bkd_serve_submit(bkd_server* s, const float* Q, int64_t m, int k,
+                     int64_t* out_idx, float* out_dist, int64_t* ticket) {
+  set_error(BKD_OK, "");
+  if (!s || !ticket) return set_error(BKD_EINVAL, "server / ticket is NULL");
+  if (m < 0 || m > s->max_q)
+    return set_error(BKD_EINVAL, "m = %lld outside [0, max_queries = %lld]",
+                     (long long)m, (long long)s->max_q);
+  if (k < 1 || k > s->kmax)
+    return set_error(BKD_EINVAL, "k = %d outside [1, k_max = %d]", k,
+                     s->kmax);
+  if (m > 0 && (!Q || !out_idx || !out_dist))
+    return set_error(BKD_EINVAL, "Q / out_idx / out_dist is NULL");
+  DeviceScope guard(s->v.device);
+  auto b = std::make_unique<Batch>();
+  b->ticket = s->next_ticket++;
+  b->Q = Q;
+  b->m = m;
+  b->k = k;
+  b->out_idx = out_idx;
+  b->out_dist = out_dist;
+  if (m > 0) {
+    b->q_dev = device_ptr(Q);
+    b->o_dev = device_ptr(out_idx) && device_ptr(out_dist);
+    s->queue.push_back(b.get());
+  } else {
+    b->status = BKD_BATCH_DONE;
+  }
+  *ticket = b->ticket;
+  s->batches[b->ticket] = std::move(b);
+  return BKD_OK;
+}
+
+int bkd_serve_step(bkd_server* s, int64_t* pending) {
+  set_error(BKD_OK, "");
+  if (!s) return set_error(BKD_EINVAL, "server is NULL");
+  s->v = view_of(s->tree);
+  DeviceScope guard(s->v.device);
+  // admit, first come first served
+  const int n_old = s->n_act;
+  while (!s->queue.empty() && !s->free_bids.empty()) {
+    Batch* b = s->queue.front();
+    const int64_t s0 = s->slots.take(b->m);
+    if (s0 < 0) break;
+    s->queue.pop_front();
+    const int bid = s->free_bids.back();
+    s->free_bids.pop_back();
+    b->s0 = s0;
+    b->bid = bid;
+    bool ok = false;
+    const int rc = s->admit(b, s0, bid, &ok);
+    if (rc != BKD_OK) {
+      s->finish(b, rc);
+      return rc;
+    }
+    if (!ok) {
+      s->finish(b, BKD_EINVAL);
+      continue;
+    }
+    b->status = BKD_BATCH_RUNNING;
+    s->running[bid] = b;
+    s->n_act += (int)b->m;
+  }
+  if (s->n_act > n_old) {
+    const int rc = s->first_round(n_old);
+    if (rc != BKD_OK) return rc;
+  }
+  if (s->n_act > 0) {
+    const int rc = s->round();
+    if (rc != BKD_OK) return rc;
+    for (int bid = 0; bid < kMaxBatches; ++bid) {
+      Batch* b = s->running[bid];
+      if (b && s->h_left[bid] == 0) {
+        const int rc2 = s->complete(b);
+        if (rc2 != BKD_OK) {
+          s->finish(b, rc2);
+          return rc2;
+        }
+      }
+    }
+  }
+  if (pending) {
+    int64_t n = (int64_t)s->queue.size();
+    for (Batch* b : s->running) n += b != nullptr;
+    *pending = n;
+  }
+  return BKD_OK;
+}
+
+int bkd_serve_status(bkd_server* s, int64_t ticket, int* status) {
+  set_error(BKD_OK, "");
+  if (!s || !status) return set_error(BKD_EINVAL, "server / status is NULL");
+  auto it = s->batches.find(ticket);
+  if (it == s->batches.end())
+    return set_error(BKD_EINVAL, "unknown ticket %lld", (long long)ticket);
+  *status = it->second->status;
+  if (*status != BKD_BATCH_QUEUED && *status != BKD_BATCH_RUNNING)
+    s->batches.erase(it);
+  return BKD_OK;
+}
+
+void bkd_serve_close(bkd_server* s) {
+  if (!s) return;
+  DeviceScope guard(s->v.device);
+  cudaStreamSynchronize(s->v.stream);
+  delete s;
+}
+
+}  // extern "C"

@@ -134,7 +134,7 @@ int run_static(const TreeView& v, char* base, const float* Q, int64_t m, int k,
   // else is fully written before it is read (init writes lists, state and the
   // active list; every round clears cnt before FindLeafBatch).
   SQ_CU(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
-  SQ_CU(launch_init(Q, m, D.d, D.Dp, qpad, lst_d, lst_i, K, state, act, ctr,
+  SQ_CU(launch_init(Q, m, D.d, D.Dp, qpad, lst_d, lst_i, K, state, act, 0u, ctr,
                     s));
   const int grid_max = leaf_kernel_grid(D.Dp, cap, v.sm_count);
   int n_act = (int)m;

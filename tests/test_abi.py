@@ -78,3 +78,19 @@ def test_query_rejects_null_handle():
 def test_binding_refuses_wrong_dtypes():
     with pytest.raises(TypeError):
         bkd.bkd_build(np.zeros((8, 2), np.float64), 1)
+
+
+def test_serving_rejects_bad_arguments_before_any_device_work():
+    lib = bkd.load()
+    out = ctypes.c_void_p()
+    assert lib.bkd_serve_open(None, 10, 100, ctypes.byref(out)) == \
+        bkd.BKD_EINVAL
+    assert "tree is NULL" in bkd.bkd_last_error()
+    ticket = ctypes.c_int64()
+    assert lib.bkd_serve_submit(None, None, 0, 1, None, None,
+                                ctypes.byref(ticket)) == bkd.BKD_EINVAL
+    pending = ctypes.c_int64()
+    assert lib.bkd_serve_step(None, ctypes.byref(pending)) == bkd.BKD_EINVAL
+    st = ctypes.c_int()
+    assert lib.bkd_serve_status(None, 1, ctypes.byref(st)) == bkd.BKD_EINVAL
+    lib.bkd_serve_close(None)  # NULL is ignored

@@ -1,0 +1,97 @@
+"""Continuous batching (bkd_serve_*): batches of uneven size and k, arriving
+while others are in flight, share the LazySearch rounds; each batch's result
+is the same alone and in the mix."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1512_02831_gb300 as bkd
+import workloads
+from parity import check
+
+pytestmark = pytest.mark.gpu
+
+
+def _serve(srv, arrivals, max_steps=200000):
+    """arrivals: list of (step, submit-callable); returns tickets by index."""
+    tickets = {}
+    step = 0
+    last = max(a for a, _ in arrivals)
+    while True:
+        for j, (a, submit) in enumerate(arrivals):
+            if a == step:
+                tickets[j] = submit()
+        pending = srv.step()
+        step += 1
+        if step > last and pending == 0:
+            return tickets
+        assert step < max_steps
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_each_batch_same_alone_and_in_the_mix(precision):
+    import torch
+    w = workloads.scaled(workloads.MIXTURE_64M, 1 << 16, 6000, 8)
+    P, Qall = w.points(), w.queries()
+    tree = bkd.bkd_build(P, w.height, precision=precision)
+    # (first query, batch size, k, arrival step, device buffers)
+    spec = [(0, 1, 10, 0, False), (1, 37, 1, 0, True), (38, 500, 50, 1, False),
+            (538, 1200, 10, 3, True), (1738, 3, 50, 3, False),
+            (1741, 2000, 7, 5, False), (3741, 900, 25, 9, True),
+            (4641, 1359, 50, 9, False)]
+    try:
+        alone = [bkd.bkd_query(tree, np.ascontiguousarray(Qall[a:a + m]), k)
+                 for a, m, k, _, _ in spec]
+        # fewer slots than queries in flight: later batches wait for slots
+        srv = bkd.Server(tree, k_max=50, max_queries=2500)
+
+        def submitter(a, m, k, dev):
+            def go():
+                Q = np.ascontiguousarray(Qall[a:a + m])
+                return srv.submit(torch.from_numpy(Q).cuda() if dev else Q, k)
+            return go
+
+        tickets = _serve(srv, [(s[3], submitter(*s[:3], s[4])) for s in spec])
+        for j, (a, m, k, _, dev) in enumerate(spec):
+            assert srv.status(tickets[j]) == bkd.BKD_BATCH_DONE
+            idx, dist = srv.result(tickets[j])
+            if dev:
+                idx, dist = idx.cpu().numpy(), dist.cpu().numpy()
+            assert np.array_equal(idx, alone[j][0]), j
+            assert np.array_equal(dist, alone[j][1]), j
+        a, m, k = spec[5][:3]
+        check(P, Qall[a:a + m], k, alone[5][0], alone[5][1],
+              oracle.brute_knn(P, Qall[a:a + m], k))
+        srv.close()
+    finally:
+        bkd.bkd_free(tree)
+
+
+def test_bad_batches_fail_alone():
+    w = workloads.scaled(workloads.MIXTURE_64M, 1 << 14, 500, 6)
+    P, Q = w.points(), w.queries()
+    tree = bkd.bkd_build(P, w.height)
+    try:
+        srv = bkd.Server(tree, k_max=10, max_queries=400)
+        with pytest.raises(bkd.BkdError):
+            srv.submit(Q[:401].copy(), 5)        # more than the slots
+        with pytest.raises(bkd.BkdError):
+            srv.submit(Q[:10].copy(), 11)        # k above k_max
+        bad = Q[:50].copy()
+        bad[7, 2] = np.nan
+        t_bad = srv.submit(bad, 5)
+        t_good = srv.submit(Q[50:300].copy(), 5)
+        t_empty = srv.submit(np.zeros((0, w.d), np.float32), 5)
+        while srv.step():
+            pass
+        assert srv.status(t_bad) == bkd.BKD_EINVAL
+        assert srv.status(t_good) == bkd.BKD_BATCH_DONE
+        assert srv.status(t_empty) == bkd.BKD_BATCH_DONE
+        idx, dist = srv.result(t_good)
+        ref_i, ref_d = bkd.bkd_query(tree, Q[50:300].copy(), 5)
+        assert np.array_equal(idx, ref_i) and np.array_equal(dist, ref_d)
+        with pytest.raises(bkd.BkdError):
+            srv.status(t_good)                   # terminal status read once
+        srv.close()
+    finally:
+        bkd.bkd_free(tree)
