@@ -140,9 +140,10 @@ struct WarpSmem {
 };
 
 // Ring depth (super-tiles per warp in the ring: one being read, the rest in
-// flight) and 16-byte components per stage.  Deeper rings measured slower:
-// the shared memory they take comes out of L1.
-__host__ __device__ constexpr int ring_depth(int) { return 4; }
+// flight) and 16-byte components per stage.  Measured best at 3 (with three
+// CTAs per SM); deeper rings are slower: their shared memory comes out of
+// L1.
+__host__ __device__ constexpr int ring_depth(int) { return 3; }
 __host__ __device__ constexpr int ring_comps(int kh) { return 2 * kh; }
 
 __host__ __device__ constexpr int warp_words(int kh, int K) {
