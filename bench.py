@@ -46,7 +46,10 @@ WORKLOADS = {"mixture64M": workloads.MIXTURE_64M,
              # same distribution, 1/4 of the points, 1/16 of the queries
              # (leaf structure 0.67 GB > L2): the case ncu captures
              "mixture16M": workloads.scaled(workloads.MIXTURE_64M, 1 << 24,
-                                            1 << 20, 14)}
+                                            1 << 20, 14),
+             # d = 27, k = 50, 64 components, 1% duplicate rows (n = 2^28,
+             # m = 2^25, h = 18; ~30 GB of points)
+             "d27k50": workloads.MIXTURE_D27}
 
 
 def args_():
@@ -171,6 +174,29 @@ def cpu_baseline(P, Q, w, seconds: float, seed: int = 7):
                        f"over queries; tree build {build_s:.1f} s not "
                        f"counted; query phase {dt:.1f} s")}
     return info, rows, res
+
+
+def l2_note(w) -> str:
+    """Whether the timed inputs exceed the 129 MB L2 (no flush needed)."""
+    dp = min(c for c in (2, 4, 6, 8, 10, 12, 16, 24, 32) if c >= w.d)
+    leaf_gb, q_gb = w.n * dp * 4 / 1e9, w.m * dp * 4 / 1e9
+    big = leaf_gb > 0.129 and q_gb > 0.129
+    return (f"inputs {'larger' if big else 'not all larger'} than L2 (leaf "
+            f"structure {leaf_gb:.2f} GB, queries {q_gb:.2f} GB)"
+            + (" - no flush needed" if big else
+               " - small case, not a bench line"))
+
+
+def data_description(w) -> str:
+    """The synthetic input of workload w, in words."""
+    if w.kind == "uniform":
+        return (f"synthetic: seeded uniform [0,1)^{w.d}; per-rank query "
+                f"sets")
+    dup = (f", {w.duplicates:.0%} of the reference rows exact copies of "
+           f"others" if w.duplicates else "")
+    return (f"synthetic: seeded Gaussian mixture ({w.components} isotropic "
+            f"components, centres U[0,1]^{w.d}, sigma logU[{w.sigma_lo},"
+            f"{w.sigma_hi}], Dirichlet(1) weights{dup}); per-rank query sets")
 
 
 # ---------------------------------------------------- multi-rank bookkeeping
@@ -508,13 +534,10 @@ def run_ours(a, w, rank, world, local_rank):
         "ms_per_step": ms_max / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16+f32" if head == 1 else "f32",
-        "data": ("synthetic: seeded Gaussian mixture (32 isotropic "
-                 "components, centres U[0,1]^10, sigma logU[0.02,0.2], "
-                 "Dirichlet(1) weights); per-rank query sets"),
+        "data": data_description(w),
         "config": dict(w.describe(), precision=names[head],
                        parallelism=f"replicas x{world}, queries sharded",
-                       l2=("inputs larger than L2 (leaf structure 2.7 GB, "
-                           "queries 0.67 GB) - no flush needed"),
+                       l2=l2_note(w),
                        tree_build_s=round(build_s, 2)),
         "e2e": e2e,
         "latency": lat,
