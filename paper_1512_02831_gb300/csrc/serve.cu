@@ -34,6 +34,7 @@
 
 #include "bkd.h"
 #include "bkd_internal.h"
+#include "slots.h"
 
 using namespace bkd;
 
@@ -82,40 +83,6 @@ struct Batch {
   int64_t s0 = -1;  // first slot
   int bid = -1;     // index into batch_left
   int status = BKD_BATCH_QUEUED;
-};
-
-// First-fit allocator of contiguous slot ranges.
-struct Slots {
-  std::map<int64_t, int64_t> free_;  // start -> length
-  void reset(int64_t n) {
-    free_.clear();
-    if (n > 0) free_[0] = n;
-  }
-  int64_t take(int64_t len) {
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second < len) continue;
-      const int64_t s = it->first, rest = it->second - len;
-      free_.erase(it);
-      if (rest > 0) free_[s + len] = rest;
-      return s;
-    }
-    return -1;
-  }
-  void give(int64_t s, int64_t len) {
-    auto it = free_.emplace(s, len).first;
-    auto nx = std::next(it);
-    if (nx != free_.end() && it->first + it->second == nx->first) {
-      it->second += nx->second;
-      free_.erase(nx);
-    }
-    if (it != free_.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == it->first) {
-        pv->second += it->second;
-        free_.erase(it);
-      }
-    }
-  }
 };
 
 template <class T>
