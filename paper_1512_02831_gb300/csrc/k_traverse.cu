@@ -81,9 +81,10 @@ __global__ void __launch_bounds__(kFindThreads)
 
 // ------------------------------------------------------------- bucketing
 // Buffer insertion of Algorithm 1 as a counting sort by leaf id: the
-// histogram is counted where the next leaf is found (FindLeafBatch, or the
-// leaf kernel's fused step); here follow the exclusive scan (also of per-leaf
-// work items of `tile` queries) and the scatter.
+// histogram is counted where the next leaf is found (FindLeafBatch, which
+// also keeps each query's rank among the queries of its leaf); here follow
+// the exclusive scan (also of per-leaf work items of `tile` queries) and the
+// scatter to offset + rank.
 // The order of queries inside a leaf's buffer is irrelevant to the results.
 
 // Two-pass scan over the leaves, 2,048 leaves (8 per thread) per block:
