@@ -187,6 +187,28 @@ int bkd_query(bkd_tree* t, const float* Q, int64_t m, int k, int64_t* out_idx,
 int bkd_query_static(bkd_tree* t, const float* Q, int64_t m, int k,
                      int64_t* out_idx, float* out_dist);
 
+/* ------------------------------------------------------------ test support
+ * Neither call has a counterpart in the paper; they let tests reach failure
+ * paths and hardware properties that the query calls depend on. */
+
+/* bkd_test_fail_alloc -- makes the nth device or pinned host allocation made
+ * by the library from now on (any handle, any thread) fail as if the memory
+ * were exhausted; 0 switches the hook off.  The call that meets the failure
+ * returns BKD_ENOMEM and leaves its handle usable (bkd_build frees what it
+ * had built).  Errors: BKD_EINVAL (nth < 0). */
+int bkd_test_fail_alloc(int64_t nth);
+
+/* bkd_probe_mma -- runs the BF16 screen's tensor-core instruction (kind 0:
+ * mma.sync m16n8k16, bf16 inputs, fp32 accumulation) on `count` instances:
+ * D = C + A Bt^T, with A count x 16 x 16 and Bt count x 8 x 16 bf16 bit
+ * patterns (row-major; row c of Bt is column c of the B operand), C and D
+ * count x 16 x 8 float32, all HOST memory.  The screen's error bound
+ * (Sec. 2.2 exactness of the answer) assumes how far this accumulation may
+ * stray from the exact sum; tests compare D with exact sums.
+ * Errors: BKD_EINVAL, BKD_ENOMEM, BKD_ECUDA. */
+int bkd_probe_mma(int kind, int count, const uint16_t* A, const uint16_t* Bt,
+                  const float* C, float* D);
+
 /* bkd_set_option -- sets a run-time option (enum bkd_option) on a handle.
  * Build-only keys are rejected with BKD_EINVAL. */
 int bkd_set_option(bkd_tree* t, int key, int64_t value);

@@ -85,12 +85,15 @@ def load():
         lib.bkd_serve_status.argtypes = [vp, i64, ctypes.POINTER(i32)]
         lib.bkd_serve_close.argtypes = [vp]
         lib.bkd_serve_close.restype = None
+        lib.bkd_test_fail_alloc.argtypes = [i64]
+        lib.bkd_probe_mma.argtypes = [i32, i32, vp, vp, vp, vp]
         lib.bkd_last_error.restype = ctypes.c_char_p
         for f in ("bkd_build", "bkd_build_with", "bkd_query",
                   "bkd_query_static", "bkd_set_option",
                   "bkd_get_stat", "bkd_tree_shape", "bkd_export_tree",
                   "bkd_serve_open", "bkd_serve_submit", "bkd_serve_step",
-                  "bkd_serve_status"):
+                  "bkd_serve_status", "bkd_test_fail_alloc",
+                  "bkd_probe_mma"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -212,6 +215,14 @@ def bkd_query_static(tree: Tree, Q, k: int, out_idx, out_dist):
     m = shape[0]
     if tuple(si) != (m, k) or tuple(sd) != (m, k):
         raise ValueError("outputs must be (m, k)")
+    if _is_torch(Q) and Q.is_cuda:
+        # the call runs on the tree's stream: make it torch's current one, so
+        # it is ordered after the work that wrote Q and before the reads of
+        # the outputs
+        import torch
+        _check(lib.bkd_set_option(tree.handle, OPTIONS["stream"],
+                                  torch.cuda.current_stream(Q.device)
+                                  .cuda_stream))
     _check(lib.bkd_query_static(tree.handle, q, m, k, oi, od))
     return out_idx, out_dist
 
@@ -250,6 +261,28 @@ def bkd_export_tree(tree: Tree):
 
 def bkd_free(tree: Tree):
     tree.close()
+
+
+def bkd_test_fail_alloc(nth: int):
+    """``bkd_test_fail_alloc``: the nth allocation from now fails (0: off)."""
+    _check(load().bkd_test_fail_alloc(int(nth)))
+
+
+def bkd_probe_mma(A, Bt, C, kind: int = 0):
+    """``bkd_probe_mma``: D = C + A Bt^T per instance on the screen's tensor
+    core instruction.  A (count, 16, 16) and Bt (count, 8, 16) uint16 bf16
+    bit patterns, C (count, 16, 8) float32; returns D like C."""
+    A = np.ascontiguousarray(A, np.uint16)
+    Bt = np.ascontiguousarray(Bt, np.uint16)
+    C = np.ascontiguousarray(C, np.float32)
+    count = A.shape[0]
+    if A.shape != (count, 16, 16) or Bt.shape != (count, 8, 16) \
+            or C.shape != (count, 16, 8):
+        raise ValueError("shapes (count,16,16), (count,8,16), (count,16,8)")
+    D = np.empty_like(C)
+    _check(load().bkd_probe_mma(kind, count, A.ctypes.data, Bt.ctypes.data,
+                                C.ctypes.data, D.ctypes.data))
+    return D
 
 
 def bkd_last_error() -> str:

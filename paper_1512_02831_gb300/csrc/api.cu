@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -58,13 +59,21 @@ int fail(int code, const char* fmt, ...) {
                   __FILE__, __LINE__);                                      \
   } while (0)
 
-bool is_device_ptr(const void* p) {
+// Where a caller's pointer lives: host memory (pageable or pinned), device
+// memory the tree's GPU can use (its own, or managed), or device memory of
+// another GPU (rejected: the kernels would read it without peer access).
+enum PtrKind { kHostPtr = 0, kDevicePtr = 1, kForeignPtr = -1 };
+
+PtrKind ptr_kind(const void* p, int device) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return kHostPtr;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return kDevicePtr;
+  if (a.type == cudaMemoryTypeDevice)
+    return a.device == device ? kDevicePtr : kForeignPtr;
+  return kHostPtr;
 }
 
 // Restores the caller's current device on scope exit.
@@ -89,7 +98,7 @@ struct DevBuf {
     if (p) cudaFree(p);
     p = nullptr;
     n = 0;
-    cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+    cudaError_t e = dev_malloc(&p, std::max<size_t>(count, 1) * sizeof(T));
     if (e == cudaSuccess) n = count;
     return e;
   }
@@ -302,7 +311,11 @@ int build_impl(const float* P, int64_t n, int d, int height,
   // points on the host
   std::vector<float> hostP;
   const float* Ph = P;
-  if (is_device_ptr(P)) {
+  const PtrKind pk = ptr_kind(P, t->device);
+  if (pk == kForeignPtr)
+    return bail(fail(BKD_EINVAL, "P is device memory of another GPU than "
+                                 "the current device %d", t->device));
+  if (pk == kDevicePtr) {
     try {
       hostP.resize((size_t)(n * d));
     } catch (...) {
@@ -350,8 +363,8 @@ int build_impl(const float* P, int64_t n, int d, int height,
   for (int64_t l = 0; l < L; ++l)
     leaf_cnt[l] = (int32_t)(H.leaf_lo[l + 1] - H.leaf_lo[l]);
   const int64_t nsplit = std::max<int64_t>(L - 1, 1);
-  if (cudaMalloc(&t->d_split, nsplit * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&t->d_leaf_cnt, L * sizeof(int32_t)) != cudaSuccess)
+  if (dev_malloc(&t->d_split, nsplit * sizeof(float)) != cudaSuccess ||
+      dev_malloc(&t->d_leaf_cnt, L * sizeof(int32_t)) != cudaSuccess)
     return bail(fail(BKD_ENOMEM, "device allocation failed (tree)"));
   {
     const int64_t nodes = 2 * L - 1;
@@ -362,7 +375,7 @@ int build_impl(const float* P, int64_t n, int d, int height,
       return bail(fail(BKD_ENOMEM, "host allocation failed (boxes)"));
     }
     fill_boxes(Ph, H, box.data());
-    if (cudaMalloc(&t->d_box, box.size() * sizeof(float)) != cudaSuccess)
+    if (dev_malloc(&t->d_box, box.size() * sizeof(float)) != cudaSuccess)
       return bail(fail(BKD_ENOMEM, "device allocation failed (boxes)"));
     if (cudaMemcpy(t->d_box, box.data(), box.size() * sizeof(float),
                    cudaMemcpyHostToDevice) != cudaSuccess)
@@ -384,8 +397,8 @@ int build_impl(const float* P, int64_t n, int d, int height,
       return bail(fail(BKD_ENOMEM, "host staging of the leaf structure"));
     }
     fill_quads(Ph, H, 0, L, qbuf.data(), obuf.data());
-    if (cudaMalloc(&t->d_pts, pts_bytes) != cudaSuccess ||
-        cudaMalloc(&t->d_orig, orig_bytes) != cudaSuccess)
+    if (dev_malloc(&t->d_pts, pts_bytes) != cudaSuccess ||
+        dev_malloc(&t->d_orig, orig_bytes) != cudaSuccess)
       return bail(fail(BKD_ENOMEM, "device allocation of %zu bytes failed",
                        pts_bytes + orig_bytes));
     if (cudaMemcpy(t->d_pts, qbuf.data(), pts_bytes, cudaMemcpyHostToDevice) !=
@@ -394,10 +407,10 @@ int build_impl(const float* P, int64_t n, int d, int height,
                    cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(fail(BKD_ECUDA, "upload of the leaf structure failed"));
   } else {
-    if (cudaHostAlloc(&t->h_pts, pts_bytes,
+    if (host_alloc(&t->h_pts, pts_bytes,
                       cudaHostAllocMapped | cudaHostAllocPortable) !=
             cudaSuccess ||
-        cudaHostAlloc(&t->h_orig, orig_bytes,
+        host_alloc(&t->h_orig, orig_bytes,
                       cudaHostAllocMapped | cudaHostAllocPortable) !=
             cudaSuccess) {
       cudaGetLastError();
@@ -413,9 +426,9 @@ int build_impl(const float* P, int64_t n, int d, int height,
       max_leaves = std::max<int64_t>(max_leaves,
                                      t->chunk_leaf[c + 1] - t->chunk_leaf[c]);
     const size_t buf_bytes = (size_t)max_leaves * H.lcap * H.Dp * sizeof(float);
-    if (cudaMalloc(&t->d_chunk_buf[0], buf_bytes) != cudaSuccess ||
-        cudaMalloc(&t->d_chunk_buf[1], buf_bytes) != cudaSuccess ||
-        cudaMalloc(&t->d_chunk_leaf, (t->n_chunks + 1) * sizeof(int32_t)) !=
+    if (dev_malloc(&t->d_chunk_buf[0], buf_bytes) != cudaSuccess ||
+        dev_malloc(&t->d_chunk_buf[1], buf_bytes) != cudaSuccess ||
+        dev_malloc(&t->d_chunk_leaf, (t->n_chunks + 1) * sizeof(int32_t)) !=
             cudaSuccess)
       return bail(fail(BKD_ENOMEM, "device chunk buffers (%zu bytes each)",
                        buf_bytes));
@@ -449,10 +462,10 @@ int build_impl(const float* P, int64_t n, int d, int height,
     }
     fill_screen(Ph, H, stride, words.data(), center.data(), bmax.data(),
                 pnmax.data());
-    if (cudaMalloc(&t->d_scr_words, words.size() * 4) != cudaSuccess ||
-        cudaMalloc(&t->d_scr_center, center.size() * 4) != cudaSuccess ||
-        cudaMalloc(&t->d_scr_bmax, bmax.size() * 4) != cudaSuccess ||
-        cudaMalloc(&t->d_scr_pnmax, pnmax.size() * 4) != cudaSuccess)
+    if (dev_malloc(&t->d_scr_words, words.size() * 4) != cudaSuccess ||
+        dev_malloc(&t->d_scr_center, center.size() * 4) != cudaSuccess ||
+        dev_malloc(&t->d_scr_bmax, bmax.size() * 4) != cudaSuccess ||
+        dev_malloc(&t->d_scr_pnmax, pnmax.size() * 4) != cudaSuccess)
       return bail(fail(BKD_ENOMEM, "device allocation failed (screen data)"));
     if (cudaMemcpy(t->d_scr_words, words.data(), words.size() * 4,
                    cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -471,10 +484,10 @@ int build_impl(const float* P, int64_t n, int d, int height,
     t->screen.kh = kh;
     t->precision = 1;
   }
-  if (cudaMalloc(&t->d_ctr, sizeof(Counters)) != cudaSuccess ||
-      cudaHostAlloc(&t->h_ctr, sizeof(Counters), cudaHostAllocDefault) !=
+  if (dev_malloc(&t->d_ctr, sizeof(Counters)) != cudaSuccess ||
+      host_alloc(&t->h_ctr, sizeof(Counters), cudaHostAllocDefault) !=
           cudaSuccess ||
-      cudaHostAlloc(&t->h_chunk_item, (t->n_chunks + 2) * sizeof(int32_t),
+      host_alloc(&t->h_chunk_item, (t->n_chunks + 2) * sizeof(int32_t),
                     cudaHostAllocDefault) != cudaSuccess)
     return bail(fail(BKD_ENOMEM, "counter allocation failed"));
 
@@ -722,6 +735,35 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
 
 namespace bkd {
 
+namespace {
+// Allocations left before the one that is made to fail (0: none fails).
+std::atomic<int64_t> g_fail_countdown{0};
+
+bool injected_failure() {
+  int64_t c = g_fail_countdown.load();
+  while (c > 0) {
+    if (g_fail_countdown.compare_exchange_weak(c, c - 1)) return c == 1;
+  }
+  return false;
+}
+}  // namespace
+
+cudaError_t dev_malloc_raw(void** p, size_t bytes) {
+  if (injected_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_alloc_raw(void** p, size_t bytes, unsigned flags) {
+  if (injected_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaHostAlloc(p, bytes, flags);
+}
+
 TreeView view_of(const bkd_tree* t) {
   TreeView v;
   v.device = t->device;
@@ -795,8 +837,14 @@ int bkd_query(bkd_tree* t, const float* Q, int64_t m, int k, int64_t* out_idx,
   if (m == 0) return BKD_OK;
   const int d = t->dev.d;
   cudaStream_t s = t->stream;
-  const bool q_dev = is_device_ptr(Q);
-  const bool o_dev = is_device_ptr(out_idx) && is_device_ptr(out_dist);
+  const PtrKind qk = ptr_kind(Q, t->device), ik = ptr_kind(out_idx, t->device),
+                dk = ptr_kind(out_dist, t->device);
+  if (qk == kForeignPtr || ik == kForeignPtr || dk == kForeignPtr)
+    return fail(BKD_EINVAL, "Q / out_idx / out_dist is device memory of "
+                            "another GPU than the tree's (device %d)",
+                t->device);
+  const bool q_dev = qk == kDevicePtr;
+  const bool o_dev = ik == kDevicePtr && dk == kDevicePtr;
   const int64_t slice = t->max_active > 0 ? t->max_active : m;
   CU(t->qdev.ensure(std::min(slice, m) * d));
   if (!o_dev) {
@@ -946,6 +994,13 @@ int bkd_export_tree(const bkd_tree* t, float* split, int64_t* leaf_lo,
 }
 
 void bkd_free(bkd_tree* t) { release(t); }
+
+int bkd_test_fail_alloc(int64_t nth) {
+  g_err.clear();
+  if (nth < 0) return fail(BKD_EINVAL, "nth must be >= 0");
+  bkd::g_fail_countdown.store(nth);
+  return BKD_OK;
+}
 
 const char* bkd_last_error(void) { return g_err.c_str(); }
 

@@ -214,6 +214,20 @@ struct TreeView {
 };
 TreeView view_of(const struct ::bkd_tree* t);
 
+// Every device and pinned host allocation of the library goes through these
+// two (api.cu): they count down the test hook of bkd_test_fail_alloc and
+// report cudaErrorMemoryAllocation for the chosen allocation.
+cudaError_t dev_malloc_raw(void** p, size_t bytes);
+cudaError_t host_alloc_raw(void** p, size_t bytes, unsigned flags);
+template <class T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc_raw(reinterpret_cast<void**>(p), bytes);
+}
+template <class T>
+inline cudaError_t host_alloc(T** p, size_t bytes, unsigned flags) {
+  return host_alloc_raw(reinterpret_cast<void**>(p), bytes, flags);
+}
+
 // Records the calling thread's bkd_last_error() message; returns `code`.
 int set_error(int code, const char* fmt, ...);
 

@@ -230,9 +230,10 @@ void fill_screen(const float* P, const HostTree& t, int64_t stride,
   const int d = t.d;
   const int kh = screen_halves(d);
   const int64_t L = (int64_t)1 << t.h;
-  // BF16 rounding error (relative, round to nearest) with margin, and its
-  // effect on a norm: |w_hat - w| <= rho |w|, |w| <= |w_hat| / (1 - rho).
-  const double rho = std::ldexp(1.0, -9) * (1.0 + 1e-4);
+  // BF16 rounding error (relative, round to nearest: 8 significant bits, so
+  // 2^-8) with margin for the float32 subtraction before it, and its effect
+  // on a norm: |w_hat - w| <= rho |w|, |w| <= |w_hat| / (1 - rho).
+  const double rho = std::ldexp(1.0, -8) * (1.0 + 1e-4);
   const double tiny = std::ldexp(1.0, -126) * std::sqrt((double)d);
   parallel_items(L, [&](int64_t leaf) {
     const int64_t lo = t.leaf_lo[leaf], cnt = t.leaf_lo[leaf + 1] - lo;
@@ -259,7 +260,8 @@ void fill_screen(const float* P, const HostTree& t, int64_t stride,
           ss += w * w;
         }
         const float pv = (float)ss;
-        // pn = pn_hi + pn_lo up to 2^-18 pn; pv - pn_hi is exact
+        // pv - pn_hi is exact (at most 16 significant bits remain); its
+        // bf16 rounding leaves pn_hi + pn_lo within 2^-16 pv of pv
         hv[d] = bf16_rn(pv);
         hv[d + 1] = bf16_rn(pv - bf16_to_float(hv[d]));
         wmax = std::max(wmax, std::sqrt(ss));

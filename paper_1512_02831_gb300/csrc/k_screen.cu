@@ -10,22 +10,33 @@
 // The tensor cores form D = v^.w^ - |w^|^2/2 (mma.sync m16n8k16, bf16 in,
 // fp32 accumulate from zero): 16 points (rows) x 8 queries (columns) per
 // instruction and k-half of 16 bf16 slots.  A point's slots hold w^ and,
-// after it, pn_hi and pn_lo (|w^|^2 = pn_hi + pn_lo up to 2^-18 of it); a
+// after it, pn_hi and pn_lo (pn = fl32(|w^|^2), pn_hi = bf16(pn), pn_lo =
+// bf16(pn - pn_hi), so |w^|^2 = pn_hi + pn_lo up to (2^-16 + 2^-24) pn); a
 // query's hold v^ and -1/2, -1/2.  So s = |v^|^2 - 2 D, and the screen test
 // s < T reads D > (|v^|^2 - T) / 2: one comparison per (query, point) pair.
 // Padding points carry pn_hi = +inf, so D = -inf there.
 //
-// Safety bound.  With rho = 2^-9 (1 + 1e-4) (bf16 round-to-nearest plus the
-// float32 subtraction), |v^ - v| <= rho |v| and |v| <= |v^| / (1 - rho), so
+// Safety bound.  bf16 keeps 8 significant bits, so round-to-nearest errs by
+// at most 2^-8 relative; with the float32 subtraction before it, rho =
+// 2^-8 (1 + 1e-4) and |v^ - v| <= rho |v|, |v| <= |v^| / (1 - rho), so
 //   |q - x| >= |v^ - w^| - A_q - B_x,  A_q = rho/(1-rho) |v^|,
-// and B_x <= B_max, the leaf's largest such term (prepared on the host).  The
-// computed s differs from |v^ - w^|^2 by at most E = 2^-14 (|v^|^2 + pn_max):
-// every product is exact, the sum of the absolute terms is at most
-// |v^|^2 + |w^|^2, the fp32 accumulation is taken to err by at most 2^-22 of
-// that per addition (16 per k-half, at most 3 halves), and the norm split and
-// the rounding of |v^|^2 add less than 2^-17 of it.  The float32 distance of
-// the exact path obeys D32 >= D (1 - g) - eta, g = (d+3) 2^-24,
-// eta = 2^-120.  Hence a point can only enter the list (D32 < bound) if
+// and B_x <= B_max, the leaf's largest such term (prepared on the host).
+// The computed s differs from |v^ - w^|^2 by at most
+//   E = 2^-14 (|v^|^2 + pn_max):
+//   * accumulation model: one MMA (16 exact bf16 products added to an fp32
+//     accumulator c) errs by at most 2^-18 (|c| + sum |a_i b_i|); the KH
+//     chained halves of one pair then err by at most KH 2^-18 S, S = the sum
+//     of the absolute products <= |v^|^2 / 2 + pn (1 + 2^-8).  (A hardware
+//     property, not an IEEE rule: the bf16 MMA probe test checks it on
+//     adversarial operands -- one large term and many small ones,
+//     cancellation, mixed exponents within a k-half.)  With KH <= 3 the
+//     error of s = |v^|^2 - 2D is <= 2^-16.4 |v^|^2 + 2^-15.4 pn;
+//   * the norm split adds (2^-16 + 2^-24) pn, the float32 chain of |v^|^2
+//     at most d 2^-24 |v^|^2 <= 2^-19 |v^|^2;
+//   * in total < 1.4e-5 |v^|^2 + 3.9e-5 pn <= E (2^-14 = 6.1e-5).
+// The float32 distance of the exact path obeys D32 >= D (1 - g) - eta,
+// g = (d+3) 2^-24, eta = 2^-120.  Hence a point can only enter the list
+// (D32 < bound) if
 //   s < T = (sqrt((bound + eta) / (1 - g)) + A_q + B_max)^2 + E,
 // evaluated once per (query, leaf) in float32 with every operation rounded
 // toward the larger threshold (divisors toward the smaller).  Kept points
@@ -448,7 +459,7 @@ __device__ __forceinline__ void setup_column(
     } else {
       // T of the header comment, every step rounded upward (divisors
       // downward) so that the float result is never too small
-      const float rho = 0x1p-9f * 1.0001f;
+      const float rho = 0x1p-8f * 1.0001f;  // bf16: 8 significant bits
       const float rr = __fdiv_ru(rho, __fsub_rd(1.f, rho));
       const float one_m_g = __fsub_rd(1.f, (float)(t.d + 3) * 0x1p-24f);
       const float aq = __fadd_ru(__fmul_ru(rr, __fsqrt_ru(ss)), 0x1p-123f);

@@ -51,13 +51,17 @@ constexpr int kMaxBatches = 4096;  // batches admitted at once
                        "%s failed: %s", #call, cudaGetErrorString(e_));    \
   } while (0)
 
-bool device_ptr(const void* p) {
+// 1: device memory the tree's GPU can use (its own, or managed); 0: host
+// memory; -1: device memory of another GPU (refused: no peer access).
+int device_ptr(const void* p, int device) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return 0;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return 1;
+  if (a.type == cudaMemoryTypeDevice) return a.device == device ? 1 : -1;
+  return 0;
 }
 
 struct DeviceScope {
@@ -87,7 +91,7 @@ struct Batch {
 
 template <class T>
 cudaError_t dev_alloc(T** p, int64_t n) {
-  return cudaMalloc(p, std::max<int64_t>(n, 1) * sizeof(T));
+  return dev_malloc(p, std::max<int64_t>(n, 1) * sizeof(T));
 }
 
 }  // namespace
@@ -333,9 +337,9 @@ int bkd_serve_open(bkd_tree* t, int k_max, int64_t max_queries,
   SV_CU(dev_alloc(&sv->batch_left, kMaxBatches));
   SV_CU(dev_alloc(&sv->d_ctr, 1));
   SV_CU(dev_alloc(&sv->d_fin, 1));
-  SV_CU(cudaHostAlloc(&sv->h_ctr, sizeof(Counters), cudaHostAllocDefault));
-  SV_CU(cudaHostAlloc(&sv->h_fin, sizeof(Counters), cudaHostAllocDefault));
-  SV_CU(cudaHostAlloc(&sv->h_left, sizeof(int32_t) * kMaxBatches,
+  SV_CU(host_alloc(&sv->h_ctr, sizeof(Counters), cudaHostAllocDefault));
+  SV_CU(host_alloc(&sv->h_fin, sizeof(Counters), cudaHostAllocDefault));
+  SV_CU(host_alloc(&sv->h_left, sizeof(int32_t) * kMaxBatches,
                       cudaHostAllocDefault));
   SV_CU(cudaMemsetAsync(sv->d_ctr, 0, sizeof(Counters), v.stream));
   SV_CU(cudaMemsetAsync(sv->batch_left, 0, sizeof(int32_t) * kMaxBatches,
@@ -370,6 +374,13 @@ int bkd_serve_submit(bkd_server* s, const float* Q, int64_t m, int k,
   if (m > 0 && (!Q || !out_idx || !out_dist))
     return set_error(BKD_EINVAL, "Q / out_idx / out_dist is NULL");
   DeviceScope guard(s->v.device);
+  const int qk = m > 0 ? device_ptr(Q, s->v.device) : 0;
+  const int ik = m > 0 ? device_ptr(out_idx, s->v.device) : 0;
+  const int dk = m > 0 ? device_ptr(out_dist, s->v.device) : 0;
+  if (qk < 0 || ik < 0 || dk < 0)
+    return set_error(BKD_EINVAL, "Q / out_idx / out_dist is device memory of "
+                                 "another GPU than the tree's (device %d)",
+                     s->v.device);
   auto b = std::make_unique<Batch>();
   b->ticket = s->next_ticket++;
   b->Q = Q;
@@ -378,8 +389,8 @@ int bkd_serve_submit(bkd_server* s, const float* Q, int64_t m, int k,
   b->out_idx = out_idx;
   b->out_dist = out_dist;
   if (m > 0) {
-    b->q_dev = device_ptr(Q);
-    b->o_dev = device_ptr(out_idx) && device_ptr(out_dist);
+    b->q_dev = qk == 1;
+    b->o_dev = ik == 1 && dk == 1;
     s->queue.push_back(b.get());
   } else {
     b->status = BKD_BATCH_DONE;

@@ -88,13 +88,17 @@ int scratch_address(int device, char** out) {
   return BKD_OK;
 }
 
-bool on_device(const void* p) {
+// True for device memory the tree's GPU can use: its own, or managed.
+// Host memory, and device memory of another GPU (which this GPU's kernels
+// could not read without peer access), are refused.
+bool on_device(const void* p, int device) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return a.type == cudaMemoryTypeManaged ||
+         (a.type == cudaMemoryTypeDevice && a.device == device);
 }
 
 #define SQ_CU(call)                                                     \
@@ -213,10 +217,11 @@ extern "C" int bkd_query_static(bkd_tree* t, const float* Q, int64_t m, int k,
   if (prev != v.device && cudaSetDevice(v.device) != cudaSuccess)
     return set_error(BKD_ECUDA, "cudaSetDevice(%d) failed", v.device);
   int rc = BKD_OK;
-  if (!on_device(Q) || !on_device(out_idx) || !on_device(out_dist)) {
+  if (!on_device(Q, v.device) || !on_device(out_idx, v.device) ||
+      !on_device(out_dist, v.device)) {
     rc = set_error(BKD_EINVAL,
                    "bkd_query_static takes device pointers only (Q, out_idx, "
-                   "out_dist)");
+                   "out_dist), on the tree's GPU (device %d)", v.device);
   } else {
     char* base = nullptr;
     rc = scratch_address(v.device, &base);

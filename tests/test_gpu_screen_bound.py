@@ -1,0 +1,247 @@
+"""The BF16 screen's safety bound, attacked where it is thinnest (needs a GPU).
+
+The screen (ProcessAllBuffers with bf16 tensor cores, float32 rescoring) may
+only skip points that provably cannot enter a candidate list, so its results
+must equal the float32 path bit for bit and the binary64 oracle.  The bound
+has three ingredients, each attacked here:
+
+  * bf16 rounding of the centred coordinates (8 significant bits: relative
+    error up to 2^-8): a hand-built case whose query and point offsets sit
+    just beyond / just short of a bf16 rounding tie, so that rounding moves
+    them apart by almost the full 2^-8 of each, and whose (k+1)-th bound is
+    just above the point's distance.  A bound that assumed 2^-9 rejects the
+    point (worked through in the test's docstring);
+  * the tensor core's fp32 accumulation: the probe entry point runs the
+    screen's MMA instruction on adversarial operands and every result is
+    compared with the exact sum against the accumulation model the bound
+    uses (error <= 2^-18 of |c| + sum |a_i b_i| per instruction);
+  * wide data: a large common offset, queries far outside the tree's box,
+    leaves of tiny spread, and d = 17 / 32 (two and three k-halves).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1512_02831_gb300 as bkd
+import workloads
+from parity import check
+
+pytestmark = pytest.mark.gpu
+
+MODEL = 2.0 ** -18   # per-instruction accumulation error the bound assumes
+
+
+def run_both(P, Q, k, h):
+    """float32 path and BF16 screen on one tree, every query through the
+    LazySearch rounds (tail kernel off)."""
+    tree = bkd.bkd_build(P, h, precision=1, tail_queries=0)
+    try:
+        bkd.bkd_set_option(tree, "precision", 0)
+        i0, d0 = bkd.bkd_query(tree, Q, k)
+        bkd.bkd_set_option(tree, "precision", 1)
+        i1, d1 = bkd.bkd_query(tree, Q, k)
+        st = {s: bkd.bkd_get_stat(tree, s) for s in bkd.STATS}
+    finally:
+        bkd.bkd_free(tree)
+    return i0, d0, i1, d1, st
+
+
+# ------------------------------------------------------------ rounding case
+def rounding_case(scale: float, d: int, mirror: bool):
+    """Two leaves split on x0 at 0.  Leaf A (x0 < 0) has the bounding box
+    [-2, -1e-3] x [-9.0312, 9.0312], centre (-1.0005, 0); leaf B holds the
+    query's two nearest rivals at distances 1.0002 and 1.0003.  The query
+    q = (0, 10.0313) lies in B, so the first (float32) round fills its k+1 =
+    2 list from B (bound 1.0003^2) and the second round screens A.  A's point
+    x = (-1e-3, 9.0312) is at distance 1.0001 < 1.0003, so it must enter.
+    Centred: v = (1.0005, 10.0313) -> bf16 (1, 10.0625) (10.0313 is past the
+    tie 10.03125), w = (0.9995, 9.0312) -> bf16 (1, 9) (9.0312 is short of
+    the tie 9.03125): |v^ - w^| = 1.0625, although |q - x| = 1.0001.  With
+    rho = 2^-8 the screen's threshold radius is ~1.0807 and keeps x; with
+    2^-9 it is ~1.0432 and x would be lost (query answered with B's point).
+    Scaling by a power of two keeps every rounding; extra dimensions are
+    zero (d = 17 / 32 use two / three k-halves)."""
+    base = np.array([
+        [-2.0, -9.0312], [-2.0, 9.0312], [-1e-3, 9.0312], [-1.5, 0.0],
+        [0.0, 11.0315], [0.0, 11.0316], [2.0, 30.0], [1.0, -30.0]],
+        np.float32)
+    q = np.array([[0.0, 10.0313]], np.float32)
+    if mirror:
+        base[:, 1] *= -1
+        q[:, 1] *= -1
+    P = np.zeros((8, d), np.float32)
+    Q = np.zeros((1, d), np.float32)
+    P[:, :2] = base * np.float32(scale)
+    Q[:, :2] = q * np.float32(scale)
+    return P, Q
+
+
+@pytest.mark.parametrize("d", [2, 17, 32])
+@pytest.mark.parametrize("scale", [2.0 ** -8, 1.0, 2.0 ** 6])
+@pytest.mark.parametrize("mirror", [False, True])
+def test_screen_keeps_point_moved_apart_by_bf16_rounding(d, scale, mirror):
+    P, Q = rounding_case(scale, d, mirror)
+    ref = oracle.brute_knn(P, Q, 1)
+    assert ref.idx[0, 0] == 2          # the point of leaf A is the answer
+    i0, d0, i1, d1, st = run_both(P, Q, 1, 1)
+    assert st["screen_pairs"] > 0      # leaf A went through the screen
+    assert i0[0, 0] == 2 and i1[0, 0] == 2, (i0, i1)
+    assert np.array_equal(d0, d1)
+    check(P, Q, 1, i1, d1, ref)
+
+
+# -------------------------------------------------------- accumulation model
+def bf16_bits(x: np.ndarray) -> np.ndarray:
+    """Round-to-nearest-even bf16 bit patterns of float32 values."""
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    r = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return r.astype(np.uint16)
+
+
+def bf16_value(b: np.ndarray) -> np.ndarray:
+    return (b.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def exact_dots(A, Bt, C):
+    """Exact C + A Bt^T per instance with math.fsum (bf16 products are exact
+    in binary64; fsum rounds the exact sum once), and the sum of absolute
+    terms."""
+    a, b = bf16_value(A), bf16_value(Bt)
+    cnt = A.shape[0]
+    out = np.empty((cnt, 16, 8))
+    mag = np.empty((cnt, 16, 8))
+    for i in range(cnt):
+        prod = a[i][:, None, :] * b[i][None, :, :]      # 16 x 8 x 16
+        for r in range(16):
+            for c in range(8):
+                terms = list(prod[r, c]) + [float(C[i, r, c])]
+                out[i, r, c] = math.fsum(terms)
+                mag[i, r, c] = math.fsum(abs(t) for t in terms)
+    return out, mag
+
+
+def adversarial_operands(rng, cnt):
+    """Instances of several kinds (a quarter each): one large product with
+    fifteen small same-sign ones just under the large one's last bits;
+    heavy cancellation (pairs of equal and opposite large products) with
+    small terms; exponents mixed over 2^-30..2^30 inside one k-half; the
+    screen's own shape (offsets, the norm split pn_hi / pn_lo against -1/2,
+    a large accumulator input)."""
+    A = np.zeros((cnt, 16, 16), np.float32)
+    B = np.zeros((cnt, 8, 16), np.float32)
+    C = np.zeros((cnt, 16, 8), np.float32)
+    for i in range(cnt):
+        kind = i % 4
+        if kind == 0:
+            A[i] = rng.uniform(1.0, 2.0, (16, 16))
+            B[i] = rng.uniform(1.0, 2.0, (8, 16))
+            big = 2.0 ** rng.integers(8, 12)
+            A[i][:, 0] *= big
+            B[i][:, 0] *= big
+            small = 2.0 ** -rng.integers(6, 10, (16, 15))
+            A[i][:, 1:] *= small
+        elif kind == 1:
+            x = rng.uniform(1.0, 2.0, (16, 8)) * 2.0 ** rng.integers(4, 10)
+            A[i][:, 0:8] = x
+            A[i][:, 8:16] = -x
+            B[i][:] = 1.0
+            A[i][:, 15] = rng.uniform(-1e-3, 1e-3, 16)
+            B[i][:, 7] = rng.uniform(1.0, 1.1, 8)
+        elif kind == 2:
+            A[i] = (rng.choice([-1, 1], (16, 16)) * rng.uniform(1, 2, (16, 16))
+                    * 2.0 ** rng.integers(-15, 15, (16, 16)))
+            B[i] = (rng.choice([-1, 1], (8, 16)) * rng.uniform(1, 2, (8, 16))
+                    * 2.0 ** rng.integers(-15, 15, (8, 16)))
+            C[i] = rng.standard_normal((16, 8)) * 2.0 ** rng.integers(-10, 10)
+        else:
+            d = 10
+            w = rng.standard_normal((16, d)) * 2.0 ** rng.integers(-4, 4)
+            wb = bf16_value(bf16_bits(w.astype(np.float32)))
+            pn = np.float32((wb ** 2).sum(1))
+            hi = bf16_value(bf16_bits(pn))
+            lo = bf16_value(bf16_bits((pn - hi).astype(np.float32)))
+            A[i][:, :d] = w
+            A[i][:, d] = hi
+            A[i][:, d + 1] = lo
+            v = rng.standard_normal((8, d)) * 2.0 ** rng.integers(-4, 4)
+            B[i][:, :d] = v
+            B[i][:, d] = -0.5
+            B[i][:, d + 1] = -0.5
+            C[i] = rng.standard_normal((16, 8)) * 4.0
+    return bf16_bits(A), bf16_bits(B), C
+
+
+def test_tensor_core_accumulation_within_the_screen_model():
+    rng = np.random.default_rng(2024)
+    A, Bt, C = adversarial_operands(rng, 512)
+    D = bkd.bkd_probe_mma(A, Bt, C)
+    exact, mag = exact_dots(A, Bt, C)
+    err = np.abs(D.astype(np.float64) - exact)
+    ratio = err / np.maximum(mag, 1e-300)
+    worst = float(ratio.max())
+    print(f"accumulation error / (|c| + sum |a b|): max {worst:.3e} "
+          f"= 2^{math.log2(worst) if worst > 0 else -math.inf:.2f}; "
+          f"model 2^-18")
+    assert np.isfinite(D).all()
+    assert worst <= MODEL, f"accumulation error {worst:.3e} exceeds 2^-18"
+
+
+def test_tensor_core_infinite_norm_slot_gives_minus_infinity():
+    """A padding point carries pn_hi = +inf against the query's -1/2: its
+    product must be -inf, never NaN, whatever the other slots hold."""
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((1, 16, 16)).astype(np.float32)
+    B = rng.standard_normal((1, 8, 16)).astype(np.float32)
+    A[0, :, 12] = np.inf
+    B[0, :, 12] = -0.5
+    C = rng.standard_normal((1, 16, 8)).astype(np.float32)
+    D = bkd.bkd_probe_mma(bf16_bits(A), bf16_bits(B), C)
+    assert (D == -np.inf).all()
+
+
+# ------------------------------------------------------------- wide data
+def _screen_vs_oracle(P, Q, k, h, rows=600):
+    i0, d0, i1, d1, st = run_both(P, Q, k, h)
+    assert st["screen_pairs"] > 0
+    assert np.array_equal(i0, i1) and np.array_equal(d0, d1)
+    sel = np.arange(min(rows, Q.shape[0]))
+    check(P, Q, k, i1, d1, oracle.brute_knn(P, Q[sel], k), rows=sel)
+    return st
+
+
+@pytest.mark.parametrize("d", [10, 17, 32])
+def test_screen_large_common_offset(d):
+    """Every coordinate offset by 1e3: centring removes the offset, but the
+    points carry float32 quantisation of ~6e-5 at that magnitude."""
+    params = workloads.mixture_params(d, 16, 0.02, 0.2, 0)
+    P = workloads.mixture(50000, params, 1) + np.float32(1000.0)
+    Q = workloads.mixture(3000, params, 2) + np.float32(1000.0)
+    _screen_vs_oracle(P, Q, 10, 7)
+
+
+@pytest.mark.parametrize("d", [10, 17, 32])
+def test_screen_far_queries(d):
+    """Queries far outside the tree's bounding box (shifted by 3 and by up
+    to 1e3 in some coordinates): |v^| is large against the leaf, where the
+    accumulation term E is largest relative to the threshold."""
+    rng = np.random.default_rng(d)
+    params = workloads.mixture_params(d, 16, 0.02, 0.2, 0)
+    P = workloads.mixture(50000, params, 1)
+    Q = workloads.mixture(3000, params, 2)
+    Q[:1000] += np.float32(3.0)
+    far = rng.choice(d, (1000, 2))
+    Q[np.arange(1000, 2000)[:, None], far] += rng.choice(
+        [-1e3, 1e3], (1000, 2)).astype(np.float32)
+    _screen_vs_oracle(P, Q, 10, 7, rows=Q.shape[0])
+
+
+@pytest.mark.parametrize("d", [4, 17, 32])
+def test_screen_tiny_spread_leaves(d):
+    """64 clusters of spread 1e-4: leaves whose points differ in the last
+    bits of their float32 coordinates."""
+    params = workloads.mixture_params(d, 64, 1e-4, 1e-4, 3)
+    P = workloads.mixture(40000, params, 1)
+    Q = workloads.mixture(3000, params, 2)
+    _screen_vs_oracle(P, Q, 8, 8)
