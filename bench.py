@@ -40,6 +40,10 @@ METRIC = ("kNN queries/s (k=10, d=10) FP32 vs BF16-screened; p50/p99 "
 LEAF_SRC = os.path.join(ROOT, "paper_1512_02831_gb300", "csrc", "k_leaf.cuh")
 TRAFFIC_NOTE = os.path.join(ROOT, "profiles",
                             "leaf_kernel_mixture64M_traffic.txt")
+SCREEN_SRC = os.path.join(ROOT, "paper_1512_02831_gb300", "csrc",
+                          "k_screen.cu")
+SCREEN_TRAFFIC_NOTE = os.path.join(ROOT, "profiles",
+                                   "screen_kernel_traffic.txt")
 
 WORKLOADS = {"mixture64M": workloads.MIXTURE_64M,
              "uniform64K": workloads.UNIFORM_64K,
@@ -148,6 +152,23 @@ def leaf_traffic_per_launch():
     if not m_sha or not m_b or m_sha.group(1) != sha:
         return None
     return float(m_b.group(1))
+
+
+def screen_traffic_per_launch(acc, launches):
+    """DRAM bytes (read + write) of an average screen launch, scaled from the
+    committed ncu capture of one launch if it was taken on the current screen
+    source: the capture's DRAM bytes per streamed operand byte times this
+    run's streamed bytes, over the run's screen launches."""
+    try:
+        text = open(SCREEN_TRAFFIC_NOTE).read()
+    except OSError:
+        return None
+    sha = hashlib.sha256(open(SCREEN_SRC, "rb").read()).hexdigest()[:16]
+    m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    m_r = re.search(r"dram_bytes_per_streamed_byte:\s*([0-9.e+-]+)", text)
+    if not m_sha or not m_r or m_sha.group(1) != sha:
+        return None
+    return float(m_r.group(1)) * acc["screen_bytes"] / max(launches, 1)
 
 
 def cpu_baseline(P, Q, w, seconds: float, seed: int = 7):
@@ -399,7 +420,8 @@ def run_ours(a, w, rank, world, local_rank):
                   "leaf_kernel_ms", "kernel_launches", "leaf_launches",
                   "tail_queries", "tail_visits", "tail_pairs", "tail_ms",
                   "screen_kept", "screen_pairs", "screen_ms", "screen_items",
-                  "screen_visits", "find_ms", "bucket_ms", "exact_ms")
+                  "screen_visits", "find_ms", "bucket_ms", "exact_ms",
+                  "screen_bytes")
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     vis = [v for v in vis.split(",") if v.strip()]
     smi_index = (vis[local_rank] if local_rank < len(vis)
@@ -491,39 +513,43 @@ def run_ours(a, w, rank, world, local_rank):
                       "peak_tflops_fma2": 2 * peak_ops},
     }
     a1 = runs[1]["acc"]
-    kh = (d + 2 + 15) // 16  # k-halves: d offsets + 2 norm slots
+    kh = (d + 5 + 15) // 16  # k-halves: d offsets, 2 norm and 3 threshold slots
+    dp = min(c for c in (2, 4, 6, 8, 10, 12, 16, 24, 32) if c >= d)
     scr_s = a1["screen_ms"] / 1000.0
     pairs_s = a1["screen_pairs"] / scr_s if scr_s else 0.0
     peak_bf16 = float(peaks.get("bf16_tflops") or 1900.0)
+    peak_hbm = float(peaks.get("hbm_gbs") or 6800.0)
+    # algorithmic bytes of the screen: the bf16 operand tiles of every work
+    # item's leaf (counted by the kernel) plus, per (query, leaf) visit, the
+    # query's padded row and its list bound and id
+    scr_bytes = a1["screen_bytes"] + a1["screen_visits"] * (4 * dp + 8)
+    # one screen launch per LazySearch round after the first
+    scr_launches = max(a1["rounds"] - a.steps, 0)
+    scr_gbs = scr_bytes / scr_s / 1e9 if scr_s else 0.0
     scr_tf = 2 * 16 * kh * pairs_s / 1e12
-    # the screen's per-pair work: a 16*KH-slot
-    # bf16 contraction on the tensor pipe and ~3 ALU operations of epilogue
-    # (form, combine, compare); the binding fraction is the roofline
-    epi_ops = 3
-    epi = epi_ops * pairs_s / 1e12
     tensor_view = {"achieved": scr_tf, "peak": peak_bf16, "unit": "TFLOP/s",
                    "frac": scr_tf / peak_bf16,
                    "basis": (f"2 x {16 * kh} flops per screened pair; peak = "
                              f"measured cuBLAS bf16 burst, 'of measured'")}
     roof_bf16 = {
-        "bound": "alu", "kernel": "screen_kernel (BF16 mma.sync screen)",
-        "achieved": epi, "peak": peak_ops, "unit": "Top/s",
-        "frac": epi / peak_ops, "traffic": None,
-        "basis": (f"ALU epilogue: {epi_ops} operations per screened (query, "
-                  f"point) pair against 128 lanes x {sm_count} SMs x "
-                  f"{sm_max:.0f} MHz (the FP32/ALU issue width of measured "
-                  f"peaks); the tensor view is far from its peak (one "
-                  f"mma.sync covers 128 pairs), so the epilogue binds; time = "
-                  f"CUDA events around every screen launch on its stream"),
+        "bound": "hbm",
+        "kernel": "screen_kernel (BF16 tcgen05 screen, fp32 rescore)",
+        "achieved": scr_gbs, "peak": peak_hbm, "unit": "GB/s",
+        "frac": scr_gbs / peak_hbm,
+        "traffic": screen_traffic_per_launch(a1, scr_launches),
+        "algorithmic_bytes_per_launch": scr_bytes / max(scr_launches, 1),
+        "basis": ("algorithmic bytes = bf16 operand tiles streamed (128 "
+                  "points x 32 kh B, one pass per work item of <= 128 "
+                  f"queries of a leaf) + {4 * dp + 8} B per (query, leaf) "
+                  "visit; time = CUDA events around every screen launch on "
+                  "its stream; peak = measured HBM copy bandwidth, 'of "
+                  "measured'"),
+        "bytes_per_step": scr_bytes / a.steps,
         "tensor_view": tensor_view,
         "screen_share_of_step": scr_s / (runs[1]["ms"] / 1000.0),
         "pairs_per_s": pairs_s,
         "kept_fraction": (a1["screen_kept"] / a1["screen_pairs"]
                           if a1["screen_pairs"] else None),
-        "exact_equivalent": {
-            "fp32_ops_per_pair_exact_path": 2 * d,
-            "top_s": 2 * d * pairs_s / 1e12,
-            "frac_of_fp32_peak": 2 * d * pairs_s / 1e12 / peak_ops},
     }
     roofline = roof_bf16 if head == 1 else roof_fp32
     names = {0: "fp32 exact path", 1: "bf16 tensor-core screen + fp32 rescore"}

@@ -87,7 +87,7 @@ enum bkd_option {
    * (one warp per query walks its remaining leaves) instead of one
    * LazySearch round per leaf.  -1 (default) = automatic (8192, growing to
    * 32768 for query sets of 2^24); 0 = never.
-   * Used for k <= 31 only.  Results do not depend on it.  Any time. */
+   * Results do not depend on it.  Any time. */
   BKD_OPT_TAIL_QUERIES = 5,
   /* Leaf scoring: 0 (default) = float32 for every (query, point) pair;
    * 1 = a BF16 tensor-core screen rejects points that provably cannot enter
@@ -117,12 +117,20 @@ enum bkd_stat {
   BKD_STAT_SCREEN_KEPT = 15,   /* pairs the BF16 screen passed to float32    */
   BKD_STAT_SCREEN_PAIRS = 16,  /* pairs the BF16 screen kernel examined      */
   BKD_STAT_SCREEN_MS = 17,     /* device time of the BF16 screen kernel      */
-  BKD_STAT_SCREEN_ITEMS = 18,  /* work items (one leaf, <= 32 queries) of it */
+  BKD_STAT_SCREEN_ITEMS = 18,  /* work items (one leaf, <= 128 queries)     */
   BKD_STAT_SCREEN_VISITS = 19, /* (query, leaf) pairs of the screened rounds */
   BKD_STAT_FIND_MS = 20,       /* device time of FindLeafBatch (all rounds)  */
   BKD_STAT_BUCKET_MS = 21,     /* device time of the bucketing (all rounds)  */
-  BKD_STAT_EXACT_MS = 22       /* device time of the binary64 re-check and
+  BKD_STAT_EXACT_MS = 22,      /* device time of the binary64 re-check and
                                   fallback search                           */
+  BKD_STAT_CHUNK_VISITS = 23,  /* chunked mode: (query, leaf) pairs scanned
+                                  (queries waiting in a chunk not brought in
+                                  that round are not counted)               */
+  BKD_STAT_SCREEN_BYTES = 24,  /* bytes of bf16 operand tiles the screen
+                                  streamed from HBM into shared memory      */
+  BKD_STAT_SCREEN_QUEUED = 25, /* pairs the screen queued for rescoring     */
+  BKD_STAT_SCREEN_OVERFLOW = 26 /* screen items rescored against the whole
+                                  leaf (their rescoring queue overflowed)  */
 };
 
 typedef struct bkd_tree bkd_tree; /* opaque; owned by the library */
@@ -187,6 +195,25 @@ int bkd_query(bkd_tree* t, const float* Q, int64_t m, int k, int64_t* out_idx,
 int bkd_query_static(bkd_tree* t, const float* Q, int64_t m, int k,
                      int64_t* out_idx, float* out_dist);
 
+/* bkd_outlier_scores -- the proximity-based outlier score of Sec. 4.3 ("rank
+ * the points according to their average distance to their k nearest
+ * neighbors"; the all-nearest-neighbours problem, queries = the reference
+ * points): for every reference point i (original row order),
+ *   out_score[i] = (1/k) sum of the Euclidean (not squared) distances from
+ *                  x_i to its k nearest neighbours among the OTHER points,
+ * neighbours taken under the same (distance, index) order as bkd_query: x_i
+ * is searched with k + 1 neighbours and its own index is dropped from the
+ * row (if exact duplicates with smaller indices fill the row, x_i is not in
+ * it and the last entry is dropped).  Distances are float32 square roots of
+ * bkd_query's squared distances, summed in binary64.
+ *   t          handle from bkd_build (resident or chunked).
+ *   k          1 <= k <= n - 1 and k + 1 <= BKD_MAX_K.
+ *   out_score  n float32, host or device memory (caller-owned).
+ * Queries run in slices of BKD_OPT_MAX_ACTIVE points (default 2^24).
+ * Errors: BKD_EINVAL, BKD_ENOMEM, BKD_ECUDA, BKD_ETIMEOUT,
+ * BKD_EUNSUPPORTED. */
+int bkd_outlier_scores(bkd_tree* t, int k, float* out_score);
+
 /* ------------------------------------------------------------ test support
  * Neither call has a counterpart in the paper; they let tests reach failure
  * paths and hardware properties that the query calls depend on. */
@@ -198,16 +225,17 @@ int bkd_query_static(bkd_tree* t, const float* Q, int64_t m, int k,
  * had built).  Errors: BKD_EINVAL (nth < 0). */
 int bkd_test_fail_alloc(int64_t nth);
 
-/* bkd_probe_mma -- runs the BF16 screen's tensor-core instruction (kind 0:
- * mma.sync m16n8k16, bf16 inputs, fp32 accumulation) on `count` instances:
- * D = C + A Bt^T, with A count x 16 x 16 and Bt count x 8 x 16 bf16 bit
- * patterns (row-major; row c of Bt is column c of the B operand), C and D
- * count x 16 x 8 float32, all HOST memory.  The screen's error bound
- * (Sec. 2.2 exactness of the answer) assumes how far this accumulation may
- * stray from the exact sum; tests compare D with exact sums.
- * Errors: BKD_EINVAL, BKD_ENOMEM, BKD_ECUDA. */
-int bkd_probe_mma(int kind, int count, const uint16_t* A, const uint16_t* Bt,
-                  const float* C, float* D);
+/* bkd_probe_umma -- the BF16 screen's Blackwell tensor-core path (operands
+ * staged in shared memory in the screen's layout, kh chained tcgen05.mma of
+ * kind::f16 with K = 16, M = 128, N = n, fp32 accumulator in tensor memory,
+ * read back with tcgen05.ld) on `count` instances: D = A Bt^T with A
+ * count x 128 x 16 kh and Bt count x n x 16 kh bf16 bit patterns
+ * (row-major), D count x 128 x n float32, all HOST memory; 16 <= n <= 256,
+ * n a multiple of 16, 1 <= kh <= 3.  Tests compare D with exact sums to pin
+ * the accumulation model of the screen's error bound.
+ * Errors: BKD_EINVAL, BKD_ENOMEM, BKD_ECUDA, BKD_ETIMEOUT. */
+int bkd_probe_umma(int n, int kh, int count, const uint16_t* A,
+                   const uint16_t* Bt, float* D);
 
 /* bkd_set_option -- sets a run-time option (enum bkd_option) on a handle.
  * Build-only keys are rejected with BKD_EINVAL. */

@@ -16,6 +16,10 @@ Two implementations, both in ``bkd_oracle.c`` (plain C, OpenMP over queries):
 Distances are squared Euclidean distances formed in binary64 from the float32
 inputs, terms added in dimension order.  Ties go to the smaller reference
 index.  Each query also reports the (k+1)-th distance (``next``).
+
+* :func:`outlier_scores` -- the proximity-based outlier score of Sec. 4.3 (a
+  point's average Euclidean distance to its k nearest other points), from
+  the brute-force definition above.
 """
 from __future__ import annotations
 
@@ -204,3 +208,21 @@ def pair_dist(P, Q, qi, pi) -> np.ndarray:
     if rc != 0:
         raise ValueError("pair index out of range")
     return out
+
+
+def outlier_scores(P, k: int, threads: int = 0) -> np.ndarray:
+    """Outlier score of Sec. 4.3 ("rank the points according to their
+    average distance to their k nearest neighbors", queries = the reference
+    set): for every point i, the mean of the binary64 Euclidean distances to
+    its k nearest neighbours among the other points.  The neighbours are the
+    first k+1 of the (distance, index) order of :func:`brute_knn` with the
+    point's own index removed -- or, when k+1 exact duplicates of smaller
+    index fill the row so that i is not in it, the last one removed."""
+    P = _f32(P)
+    n = P.shape[0]
+    res = brute_knn(P, P, k + 1, threads)
+    own = res.idx == np.arange(n)[:, None]
+    drop = np.where(own.any(axis=1), own.argmax(axis=1), k)
+    keep = np.ones(res.idx.shape, bool)
+    keep[np.arange(n), drop] = False
+    return np.sqrt(res.dist[keep].reshape(n, k)).mean(axis=1)

@@ -43,7 +43,8 @@ STATS = {"rounds": 1, "leaf_visits": 2, "pairs": 3, "resorted": 4,
          "tail_visits": 12, "tail_pairs": 13, "tail_ms": 14,
          "screen_kept": 15, "screen_pairs": 16, "screen_ms": 17,
          "screen_items": 18, "screen_visits": 19, "find_ms": 20,
-         "bucket_ms": 21, "exact_ms": 22}
+         "bucket_ms": 21, "exact_ms": 22, "chunk_visits": 23,
+         "screen_bytes": 24, "screen_queued": 25, "screen_overflow": 26}
 
 _lock = threading.Lock()
 _lib = None
@@ -85,15 +86,17 @@ def load():
         lib.bkd_serve_status.argtypes = [vp, i64, ctypes.POINTER(i32)]
         lib.bkd_serve_close.argtypes = [vp]
         lib.bkd_serve_close.restype = None
+        lib.bkd_outlier_scores.argtypes = [vp, i32, vp]
         lib.bkd_test_fail_alloc.argtypes = [i64]
-        lib.bkd_probe_mma.argtypes = [i32, i32, vp, vp, vp, vp]
+        lib.bkd_probe_umma.argtypes = [i32, i32, i32, vp, vp, vp]
         lib.bkd_last_error.restype = ctypes.c_char_p
         for f in ("bkd_build", "bkd_build_with", "bkd_query",
                   "bkd_query_static", "bkd_set_option",
                   "bkd_get_stat", "bkd_tree_shape", "bkd_export_tree",
                   "bkd_serve_open", "bkd_serve_submit", "bkd_serve_step",
                   "bkd_serve_status", "bkd_test_fail_alloc",
-                  "bkd_probe_mma"):
+                  "bkd_outlier_scores",
+                  "bkd_probe_umma"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -227,6 +230,30 @@ def bkd_query_static(tree: Tree, Q, k: int, out_idx, out_dist):
     return out_idx, out_dist
 
 
+def bkd_outlier_scores(tree: Tree, k: int, out=None, device=None):
+    """``bkd_outlier_scores``: (n,) float32 mean distance of every reference
+    point to its k nearest other points.  ``out`` (n,) float32 numpy array or
+    torch tensor; by default a numpy array, or a CUDA tensor on ``device``."""
+    lib = load()
+    n = bkd_tree_shape(tree)["n"]
+    if out is None:
+        if device is not None:
+            import torch
+            out = torch.empty(n, dtype=torch.float32, device=device)
+        else:
+            out = np.empty(n, np.float32)
+    o, shape = _ptr(out, "f32")
+    if tuple(shape) != (n,):
+        raise ValueError("out must be (n,)")
+    if _is_torch(out) and out.is_cuda:
+        import torch
+        _check(lib.bkd_set_option(tree.handle, OPTIONS["stream"],
+                                  torch.cuda.current_stream(out.device)
+                                  .cuda_stream))
+    _check(lib.bkd_outlier_scores(tree.handle, k, o))
+    return out
+
+
 def bkd_set_option(tree: Tree, name: str, value: int):
     _check(load().bkd_set_option(tree.handle, OPTIONS[name], int(value)))
 
@@ -268,20 +295,19 @@ def bkd_test_fail_alloc(nth: int):
     _check(load().bkd_test_fail_alloc(int(nth)))
 
 
-def bkd_probe_mma(A, Bt, C, kind: int = 0):
-    """``bkd_probe_mma``: D = C + A Bt^T per instance on the screen's tensor
-    core instruction.  A (count, 16, 16) and Bt (count, 8, 16) uint16 bf16
-    bit patterns, C (count, 16, 8) float32; returns D like C."""
+def bkd_probe_umma(A, Bt):
+    """``bkd_probe_umma``: D = A Bt^T per instance on the screen's
+    tcgen05 path.  A (count, 128, 16 kh) and Bt (count, n, 16 kh) uint16
+    bf16 bit patterns; returns D (count, 128, n) float32."""
     A = np.ascontiguousarray(A, np.uint16)
     Bt = np.ascontiguousarray(Bt, np.uint16)
-    C = np.ascontiguousarray(C, np.float32)
-    count = A.shape[0]
-    if A.shape != (count, 16, 16) or Bt.shape != (count, 8, 16) \
-            or C.shape != (count, 16, 8):
-        raise ValueError("shapes (count,16,16), (count,8,16), (count,16,8)")
-    D = np.empty_like(C)
-    _check(load().bkd_probe_mma(kind, count, A.ctypes.data, Bt.ctypes.data,
-                                C.ctypes.data, D.ctypes.data))
+    count, rows, kdim = A.shape
+    n = Bt.shape[1]
+    if rows != 128 or kdim % 16 or Bt.shape != (count, n, kdim):
+        raise ValueError("shapes (count,128,16kh), (count,n,16kh)")
+    D = np.empty((count, 128, n), np.float32)
+    _check(load().bkd_probe_umma(n, kdim // 16, count, A.ctypes.data,
+                                 Bt.ctypes.data, D.ctypes.data))
     return D
 
 

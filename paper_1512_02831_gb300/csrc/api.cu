@@ -125,7 +125,7 @@ struct bkd_tree {
   int32_t* d_leaf_cnt = nullptr;
   float* d_box = nullptr;
   // BF16 screen data (built on request, resident trees only)
-  uint32_t* d_scr_words = nullptr;
+  uint16_t* d_scr_words = nullptr;
   float *d_scr_center = nullptr, *d_scr_bmax = nullptr,
         *d_scr_pnmax = nullptr;
   ScreenData screen;
@@ -145,13 +145,15 @@ struct bkd_tree {
   DevBuf<uint32_t> lst_i, act_a, act_b, fb_list;
   DevBuf<uint64_t> state;  // per query: TravState
   DevBuf<int2> placed;  // per active position: (next leaf, rank in its buffer)
-  DevBuf<int32_t> cnt, off, cursor, toff, chunk_item;
+  DevBuf<int32_t> cnt, off, cursor, toff, chunk_item, nact;
   DevBuf<Item> items;
-  DevBuf<int64_t> out_idx;
-  DevBuf<float> out_dist;
+  DevBuf<int64_t> out_idx, inv;
+  DevBuf<float> out_dist, score;
   Counters* d_ctr = nullptr;
   Counters* h_ctr = nullptr;     // pinned
   int32_t* h_chunk_item = nullptr;
+  uint8_t* d_chunk_done = nullptr;  // per chunk: scanned in the last round
+  uint8_t* h_chunk_done = nullptr;  // pinned staging of it
   int max_active = 0;
   int tail_queries = -1;
   // timing
@@ -166,7 +168,8 @@ struct bkd_tree {
          st_tail_visits = 0, st_tail_pairs = 0, st_tail_ms = 0,
          st_screen_kept = 0, st_screen_pairs = 0, st_screen_ms = 0,
          st_screen_items = 0, st_screen_visits = 0, st_find_ms = 0,
-         st_bucket_ms = 0, st_exact_ms = 0;
+         st_bucket_ms = 0, st_exact_ms = 0, st_chunk_visits = 0,
+         st_screen_bytes = 0, st_screen_queued = 0, st_screen_overflow = 0;
 
   cudaEvent_t next_event() {
     if (ev_used == ev_pool.size()) {
@@ -213,12 +216,17 @@ void release(bkd_tree* t) {
   t->cursor.release();
   t->toff.release();
   t->chunk_item.release();
+  t->nact.release();
   t->items.release();
   t->out_idx.release();
   t->out_dist.release();
+  t->inv.release();
+  t->score.release();
   cudaFree(t->d_ctr);
   if (t->h_ctr) cudaFreeHost(t->h_ctr);
   if (t->h_chunk_item) cudaFreeHost(t->h_chunk_item);
+  cudaFree(t->d_chunk_done);
+  if (t->h_chunk_done) cudaFreeHost(t->h_chunk_done);
   for (auto e : t->ev_pool) cudaEventDestroy(e);
   for (int b = 0; b < 2; ++b) {
     if (t->ev_copied[b]) cudaEventDestroy(t->ev_copied[b]);
@@ -449,25 +457,25 @@ int build_impl(const float* P, int64_t n, int d, int height,
                        "the BF16 screen needs a tree resident in device "
                        "memory"));
     const int kh = screen_halves(d);
-    const int64_t stride = screen_stride(H.lcap);
-    std::vector<uint32_t> words;
+    const int64_t tiles = screen_tiles(H.lcap);
+    std::vector<uint16_t> words;
     std::vector<float> center, bmax, pnmax;
     try {
-      words.resize((size_t)L * kh * stride * 8);
+      words.resize((size_t)L * tiles * kScreenRows * 16 * kh);
       center.resize((size_t)L * d);
       bmax.resize(L);
       pnmax.resize(L);
     } catch (...) {
       return bail(fail(BKD_ENOMEM, "host staging of the screen data"));
     }
-    fill_screen(Ph, H, stride, words.data(), center.data(), bmax.data(),
+    fill_screen(Ph, H, tiles, words.data(), center.data(), bmax.data(),
                 pnmax.data());
-    if (dev_malloc(&t->d_scr_words, words.size() * 4) != cudaSuccess ||
+    if (dev_malloc(&t->d_scr_words, words.size() * 2) != cudaSuccess ||
         dev_malloc(&t->d_scr_center, center.size() * 4) != cudaSuccess ||
         dev_malloc(&t->d_scr_bmax, bmax.size() * 4) != cudaSuccess ||
         dev_malloc(&t->d_scr_pnmax, pnmax.size() * 4) != cudaSuccess)
       return bail(fail(BKD_ENOMEM, "device allocation failed (screen data)"));
-    if (cudaMemcpy(t->d_scr_words, words.data(), words.size() * 4,
+    if (cudaMemcpy(t->d_scr_words, words.data(), words.size() * 2,
                    cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(t->d_scr_center, center.data(), center.size() * 4,
                    cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -477,7 +485,7 @@ int build_impl(const float* P, int64_t n, int d, int height,
                    cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(fail(BKD_ECUDA, "upload of the screen data failed"));
     t->screen.words = t->d_scr_words;
-    t->screen.stride = stride;
+    t->screen.tiles = tiles;
     t->screen.center = t->d_scr_center;
     t->screen.bmax = t->d_scr_bmax;
     t->screen.pnmax = t->d_scr_pnmax;
@@ -487,8 +495,12 @@ int build_impl(const float* P, int64_t n, int d, int height,
   if (dev_malloc(&t->d_ctr, sizeof(Counters)) != cudaSuccess ||
       host_alloc(&t->h_ctr, sizeof(Counters), cudaHostAllocDefault) !=
           cudaSuccess ||
-      host_alloc(&t->h_chunk_item, (t->n_chunks + 2) * sizeof(int32_t),
-                    cudaHostAllocDefault) != cudaSuccess)
+      host_alloc(&t->h_chunk_item, 2 * (t->n_chunks + 1) * sizeof(int32_t),
+                    cudaHostAllocDefault) != cudaSuccess ||
+      (chunked &&
+       (dev_malloc(&t->d_chunk_done, t->n_chunks) != cudaSuccess ||
+        host_alloc(&t->h_chunk_done, t->n_chunks, cudaHostAllocDefault) !=
+            cudaSuccess)))
     return bail(fail(BKD_ENOMEM, "counter allocation failed"));
 
   DevTree& D = t->dev;
@@ -502,6 +514,8 @@ int build_impl(const float* P, int64_t n, int d, int height,
   D.Dp = H.Dp;
   D.h = height;
   D.lcap = H.lcap;
+  D.n_chunks = t->n_chunks;
+  D.chunk_done = chunked ? t->d_chunk_done : nullptr;
   for (int i = 0; i < n_options; ++i) {
     const int64_t key = options[2 * i], val = options[2 * i + 1];
     if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE ||
@@ -517,6 +531,46 @@ int build_impl(const float* P, int64_t n, int d, int height,
   return BKD_OK;
 }
 
+void reset_stats(bkd_tree* t) {
+  t->st_rounds = t->st_visits = t->st_pairs = t->st_resorted =
+      t->st_fallback = t->st_leaf_ms = t->st_chunk_bytes = t->st_copy_ms =
+          t->st_leaf_launches = t->st_launches = t->st_tail_queries =
+              t->st_tail_visits = t->st_tail_pairs = t->st_tail_ms =
+                  t->st_screen_kept = t->st_screen_pairs = t->st_screen_ms = 0;
+  t->st_screen_items = t->st_screen_visits = 0;
+  t->st_find_ms = t->st_bucket_ms = t->st_exact_ms = 0;
+  t->st_chunk_visits = t->st_screen_bytes = 0;
+  t->st_screen_queued = t->st_screen_overflow = 0;
+  t->ev_used = 0;
+  t->find_ev.clear();
+  t->bucket_ev.clear();
+  t->exact_ev.clear();
+  t->leaf_ev.clear();
+  t->copy_ev.clear();
+  t->tail_ev.clear();
+  t->screen_ev.clear();
+}
+
+// Sums the CUDA-event timings of the last call into the stats.
+void collect_timings(bkd_tree* t) {
+  const std::pair<std::vector<std::pair<cudaEvent_t, cudaEvent_t>>*,
+                  double*>
+      phases[] = {{&t->leaf_ev, &t->st_leaf_ms},
+                  {&t->copy_ev, &t->st_copy_ms},
+                  {&t->tail_ev, &t->st_tail_ms},
+                  {&t->screen_ev, &t->st_screen_ms},
+                  {&t->find_ev, &t->st_find_ms},
+                  {&t->bucket_ev, &t->st_bucket_ms},
+                  {&t->exact_ev, &t->st_exact_ms}};
+  for (const auto& ph : phases)
+    for (auto& pr : *ph.first) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess)
+        *ph.second += ms;
+    }
+  cudaGetLastError();
+}
+
 // One LazySearch over queries already in t->qdev[0..m) (row-major m x d).
 // Results go to device buffers out_idx / out_dist.
 int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
@@ -526,7 +580,8 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   const int Dp = D.Dp;
   cudaStream_t s = t->stream;
   const int64_t L = t->n_leaves;
-  const int64_t max_items = m / kScreenTile + L + 1;  // kScreenTile <= kPipeTile
+  const int64_t max_items =
+      m / std::min(kScreenTile, kPipeTile) + L + 1;  // items of any round
   CU(t->qpad.ensure(m * Dp));
   CU(t->lst_d.ensure(m * K));
   CU(t->lst_i.ensure(m * K));
@@ -540,7 +595,8 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   CU(t->off.ensure(L + 1));
   CU(t->toff.ensure(L + 1));
   CU(t->items.ensure(max_items));
-  if (t->chunked) CU(t->chunk_item.ensure(t->n_chunks + 1));
+  CU(t->nact.ensure(2));
+  if (t->chunked) CU(t->chunk_item.ensure(2 * (t->n_chunks + 1)));
 
   CU(cudaMemsetAsync(t->d_ctr, 0, sizeof(Counters), s));
   CU(launch_init(t->qdev.p, m, D.d, Dp, t->qpad.p, t->lst_d.p, t->lst_i.p, K,
@@ -558,30 +614,40 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   int n_act = (int)m;
   const int grid_max = leaf_kernel_grid(Dp, cap, t->sm_count);
   const int screen_max =
-      t->precision == 1 ? screen_grid(t->screen.kh, D.lcap, K, t->sm_count)
+      t->precision == 1
+          ? screen_grid(t->screen.kh, Dp, D.lcap, K, t->sm_count)
                         : 0;
-  // the tail kernel spreads a list over the 32 lanes of a warp; automatic
-  // threshold: 8,192 active queries, up to 32,768 for the largest query
+  // the tail kernel spreads a list over the 32 lanes of a warp (two
+  // entries per lane above 32); automatic threshold: 8,192 active queries, up to 32,768 for the largest query
   // sets (measured on 2^24 queries)
   const int64_t tail_auto =
       std::max<int64_t>(8192, std::min<int64_t>(32768, m / 512));
-  const int tail = K > 32 ? 0
-                          : (int)(t->tail_queries >= 0 ? t->tail_queries
-                                                       : tail_auto);
+  const int tail =
+      (int)(t->tail_queries >= 0 ? t->tail_queries : tail_auto);
   // A round: FindLeafBatch over the active queries (it also counts every
-  // query into its next leaf), bucketing by leaf, ProcessAllBuffers.
+  // query into its next leaf), bucketing by leaf, ProcessAllBuffers.  The
+  // host looks at the counters after a round's bucketing (all done: stop;
+  // few left: tail kernel).  On a resident tree it then queues a batch of
+  // further rounds without waiting: their kernels read the active and item
+  // counts on the device, and a round whose queries have all finished does
+  // nothing.  A chunked tree needs the host every round (the chunk
+  // schedule).
   int round = 0;
-  for (;;) {
+  CU(launch_fill(t->nact.p, 1, (int32_t)m, s));
+  t->st_launches += 1;
+  auto start_round = [&](bool dev_counts) -> int {
     // a round that ends in the BF16 screen (the first round stays on the
     // float32 kernel: every list is still empty there) buckets its queries
-    // into the screen's smaller items
+    // into the screen's items
     const bool screened =
         !t->chunked && t->precision == 1 && round > 0 && screen_max > 0;
+    const int32_t* nin = dev_counts ? t->nact.p + (round & 1) : nullptr;
+    int32_t* nout = t->nact.p + ((round + 1) & 1);
     cudaEvent_t f0 = t->next_event(), f1 = t->next_event();
     if (f0) cudaEventRecord(f0, s);
     CU(cudaMemsetAsync(t->cnt.p, 0, sizeof(int32_t) * L, s));
     CU(launch_find_leaf(D, t->qpad.p, act, n_act, t->state.p, t->lst_d.p, K,
-                        t->placed.p, t->cnt.p, s));
+                        t->placed.p, t->cnt.p, s, nin));
     if (f1) cudaEventRecord(f1, s);
     if (f0 && f1) t->find_ev.push_back({f0, f1});
     t->st_launches += 1;
@@ -590,25 +656,144 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
     CU(launch_bucket(t->placed.p, act, n_act, (int)L,
                      screened ? kScreenTile : kPipeTile,
                      t->d_leaf_cnt, t->cnt.p, t->off.p, t->cursor.p,
-                     t->toff.p, t->items.p, nxt, t->d_ctr, s));
+                     t->toff.p, t->items.p, nxt, t->d_ctr, s, nin, nout));
     if (b1) cudaEventRecord(b1, s);
     if (b0 && b1) t->bucket_ev.push_back({b0, b1});
     t->st_launches += 3;
     if (t->chunked) {
-      CU(launch_chunk_items(t->toff.p, t->d_chunk_leaf, t->n_chunks,
-                            t->chunk_item.p, s));
+      CU(launch_chunk_items(t->toff.p, t->off.p, t->d_chunk_leaf,
+                            t->n_chunks, t->chunk_item.p, s));
       CU(cudaMemcpyAsync(t->h_chunk_item, t->chunk_item.p,
-                         (t->n_chunks + 1) * sizeof(int32_t),
+                         2 * (t->n_chunks + 1) * sizeof(int32_t),
                          cudaMemcpyDeviceToHost, s));
       t->st_launches += 1;
     }
+    return BKD_OK;
+  };
+  // ProcessAllBuffers of the round just bucketed (n_items < 0: the count is
+  // read on the device), then the bucketed list becomes the active list
+  auto process_round = [&](int n_items) -> int {
+    const bool screened =
+        !t->chunked && t->precision == 1 && round > 0 && screen_max > 0;
+    if (screened) {
+      // BF16 tensor-core screen + exact float32 rescoring
+      cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
+      if (e0) cudaEventRecord(e0, s);
+      CU(launch_screen(D, t->screen, t->items.p, 0, n_items, t->d_ctr, nxt,
+                       t->qpad.p, t->lst_d.p, t->lst_i.p, K, screen_max, s));
+      if (e1) cudaEventRecord(e1, s);
+      if (e0 && e1) t->screen_ev.push_back({e0, e1});
+      t->st_launches += 1;
+    } else if (!t->chunked) {
+      const int grid = n_items >= 0 ? std::min(grid_max, n_items) : grid_max;
+      cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
+      if (e0) cudaEventRecord(e0, s);
+      CU(launch_leaf(D, cap, t->items.p, 0, n_items, t->d_ctr, t->d_pts, 0,
+                     nxt, t->qpad.p, t->lst_d.p, t->lst_i.p, K, grid, s));
+      if (e1) cudaEventRecord(e1, s);
+      if (e0 && e1) t->leaf_ev.push_back({e0, e1});
+      t->st_leaf_launches += 1;
+      t->st_launches += 1;
+    } else {
+      // Brute / Copy / Wait (Sec. 3.2) on the chunks the schedule picks.
+      // The paper streams every chunk in every ProcessAllBuffers call and
+      // relies on its half-full trigger to make calls rare; here a round
+      // keeps running the two chunks resident in the device buffers while
+      // their buffers hold queries (traversals move mostly between nearby
+      // leaves, which share a chunk), and brings in the chunk with the most
+      // buffered queries when a buffer is empty or that chunk holds more
+      // than twice the resident work.  Queries buffered in other chunks
+      // wait there (FindLeafBatch re-places them) until their chunk comes
+      // in.  Results do not depend on the schedule.
+      const int N = t->n_chunks;
+      const int32_t* ci = t->h_chunk_item;          // first item per chunk
+      const int32_t* cq = t->h_chunk_item + N + 1;  // first query per chunk
+      auto work = [&](int c) { return c < 0 ? 0 : cq[c + 1] - cq[c]; };
+      int best = -1;
+      for (int c = 0; c < N; ++c)
+        if (c != t->buf_chunk[0] && c != t->buf_chunk[1] && work(c) > 0 &&
+            (best < 0 || work(c) > work(best)))
+          best = c;
+      const int wres = work(t->buf_chunk[0]) + work(t->buf_chunk[1]);
+      int load_b = -1;
+      if (best >= 0) {
+        if (t->buf_chunk[0] < 0)
+          load_b = 0;
+        else if (t->buf_chunk[1] < 0)
+          load_b = 1;
+        else if (wres == 0 || work(best) > 2 * wres)
+          load_b = work(t->buf_chunk[0]) <= work(t->buf_chunk[1]) ? 0 : 1;
+      }
+      if (load_b >= 0) {
+        const int c = best;
+        const int64_t leaf_a = t->chunk_leaf[c], leaf_b = t->chunk_leaf[c + 1];
+        const size_t off_f = (size_t)leaf_a * D.lcap * Dp;
+        const size_t bytes =
+            (size_t)(leaf_b - leaf_a) * D.lcap * Dp * sizeof(float);
+        CU(cudaStreamWaitEvent(t->copy_stream, t->ev_free[load_b], 0));
+        cudaEvent_t c0 = t->next_event(), c1 = t->next_event();
+        if (c0) cudaEventRecord(c0, t->copy_stream);
+        CU(cudaMemcpyAsync(t->d_chunk_buf[load_b], t->h_pts + off_f, bytes,
+                           cudaMemcpyHostToDevice, t->copy_stream));
+        if (c1) cudaEventRecord(c1, t->copy_stream);
+        if (c0 && c1) t->copy_ev.push_back({c0, c1});
+        CU(cudaEventRecord(t->ev_copied[load_b], t->copy_stream));
+        t->buf_chunk[load_b] = c;
+        t->st_chunk_bytes += (double)bytes;
+      }
+      std::fill(t->h_chunk_done, t->h_chunk_done + N, (uint8_t)0);
+      // the retained chunk first: its Brute hides the Copy of the other
+      const int order[2] = {load_b == 0 ? 1 : 0, load_b == 0 ? 0 : 1};
+      for (int b : order) {
+        const int c = t->buf_chunk[b];
+        if (c < 0 || work(c) == 0) continue;
+        const int ilo = ci[c], ihi = ci[c + 1];
+        CU(cudaStreamWaitEvent(s, t->ev_copied[b], 0));
+        const int grid = std::min(grid_max, ihi - ilo);
+        cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
+        if (e0) cudaEventRecord(e0, s);
+        CU(launch_leaf(D, cap, t->items.p, ilo, ihi, t->d_ctr,
+                       t->d_chunk_buf[b], t->chunk_leaf[c], nxt, t->qpad.p,
+                       t->lst_d.p, t->lst_i.p, K, grid, s));
+        if (e1) cudaEventRecord(e1, s);
+        if (e0 && e1) t->leaf_ev.push_back({e0, e1});
+        CU(cudaEventRecord(t->ev_free[b], s));
+        t->h_chunk_done[c] = 1;
+        t->st_chunk_visits += work(c);
+        t->st_leaf_launches += 1;
+        t->st_launches += 1;
+      }
+      // which chunks this round scanned, for the next FindLeafBatch
+      CU(cudaMemcpyAsync(t->d_chunk_done, t->h_chunk_done, N,
+                         cudaMemcpyHostToDevice, s));
+    }
+    t->st_rounds += 1;
+    std::swap(act, nxt);
+    ++round;
+    return BKD_OK;
+  };
+  int rc = start_round(false);
+  if (rc != BKD_OK) return rc;
+  // bucketing totals of the first round (float32 kernel) and of the last
+  // (not processed: everything done, or handed to the tail kernel)
+  unsigned long long first_pairs = 0, first_items = 0, first_visits = 0;
+  unsigned long long last_pairs = 0, last_items = 0, last_visits = 0;
+  for (bool first = true;; first = false) {
     CU(cudaMemcpyAsync(t->h_ctr, t->d_ctr, sizeof(Counters),
                        cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     if (t->h_ctr->err & kErrTimeout)
-      return fail(BKD_ETIMEOUT, "a leaf-segment copy did not complete");
+      return fail(BKD_ETIMEOUT, "a bounded device-side wait ran out");
     const int n_next = t->h_ctr->n_next;
     const int n_items = t->h_ctr->n_items;
+    last_pairs = t->h_ctr->pairs;
+    last_items = (unsigned long long)n_items;
+    last_visits = (unsigned long long)n_next;
+    if (first) {
+      first_pairs = last_pairs;
+      first_items = last_items;
+      first_visits = last_visits;
+    }
     if (n_next == 0) break;
     if (n_next <= tail) {
       // finish the remaining queries in one launch, one warp per query,
@@ -624,82 +809,22 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
       t->st_launches += 1;
       break;
     }
-    t->st_rounds += 1;
-    t->st_visits += n_next;
-    if (screened) {
-      // BF16 tensor-core screen + exact float32 rescoring
-      cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
-      if (e0) cudaEventRecord(e0, s);
-      CU(launch_screen(D, t->screen, t->items.p, 0, n_items, t->d_ctr, nxt,
-                       t->qpad.p, t->lst_d.p, t->lst_i.p, K, screen_max, s));
-      if (e1) cudaEventRecord(e1, s);
-      if (e0 && e1) t->screen_ev.push_back({e0, e1});
-      t->st_screen_pairs += (double)t->h_ctr->pairs;  // whole round
-      t->st_screen_items += n_items;
-      t->st_screen_visits += n_next;
-      t->st_launches += 1;
-    } else if (!t->chunked) {
-      t->st_pairs += (double)t->h_ctr->pairs;
-      const int grid = std::min(grid_max, n_items);
-      cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
-      if (e0) cudaEventRecord(e0, s);
-      CU(launch_leaf(D, cap, t->items.p, 0, n_items, t->d_ctr, t->d_pts, 0,
-                     nxt, t->qpad.p, t->lst_d.p, t->lst_i.p, K, grid, s));
-      if (e1) cudaEventRecord(e1, s);
-      if (e0 && e1) t->leaf_ev.push_back({e0, e1});
-      t->st_leaf_launches += 1;
-      t->st_launches += 1;
-    } else {
-      // Brute / Copy / Wait over the chunks holding buffered queries
-      t->st_pairs += (double)t->h_ctr->pairs;
-      const int N = t->n_chunks;
-      const bool forward = (round % 2) == 0;
-      int prev_b = -1;
-      for (int i = 0; i < N; ++i) {
-        const int c = forward ? i : N - 1 - i;
-        const int ilo = t->h_chunk_item[c], ihi = t->h_chunk_item[c + 1];
-        if (ihi <= ilo) continue;
-        int b;
-        if (t->buf_chunk[0] == c)
-          b = 0;
-        else if (t->buf_chunk[1] == c)
-          b = 1;
-        else
-          b = prev_b < 0 ? (t->buf_chunk[0] == -1 ? 0 : 1) : 1 - prev_b;
-        const int64_t leaf_a = t->chunk_leaf[c], leaf_b = t->chunk_leaf[c + 1];
-        if (t->buf_chunk[b] != c) {
-          const size_t off_f = (size_t)leaf_a * D.lcap * Dp;
-          const size_t bytes =
-              (size_t)(leaf_b - leaf_a) * D.lcap * Dp * sizeof(float);
-          CU(cudaStreamWaitEvent(t->copy_stream, t->ev_free[b], 0));
-          cudaEvent_t c0 = t->next_event(), c1 = t->next_event();
-          if (c0) cudaEventRecord(c0, t->copy_stream);
-          CU(cudaMemcpyAsync(t->d_chunk_buf[b], t->h_pts + off_f, bytes,
-                             cudaMemcpyHostToDevice, t->copy_stream));
-          if (c1) cudaEventRecord(c1, t->copy_stream);
-          if (c0 && c1) t->copy_ev.push_back({c0, c1});
-          CU(cudaEventRecord(t->ev_copied[b], t->copy_stream));
-          t->buf_chunk[b] = c;
-          t->st_chunk_bytes += (double)bytes;
-        }
-        CU(cudaStreamWaitEvent(s, t->ev_copied[b], 0));
-        const int grid = std::min(grid_max, ihi - ilo);
-        cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
-        if (e0) cudaEventRecord(e0, s);
-        CU(launch_leaf(D, cap, t->items.p, ilo, ihi, t->d_ctr,
-                       t->d_chunk_buf[b], leaf_a, nxt, t->qpad.p, t->lst_d.p,
-                       t->lst_i.p, K, grid, s));
-        if (e1) cudaEventRecord(e1, s);
-        if (e0 && e1) t->leaf_ev.push_back({e0, e1});
-        CU(cudaEventRecord(t->ev_free[b], s));
-        t->st_leaf_launches += 1;
-        t->st_launches += 1;
-        prev_b = b;
-      }
+    rc = process_round(n_items);
+    if (rc != BKD_OK) return rc;
+    n_act = n_next;  // an upper bound of every later round's active count
+    // rounds queued before the host looks again: many while far from the
+    // tail threshold, one when close to it (or chunked)
+    const int batch = t->chunked ? 1
+                      : n_next > 16 * std::max(tail, 1024) ? 16
+                      : n_next > 4 * std::max(tail, 1024)  ? 4
+                                                            : 1;
+    for (int j = 1; j < batch; ++j) {
+      rc = start_round(true);
+      if (rc == BKD_OK) rc = process_round(-1);
+      if (rc != BKD_OK) return rc;
     }
-    std::swap(act, nxt);
-    n_act = n_next;
-    ++round;
+    rc = start_round(!t->chunked);
+    if (rc != BKD_OK) return rc;
   }
   cudaEvent_t x0 = t->next_event();
   if (x0) cudaEventRecord(x0, s);
@@ -719,6 +844,23 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   t->st_tail_visits += (double)t->h_ctr->tail_visits;
   t->st_tail_pairs += (double)t->h_ctr->tail_pairs;
   t->st_screen_kept += (double)t->h_ctr->screen_kept;
+  t->st_pairs += (double)t->h_ctr->leaf_pairs;
+  // rounds processed = every bucketing but the last; screened rounds = all
+  // processed rounds but the first
+  {
+    const Counters& h = *t->h_ctr;
+    t->st_visits += (double)(h.rounds_visits - last_visits);
+    if (t->precision == 1 && screen_max > 0 && !t->chunked &&
+        h.rounds_visits > first_visits + last_visits) {
+      t->st_screen_visits +=
+          (double)(h.rounds_visits - first_visits - last_visits);
+      t->st_screen_pairs += (double)(h.rounds_pairs - first_pairs - last_pairs);
+      t->st_screen_items += (double)(h.rounds_items - first_items - last_items);
+    }
+  }
+  t->st_screen_bytes += (double)t->h_ctr->screen_bytes;
+  t->st_screen_queued += (double)t->h_ctr->screen_queued;
+  t->st_screen_overflow += (double)t->h_ctr->screen_overflow;
   t->st_resorted += t->h_ctr->n_resorted;
   if (n_fb > 0) {
     CU(launch_fallback(D, n_fb, t->fb_list.p, k, K, t->qpad.p, t->lst_d.p,
@@ -819,21 +961,7 @@ int bkd_query(bkd_tree* t, const float* Q, int64_t m, int k, int64_t* out_idx,
   if (m >= (int64_t)1 << 31)
     return fail(BKD_EUNSUPPORTED, "m >= 2^31; slice the query set");
   DeviceGuard guard(t->device);
-  t->st_rounds = t->st_visits = t->st_pairs = t->st_resorted =
-      t->st_fallback = t->st_leaf_ms = t->st_chunk_bytes = t->st_copy_ms =
-          t->st_leaf_launches = t->st_launches = t->st_tail_queries =
-              t->st_tail_visits = t->st_tail_pairs = t->st_tail_ms =
-                  t->st_screen_kept = t->st_screen_pairs = t->st_screen_ms = 0;
-  t->st_screen_items = t->st_screen_visits = 0;
-  t->st_find_ms = t->st_bucket_ms = t->st_exact_ms = 0;
-  t->ev_used = 0;
-  t->find_ev.clear();
-  t->bucket_ev.clear();
-  t->exact_ev.clear();
-  t->leaf_ev.clear();
-  t->copy_ev.clear();
-  t->tail_ev.clear();
-  t->screen_ev.clear();
+  reset_stats(t);
   if (m == 0) return BKD_OK;
   const int d = t->dev.d;
   cudaStream_t s = t->stream;
@@ -870,38 +998,53 @@ int bkd_query(bkd_tree* t, const float* Q, int64_t m, int k, int64_t* out_idx,
   }
   CU(cudaStreamSynchronize(s));
   if (t->copy_stream) CU(cudaStreamSynchronize(t->copy_stream));
-  for (auto& pr : t->leaf_ev) {
-    float ms = 0;
-    if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess)
-      t->st_leaf_ms += ms;
+  collect_timings(t);
+  return BKD_OK;
+}
+
+int bkd_outlier_scores(bkd_tree* t, int k, float* out_score) {
+  g_err.clear();
+  if (!t) return fail(BKD_EINVAL, "tree is NULL");
+  const int64_t n = t->dev.n;
+  if (k < 1 || (int64_t)k + 1 > n)
+    return fail(BKD_EINVAL, "k must be in [1, n - 1] (got %d)", k);
+  if (k + 1 > BKD_MAX_K)
+    return fail(BKD_EUNSUPPORTED, "k + 1 = %d exceeds BKD_MAX_K = %d", k + 1,
+                BKD_MAX_K);
+  if (!out_score) return fail(BKD_EINVAL, "out_score is NULL");
+  DeviceGuard guard(t->device);
+  const PtrKind ok = ptr_kind(out_score, t->device);
+  if (ok == kForeignPtr)
+    return fail(BKD_EINVAL, "out_score is device memory of another GPU");
+  reset_stats(t);
+  cudaStream_t s = t->stream;
+  const int d = t->dev.d, K = k + 1;
+  const int64_t slots = t->n_leaves * t->dev.lcap;
+  const int64_t slice =
+      std::min<int64_t>(n, t->max_active > 0 ? t->max_active : 1 << 24);
+  CU(t->inv.ensure(n));
+  CU(t->qdev.ensure(slice * d));
+  CU(t->out_idx.ensure(slice * K));
+  CU(t->out_dist.ensure(slice * K));
+  if (ok != kDevicePtr) CU(t->score.ensure(slice));
+  // pts / orig: device memory, or mapped pinned host memory (chunked)
+  CU(launch_inverse(t->dev.orig, slots, t->inv.p, s));
+  for (int64_t i0 = 0; i0 < n; i0 += slice) {
+    const int64_t mm = std::min(slice, n - i0);
+    CU(launch_gather(t->dev.pts, t->dev.Dp, d, t->inv.p, i0, mm, t->qdev.p,
+                     s));
+    int rc = search(t, mm, K, t->out_idx.p, t->out_dist.p);
+    if (rc != BKD_OK) return rc;
+    float* dst = ok == kDevicePtr ? out_score + i0 : t->score.p;
+    CU(launch_score(t->out_idx.p, t->out_dist.p, i0, mm, k, dst, s));
+    if (ok != kDevicePtr)
+      CU(cudaMemcpyAsync(out_score + i0, t->score.p, sizeof(float) * mm,
+                         cudaMemcpyDeviceToHost, s));
+    t->st_launches += 3;
   }
-  for (auto& pr : t->copy_ev) {
-    float ms = 0;
-    if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess)
-      t->st_copy_ms += ms;
-  }
-  for (auto& pr : t->tail_ev) {
-    float ms = 0;
-    if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess)
-      t->st_tail_ms += ms;
-  }
-  for (auto& pr : t->screen_ev) {
-    float ms = 0;
-    if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess)
-      t->st_screen_ms += ms;
-  }
-  const std::pair<std::vector<std::pair<cudaEvent_t, cudaEvent_t>>*,
-                  double*>
-      phases[] = {{&t->find_ev, &t->st_find_ms},
-                  {&t->bucket_ev, &t->st_bucket_ms},
-                  {&t->exact_ev, &t->st_exact_ms}};
-  for (const auto& ph : phases)
-    for (auto& pr : *ph.first) {
-      float ms = 0;
-      if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess)
-        *ph.second += ms;
-    }
-  cudaGetLastError();
+  CU(cudaStreamSynchronize(s));
+  if (t->copy_stream) CU(cudaStreamSynchronize(t->copy_stream));
+  collect_timings(t);
   return BKD_OK;
 }
 
@@ -965,6 +1108,10 @@ int bkd_get_stat(const bkd_tree* t, int key, double* value) {
     case BKD_STAT_FIND_MS: *value = t->st_find_ms; break;
     case BKD_STAT_BUCKET_MS: *value = t->st_bucket_ms; break;
     case BKD_STAT_EXACT_MS: *value = t->st_exact_ms; break;
+    case BKD_STAT_CHUNK_VISITS: *value = t->st_chunk_visits; break;
+    case BKD_STAT_SCREEN_BYTES: *value = t->st_screen_bytes; break;
+    case BKD_STAT_SCREEN_QUEUED: *value = t->st_screen_queued; break;
+    case BKD_STAT_SCREEN_OVERFLOW: *value = t->st_screen_overflow; break;
     default: return fail(BKD_EINVAL, "unknown stat %d", key);
   }
   return BKD_OK;

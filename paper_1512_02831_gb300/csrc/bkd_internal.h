@@ -79,6 +79,16 @@ struct Counters {
   unsigned long long tail_pairs;   // (query, point) pairs of the tail kernel
   unsigned long long tail_visits;  // (query, leaf) visits of the tail kernel
   unsigned long long screen_kept;  // pairs the BF16 screen passed on
+  unsigned long long leaf_pairs;   // (query, point) pairs the float32 leaf
+                                   // kernel scored
+  unsigned long long screen_bytes; // operand-tile bytes the screen streamed
+  // sums over the rounds of a LazySearch (written by the bucketing)
+  unsigned long long rounds_pairs;   // (query, point) pairs scheduled
+  unsigned long long rounds_visits;  // (query, leaf) pairs bucketed
+  unsigned long long rounds_items;   // work items
+  unsigned long long rounds_run;     // rounds with at least one query
+  unsigned long long screen_queued;  // pairs queued for exact rescoring
+  unsigned long long screen_overflow;  // screen items whose queue overflowed
 };
 
 constexpr int kErrNonFinite = 1;   // a query holds a non-finite / huge value
@@ -96,6 +106,11 @@ struct DevTree {
   int64_t n;
   int d, Dp, h;
   int64_t lcap;            // slots per leaf (multiple of 4)
+  // chunked mode: N leaf chunks (chunk of leaf l = floor(l N / 2^h)) and,
+  // per chunk, whether the last round scanned its buffers (device; nullptr
+  // in resident mode, where every round scans every buffer)
+  int n_chunks;
+  const uint8_t* chunk_done;
 };
 
 // ------------------------------------------------------------- launchers
@@ -119,28 +134,38 @@ cudaError_t launch_retire(const int2* placed, const uint32_t* act, int n_act,
 // round): per position of `act`, placed = (next leaf, rank among the
 // queries that go to it) or (-1, 0) when done; the new pending leaf in
 // state; cnt[leaf] counts the queries that go on (cnt must start at 0).
+// In chunked mode a query whose pending leaf lies in a chunk the last round
+// did not scan (t.chunk_done) stays in that leaf's buffer: it is placed
+// there again and its traversal does not advance.
+// n_act_dev (optional): the active count read on the device (rounds queued
+// without a host round trip); n_act is then an upper bound (grid size).
 cudaError_t launch_find_leaf(const DevTree& t, const float* qpad,
                              const uint32_t* act, int n_act, uint64_t* state,
                              const float* lst_d, int K, int2* placed,
-                             int32_t* cnt, cudaStream_t s);
+                             int32_t* cnt, cudaStream_t s,
+                             const int32_t* n_act_dev = nullptr);
 
 // Buffer insertion from per-leaf counts `cnt` and the placements of
 // FindLeafBatch: offsets, work items of `tile` queries, round totals, and
 // the active list bucketed by leaf into `next`.  cursor must hold
 // max(n_leaves, 4) int32: between the two scan passes it carries one
 // 16-byte partial sum per 2,048 leaves.
+// n_act_dev as in launch_find_leaf; n_next_dev (optional) receives the
+// round's bucketed count (the next round's active count).
 cudaError_t launch_bucket(const int2* placed, const uint32_t* act,
                           int n_act, int n_leaves, int tile,
                           const int32_t* leaf_cnt, const int32_t* cnt,
                           int32_t* off, int32_t* cursor, int32_t* toff,
                           Item* items, uint32_t* next, Counters* ctr,
-                          cudaStream_t s);
+                          cudaStream_t s, const int32_t* n_act_dev = nullptr,
+                          int32_t* n_next_dev = nullptr);
 
 // chunk_item[c] = first item of chunk c (leaves [chunk_leaf[c],
-// chunk_leaf[c+1])), for c = 0..n_chunks.
-cudaError_t launch_chunk_items(const int32_t* toff, const int32_t* chunk_leaf,
-                               int n_chunks, int32_t* chunk_item,
-                               cudaStream_t s);
+// chunk_leaf[c+1])) and chunk_item[n_chunks + 1 + c] = its first buffered
+// query, for c = 0..n_chunks.
+cudaError_t launch_chunk_items(const int32_t* toff, const int32_t* off,
+                               const int32_t* chunk_leaf, int n_chunks,
+                               int32_t* chunk_item, cudaStream_t s);
 
 // ProcessAllBuffers over items [item_lo, item_hi) (item_hi < 0: read the
 // count from ctr).  pts / leaf0: the quads of leaf `leaf0` start at pts.
@@ -154,27 +179,36 @@ int leaf_kernel_grid(int Dp, int cap, int sm_count);
 
 // BF16 screen data on the device (see fill_screen).
 struct ScreenData {
-  const uint32_t* words = nullptr;
+  const uint16_t* words = nullptr;  // operand tiles, `tiles` per leaf
   const float* center = nullptr;
   const float* bmax = nullptr;
   const float* pnmax = nullptr;
-  int64_t stride = 0;  // slots per leaf in words
+  int64_t tiles = 0;  // 128-point tiles per leaf
   int kh = 0;
 };
 
-// Queries per work item of a screened round (up to four 8-query n-blocks
-// of one m16n8k16 tile column set, one warp per item).
-constexpr int kScreenTile = 32;
-// Slots per leaf of the screen arrays: the leaf capacity rounded up to the
-// 32-point super-tile (two 16-point m-tiles).
-inline int64_t screen_stride(int64_t lcap) { return (lcap + 31) / 32 * 32; }
+// The screen's tensor-core shape: points are the MMA's M = 128 rows (one
+// operand tile of a leaf), the buffered queries of one leaf its N <= 128
+// columns (one work item), K = 16 slots per k-half.
+constexpr int kScreenRows = 128;
+constexpr int kScreenTile = 128;  // queries per work item of a screened round
+inline int64_t screen_tiles(int64_t lcap) {
+  return (lcap + kScreenRows - 1) / kScreenRows;
+}
+// Byte offset of row r's k-group kg (slots 8 kg .. 8 kg + 7) in an operand
+// tile of kh k-halves: the canonical no-swizzle K-major layout of the MMA
+// (8-row core matrices of 16-byte rows; core matrices adjacent in K 128
+// bytes apart, 8-row groups 256 kh bytes apart).
+__host__ __device__ inline uint32_t screen_row_offset(int r, int kg, int kh) {
+  return (uint32_t)((r >> 3) * (256 * kh) + kg * 128 + (r & 7) * 16);
+}
 
 // ProcessAllBuffers with the BF16 tensor-core screen and exact float32
 // rescoring (k_screen.cu); same candidate lists as launch_leaf on a
 // resident tree, over items of at most kScreenTile queries.  screen_grid:
-// resident CTAs (0 if the shared memory does not fit or the leaf capacity
-// is out of range).
-int screen_grid(int kh, int64_t lcap, int K, int sm_count);
+// resident CTAs (0 if the kernel does not fit: shared memory, tensor
+// memory, leaf capacity).
+int screen_grid(int kh, int Dp, int64_t lcap, int K, int sm_count);
 cudaError_t launch_screen(const DevTree& t, const ScreenData& sd,
                           const Item* items, int item_lo, int item_hi,
                           Counters* ctr, const uint32_t* act,
@@ -198,6 +232,18 @@ cudaError_t launch_recheck(const DevTree& t, int64_t m, int k, int K,
 cudaError_t launch_fallback(const DevTree& t, int n_fb, const uint32_t* fb_list,
                             int k, int K, const float* qpad, const float* lst_d,
                             int64_t* out_idx, float* out_dist, cudaStream_t s);
+
+// Outlier score of Sec. 4.3 (k_outlier.cu): inv[orig[s]] = s for every
+// occupied slot; Q[r] = the point of original index i0 + r (r < m), read
+// from the quads at pts; out[r] = mean of the square roots of the k
+// distances of row r of the (k+1)-lists idx / dist, without the point's own
+// index (or without the last entry if the row does not hold it).
+cudaError_t launch_inverse(const int64_t* orig, int64_t slots, int64_t* inv,
+                           cudaStream_t s);
+cudaError_t launch_gather(const float* pts, int Dp, int d, const int64_t* inv,
+                          int64_t i0, int64_t m, float* Q, cudaStream_t s);
+cudaError_t launch_score(const int64_t* idx, const float* dist, int64_t i0,
+                         int64_t m, int k, float* out, cudaStream_t s);
 
 // Read-only view of a tree handle for entry points outside api.cu.
 struct TreeView {
@@ -251,21 +297,21 @@ const char* build_host_tree(const float* P, int64_t n, int d, int h,
 // = maximum; dimensions d..Dp-1 are [0, 0].
 void fill_boxes(const float* P, const HostTree& t, float* box);
 
-// k-halves of 16 bf16 slots the BF16 screen uses: the d offsets plus two
-// slots that carry the point's squared norm (1 for d <= 14, 2 for d <= 30,
-// else 3).
-inline int screen_halves(int d) { return (d + 2 + 15) / 16; }
+// k-halves of 16 bf16 slots the BF16 screen uses: the d offsets, two slots
+// for the point's squared norm and three for the query's threshold (1 for
+// d <= 11, 2 for d <= 27, else 3).
+inline int screen_halves(int d) { return (d + 5 + 15) / 16; }
 
-// Data of the BF16 screen, per leaf (stride slots per leaf, see
-// screen_stride): the centre c (midpoint of the leaf's bounding box), every
-// point's offset bf16(fl(x - c)) in slots 0..d-1 and its squared norm pn
-// (binary64 sum rounded to float) split as pn_hi = bf16(pn), pn_lo =
-// bf16(pn - pn_hi) in slots d, d+1 (padding slots: pn_hi = +inf), packed as
-// bf16 pairs (8 words per point and k-half, in m16n8k16 A-fragment order,
-// see build.cpp); per leaf bmax (upper bound on the offset rounding error
-// norm) and pnmax (largest pn).
-void fill_screen(const float* P, const HostTree& t, int64_t stride,
-                 uint32_t* words, float* center, float* bmax, float* pnmax);
+// Data of the BF16 screen, per leaf: the centre c (midpoint of the leaf's
+// bounding box); per point (a row of the leaf's operand tiles, `tiles` of
+// 128 rows each, 128 x 16 kh bf16 per tile in the layout of
+// screen_row_offset) its offset bf16(fl(x - c)) in slots 0..d-1, its
+// squared norm pn (binary64 sum rounded to float) split as pn_hi = bf16(pn),
+// pn_lo = bf16(pn - pn_hi) in slots d, d+1, and 1.0 in slots d+2..d+4
+// (padding rows: pn_hi = +inf, everything else 0); per leaf bmax (upper
+// bound on the offset rounding error norm) and pnmax (largest pn).
+void fill_screen(const float* P, const HostTree& t, int64_t tiles,
+                 uint16_t* words, float* center, float* bmax, float* pnmax);
 
 // Writes the quads and orig arrays for leaves [leaf_lo_id, leaf_hi_id)
 // into host buffers (`pts` and `orig` point at leaf leaf_lo_id's first slot).

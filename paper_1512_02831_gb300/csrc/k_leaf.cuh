@@ -218,6 +218,9 @@ __global__ void __launch_bounds__(kPipeThreads)
     const Item w = items[it];
     const int nq = (leaf_cnt[w.leaf] + 3) >> 2;
     const int nseg = (nq + kPipeSegQuads - 1) / kPipeSegQuads;
+    if (tid == 0)
+      atomicAdd(&ctr->leaf_pairs,
+                (unsigned long long)w.count * (unsigned long long)leaf_cnt[w.leaf]);
     const bool on = tid < w.count;
     uint32_t q = 0;
     uint64_t qq[D];

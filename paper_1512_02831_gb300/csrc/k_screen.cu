@@ -1,106 +1,252 @@
-// k_screen.cu -- ProcessAllBuffers with a BF16 tensor-core screen.
+// k_screen.cu -- ProcessAllBuffers with a BF16 tensor-core screen (tcgen05).
 //
 // Same candidate lists as the float32 leaf kernel (every point whose float32
 // distance could still enter a query's list is scored exactly), but most
-// points are rejected by a cheap screen first:
+// (query, point) pairs are rejected by a cheap screen first:
 //
 //   v = q - c, w = x - c (c: centre of the leaf), rounded to bf16 (v^, w^);
 //   s = |v^|^2 + |w^|^2 - 2 v^.w^.
 //
-// The tensor cores form D = v^.w^ - |w^|^2/2 (mma.sync m16n8k16, bf16 in,
-// fp32 accumulate from zero): 16 points (rows) x 8 queries (columns) per
-// instruction and k-half of 16 bf16 slots.  A point's slots hold w^ and,
-// after it, pn_hi and pn_lo (pn = fl32(|w^|^2), pn_hi = bf16(pn), pn_lo =
-// bf16(pn - pn_hi), so |w^|^2 = pn_hi + pn_lo up to (2^-16 + 2^-24) pn); a
-// query's hold v^ and -1/2, -1/2.  So s = |v^|^2 - 2 D, and the screen test
-// s < T reads D > (|v^|^2 - T) / 2: one comparison per (query, point) pair.
-// Padding points carry pn_hi = +inf, so D = -inf there.
+// The tensor cores form, per (point, query) pair, in one dot product of
+// 16 KH bf16 slots accumulated in fp32,
+//   X = v^.w^ - (pn_hi + pn_lo) / 2 + (t_hi + t_mid + t_lo)
+// where a point's row holds w^, its squared norm pn = fl32(|w^|^2) split as
+// pn_hi = bf16(pn), pn_lo = bf16(pn - pn_hi) (|w^|^2 = pn_hi + pn_lo up to
+// (2^-16 + 2^-24) pn), and 1, 1, 1; a query's column holds v^, -1/2, -1/2
+// and its threshold t = thr / 2 split exactly into three bf16 parts.  The
+// screen keeps a pair iff X > 0, i.e. iff s - |v^|^2 < thr: the threshold
+// is folded into the contraction, so the epilogue only asks whether the
+// largest of a row's values is positive.  Padding points (pn_hi = +inf)
+// score -inf; padding columns carry t = -2^126, columns whose list is not
+// full yet t = +2^126 (every point is a candidate).
 //
 // Safety bound.  bf16 keeps 8 significant bits, so round-to-nearest errs by
 // at most 2^-8 relative; with the float32 subtraction before it, rho =
-// 2^-8 (1 + 1e-4) and |v^ - v| <= rho |v|, |v| <= |v^| / (1 - rho), so
+// 2^-8 (1 + 1e-4), |v^ - v| <= rho |v|, |v| <= |v^| / (1 - rho), so
 //   |q - x| >= |v^ - w^| - A_q - B_x,  A_q = rho/(1-rho) |v^|,
 // and B_x <= B_max, the leaf's largest such term (prepared on the host).
-// The computed s differs from |v^ - w^|^2 by at most
-//   E = 2^-14 (|v^|^2 + pn_max):
-//   * accumulation model: one MMA (16 exact bf16 products added to an fp32
-//     accumulator c) errs by at most 2^-18 (|c| + sum |a_i b_i|); the KH
-//     chained halves of one pair then err by at most KH 2^-18 S, S = the sum
-//     of the absolute products <= |v^|^2 / 2 + pn (1 + 2^-8).  (A hardware
-//     property, not an IEEE rule: the bf16 MMA probe test checks it on
-//     adversarial operands -- one large term and many small ones,
-//     cancellation, mixed exponents within a k-half.)  With KH <= 3 the
-//     error of s = |v^|^2 - 2D is <= 2^-16.4 |v^|^2 + 2^-15.4 pn;
-//   * the norm split adds (2^-16 + 2^-24) pn, the float32 chain of |v^|^2
-//     at most d 2^-24 |v^|^2 <= 2^-19 |v^|^2;
-//   * in total < 1.4e-5 |v^|^2 + 3.9e-5 pn <= E (2^-14 = 6.1e-5).
 // The float32 distance of the exact path obeys D32 >= D (1 - g) - eta,
-// g = (d+3) 2^-24, eta = 2^-120.  Hence a point can only enter the list
-// (D32 < bound) if
-//   s < T = (sqrt((bound + eta) / (1 - g)) + A_q + B_max)^2 + E,
-// evaluated once per (query, leaf) in float32 with every operation rounded
-// toward the larger threshold (divisors toward the smaller).  Kept points
-// are scored with the exact float32 chain of the leaf kernel and inserted
-// with the same strict rule in ascending slot order, so the lists -- and the
-// answers -- are bit for bit those of the float32 path.
+// g = (d+3) 2^-24, eta = 2^-120, so a point can only enter the list
+// (D32 < bound) if |v^ - w^| < Rb = sqrt((bound + eta) / (1 - g)) + A_q +
+// B_max, i.e. if 2 v^.w^ > |v^|^2 + |w^|^2 - Rb^2.  Then, with thr >= Rb^2
+// + E - qn (qn the float32 |v^|^2),
+//   X > (|v^|^2 - qn + E + pn_err) / 2,  pn_err = |w^|^2 - pn_hi - pn_lo,
+// and the computed X stays positive if E covers the roundings:
+//   * accumulation model: one MMA k-step (16 exact bf16 products added to
+//     an fp32 accumulator c) errs by at most 2^-18 (|c| + sum |a_i b_i|), so
+//     the KH chained k-halves of one pair err by at most KH 2^-18 S, S the
+//     sum of the absolute products <= |v^|^2/2 + pn (1 + 2^-8) + 0.51 |thr|.
+//     (A hardware property, not an IEEE rule: the MMA probe test checks it
+//     on adversarial operands -- one large term and many small ones,
+//     cancellation, mixed exponents within a k-half.)  Twice that (the test
+//     compares 2X) is <= 2^-16.4 |v^|^2 + 2^-15.4 pn + 2^-16.3 |thr|;
+//   * the norm split adds (2^-16 + 2^-24) pn, the float32 chain of |v^|^2 at
+//     most d 2^-24 |v^|^2 <= 2^-19 |v^|^2;
+//   * |thr| <= Rb^2 + E + qn;
+// so E = 2^-13 (|v^|^2 + Rb^2) + 2^-14 pn_max + 2^-120 suffices (the last
+// term covers a threshold split that underflows).  thr is formed once per
+// (query, leaf) in float32 with every operation rounded toward the larger
+// threshold (divisors toward the smaller).  Kept pairs are scored with the
+// exact float32 chain of the leaf kernel and inserted with the same strict
+// rule, so the lists hold the same k+1 smallest float32 distances as the
+// float32 path, and the answers (re-check and fallback read nothing else)
+// are the same.
 //
-// Work layout.  One warp per item (one leaf, at most 32 buffered queries,
-// i.e. up to four 8-query column blocks).  Each lane streams its own A
-// fragments of the leaf through a small shared-memory ring (cp.async, L2
-// only).  Kept pairs go to a per-warp queue; a full queue is scored 32
-// pairs at a time and inserted per query in queue order.  A query's list is
-// read from global memory only when a point is inserted into it, and
-// written back only then.
+// Work layout (one CTA per work item at a time: one leaf, <= 128 of its
+// buffered queries, items taken from a launch-wide counter):
+//   warp 0 (one thread)  claims items, publishes them in a small ring, and
+//                        streams the leaf's 128-point operand tiles (bulk
+//                        copies, 4 KB per k-half) into a deep shared-memory
+//                        ring, across item boundaries;
+//   warp 1               allocates tensor memory; one thread issues, per
+//                        tile, KH tcgen05.mma (M = 128 points, N = the
+//                        item's queries rounded up to 16, K = 16) into one of
+//                        two fp32 accumulators in tensor memory, and commits
+//                        them to mbarriers (ring slot free, accumulator full);
+//   warps 2-5            the epilogue: prepare the item's query operand
+//                        (B) and thresholds; per tile read the accumulator
+//                        (tcgen05.ld, row = point, column = query), take the
+//                        largest value of each row with three-input max, and
+//                        hand the accumulator back; the rare rows with a
+//                        positive value are rescored exactly and inserted
+//                        into the queries' lists (shared memory, loaded from
+//                        HBM on first insertion, written back at item end).
+// Every wait is bounded: a wait that runs out sets kErrTimeout, every role
+// then leaves, copies and MMAs in flight are waited for (bounded), and the
+// tensor memory is released.
 #include <cuda_bf16.h>
 
 #include <algorithm>
 
 #include "bkd.h"
 #include "bkd_internal.h"
+#include "k_leaf.cuh"
 
 namespace bkd {
 namespace {
 
-constexpr int kScrWarps = 8;
-constexpr int kScrThreads = kScrWarps * 32;
-constexpr int kQueue = 64;  // kept pairs per warp between two scorings
-static_assert(kScreenTile == 32, "one query column per lane");
+constexpr int kEpiThreads = 128;              // 4 epilogue warps
+constexpr int kGrpThreads = 128;              // 4 warps per column group
+constexpr int kThreads = 64 + kEpiThreads + 2 * kGrpThreads;
+constexpr int kItemRing = 4;                  // published items in flight
+constexpr int kQcap = 1024;                   // rescoring queue per group
+constexpr uint32_t kAccCols = 128;            // tensor-memory columns per acc
+constexpr uint32_t kTmemCols = 2 * kAccCols;  // two accumulators
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<const uint32_t*>(&v);
+__host__ __device__ constexpr int ring_stages(int kh) {
+  return kh == 1 ? 8 : 4;
+}
+__host__ __device__ constexpr uint32_t tile_bytes(int kh) {
+  return 4096u * (uint32_t)kh;
 }
 
-__device__ __forceinline__ float bf16_lo(uint32_t w) {
-  return __uint_as_float(w << 16);
-}
-__device__ __forceinline__ float bf16_hi(uint32_t w) {
-  return __uint_as_float(w & 0xffff0000u);
+// Shared-memory layout (byte offsets into the dynamic shared memory); the
+// per-group pieces exist twice (group g at offset + g * stride).
+struct Layout {
+  uint32_t ring, bop, grp, grp_stride, qc, colq, colb, colx, queue, qd,
+      items, bars, misc, total;
+};
+
+__host__ __device__ inline uint32_t take(uint32_t& o, uint32_t bytes,
+                                         uint32_t align) {
+  o = (o + align - 1) / align * align;
+  const uint32_t r = o;
+  o += bytes;
+  return r;
 }
 
-// acc = a (16x16 bf16, row) x b (16x8 bf16, col) + acc, fp32.
-__device__ __forceinline__ void mma_bf16(float (&acc)[4], uint32_t a0,
-                                         uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
+__host__ __device__ inline Layout layout_of(int kh, int Dp) {
+  Layout L;
+  uint32_t o = 0;
+  L.ring = take(o, ring_stages(kh) * tile_bytes(kh), 1024);
+  L.bop = take(o, 2 * tile_bytes(kh), 1024);  // one B operand per group
+  uint32_t g = 0;  // offsets inside one group's block
+  L.qc = take(g, 128u * Dp * 4, 16);
+  L.colq = take(g, 128 * 4, 16);
+  L.colb = take(g, 128 * 4, 16);
+  L.colx = take(g, 128 * 4, 16);
+  L.queue = take(g, kQcap * 4, 16);
+  L.qd = take(g, kQcap * 4, 16);
+  L.grp_stride = (g + 15) / 16 * 16;
+  L.grp = take(o, 2 * L.grp_stride, 16);
+  L.items = take(o, kItemRing * 16, 16);
+  L.bars = take(o, (2 * ring_stages(kh) + 4 + 6 + 2 * kItemRing) * 8, 8);
+  L.misc = take(o, 32, 16);
+  L.total = o;
+  return L;
+}
+
+// ----------------------------------------------------------- primitives
+__device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-      "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};"
-      : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+      "{\n .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
 }
 
-// acc = a x b, accumulated from zero.
-__device__ __forceinline__ void mma_bf16_z(float (&acc)[4], uint32_t a0,
-                                           uint32_t a1, uint32_t a2,
-                                           uint32_t a3, uint32_t b0,
-                                           uint32_t b1) {
+// Waits for phase `parity` of `bar`; false once the CTA aborted or the wait
+// ran out (~2^31 cycles: then it aborts the CTA and reports the timeout).
+__device__ __noinline__ bool bar_wait(uint32_t bar, uint32_t parity,
+                                      volatile int* abort, Counters* ctr) {
+  const long long t0 = clock64();
+  for (;;) {
+    if (bar_try(bar, parity)) return true;
+    if (*abort) return false;
+    if (clock64() - t0 > (1ll << 31)) {
+      *abort = 1;
+      atomicOr(&ctr->err, kErrTimeout);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void bar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor of an operand tile in the layout of
+// screen_row_offset (no swizzle, K-major): start address, leading-dimension
+// byte offset (K direction: 128), stride-dimension byte offset (8-row
+// groups: 256 kh), descriptor version 1.
+__device__ __forceinline__ uint64_t op_desc(uint32_t saddr, int kh) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) |
+         ((uint64_t)(128u >> 4) << 16) |
+         ((uint64_t)(((uint32_t)kh * 256u) >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: bf16 A and B, fp32 accumulator,
+// both K-major, M = 128, N = n (multiple of 16, <= 256).
+__device__ __forceinline__ uint32_t mma_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b,
+                                       uint32_t idesc, uint32_t accumulate) {
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-      "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%10, %10, %10, %10};"
-      : "=f"(acc[0]), "=f"(acc[1]), "=f"(acc[2]), "=f"(acc[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1), "f"(0.f));
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+      "[%0];" ::"r"(bar)
+      : "memory");
+}
+
+// 16 / 32 consecutive accumulator columns of this thread's lane, waited for
+// inside the same statement (so no use can be scheduled before the wait).
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, "
+      "%7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]),
+        "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]),
+        "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, "
+      "%7, %8, %9, %10, %11, %12, %13, %14, %15}, [%32];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, "
+      "%22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%33];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]),
+        "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]),
+        "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+        "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr), "r"(taddr + 16u)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // max(a, b, c) (three-input float max of sm_100 and later).
@@ -110,9 +256,44 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
   return r;
 }
 
+// Named barriers of 128 threads (id 1: the epilogue warps, id 2 + g:
+// column group g), with an OR over a predicate.
+template <int ID>
+__device__ __forceinline__ bool sync128_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+      " bar.red.or.pred q, %2, 128, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(ID)
+      : "memory");
+  return r != 0;
+}
+template <int ID>
+__device__ __forceinline__ void sync128() {
+  asm volatile("bar.sync %0, 128;" ::"n"(ID) : "memory");
+}
+__device__ __forceinline__ bool group_sync_or(int g, bool v) {
+  return g ? sync128_or<3>(v) : sync128_or<2>(v);
+}
+__device__ __forceinline__ void group_sync(int g) {
+  if (g)
+    sync128<3>();
+  else
+    sync128<2>();
+}
+
+__device__ __forceinline__ float bf16_value(uint16_t h) {
+  return __uint_as_float((uint32_t)h << 16);
+}
+__device__ __forceinline__ uint16_t bf16_bits(float f) {
+  const __nv_bfloat16 b = __float2bfloat16_rn(f);
+  return *reinterpret_cast<const uint16_t*>(&b);
+}
+
 // Exact float32 distance of query coordinates qp (Dp, zero-padded) to the
 // point in `slot`: the leaf kernel's chain, one dimension at a time.
-__device__ __forceinline__ float exact_dist(const float* __restrict__ qp,
+__device__ __forceinline__ float exact_dist(const float* qp,
                                             const float* __restrict__ pts,
                                             int Dp, uint32_t slot) {
   const float* quad = pts + (size_t)(slot >> 2) * 4 * Dp + (slot & 3);
@@ -125,414 +306,489 @@ __device__ __forceinline__ float exact_dist(const float* __restrict__ qp,
   return e;
 }
 
-// Per-warp shared memory (32-bit words):
-//   ring   R x NC x 32 x 4  super-tiles in flight: stage, component, lane
-//                       (each lane copies, and later reads, only its own
-//                       fragments; NC = 2 KH 16-byte components)
-//   rec    32 x KH x 8   bf16 offsets of the item's queries (B operand)
-//   tneg   32            -T'/2 per query column (+inf: unused column)
-//   qid    32            query ids
-//   bound  32            last entry of each column's candidate list
-//   flag   32            bit 0: list copied into ld/li, bit 1: list changed
-//   queue  kQueue        kept pairs: (slot in leaf) << 5 | column
-//   qd     kQueue        their exact float32 distances
-//   ld, li 32 x K each   candidate lists, read on first insertion
-struct WarpSmem {
-  uint4* ring;
-  uint32_t* rec;
-  float* tneg;
-  uint32_t* qid;
-  float* bound;
-  uint32_t* flag;
-  uint32_t* queue;
-  float* qd;
-  float* ld;
-  uint32_t* li;
+// The screen's view of its dynamic shared memory.
+struct Smem {
+  uint8_t* base;
+  uint32_t base_u32;
+  Layout L;
+  int S;
+  __device__ uint32_t ring_u32(int s, int kh) const {
+    return base_u32 + L.ring + (uint32_t)s * tile_bytes(kh);
+  }
+  __device__ uint32_t bop_u32(int g, int kh) const {
+    return base_u32 + L.bop + (uint32_t)g * tile_bytes(kh);
+  }
+  __device__ uint8_t* grp(int g) const {
+    return base + L.grp + (uint32_t)g * L.grp_stride;
+  }
+  __device__ uint32_t bar(int i) const { return base_u32 + L.bars + 8u * i; }
+  __device__ uint32_t afull(int s) const { return bar(s); }
+  __device__ uint32_t aempty(int s) const { return bar(S + s); }
+  __device__ uint32_t accfull(int b) const { return bar(2 * S + b); }
+  __device__ uint32_t accempty(int b) const { return bar(2 * S + 2 + b); }
+  __device__ uint32_t bready(int g) const { return bar(2 * S + 4 + g); }
+  __device__ uint32_t epidone(int g) const { return bar(2 * S + 6 + g); }
+  __device__ uint32_t qfree(int g) const { return bar(2 * S + 8 + g); }
+  __device__ uint32_t itemfull(int i) const { return bar(2 * S + 10 + i); }
+  __device__ uint32_t itemempty(int i) const {
+    return bar(2 * S + 10 + kItemRing + i);
+  }
+  __device__ int4* items() const {
+    return reinterpret_cast<int4*>(base + L.items);
+  }
+  // misc words: [0] tensor-memory base, [1] abort, [2 + g] queue count of
+  // group g, [4 + g] queue overflow of group g
+  __device__ uint32_t* misc() const {
+    return reinterpret_cast<uint32_t*>(base + L.misc);
+  }
 };
 
-// Ring depth (super-tiles per warp in the ring: one being read, the rest in
-// flight) and 16-byte components per stage.  Measured best at 3 (with three
-// CTAs per SM); deeper rings are slower: their shared memory comes out of
-// L1.
-__host__ __device__ constexpr int ring_depth(int) { return 3; }
-__host__ __device__ constexpr int ring_comps(int kh) { return 2 * kh; }
-
-__host__ __device__ constexpr int warp_words(int kh, int K) {
-  return ring_depth(kh) * ring_comps(kh) * 128 + kh * 256 + 128 +
-         2 * kQueue + 64 * K;
-}
-
-template <int KH>
-__device__ __forceinline__ WarpSmem warp_smem(uint32_t* base, int warp,
-                                              int K) {
-  uint32_t* p = base + (size_t)warp * warp_words(KH, K);
-  WarpSmem w;
-  w.ring = reinterpret_cast<uint4*>(p);
-  p += ring_depth(KH) * ring_comps(KH) * 128;
-  w.rec = p;
-  w.tneg = reinterpret_cast<float*>(p + KH * 256);
-  w.qid = p + KH * 256 + 32;
-  w.bound = reinterpret_cast<float*>(w.qid + 32);
-  w.flag = w.qid + 64;
-  w.queue = w.qid + 96;
-  w.qd = reinterpret_cast<float*>(w.queue + kQueue);
-  w.ld = w.qd + kQueue;
-  w.li = reinterpret_cast<uint32_t*>(w.ld + 32 * K);
-  return w;
-}
-
-// Scores the queued pairs (one per lane at a time) and inserts them, per
-// query column, in queue order -- which is ascending slot order per column.
-// Out of line: it runs for a few tiles only, and inlined copies would crowd
-// the instruction cache.
-__device__ __noinline__ void drain(const DevTree& t, int leaf,
-                                   const float* __restrict__ qpad,
-                                   const float* __restrict__ lst_d,
-                                   const uint32_t* __restrict__ lst_i, int K,
-                                   const WarpSmem& ws, int lane, int nq,
-                                   int ncol) {
-  __syncwarp();
-  const uint32_t slot0 = (uint32_t)((int64_t)leaf * t.lcap);
-  for (int e = lane; e < nq; e += 32) {
-    const uint32_t en = ws.queue[e];
-    const uint32_t q = ws.qid[en & 31u];
-    ws.qd[e] = exact_dist(qpad + (size_t)q * t.Dp, t.pts, t.Dp,
-                          slot0 + (en >> 5));
-  }
-  __syncwarp();
-  if (lane < ncol) {
-    float* ld = ws.ld + lane * K;
-    uint32_t* li = ws.li + lane * K;
-    const uint32_t q = ws.qid[lane];
-    float bound = ws.bound[lane];
-    uint32_t flag = ws.flag[lane];
-    for (int e = 0; e < nq; ++e) {
-      const uint32_t en = ws.queue[e];
-      if ((int)(en & 31u) != lane) continue;
-      const float dv = ws.qd[e];
-      if (!(dv < bound)) continue;
-      if (!(flag & 1u)) {
-        for (int j = 0; j < K; ++j) {
-          ld[j] = lst_d[(size_t)q * K + j];
-          li[j] = lst_i[(size_t)q * K + j];
-        }
-      }
-      int pos = K - 1;
-      while (pos > 0 && ld[pos - 1] > dv) {
-        ld[pos] = ld[pos - 1];
-        li[pos] = li[pos - 1];
-        --pos;
-      }
-      ld[pos] = dv;
-      li[pos] = slot0 + (en >> 5);
-      bound = ld[K - 1];
-      flag = 3u;
-    }
-    ws.bound[lane] = bound;
-    ws.flag[lane] = flag;
-  }
-  __syncwarp();
-}
-
-// One 32-point super-tile in registers: per k-half the A fragments of rows
-// g and g + 8 of both m-tiles.
-template <int KH>
-struct Super {
-  uint4 a[KH][2];
-};
-
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                   (uint32_t)__cvta_generic_to_shared(dst)),
-               "l"(__cvta_generic_to_global(src))
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-// Copies this lane's fragments of super-tile S into ring stage `slot`.
-template <int KH>
-__device__ __forceinline__ void issue_super(const WarpSmem& ws, int slot,
-                                            int lane, const uint4* wb,
-                                            int64_t hstep, int S) {
-  uint4* dst = ws.ring + (size_t)slot * ring_comps(KH) * 32 + lane;
-  const uint4* src = wb + (int64_t)S * 64;
-#pragma unroll
-  for (int h = 0; h < KH; ++h) {
-    cp_async16(dst + (2 * h) * 32, src + h * hstep);
-    cp_async16(dst + (2 * h + 1) * 32, src + h * hstep + 32);
-  }
-}
-
-template <int KH>
-__device__ __forceinline__ void read_super(Super<KH>& x, const WarpSmem& ws,
-                                           int slot, int lane) {
-  const uint4* src = ws.ring + (size_t)slot * ring_comps(KH) * 32 + lane;
-#pragma unroll
-  for (int h = 0; h < KH; ++h) {
-    x.a[h][0] = src[(2 * h) * 32];
-    x.a[h][1] = src[(2 * h + 1) * 32];
-  }
-}
-
-// acc[nb] = (m-tile a of x) . (column block nb of b) = v^.w^ - |w^|^2 / 2.
-template <int KH, int NB>
-__device__ __forceinline__ void super_mma(float (&acc)[NB][4],
-                                          const Super<KH>& x,
-                                          const uint32_t (&b)[NB][KH][2],
-                                          int a) {
-#pragma unroll
-  for (int nb = 0; nb < NB; ++nb) {
-#pragma unroll
-    for (int h = 0; h < KH; ++h) {
-      const uint4 r0 = x.a[h][0], r1 = x.a[h][1];
-      const uint32_t a0 = a ? r0.z : r0.x, a1 = a ? r1.z : r1.x,
-                     a2 = a ? r0.w : r0.y, a3 = a ? r1.w : r1.y;
-      if (h == 0)
-        mma_bf16_z(acc[nb], a0, a1, a2, a3, b[nb][h][0], b[nb][h][1]);
-      else
-        mma_bf16(acc[nb], a0, a1, a2, a3, b[nb][h][0], b[nb][h][1]);
-    }
-  }
-}
-
-// The screen over one leaf for NB 8-query column blocks, one 32-point
-// super-tile (two m16n8k16 m-tiles) per step, with ring_depth - 1 further
-// super-tiles on their way into shared memory (cp.async).
-template <int KH, int NB>
-__device__ __forceinline__ void scan_leaf(
-    const DevTree& t, const ScreenData& sc, int leaf, int npt,
-    const WarpSmem& ws, int lane, const float* __restrict__ qpad,
-    const float* __restrict__ lst_d, const uint32_t* __restrict__ lst_i,
-    int K, int ncol, unsigned long long& kept) {
-  const int g = lane >> 2, tq = lane & 3;
-  const unsigned full = 0xffffffffu;
-  uint32_t b[NB][KH][2];
-  float tn[NB][2];
-#pragma unroll
-  for (int nb = 0; nb < NB; ++nb) {
-#pragma unroll
-    for (int h = 0; h < KH; ++h) {
-      const uint2 v = *reinterpret_cast<const uint2*>(
-          ws.rec + ((nb * 8 + g) * KH + h) * 8 + 2 * tq);
-      b[nb][h][0] = v.x;
-      b[nb][h][1] = v.y;
-    }
-    tn[nb][0] = ws.tneg[nb * 8 + 2 * tq];
-    tn[nb][1] = ws.tneg[nb * 8 + 2 * tq + 1];
-  }
-  const int64_t st = sc.stride;
-  const int64_t hstep = st * 2;  // uint4 per k-half of a leaf
-  const uint4* wb = reinterpret_cast<const uint4*>(sc.words) +
-                    (size_t)leaf * KH * hstep + g * 4 + tq;
-  const int nsup = (npt + 31) >> 5;
-  constexpr int R = ring_depth(KH);
-#pragma unroll
-  for (int j = 0; j < R - 1; ++j) {
-    if (j < nsup) issue_super<KH>(ws, j, lane, wb, hstep, j);
-    cp_async_commit();  // possibly empty: one group per super-tile
-  }
-  int nq = 0;
-  int slot = 0, fill = R - 1;  // stage read now, stage refilled now
-  for (int S = 0; S < nsup; ++S) {
-    // the stage refilled was read in the previous step (its values were
-    // consumed by the multiplications there)
-    if (S + R - 1 < nsup) issue_super<KH>(ws, fill, lane, wb, hstep, S + R - 1);
-    cp_async_commit();
-    cp_async_wait<R - 1>();  // super-tile S has landed
-    Super<KH> x;
-    read_super<KH>(x, ws, slot, lane);
-    slot = slot + 1 == R ? 0 : slot + 1;
-    fill = fill + 1 == R ? 0 : fill + 1;
-    // the hot path only asks whether any pair of the super-tile passes:
-    // per query column the largest D over its 4 rows (2 per m-tile)
-    float cm[NB][2];
-    {
-      float acc[NB][4];
-      super_mma<KH, NB>(acc, x, b, 0);
-#pragma unroll
-      for (int nb = 0; nb < NB; ++nb) {
-        cm[nb][0] = fmaxf(acc[nb][0], acc[nb][2]);
-        cm[nb][1] = fmaxf(acc[nb][1], acc[nb][3]);
-      }
-      super_mma<KH, NB>(acc, x, b, 1);
-#pragma unroll
-      for (int nb = 0; nb < NB; ++nb) {
-        cm[nb][0] = fmax3(cm[nb][0], acc[nb][0], acc[nb][2]);
-        cm[nb][1] = fmax3(cm[nb][1], acc[nb][1], acc[nb][3]);
-      }
-    }
-    bool any = false;
-#pragma unroll
-    for (int nb = 0; nb < NB; ++nb)
-      any = any || cm[nb][0] > tn[nb][0] || cm[nb][1] > tn[nb][1];
-    if (__any_sync(full, any)) {
-      // rare: multiply again and collect the passing pairs; bit
-      // 16 a + 8 r + 2 nb + p = row 8 r + g of m-tile a, column
-      // 8 nb + 2 tq + p, so ascending bits append tile by tile, rows g
-      // before rows g + 8, lanes ascending: ascending slot order within
-      // every column
-      uint32_t keep = 0;
-#pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        float acc[NB][4];
-        super_mma<KH, NB>(acc, x, b, a);
-#pragma unroll
-        for (int nb = 0; nb < NB; ++nb) {
-          const int s0 = 16 * a + 2 * nb;
-          keep |= (acc[nb][0] > tn[nb][0] ? 1u : 0u) << s0;
-          keep |= (acc[nb][1] > tn[nb][1] ? 1u : 0u) << (s0 + 1);
-          keep |= (acc[nb][2] > tn[nb][0] ? 1u : 0u) << (s0 + 8);
-          keep |= (acc[nb][3] > tn[nb][1] ? 1u : 0u) << (s0 + 9);
-        }
-      }
-      uint32_t U = __reduce_or_sync(full, keep);
-      while (U) {
-        const int bit = __ffs(U) - 1;
-        U &= U - 1u;
-        const bool kk = (keep >> bit) & 1u;
-        const unsigned m = __ballot_sync(full, kk);
-        const int n = __popc(m);
-        if (nq + n > kQueue) {
-          drain(t, leaf, qpad, lst_d, lst_i, K, ws, lane, nq, ncol);
-          nq = 0;
-        }
-        if (kk)
-          ws.queue[nq + __popc(m & ((1u << lane) - 1u))] =
-              ((uint32_t)(S * 32 + (bit >> 4) * 16 + ((bit >> 3) & 1) * 8 + g)
-               << 5) |
-              (uint32_t)(((bit >> 1) & 3) * 8 + 2 * tq + (bit & 1));
-        nq += n;
-        kept += (unsigned long long)n;
-      }
-    }
-  }
-  cp_async_wait<0>();  // only empty groups remain; the ring is free
-  if (nq) drain(t, leaf, qpad, lst_d, lst_i, K, ws, lane, nq, ncol);
-}
-
-// Lane c < w.count: query id, current bound, bf16 offsets (B record) and
-// the screen threshold of query column c; other lanes: an unused column.
+// Column e of item (leaf, start, count), prepared by its column group g:
+// the query operand row of B (group g's buffer), the query's padded
+// coordinates, id and list bound.  A column whose list is not full yet
+// (bound +inf: every point may enter) is marked for an exact scan of the
+// whole leaf and screened out (threshold -2^126); rows e >= count are
+// padding columns (never kept).
 template <int KH>
 __device__ __forceinline__ void setup_column(
-    const DevTree& t, const ScreenData& sc, const Item& w, int lane,
-    const uint32_t* __restrict__ act, const float* __restrict__ qpad,
-    const float* __restrict__ lst_d, int K, const WarpSmem& ws) {
-  const float inf = __int_as_float(0x7f800000);
-  uint32_t* rec = ws.rec + lane * KH * 8;
-  float tneg = inf;  // unused columns keep nothing
-  if (lane < w.count) {
-    const uint32_t q = act[w.start + lane];
-    ws.qid[lane] = q;
+    const DevTree& t, const ScreenData& sc, int leaf, int start, int count,
+    int e, int g, const uint32_t* __restrict__ act,
+    const float* __restrict__ qpad, const float* __restrict__ lst_d, int K,
+    const Smem& sm) {
+  uint8_t* gp = sm.grp(g);
+  float* qc = reinterpret_cast<float*>(gp + sm.L.qc) + e * t.Dp;
+  uint32_t* colq = reinterpret_cast<uint32_t*>(gp + sm.L.colq);
+  float* colb = reinterpret_cast<float*>(gp + sm.L.colb);
+  uint32_t* colx = reinterpret_cast<uint32_t*>(gp + sm.L.colx);
+  const int d = t.d;
+  uint16_t th = 0xfe80, tm = 0, tl = 0;  // -2^126: never kept
+  float vq[16 * KH];
+#pragma unroll
+  for (int i = 0; i < 16 * KH; ++i) vq[i] = 0.f;
+  if (e < count) {
+    const uint32_t q = act[start + e];
     const float bound = lst_d[(size_t)q * K + K - 1];
-    ws.bound[lane] = bound;
-    ws.flag[lane] = 0u;
+    colq[e] = q;
+    colb[e] = bound;
+    colx[e] = isinf(bound) ? 1u : 0u;
     const float* qp = qpad + (size_t)q * t.Dp;
-    const float* c = sc.center + (size_t)w.leaf * t.d;
+    const float* c = sc.center + (size_t)leaf * d;
+    for (int i = 0; i < t.Dp; ++i) qc[i] = qp[i];
     float qn = 0.f, ss = 0.f;  // |v^|^2 rounded to nearest / upward
-#pragma unroll
-    for (int h = 0; h < KH; ++h)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        // slots: v^ (0..d-1), then -1/2 twice against the point's norm
-        const int k0 = 16 * h + 2 * j, d = t.d;
-        const float a0 = k0 < d ? __fsub_rn(qp[k0], c[k0])
-                                : (k0 < d + 2 ? -0.5f : 0.f);
-        const float a1 = k0 + 1 < d ? __fsub_rn(qp[k0 + 1], c[k0 + 1])
-                                    : (k0 + 1 < d + 2 ? -0.5f : 0.f);
-        const uint32_t wd = pack_bf16(a0, a1);
-        rec[h * 8 + (j < 4 ? 2 * j : 2 * (j - 4) + 1)] = wd;
-        const float v0 = k0 < d ? bf16_lo(wd) : 0.f;
-        const float v1 = k0 + 1 < d ? bf16_hi(wd) : 0.f;
-        qn = __fmaf_rn(v0, v0, qn);
-        qn = __fmaf_rn(v1, v1, qn);
-        ss = __fmaf_ru(v0, v0, ss);
-        ss = __fmaf_ru(v1, v1, ss);
-      }
-    if (isinf(bound)) {
-      tneg = -inf;  // list not full: every point is a candidate
-    } else {
-      // T of the header comment, every step rounded upward (divisors
+    for (int i = 0; i < d; ++i) {
+      const float v = bf16_value(bf16_bits(__fsub_rn(qp[i], c[i])));
+      vq[i] = v;
+      qn = __fmaf_rn(v, v, qn);
+      ss = __fmaf_ru(v, v, ss);
+    }
+    if (!isinf(bound)) {
+      // thr of the header comment, every step rounded upward (divisors
       // downward) so that the float result is never too small
       const float rho = 0x1p-8f * 1.0001f;  // bf16: 8 significant bits
       const float rr = __fdiv_ru(rho, __fsub_rd(1.f, rho));
-      const float one_m_g = __fsub_rd(1.f, (float)(t.d + 3) * 0x1p-24f);
+      const float one_m_g = __fsub_rd(1.f, (float)(d + 3) * 0x1p-24f);
       const float aq = __fadd_ru(__fmul_ru(rr, __fsqrt_ru(ss)), 0x1p-123f);
       const float R =
           __fsqrt_ru(__fdiv_ru(__fadd_ru(bound, 0x1p-120f), one_m_g));
-      const float Rb = __fadd_ru(__fadd_ru(R, aq), sc.bmax[w.leaf]);
-      const float E = __fmul_ru(0x1p-14f, __fadd_ru(ss, sc.pnmax[w.leaf]));
-      const float thr = __fsub_ru(__fadd_ru(__fmul_ru(Rb, Rb), E), qn);
-      tneg = -0.5f * thr;  // exact scale
+      const float Rb = __fadd_ru(__fadd_ru(R, aq), sc.bmax[leaf]);
+      const float Rb2 = __fmul_ru(Rb, Rb);
+      const float E = __fadd_ru(
+          __fmul_ru(0x1p-13f, __fadd_ru(ss, Rb2)),
+          __fadd_ru(__fmul_ru(0x1p-14f, sc.pnmax[leaf]), 0x1p-120f));
+      const float thr = __fsub_ru(__fadd_ru(Rb2, E), qn);
+      // t = thr / 2 split into three bf16 parts; each remainder is exact in
+      // float32 (it keeps at most 16, then 8 significant bits)
+      const float tt = 0.5f * thr;
+      th = bf16_bits(tt);
+      const float r1 = __fsub_rn(tt, bf16_value(th));
+      tm = bf16_bits(r1);
+      const float r2 = __fsub_rn(r1, bf16_value(tm));
+      tl = bf16_bits(r2);
     }
-  } else {
-#pragma unroll
-    for (int i = 0; i < KH * 8; ++i) rec[i] = 0u;
   }
-  ws.tneg[lane] = tneg;
+  // slots: v^ (0..d-1), -1/2, -1/2 against the norm split, the threshold
+  uint16_t hv[16 * KH];
+#pragma unroll
+  for (int i = 0; i < 16 * KH; ++i) hv[i] = bf16_bits(vq[i]);
+  hv[d] = 0xbf00;
+  hv[d + 1] = 0xbf00;
+  hv[d + 2] = th;
+  hv[d + 3] = tm;
+  hv[d + 4] = tl;
+  uint8_t* bop = sm.base + sm.L.bop + g * tile_bytes(KH);
+#pragma unroll
+  for (int kg = 0; kg < 2 * KH; ++kg) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      w[j] = (uint32_t)hv[8 * kg + 2 * j] |
+             ((uint32_t)hv[8 * kg + 2 * j + 1] << 16);
+    *reinterpret_cast<uint4*>(bop + screen_row_offset(e, kg, KH)) =
+        make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// Sorted insertion of (dv, id) into the list Ld/Li of K entries (dv below
+// the last entry); an equal entry already present stays in front.
+__device__ __forceinline__ void insert_entry(float* Ld, uint32_t* Li, int K,
+                                             float dv, uint32_t id) {
+  int pos = K - 1;
+  while (pos > 0 && Ld[pos - 1] > dv) {
+    Ld[pos] = Ld[pos - 1];
+    Li[pos] = Li[pos - 1];
+    --pos;
+  }
+  Ld[pos] = dv;
+  Li[pos] = id;
+}
+
+// Exact rescoring of item (leaf, count, np points) by its column group g
+// (thread e): the queued (point, column) pairs that passed the screen are
+// scored with the float32 chain, then thread e inserts its column's pairs
+// below the bound into the query's list, which it reads from HBM on the
+// first insertion and writes back once.  Columns marked for a full scan
+// (list not full at setup), and every column after a queue overflow, are
+// scored against every point of the leaf instead.
+__device__ void rescore_item(const DevTree& t, int leaf, int count, int np,
+                             int e, int g, int K, float* __restrict__ lst_d,
+                             uint32_t* __restrict__ lst_i, const Smem& sm,
+                             Counters* ctr) {
+  uint8_t* gp = sm.grp(g);
+  const float* qc = reinterpret_cast<const float*>(gp + sm.L.qc);
+  const uint32_t* colq = reinterpret_cast<const uint32_t*>(gp + sm.L.colq);
+  const float* colb = reinterpret_cast<const float*>(gp + sm.L.colb);
+  const uint32_t* colx = reinterpret_cast<const uint32_t*>(gp + sm.L.colx);
+  const uint32_t* queue = reinterpret_cast<const uint32_t*>(gp + sm.L.queue);
+  float* qd = reinterpret_cast<float*>(gp + sm.L.qd);
+  const int nq = min((int)sm.misc()[2 + g], kQcap);
+  const bool ovf = sm.misc()[4 + g] != 0;
+  if (e == 0) {
+    atomicAdd(&ctr->screen_queued, (unsigned long long)sm.misc()[2 + g]);
+    if (ovf) atomicAdd(&ctr->screen_overflow, 1ull);
+  }
+  const uint32_t slot0 = (uint32_t)((int64_t)leaf * t.lcap);
+  if (!ovf)
+    for (int i = e; i < nq; i += kGrpThreads) {
+      const uint32_t en = queue[i];
+      qd[i] = exact_dist(qc + (en & 127u) * t.Dp, t.pts, t.Dp,
+                         slot0 + (en >> 7));
+    }
+  group_sync(g);
+  if (e < count) {
+    float Ld[BKD_MAX_K + 1];
+    uint32_t Li[BKD_MAX_K + 1];
+    float bound = colb[e];
+    bool loaded = false;
+    const uint32_t q = colq[e];
+    auto take_pair = [&](float dv, uint32_t id) {
+      if (!(dv < bound)) return;
+      if (!loaded) {
+        for (int j = 0; j < K; ++j) {
+          Ld[j] = lst_d[(size_t)q * K + j];
+          Li[j] = lst_i[(size_t)q * K + j];
+        }
+        loaded = true;
+      }
+      insert_entry(Ld, Li, K, dv, id);
+      bound = Ld[K - 1];
+    };
+    if (ovf || colx[e]) {
+      for (int u = 0; u < np; ++u)
+        take_pair(exact_dist(qc + e * t.Dp, t.pts, t.Dp, slot0 + u),
+                  slot0 + u);
+    } else {
+      for (int i = 0; i < nq; ++i) {
+        const uint32_t en = queue[i];
+        if ((int)(en & 127u) == e) take_pair(qd[i], slot0 + (en >> 7));
+      }
+    }
+    if (loaded)
+      for (int j = 0; j < K; ++j) {
+        lst_d[(size_t)q * K + j] = Ld[j];
+        lst_i[(size_t)q * K + j] = Li[j];
+      }
+  }
+  group_sync(g);  // the group's queue and column data are free again
 }
 
 template <int KH>
-__global__ void __launch_bounds__(kScrThreads, KH == 1 ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, 2)
     screen_kernel(DevTree t, ScreenData sc, const Item* __restrict__ items,
                   int item_lo, int item_hi, Counters* ctr,
                   const uint32_t* __restrict__ act,
                   const float* __restrict__ qpad, float* __restrict__ lst_d,
                   uint32_t* __restrict__ lst_i, int K) {
-  extern __shared__ __align__(16) uint32_t smem_words[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const WarpSmem ws = warp_smem<KH>(smem_words, warp, K);
-  unsigned long long kept = 0;
-  // items are taken one at a time from a launch-wide counter: their costs
-  // differ (leaf size, column blocks, rescoring), a static split leaves SMs
-  // idle at the end of the launch
-  for (;;) {
-    int it = 0;
-    if (lane == 0) it = atomicAdd(&ctr->screen_next, 1);
-    it = __shfl_sync(0xffffffffu, it, 0) + item_lo;
-    if (it >= item_hi) break;
-    const Item w = items[it];
-    setup_column<KH>(t, sc, w, lane, act, qpad, lst_d, K, ws);
-    __syncwarp();
-    const int npt = t.leaf_cnt[w.leaf];
-    const int ncol = w.count;
-    switch ((ncol + 7) >> 3) {
-      case 1:
-        scan_leaf<KH, 1>(t, sc, w.leaf, npt, ws, lane, qpad, lst_d, lst_i, K,
-                         ncol, kept);
-        break;
-      case 2:
-        scan_leaf<KH, 2>(t, sc, w.leaf, npt, ws, lane, qpad, lst_d, lst_i, K,
-                         ncol, kept);
-        break;
-      case 3:
-        scan_leaf<KH, 3>(t, sc, w.leaf, npt, ws, lane, qpad, lst_d, lst_i, K,
-                         ncol, kept);
-        break;
-      default:
-        scan_leaf<KH, 4>(t, sc, w.leaf, npt, ws, lane, qpad, lst_d, lst_i, K,
-                         ncol, kept);
-        break;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  Smem sm;
+  sm.base = smem_raw;
+  sm.base_u32 = (uint32_t)__cvta_generic_to_shared(smem_raw);
+  sm.L = layout_of(KH, t.Dp);
+  sm.S = ring_stages(KH);
+  const int S = sm.S;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile int* abort = reinterpret_cast<volatile int*>(sm.misc() + 1);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(sm.afull(s), 1);
+      mbar_init(sm.aempty(s), 1);
     }
-    if (lane < ncol && (ws.flag[lane] & 2u)) {
-      const uint32_t q = ws.qid[lane];
-      for (int j = 0; j < K; ++j) {
-        lst_d[(size_t)q * K + j] = ws.ld[lane * K + j];
-        lst_i[(size_t)q * K + j] = ws.li[lane * K + j];
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(sm.accfull(b), 1);
+      mbar_init(sm.accempty(b), kEpiThreads);
+      mbar_init(sm.bready(b), kGrpThreads);
+      mbar_init(sm.epidone(b), kEpiThreads);
+      mbar_init(sm.qfree(b), kGrpThreads);
+    }
+    for (int i = 0; i < kItemRing; ++i) {
+      mbar_init(sm.itemfull(i), 1);
+      mbar_init(sm.itemempty(i), 1 + kEpiThreads + kGrpThreads);
+    }
+    for (int i = 1; i < 8; ++i) sm.misc()[i] = 0;
+    mbar_init_fence();
+  }
+  if (warp == 1) {
+    asm volatile(
+        "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::
+            "r"(sm.base_u32 + sm.L.misc),
+        "r"(kTmemCols)
+        : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;"
+                 ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm.misc()[0];
+  const int64_t tiles = sc.tiles;
+  const uint8_t* words = reinterpret_cast<const uint8_t*>(sc.words);
+
+  if (warp == 0) {
+    // ------------------------------------------------------- producer
+    // (item_hi < 0: this round's item count, read on the device)
+    const int hi = item_hi >= 0 ? item_hi : ctr->n_items;
+    if (lane == 0) {
+      uint32_t c = 0;  // tiles issued
+      uint32_t last[8];  // last tile issued into each ring slot + 1
+      for (int s = 0; s < S; ++s) last[s] = 0;
+      for (int n = 0;; ++n) {
+        const int ir = n % kItemRing;
+        if (!bar_wait(sm.itemempty(ir), ((n / kItemRing) & 1) ^ 1, abort,
+                      ctr))
+          break;
+        const int it = atomicAdd(&ctr->screen_next, 1) + item_lo;
+        if (it >= hi) {
+          // two end marks: one for each column group
+          sm.items()[ir] = make_int4(-1, 0, 0, 0);
+          bar_arrive(sm.itemfull(ir));
+          const int ir2 = (n + 1) % kItemRing;
+          if (bar_wait(sm.itemempty(ir2), (((n + 1) / kItemRing) & 1) ^ 1,
+                       abort, ctr)) {
+            sm.items()[ir2] = make_int4(-1, 0, 0, 0);
+            bar_arrive(sm.itemfull(ir2));
+          }
+          break;
+        }
+        const Item w = items[it];
+        const int nt = (t.leaf_cnt[w.leaf] + kScreenRows - 1) / kScreenRows;
+        sm.items()[ir] = make_int4(w.leaf, w.start, w.count, nt);
+        bar_arrive(sm.itemfull(ir));
+        const uint8_t* src = words + (size_t)w.leaf * tiles * tile_bytes(KH);
+        bool ok = true;
+        for (int ti = 0; ti < nt; ++ti, ++c) {
+          const int s = c % S;
+          if (!bar_wait(sm.aempty(s), ((c / S) & 1) ^ 1, abort, ctr)) {
+            ok = false;
+            break;
+          }
+          bulk_load(sm.ring_u32(s, KH), src + (size_t)ti * tile_bytes(KH),
+                    tile_bytes(KH), sm.afull(s));
+          last[s] = c + 1;
+        }
+        if (!ok) break;
+      }
+      if (c)
+        atomicAdd(&ctr->screen_bytes,
+                  (unsigned long long)c * tile_bytes(KH));
+      // copies still in flight land before the CTA leaves
+      for (int s = 0; s < S; ++s)
+        if (last[s]) {
+          const uint32_t cl = last[s] - 1;
+          const long long t0 = clock64();
+          while (!bar_try(sm.afull(s), (cl / S) & 1) &&
+                 clock64() - t0 < (1ll << 31)) {
+          }
+        }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      uint32_t c = 0;  // tiles consumed
+      bool issued = false;
+      for (int n = 0;; ++n) {
+        const int ir = n % kItemRing;
+        if (!bar_wait(sm.itemfull(ir), (n / kItemRing) & 1, abort, ctr))
+          break;
+        const int4 dsc = sm.items()[ir];
+        bar_arrive(sm.itemempty(ir));
+        if (dsc.x < 0) break;
+        const int g = n & 1;
+        if (!bar_wait(sm.bready(g), (n >> 1) & 1, abort, ctr)) break;
+        const uint32_t idesc = mma_idesc((dsc.z + 15) & ~15);
+        const uint32_t bop = sm.bop_u32(g, KH);
+        bool ok = true;
+        for (int ti = 0; ti < dsc.w; ++ti, ++c) {
+          const int s = c % S, b = c & 1;
+          if (!bar_wait(sm.afull(s), (c / S) & 1, abort, ctr) ||
+              !bar_wait(sm.accempty(b), ((c >> 1) & 1) ^ 1, abort, ctr)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = sm.ring_u32(s, KH);
+#pragma unroll
+          for (int h = 0; h < KH; ++h)
+            tc_mma(tmem + (uint32_t)b * kAccCols, op_desc(a0 + 256u * h, KH),
+                   op_desc(bop + 256u * h, KH), idesc, h > 0 ? 1u : 0u);
+          tc_commit(sm.aempty(s));
+          tc_commit(sm.accfull(b));
+          issued = true;
+        }
+        if (!ok) break;
+      }
+      if (issued) {
+        // the last MMA (and with it every earlier one) has completed
+        const uint32_t cl = c - 1;
+        const long long t0 = clock64();
+        while (!bar_try(sm.accfull(cl & 1), (cl >> 1) & 1) &&
+               clock64() - t0 < (1ll << 31)) {
+        }
       }
     }
-    __syncwarp();
+  } else if (warp < 6) {
+    // ------------------------------------------------------- epilogue
+    // Every decision to leave is taken by all 128 epilogue threads together
+    // (an OR over the group at its named barrier); a failed wait inside an
+    // item only skips that tile's accumulator reads (warp-uniform, as
+    // tcgen05.ld requires).
+    const int quarter = warp & 3;  // tensor-memory lanes 32 quarter ..
+    const int row = 32 * quarter + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
+    uint32_t c = 0;
+    unsigned long long kept = 0;
+    for (int n = 0;; ++n) {
+      const int ir = n % kItemRing, g = n & 1;
+      bool got = bar_wait(sm.itemfull(ir), (n / kItemRing) & 1, abort, ctr);
+      int4 dsc = make_int4(-1, 0, 0, 0);
+      if (got) {
+        dsc = sm.items()[ir];
+        bar_arrive(sm.itemempty(ir));
+      }
+      // the group's queue is free once it rescored its previous item
+      if (got && dsc.x >= 0)
+        got = bar_wait(sm.qfree(g), ((n >> 1) & 1) ^ 1, abort, ctr);
+      if (threadIdx.x == 64 && got) {
+        sm.misc()[2 + g] = 0;
+        sm.misc()[4 + g] = 0;
+      }
+      if (sync128_or<1>(!got) || dsc.x < 0) break;
+      const int nt = dsc.w, ncol = (dsc.z + 15) & ~15;
+      uint32_t* queue =
+          reinterpret_cast<uint32_t*>(sm.grp(g) + sm.L.queue);
+      bool ok = true;
+      for (int ti = 0; ti < nt; ++ti, ++c) {
+        const int b = c & 1;
+        const bool gt = __all_sync(
+            0xffffffffu, bar_wait(sm.accfull(b), (c >> 1) & 1, abort, ctr));
+        ok = ok && gt;
+        const uint32_t ta = lane_base + (uint32_t)b * kAccCols;
+        uint32_t mask[4] = {0u, 0u, 0u, 0u};
+        if (gt) tc_fence_after();
+#pragma unroll 1
+        for (int c0 = 0; gt && c0 < ncol; c0 += 32) {
+          float v[32];
+          if (c0 + 32 <= ncol) {
+            tc_ld32(ta + (uint32_t)c0, v);
+          } else {
+            tc_ld16(ta + (uint32_t)c0, v);
+#pragma unroll
+            for (int i = 16; i < 32; ++i) v[i] = -INFINITY;
+          }
+          float m[11];
+#pragma unroll
+          for (int i = 0; i < 10; ++i)
+            m[i] = fmax3(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
+          m[10] = fmaxf(v[30], v[31]);
+          const float mm = fmax3(fmax3(m[0], m[1], m[2]),
+                                 fmax3(m[3], m[4], m[5]),
+                                 fmax3(fmax3(m[6], m[7], m[8]), m[9], m[10]));
+          if (mm > 0.f) {
+            uint32_t bits = 0u;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) bits |= (v[i] > 0.f ? 1u : 0u) << i;
+            mask[c0 >> 5] = bits;
+          }
+        }
+        if (gt) {
+          tc_fence_before();
+          bar_arrive(sm.accempty(b));
+        }
+        // rare: queue this row's passing columns for the column group
+        const int np = __popc(mask[0]) + __popc(mask[1]) + __popc(mask[2]) +
+                       __popc(mask[3]);
+        if (np) {
+          kept += np;
+          int at = (int)atomicAdd(sm.misc() + 2 + g, (uint32_t)np);
+          const uint32_t u = (uint32_t)(ti * kScreenRows + row);
+          for (int w = 0; w < 4; ++w)
+            for (uint32_t mw = mask[w]; mw; mw &= mw - 1u, ++at)
+              if (at < kQcap)
+                queue[at] = (u << 7) | (uint32_t)(32 * w + __ffs(mw) - 1);
+          if (at > kQcap) sm.misc()[4 + g] = 1;
+        }
+      }
+      // queue complete: the column group may rescore
+      bar_arrive(sm.epidone(g));
+      if (sync128_or<1>(!ok)) break;
+    }
+    if (kept) atomicAdd(&ctr->screen_kept, kept);
+  } else {
+    // ------------------------------------------------- column groups
+    // Group g takes the items n = g, g + 2, ...: it prepares the query
+    // operand of item n, and once the epilogue has queued item n's
+    // survivors it rescores them; meanwhile the other group's item runs on
+    // the tensor cores.
+    const int g = (warp - 6) >> 2;
+    const int e = threadIdx.x - 64 - kEpiThreads - g * kGrpThreads;
+    for (int n = g;; n += 2) {
+      const int ir = n % kItemRing;
+      const bool got =
+          bar_wait(sm.itemfull(ir), (n / kItemRing) & 1, abort, ctr);
+      int4 dsc = make_int4(-1, 0, 0, 0);
+      if (got) {
+        dsc = sm.items()[ir];
+        bar_arrive(sm.itemempty(ir));
+      }
+      if (group_sync_or(g, !got) || dsc.x < 0) break;
+      setup_column<KH>(t, sc, dsc.x, dsc.y, dsc.z, e, g, act, qpad, lst_d, K,
+                       sm);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bar_arrive(sm.bready(g));
+      const bool done =
+          bar_wait(sm.epidone(g), (n >> 1) & 1, abort, ctr);
+      if (group_sync_or(g, !done)) break;
+      rescore_item(t, dsc.x, dsc.z, t.leaf_cnt[dsc.x], e, g, K, lst_d, lst_i,
+                   sm, ctr);
+      bar_arrive(sm.qfree(g));
+    }
   }
-  if (lane == 0 && kept) atomicAdd(&ctr->screen_kept, kept);
-}
-
-size_t screen_smem(int kh, int K) {
-  return (size_t)kScrWarps * warp_words(kh, K) * 4;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::
+                     "r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
 }
 
 const void* screen_kernel_for(int kh) {
@@ -544,23 +800,113 @@ const void* screen_kernel_for(int kh) {
   }
 }
 
+// Dynamic shared memory of a launch: the layout, raised if needed so that
+// at most two CTAs share an SM (two accumulator pairs fill its tensor
+// memory: an allocation never has to wait for another CTA).
+size_t screen_smem(int kh, int Dp) {
+  const size_t need = layout_of(kh, Dp).total;
+  return std::max<size_t>(need, 80 * 1024);
+}
+
+// ------------------------------------------------------------ MMA probe
+// One CTA per instance: D = A Bt^T with A 128 x 16 kh, Bt n x 16 kh (bf16,
+// row-major), through the screen's operand layout, descriptors, KH chained
+// MMAs into tensor memory and tcgen05.ld.
+template <int KH>
+__global__ void __launch_bounds__(128)
+    umma_probe_kernel(int n, const uint16_t* __restrict__ A,
+                      const uint16_t* __restrict__ Bt, float* __restrict__ D,
+                      Counters* ctr) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  const uint32_t base = (uint32_t)__cvta_generic_to_shared(smem_raw);
+  const uint32_t aoff = 0, boff = tile_bytes(KH),
+                 baroff = boff + 2 * tile_bytes(KH), toff = baroff + 8;
+  const int inst = blockIdx.x, tid = threadIdx.x, warp = tid >> 5;
+  const uint16_t* a = A + (size_t)inst * 128 * 16 * KH;
+  const uint16_t* bt = Bt + (size_t)inst * n * 16 * KH;
+  for (int kg = 0; kg < 2 * KH; ++kg) {
+    *reinterpret_cast<uint4*>(smem_raw + aoff +
+                              screen_row_offset(tid, kg, KH)) =
+        *reinterpret_cast<const uint4*>(a + (size_t)tid * 16 * KH + 8 * kg);
+    for (int r = tid; r < n; r += 128)
+      *reinterpret_cast<uint4*>(smem_raw + boff +
+                                screen_row_offset(r, kg, KH)) =
+          *reinterpret_cast<const uint4*>(bt + (size_t)r * 16 * KH + 8 * kg);
+  }
+  if (tid == 0) {
+    mbar_init(base + baroff, 1);
+    mbar_init_fence();
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == 0) {
+    asm volatile(
+        "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::
+            "r"(base + toff),
+        "r"(256u)
+        : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;"
+                 ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *reinterpret_cast<uint32_t*>(smem_raw + toff);
+  if (tid == 0) {
+    for (int h = 0; h < KH; ++h)
+      tc_mma(tmem, op_desc(base + aoff + 256u * h, KH),
+             op_desc(base + boff + 256u * h, KH), mma_idesc(n),
+             h > 0 ? 1u : 0u);
+    tc_commit(base + baroff);
+  }
+  const long long t0 = clock64();
+  bool ok = true;
+  while (!bar_try(base + baroff, 0)) {
+    if (clock64() - t0 > (1ll << 31)) {
+      ok = false;
+      break;
+    }
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(&ctr->err, kErrTimeout);
+  } else {
+    tc_fence_after();
+    const uint32_t lb = tmem + ((uint32_t)(32 * warp) << 16);
+    for (int c0 = 0; c0 < n; c0 += 16) {
+      float v[16];
+      tc_ld16(lb + (uint32_t)c0, v);
+      for (int i = 0; i < 16; ++i)
+        D[((size_t)inst * 128 + tid) * n + c0 + i] = v[i];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::
+                     "r"(tmem),
+                 "r"(256u)
+                 : "memory");
+}
+
 }  // namespace
 
-int screen_grid(int kh, int64_t lcap, int K, int sm_count) {
-  // slots in a queue entry: 27 bits
+int screen_grid(int kh, int Dp, int64_t lcap, int K, int sm_count) {
   if (kh < 1 || kh > 3 || K < 1 || K > BKD_MAX_K + 1 ||
-      lcap >= ((int64_t)1 << 27))
+      lcap >= ((int64_t)1 << 24))
     return 0;
-  const size_t smem = screen_smem(kh, K);
+  const size_t smem = screen_smem(kh, Dp);
   const void* k = screen_kernel_for(kh);
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (smem > 227 * 1024 ||
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return 0;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kScrThreads,
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads,
                                                     smem) != cudaSuccess ||
       per_sm < 1)
     return 0;
+  // tensor memory: 512 columns per SM, kTmemCols per CTA
+  if (per_sm * kTmemCols > 512) return 0;
   return per_sm * sm_count;
 }
 
@@ -569,23 +915,26 @@ cudaError_t launch_screen(const DevTree& t, const ScreenData& sd,
                           Counters* ctr, const uint32_t* act,
                           const float* qpad, float* lst_d, uint32_t* lst_i,
                           int K, int grid, cudaStream_t s) {
-  const int n = item_hi - item_lo;
-  if (n <= 0 || grid <= 0) return cudaSuccess;
-  grid = std::min(grid, (n + kScrWarps - 1) / kScrWarps);
-  const size_t smem = screen_smem(sd.kh, K);
+  if (item_hi >= 0) {
+    const int n = item_hi - item_lo;
+    if (n <= 0) return cudaSuccess;
+    grid = std::min(grid, n);
+  }
+  if (grid <= 0) return cudaSuccess;
+  const size_t smem = screen_smem(sd.kh, t.Dp);
   cudaError_t e = cudaMemsetAsync(&ctr->screen_next, 0, sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
   switch (sd.kh) {
     case 1:
-      screen_kernel<1><<<grid, kScrThreads, smem, s>>>(
+      screen_kernel<1><<<grid, kThreads, smem, s>>>(
           t, sd, items, item_lo, item_hi, ctr, act, qpad, lst_d, lst_i, K);
       break;
     case 2:
-      screen_kernel<2><<<grid, kScrThreads, smem, s>>>(
+      screen_kernel<2><<<grid, kThreads, smem, s>>>(
           t, sd, items, item_lo, item_hi, ctr, act, qpad, lst_d, lst_i, K);
       break;
     case 3:
-      screen_kernel<3><<<grid, kScrThreads, smem, s>>>(
+      screen_kernel<3><<<grid, kThreads, smem, s>>>(
           t, sd, items, item_lo, item_hi, ctr, act, qpad, lst_d, lst_i, K);
       break;
     default:
@@ -595,3 +944,60 @@ cudaError_t launch_screen(const DevTree& t, const ScreenData& sd,
 }
 
 }  // namespace bkd
+
+// Test support (declared in bkd.h): the screen's MMA path on given operands.
+extern "C" int bkd_probe_umma(int n, int kh, int count, const uint16_t* A,
+                              const uint16_t* Bt, float* D) {
+  using namespace bkd;
+  set_error(BKD_OK, "");
+  if (kh < 1 || kh > 3 || n < 16 || n > 256 || n % 16 != 0)
+    return set_error(BKD_EINVAL, "n must be 16..256 (multiple of 16), kh 1..3");
+  if (count < 0 || count > (1 << 16))
+    return set_error(BKD_EINVAL, "count out of range");
+  if (count == 0) return BKD_OK;
+  if (!A || !Bt || !D) return set_error(BKD_EINVAL, "NULL argument");
+  const size_t na = (size_t)count * 128 * 16 * kh * 2,
+               nb = (size_t)count * n * 16 * kh * 2,
+               nd = (size_t)count * 128 * n * 4;
+  char* buf = nullptr;
+  cudaError_t e = dev_malloc(&buf, na + nb + nd + sizeof(Counters));
+  if (e != cudaSuccess)
+    return set_error(BKD_ENOMEM, "probe buffers: %s", cudaGetErrorString(e));
+  uint16_t* dA = reinterpret_cast<uint16_t*>(buf);
+  uint16_t* dB = reinterpret_cast<uint16_t*>(buf + na);
+  float* dD = reinterpret_cast<float*>(buf + na + nb);
+  Counters* dC = reinterpret_cast<Counters*>(buf + na + nb + nd);
+  int rc = BKD_OK;
+  // at most two probe CTAs per SM: their tensor-memory allocations (256
+  // columns each) never wait for one another
+  const size_t smem = std::max<size_t>(3 * tile_bytes(kh) + 64, 100 * 1024);
+  const void* kern = kh == 1   ? (const void*)umma_probe_kernel<1>
+                     : kh == 2 ? (const void*)umma_probe_kernel<2>
+                               : (const void*)umma_probe_kernel<3>;
+  if (cudaMemcpy(dA, A, na, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dB, Bt, nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(dC, 0, sizeof(Counters)) != cudaSuccess ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess) {
+    rc = set_error(BKD_ECUDA, "probe set-up failed");
+  } else {
+    if (kh == 1)
+      umma_probe_kernel<1><<<count, 128, smem>>>(n, dA, dB, dD, dC);
+    else if (kh == 2)
+      umma_probe_kernel<2><<<count, 128, smem>>>(n, dA, dB, dD, dC);
+    else
+      umma_probe_kernel<3><<<count, 128, smem>>>(n, dA, dB, dD, dC);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    Counters h{};
+    if (e == cudaSuccess)
+      e = cudaMemcpy(&h, dC, sizeof(Counters), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(D, dD, nd, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+      rc = set_error(BKD_ECUDA, "probe failed: %s", cudaGetErrorString(e));
+    else if (h.err & kErrTimeout)
+      rc = set_error(BKD_ETIMEOUT, "probe MMA did not complete");
+  }
+  cudaFree(buf);
+  return rc;
+}

@@ -12,6 +12,7 @@
 // spread over the warp (lane j holds entry j) and a candidate is inserted iff
 // its distance is strictly below the last entry, so the list ends with the
 // same multiset of k+1 smallest float32 distances as the round-by-round path.
+// Lists of up to 64 entries (k <= 63) take two entries per lane.
 #include "bkd.h"
 #include "k_leaf.cuh"
 #include "traverse.cuh"
@@ -21,7 +22,70 @@ namespace {
 
 constexpr int kTailWarps = 4;
 
-template <int D>
+// The candidate list of K <= 64 entries spread over the warp: lane j holds
+// entry j and, when TWO, entry 32 + j.  Inserting (cd, id) below the bound
+// moves every entry from its sorted position on up by one place.
+template <bool TWO>
+struct WarpList {
+  float d0 = __builtin_huge_valf(), d1 = __builtin_huge_valf();
+  uint32_t i0 = kNoSlot, i1 = kNoSlot;
+  __device__ void load(const float* ld, const uint32_t* li, int K, int lane) {
+    if (lane < K) {
+      d0 = ld[lane];
+      i0 = li[lane];
+    }
+    if (TWO && 32 + lane < K) {
+      d1 = ld[32 + lane];
+      i1 = li[32 + lane];
+    }
+  }
+  __device__ void store(float* ld, uint32_t* li, int K, int lane) const {
+    if (lane < K) {
+      ld[lane] = d0;
+      li[lane] = i0;
+    }
+    if (TWO && 32 + lane < K) {
+      ld[32 + lane] = d1;
+      li[32 + lane] = i1;
+    }
+  }
+  __device__ float bound(int K) const {
+    const unsigned full = 0xffffffffu;
+    if (!TWO || K <= 32) return __shfl_sync(full, d0, K - 1);
+    return __shfl_sync(full, d1, K - 33);
+  }
+  // requires cd below the bound (warp-uniform)
+  __device__ void insert(float cd, uint32_t id, int K, int lane) {
+    const unsigned full = 0xffffffffu;
+    int pos = __popc(__ballot_sync(full, lane < K && d0 <= cd));
+    if (TWO) pos += __popc(__ballot_sync(full, 32 + lane < K && d1 <= cd));
+    const float u0 = __shfl_up_sync(full, d0, 1);
+    const uint32_t v0 = __shfl_up_sync(full, i0, 1);
+    if (TWO) {
+      const float u1 = __shfl_up_sync(full, d1, 1);
+      const uint32_t v1 = __shfl_up_sync(full, i1, 1);
+      const float c31 = __shfl_sync(full, d0, 31);
+      const uint32_t j31 = __shfl_sync(full, i0, 31);
+      const int k1 = 32 + lane;
+      if (k1 > pos) {
+        d1 = lane ? u1 : c31;
+        i1 = lane ? v1 : j31;
+      } else if (k1 == pos) {
+        d1 = cd;
+        i1 = id;
+      }
+    }
+    if (lane > pos) {
+      d0 = u0;
+      i0 = v0;
+    } else if (lane == pos) {
+      d0 = cd;
+      i0 = id;
+    }
+  }
+};
+
+template <int D, bool TWO>
 __global__ void __launch_bounds__(kTailWarps * 32)
     tail_kernel(DevTree t, const float4* __restrict__ pts,
                 const uint32_t* __restrict__ act, int n_act,
@@ -43,13 +107,9 @@ __global__ void __launch_bounds__(kTailWarps * 32)
       const float x = qp[i];
       qq[i] = pk2(x, x);
     }
-    float myd = __int_as_float(0x7f800000);
-    uint32_t myi = kNoSlot;
-    if (lane < K) {
-      myd = lst_d[(size_t)q * K + lane];
-      myi = lst_i[(size_t)q * K + lane];
-    }
-    float bound = __shfl_sync(full, myd, K - 1);
+    WarpList<TWO> L;
+    L.load(lst_d + (size_t)q * K, lst_i + (size_t)q * K, K, lane);
+    float bound = L.bound(K);
     F32Bound<D> bx;
     bx.load(qp);
     // state holds the query's pending leaf: scan it, then walk on
@@ -107,26 +167,14 @@ __global__ void __launch_bounds__(kTailWarps * 32)
           for (int j = 0; j < 4; ++j) {
             const float cd = __shfl_sync(full, e[j], src);
             if (cd < bound) {  // warp-uniform
-              const int pos = __popc(__ballot_sync(full, lane < K && myd <= cd));
-              const float upd = __shfl_up_sync(full, myd, 1);
-              const uint32_t upi = __shfl_up_sync(full, myi, 1);
-              if (lane > pos) {
-                myd = upd;
-                myi = upi;
-              } else if (lane == pos) {
-                myd = cd;
-                myi = id + j;
-              }
-              bound = __shfl_sync(full, myd, K - 1);
+              L.insert(cd, id + j, K, lane);
+              bound = L.bound(K);
             }
           }
         }
       }
     }
-    if (lane < K) {
-      lst_d[(size_t)q * K + lane] = myd;
-      lst_i[(size_t)q * K + lane] = myi;
-    }
+    L.store(lst_d + (size_t)q * K, lst_i + (size_t)q * K, K, lane);
     if (lane == 0) state[q] = trav_state(kDone, 0u);
   }
   if (lane == 0 && visits) {
@@ -137,9 +185,14 @@ __global__ void __launch_bounds__(kTailWarps * 32)
 
 #define BKD_TAIL_CASE(DIM)                                                   \
   case DIM:                                                                  \
-    tail_kernel<DIM><<<grid, kTailWarps * 32, 0, s>>>(                       \
-        t, reinterpret_cast<const float4*>(pts), act, n_act, state, qpad,    \
-        lst_d, lst_i, K, ctr);                                               \
+    if (K <= 32)                                                             \
+      tail_kernel<DIM, false><<<grid, kTailWarps * 32, 0, s>>>(              \
+          t, reinterpret_cast<const float4*>(pts), act, n_act, state, qpad,  \
+          lst_d, lst_i, K, ctr);                                             \
+    else                                                                     \
+      tail_kernel<DIM, true><<<grid, kTailWarps * 32, 0, s>>>(               \
+          t, reinterpret_cast<const float4*>(pts), act, n_act, state, qpad,  \
+          lst_d, lst_i, K, ctr);                                             \
     return cudaGetLastError();
 
 }  // namespace
@@ -149,6 +202,7 @@ cudaError_t launch_tail(const DevTree& t, const float* pts,
                         const float* qpad, float* lst_d, uint32_t* lst_i,
                         int K, Counters* ctr, int sm_count, cudaStream_t s) {
   if (n_act <= 0) return cudaSuccess;
+  if (K < 1 || K > 64) return cudaErrorInvalidValue;
   const int grid = std::min((n_act + kTailWarps - 1) / kTailWarps,
                             sm_count * 16);
   switch (t.Dp) { BKD_LEAF_DIMS(BKD_TAIL_CASE) default: break; }

@@ -53,17 +53,27 @@ template <int D>
 __global__ void __launch_bounds__(kFindThreads)
     find_leaf_kernel(DevTree t, const float* __restrict__ qpad,
                      const uint32_t* __restrict__ act, int n_act,
+                     const int32_t* __restrict__ n_act_dev,
                      uint64_t* __restrict__ state,
                      const float* __restrict__ lst_d, int K,
                      int2* __restrict__ placed,
                      int32_t* __restrict__ cnt) {
   const int pos = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pos >= n_act) return;
+  if (pos >= (n_act_dev ? *n_act_dev : n_act)) return;
   const uint32_t q = act[pos];
   const float* qp = qpad + (size_t)q * D;
   const uint64_t st = state[q];
   const int node = state_node(st);
   uint32_t mask = state_mask(st);
+  if (t.chunk_done && node >= 0) {
+    // chunked mode: was the pending leaf's chunk scanned last round?
+    const int leaf = node - ((1 << t.h) - 1);
+    const int c = (int)(((int64_t)leaf * t.n_chunks) >> t.h);
+    if (!t.chunk_done[c]) {
+      placed[pos] = make_int2(leaf, atomicAdd(cnt + leaf, 1));
+      return;  // still buffered there; the traversal waits
+    }
+  }
   const float bound = node == kStart ? __int_as_float(0x7f800000)
                                      : lst_d[(size_t)q * K + (K - 1)];
   F32Bound<D> bx;
@@ -154,7 +164,8 @@ __global__ void __launch_bounds__(kScanBlock)
                       const int32_t* __restrict__ leaf_cnt,
                       const ScanPart* __restrict__ parts,
                       int32_t* __restrict__ off, int32_t* __restrict__ toff,
-                      Item* __restrict__ items, Counters* ctr) {
+                      Item* __restrict__ items, Counters* ctr,
+                      int32_t* __restrict__ n_next_dev) {
   __shared__ int32_t wq[kScanBlock / 32], wt[kScanBlock / 32];
   __shared__ int32_t bq0, bt0;
   __shared__ unsigned long long ptot;
@@ -232,25 +243,35 @@ __global__ void __launch_bounds__(kScanBlock)
     ctr->n_next = xq;
     ctr->n_items = xt;
     ctr->pairs = ptot;
+    ctr->rounds_pairs += ptot;
+    ctr->rounds_visits += (unsigned long long)xq;
+    ctr->rounds_items += (unsigned long long)xt;
+    if (xq > 0) ctr->rounds_run += 1;
+    if (n_next_dev) *n_next_dev = xq;
   }
 }
 
 __global__ void scatter_kernel(const int2* __restrict__ placed,
                                const uint32_t* __restrict__ act, int n,
+                               const int32_t* __restrict__ n_dev,
                                const int32_t* __restrict__ off,
                                uint32_t* __restrict__ next) {
   const int pos = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pos >= n) return;
+  if (pos >= (n_dev ? *n_dev : n)) return;
   const int2 p = placed[pos];
   if (p.x < 0) return;
   next[off[p.x] + p.y] = act[pos];
 }
 
 __global__ void chunk_items_kernel(const int32_t* __restrict__ toff,
+                                   const int32_t* __restrict__ off,
                                    const int32_t* __restrict__ chunk_leaf,
                                    int n_chunks, int32_t* __restrict__ out) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c <= n_chunks) out[c] = toff[chunk_leaf[c]];
+  if (c <= n_chunks) {
+    out[c] = toff[chunk_leaf[c]];
+    out[n_chunks + 1 + c] = off[chunk_leaf[c]];
+  }
 }
 
 __global__ void fill_kernel(int32_t* __restrict__ v, int64_t n,
@@ -301,13 +322,14 @@ cudaError_t launch_init(const float* Q, int64_t m, int d, int Dp, float* qpad,
 cudaError_t launch_find_leaf(const DevTree& t, const float* qpad,
                              const uint32_t* act, int n_act, uint64_t* state,
                              const float* lst_d, int K, int2* placed,
-                             int32_t* cnt, cudaStream_t s) {
+                             int32_t* cnt, cudaStream_t s,
+                             const int32_t* n_act_dev) {
   if (n_act == 0) return cudaSuccess;
 #define BKD_FIND_CASE(DIM)                                                  \
   case DIM:                                                                 \
     find_leaf_kernel<DIM><<<blocks(n_act, kFindThreads), kFindThreads, 0,   \
-                            s>>>(t, qpad, act, n_act, state, lst_d, K,      \
-                                 placed, cnt);                              \
+                            s>>>(t, qpad, act, n_act, n_act_dev, state,     \
+                                 lst_d, K, placed, cnt);                    \
     return cudaGetLastError();
   switch (t.Dp) { BKD_DIMS(BKD_FIND_CASE) default: break; }
 #undef BKD_FIND_CASE
@@ -319,7 +341,8 @@ cudaError_t launch_bucket(const int2* placed, const uint32_t* act,
                           const int32_t* leaf_cnt, const int32_t* cnt,
                           int32_t* off, int32_t* cursor, int32_t* toff,
                           Item* items, uint32_t* next, Counters* ctr,
-                          cudaStream_t s) {
+                          cudaStream_t s, const int32_t* n_act_dev,
+                          int32_t* n_next_dev) {
   // the cursor array (4 bytes per leaf) holds the 16-byte tile sums (one per
   // 2,048 leaves)
   ScanPart* parts = reinterpret_cast<ScanPart*>(cursor);
@@ -328,18 +351,18 @@ cudaError_t launch_bucket(const int2* placed, const uint32_t* act,
                                                   leaf_cnt, parts);
   scan_write_kernel<<<nparts, kScanBlock, 0, s>>>(cnt, n_leaves, tile,
                                                   leaf_cnt, parts, off, toff,
-                                                  items, ctr);
+                                                  items, ctr, n_next_dev);
   if (n_act > 0)
-    scatter_kernel<<<blocks(n_act, 256), 256, 0, s>>>(placed, act, n_act, off,
-                                                      next);
+    scatter_kernel<<<blocks(n_act, 256), 256, 0, s>>>(placed, act, n_act,
+                                                      n_act_dev, off, next);
   return cudaGetLastError();
 }
 
-cudaError_t launch_chunk_items(const int32_t* toff, const int32_t* chunk_leaf,
-                               int n_chunks, int32_t* chunk_item,
-                               cudaStream_t s) {
+cudaError_t launch_chunk_items(const int32_t* toff, const int32_t* off,
+                               const int32_t* chunk_leaf, int n_chunks,
+                               int32_t* chunk_item, cudaStream_t s) {
   chunk_items_kernel<<<blocks(n_chunks + 1, 128), 128, 0, s>>>(
-      toff, chunk_leaf, n_chunks, chunk_item);
+      toff, off, chunk_leaf, n_chunks, chunk_item);
   return cudaGetLastError();
 }
 

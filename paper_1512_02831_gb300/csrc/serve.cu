@@ -333,7 +333,7 @@ int bkd_serve_open(bkd_tree* t, int k_max, int64_t max_queries,
   SV_CU(dev_alloc(&sv->off, L + 1));
   SV_CU(dev_alloc(&sv->cursor, std::max<int64_t>(L, 4)));
   SV_CU(dev_alloc(&sv->toff, L + 1));
-  SV_CU(dev_alloc(&sv->items, Q / kScreenTile + L + 1));
+  SV_CU(dev_alloc(&sv->items, Q / std::min(kScreenTile, kPipeTile) + L + 1));
   SV_CU(dev_alloc(&sv->batch_left, kMaxBatches));
   SV_CU(dev_alloc(&sv->d_ctr, 1));
   SV_CU(dev_alloc(&sv->d_fin, 1));
@@ -347,7 +347,8 @@ int bkd_serve_open(bkd_tree* t, int k_max, int64_t max_queries,
   SV_CU(cudaStreamSynchronize(v.stream));
   sv->grid_max = leaf_kernel_grid(D.Dp, sv->cap, v.sm_count);
   sv->screen_max = v.screen.words
-                       ? screen_grid(v.screen.kh, D.lcap, sv->K, v.sm_count)
+                       ? screen_grid(v.screen.kh, D.Dp, D.lcap, sv->K,
+                                     v.sm_count)
                        : 0;
   if (sv->grid_max <= 0)
     return set_error(BKD_EUNSUPPORTED, "no leaf kernel for d = %d, k = %d",

@@ -12,9 +12,10 @@ has three ingredients, each attacked here:
     just above the point's distance.  A bound that assumed 2^-9 rejects the
     point (worked through in the test's docstring);
   * the tensor core's fp32 accumulation: the probe entry point runs the
-    screen's MMA instruction on adversarial operands and every result is
-    compared with the exact sum against the accumulation model the bound
-    uses (error <= 2^-18 of |c| + sum |a_i b_i| per instruction);
+    screen's tcgen05 path (its operand layout, descriptors and chained
+    MMAs) on adversarial operands and every result is compared with the
+    exact sum against the accumulation model the bound uses (error <=
+    2^-18 of the sum of absolute products per chained k-half);
   * wide data: a large common offset, queries far outside the tree's box,
     leaves of tiny spread, and d = 17 / 32 (two and three k-halves).
 """
@@ -101,104 +102,128 @@ def bf16_bits(x: np.ndarray) -> np.ndarray:
 
 
 def bf16_value(b: np.ndarray) -> np.ndarray:
-    return (b.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    return (np.asarray(b).astype(np.uint32) << 16).view(np.float32) \
+        .astype(np.float64)
 
 
-def exact_dots(A, Bt, C):
-    """Exact C + A Bt^T per instance with math.fsum (bf16 products are exact
-    in binary64; fsum rounds the exact sum once), and the sum of absolute
-    terms."""
+def exact_dots(A, Bt):
+    """Exact A Bt^T per instance with math.fsum (bf16 products are exact in
+    binary64; fsum rounds the exact sum once) and the sums of the absolute
+    products."""
     a, b = bf16_value(A), bf16_value(Bt)
-    cnt = A.shape[0]
-    out = np.empty((cnt, 16, 8))
-    mag = np.empty((cnt, 16, 8))
+    cnt, rows, _ = a.shape
+    n = b.shape[1]
+    out = np.empty((cnt, rows, n))
+    mag = np.einsum("irk,ick->irc", np.abs(a), np.abs(b))
     for i in range(cnt):
-        prod = a[i][:, None, :] * b[i][None, :, :]      # 16 x 8 x 16
-        for r in range(16):
-            for c in range(8):
-                terms = list(prod[r, c]) + [float(C[i, r, c])]
-                out[i, r, c] = math.fsum(terms)
-                mag[i, r, c] = math.fsum(abs(t) for t in terms)
+        prod = a[i][:, None, :] * b[i][None, :, :]
+        for r in range(rows):
+            for c in range(n):
+                out[i, r, c] = math.fsum(prod[r, c])
     return out, mag
 
 
-def adversarial_operands(rng, cnt):
-    """Instances of several kinds (a quarter each): one large product with
-    fifteen small same-sign ones just under the large one's last bits;
-    heavy cancellation (pairs of equal and opposite large products) with
-    small terms; exponents mixed over 2^-30..2^30 inside one k-half; the
-    screen's own shape (offsets, the norm split pn_hi / pn_lo against -1/2,
-    a large accumulator input)."""
-    A = np.zeros((cnt, 16, 16), np.float32)
-    B = np.zeros((cnt, 8, 16), np.float32)
-    C = np.zeros((cnt, 16, 8), np.float32)
+def adversarial_operands(rng, cnt, n, kh):
+    """Instances of four kinds: (0) one large product with small same-sign
+    ones just under its last bits, so that truncating alignment would lose
+    them all in the same direction; (1) heavy cancellation: pairs of equal
+    and opposite large products plus small terms; (2) exponents mixed over
+    2^-15..2^15 inside each k-half; (3) the screen's own rows and columns:
+    centred offsets, the norm split against -1/2 and a threshold split into
+    three bf16 parts."""
+    K = 16 * kh
+    A = np.zeros((cnt, 128, K), np.float32)
+    B = np.zeros((cnt, n, K), np.float32)
     for i in range(cnt):
         kind = i % 4
         if kind == 0:
-            A[i] = rng.uniform(1.0, 2.0, (16, 16))
-            B[i] = rng.uniform(1.0, 2.0, (8, 16))
+            A[i] = rng.uniform(1.0, 2.0, (128, K))
+            B[i] = rng.uniform(1.0, 2.0, (n, K))
             big = 2.0 ** rng.integers(8, 12)
             A[i][:, 0] *= big
             B[i][:, 0] *= big
-            small = 2.0 ** -rng.integers(6, 10, (16, 15))
-            A[i][:, 1:] *= small
+            A[i][:, 1:] *= 2.0 ** -rng.integers(6, 10, (128, K - 1))
         elif kind == 1:
-            x = rng.uniform(1.0, 2.0, (16, 8)) * 2.0 ** rng.integers(4, 10)
-            A[i][:, 0:8] = x
-            A[i][:, 8:16] = -x
+            half = K // 2
+            x = rng.uniform(1.0, 2.0, (128, half)) * 2.0 ** rng.integers(4, 10)
+            A[i][:, :half] = x
+            A[i][:, half:] = -x
             B[i][:] = 1.0
-            A[i][:, 15] = rng.uniform(-1e-3, 1e-3, 16)
-            B[i][:, 7] = rng.uniform(1.0, 1.1, 8)
+            A[i][:, K - 1] = rng.uniform(-1e-3, 1e-3, 128)
+            B[i][:, half - 1] = rng.uniform(1.0, 1.1, n)
         elif kind == 2:
-            A[i] = (rng.choice([-1, 1], (16, 16)) * rng.uniform(1, 2, (16, 16))
-                    * 2.0 ** rng.integers(-15, 15, (16, 16)))
-            B[i] = (rng.choice([-1, 1], (8, 16)) * rng.uniform(1, 2, (8, 16))
-                    * 2.0 ** rng.integers(-15, 15, (8, 16)))
-            C[i] = rng.standard_normal((16, 8)) * 2.0 ** rng.integers(-10, 10)
+            A[i] = (rng.choice([-1, 1], (128, K)) * rng.uniform(1, 2, (128, K))
+                    * 2.0 ** rng.integers(-15, 15, (128, K)))
+            B[i] = (rng.choice([-1, 1], (n, K)) * rng.uniform(1, 2, (n, K))
+                    * 2.0 ** rng.integers(-15, 15, (n, K)))
         else:
-            d = 10
-            w = rng.standard_normal((16, d)) * 2.0 ** rng.integers(-4, 4)
-            wb = bf16_value(bf16_bits(w.astype(np.float32)))
-            pn = np.float32((wb ** 2).sum(1))
+            d = K - 5
+            sc = 2.0 ** rng.integers(-4, 4)
+            w = bf16_value(bf16_bits((rng.standard_normal((128, d)) * sc)
+                                     .astype(np.float32)))
+            pn = (w ** 2).sum(1).astype(np.float32)
             hi = bf16_value(bf16_bits(pn))
             lo = bf16_value(bf16_bits((pn - hi).astype(np.float32)))
             A[i][:, :d] = w
             A[i][:, d] = hi
             A[i][:, d + 1] = lo
-            v = rng.standard_normal((8, d)) * 2.0 ** rng.integers(-4, 4)
+            A[i][:, d + 2:d + 5] = 1.0
+            v = rng.standard_normal((n, d)) * sc
+            t = (rng.uniform(0.5, 2.0, n) * (v ** 2).sum(1)).astype(np.float32)
+            th = bf16_value(bf16_bits(t))
+            tm = bf16_value(bf16_bits((t - th).astype(np.float32)))
+            tl = bf16_value(bf16_bits((t - th - tm).astype(np.float32)))
             B[i][:, :d] = v
             B[i][:, d] = -0.5
             B[i][:, d + 1] = -0.5
-            C[i] = rng.standard_normal((16, 8)) * 4.0
-    return bf16_bits(A), bf16_bits(B), C
+            B[i][:, d + 2], B[i][:, d + 3], B[i][:, d + 4] = th, tm, tl
+    return bf16_bits(A), bf16_bits(B)
 
 
-def test_tensor_core_accumulation_within_the_screen_model():
-    rng = np.random.default_rng(2024)
-    A, Bt, C = adversarial_operands(rng, 512)
-    D = bkd.bkd_probe_mma(A, Bt, C)
-    exact, mag = exact_dots(A, Bt, C)
+@pytest.mark.parametrize("n,kh", [(16, 1), (48, 1), (128, 1), (32, 2),
+                                  (128, 3)])
+def test_tensor_core_accumulation_within_the_screen_model(n, kh):
+    """Every result of the screen's tcgen05 path is within kh 2^-18 of the
+    sum of its absolute products from the exact sum (the model of the
+    bound); also checks the operand layout and descriptors (a wrong layout
+    gives wrong sums, far outside the model)."""
+    rng = np.random.default_rng(2024 + n + kh)
+    A, Bt = adversarial_operands(rng, 8, n, kh)
+    D = bkd.bkd_probe_umma(A, Bt)
+    exact, mag = exact_dots(A, Bt)
     err = np.abs(D.astype(np.float64) - exact)
     ratio = err / np.maximum(mag, 1e-300)
     worst = float(ratio.max())
-    print(f"accumulation error / (|c| + sum |a b|): max {worst:.3e} "
-          f"= 2^{math.log2(worst) if worst > 0 else -math.inf:.2f}; "
-          f"model 2^-18")
+    print(f"n={n} kh={kh}: accumulation error / sum |a b|: max {worst:.3e}"
+          f" = 2^{math.log2(worst) if worst > 0 else -math.inf:.2f}; "
+          f"model {kh} x 2^-18")
     assert np.isfinite(D).all()
-    assert worst <= MODEL, f"accumulation error {worst:.3e} exceeds 2^-18"
+    assert worst <= kh * MODEL, f"accumulation error {worst:.3e}"
 
 
-def test_tensor_core_infinite_norm_slot_gives_minus_infinity():
-    """A padding point carries pn_hi = +inf against the query's -1/2: its
-    product must be -inf, never NaN, whatever the other slots hold."""
+def test_tensor_core_padding_rows_and_columns():
+    """A padding point (pn_hi = +inf against the query's -1/2) gives -inf,
+    never NaN, also against a column whose threshold is +2^126 (list not
+    full); a padding column (threshold -2^126) gives a large negative value
+    against every real point."""
     rng = np.random.default_rng(3)
-    A = rng.standard_normal((1, 16, 16)).astype(np.float32)
-    B = rng.standard_normal((1, 8, 16)).astype(np.float32)
-    A[0, :, 12] = np.inf
-    B[0, :, 12] = -0.5
-    C = rng.standard_normal((1, 16, 8)).astype(np.float32)
-    D = bkd.bkd_probe_mma(bf16_bits(A), bf16_bits(B), C)
-    assert (D == -np.inf).all()
+    d = 10
+    A = np.zeros((1, 128, 16), np.float32)
+    B = np.zeros((1, 16, 16), np.float32)
+    A[0, :, :d] = rng.standard_normal((128, d))
+    A[0, :, d] = 1.0
+    A[0, :, d + 2:d + 5] = 1.0
+    A[0, 100:, :] = 0.0
+    A[0, 100:, d] = np.inf
+    B[0, :, :d] = rng.standard_normal((16, d))
+    B[0, :, d:d + 2] = -0.5
+    B[0, :8, d + 2] = 2.0 ** 126
+    B[0, 8:12, d + 2] = -(2.0 ** 126)
+    D = bkd.bkd_probe_umma(bf16_bits(A), bf16_bits(B))[0]
+    assert (D[100:] == -np.inf).all()
+    assert (D[:100, :8] > 2.0 ** 125).all()
+    assert (D[:100, 8:12] < -(2.0 ** 125)).all()
+    assert np.isfinite(D[:100]).all()
 
 
 # ------------------------------------------------------------- wide data

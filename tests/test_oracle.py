@@ -326,3 +326,35 @@ def test_pins_catch_mutant(oracle_mod, tmp_path, name):
     failures += check_tree_structure(oracle_mod,
                                      workloads.uniform(200, 3, 1), 4, lib)
     assert failures, f"mutant '{name}' passed every pin"
+
+
+def test_outlier_scores_hand_cases(oracle_mod):
+    """Sec. 4.3 outlier score against hand-computed values (own index
+    removed from the k+1 list, or the last entry when duplicates fill it)."""
+    data = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "outlier_cases.json")))
+    for case in data["cases"]:
+        P = np.array(case["P"], np.float32)
+        got = oracle_mod.outlier_scores(P, case["k"])
+        assert np.allclose(got, case["score"], rtol=0, atol=1e-12), \
+            (case["name"], got)
+
+
+def test_outlier_scores_grid_closed_form(oracle_mod):
+    """Closed forms on the integer grid {0..9}^2: every point has at least
+    two neighbours at distance 1, so k = 2 scores 1 everywhere; with k = 4
+    an interior point has four at 1 (score 1), a corner two at 1, one at
+    sqrt 2 and then two at 2 (score (1 + 1 + sqrt 2 + 2) / 4), and an edge
+    point three at 1 and then two at sqrt 2 (score (3 + sqrt 2) / 4)."""
+    g = np.stack(np.meshgrid(np.arange(10), np.arange(10), indexing="ij"),
+                 -1).reshape(-1, 2).astype(np.float32)
+    s2 = oracle_mod.outlier_scores(g, 2)
+    assert np.allclose(s2, 1.0)
+    s4 = oracle_mod.outlier_scores(g, 4)
+    inside = (g[:, 0] > 0) & (g[:, 0] < 9) & (g[:, 1] > 0) & (g[:, 1] < 9)
+    assert np.allclose(s4[inside], 1.0)
+    corner = ((g[:, 0] == 0) | (g[:, 0] == 9)) & ((g[:, 1] == 0)
+                                                  | (g[:, 1] == 9))
+    assert np.allclose(s4[corner], (1 + 1 + np.sqrt(2) + 2) / 4)
+    edge = ~inside & ~corner
+    assert np.allclose(s4[edge], (3 + np.sqrt(2)) / 4)
