@@ -72,6 +72,13 @@ def args_():
                     help="time budget of the per-batch latency sample")
     ap.add_argument("--streamer", action="store_true",
                     help="measure the chunk streamer (bigger mode) instead")
+    ap.add_argument("--streamer-n", type=int, default=0,
+                    help="streamer workload: reference points (default: "
+                         "the 2^24-point mixture)")
+    ap.add_argument("--streamer-m", type=int, default=1 << 20)
+    ap.add_argument("--streamer-h", type=int, default=20)
+    ap.add_argument("--streamer-resident", action="store_true",
+                    help="with --streamer-n: also time the resident tree")
     return ap.parse_args()
 
 
@@ -625,17 +632,26 @@ def run_ours(a, w, rank, world, local_rank):
 
 
 def run_streamer(a):
-    """Bigger mode: the leaf structure in pinned host memory, streamed in N
-    leaf-aligned chunks through two device buffers on a copy stream (the
-    chunk streamer).  Per N: queries/s, bytes copied, copy-stream bandwidth
-    against a pinned host-to-device copy measured here, and equality with the
-    resident tree's results."""
+    """Bigger mode: the leaf structure in pinned host memory, streamed through
+    two device chunk buffers on a copy stream (the chunk streamer).  Modes:
+    resident; leaf-aligned chunks N in {1, 3, 10} (the resident chunks keep
+    running while they hold buffered queries); the paper's point chunks N in
+    {3, 10} (every chunk with buffered queries streamed every round).  Per
+    mode: queries/s, bytes copied and passes over the leaf structure,
+    copy-stream bandwidth against a pinned host-to-device copy measured
+    here, and equality with the resident tree's results."""
     import torch
     import paper_1512_02831_gb300 as bkd
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    w = WORKLOADS["mixture16M"]
+    if a.streamer_n:
+        w = workloads.scaled(workloads.MIXTURE_64M, a.streamer_n,
+                             a.streamer_m, a.streamer_h)
+    else:
+        w = WORKLOADS["mixture16M"]
+    t0 = time.perf_counter()
     P, Q = w.points(), w.queries()
+    gen_s = time.perf_counter() - t0
     m, k = Q.shape[0], w.k
     Qd = torch.from_numpy(Q).to(dev)
     # host-to-device peak: 1 GiB from pinned memory, best of 5
@@ -651,35 +667,54 @@ def run_streamer(a):
         torch.cuda.synchronize()
         best = max(best, src.numel() * 4 / (e0.elapsed_time(e1) / 1e3) / 1e9)
     del src, dst
+    dp = min(c for c in (2, 4, 6, 8, 10, 12, 16, 24, 32) if c >= w.d)
+    structure = w.n * dp * 4
     out = {"metric": "chunk streamer (bigger mode)", "workload": w.describe(),
-           "h2d_peak_gbs": best, "modes": {}}
+           "h2d_peak_gbs": best, "leaf_structure_gb": structure / 1e9,
+           "data_generation_s": round(gen_s, 1), "modes": {}}
     ref = None
-    for n_chunks in (0, 1, 3, 10):
-        opts = {"chunks": n_chunks} if n_chunks else {}
+    modes = [("resident", {})] if not a.streamer_n or a.streamer_resident \
+        else []
+    modes += [(f"chunks={c}", {"chunks": c}) for c in (1, 3, 10)]
+    modes += [(f"point_chunks={c}", {"chunks": c, "point_chunks": 1})
+              for c in (3, 10)]
+    for name, opts in modes:
+        t0 = time.perf_counter()
         tree = bkd.bkd_build(P, w.height, **opts)
-        bkd.bkd_query(tree, Qd, k)  # warm-up
+        build_s = time.perf_counter() - t0
+        if not a.streamer_n:
+            bkd.bkd_query(tree, Qd, k)  # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         idx, dist = bkd.bkd_query(tree, Qd, k)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         st = {x: bkd.bkd_get_stat(tree, x)
-              for x in ("chunk_bytes", "copy_ms", "rounds", "leaf_kernel_ms")}
+              for x in ("chunk_bytes", "copy_ms", "rounds", "leaf_kernel_ms",
+                        "chunk_visits", "leaf_visits")}
         shape = bkd.bkd_tree_shape(tree)
         bkd.bkd_free(tree)
         if ref is None:
             ref = (idx.clone(), dist.clone())
         gbs = (st["chunk_bytes"] / (st["copy_ms"] / 1e3) / 1e9
                if st["copy_ms"] > 0 else None)
-        out["modes"]["resident" if not n_chunks else f"chunks={n_chunks}"] = {
-            "chunked": shape["chunked"], "queries_per_s": m / dt,
-            "ms": dt * 1e3, "rounds": st["rounds"],
-            "copied_gb": st["chunk_bytes"] / 1e9, "copy_ms": st["copy_ms"],
-            "copy_gbs": gbs,
+        out["modes"][name] = {
+            "chunked": shape["chunked"], "chunks": shape["chunks"],
+            "queries_per_s": m / dt, "ms": dt * 1e3, "build_s": build_s,
+            "rounds": st["rounds"],
+            "copied_gb": st["chunk_bytes"] / 1e9,
+            "passes_over_structure": st["chunk_bytes"] / structure,
+            "copy_ms": st["copy_ms"], "copy_gbs": gbs,
             "copy_frac_of_h2d_peak": gbs / best if gbs else None,
             "leaf_kernel_ms": st["leaf_kernel_ms"],
-            "identical_to_resident": bool(torch.equal(idx, ref[0])
-                                          and torch.equal(dist, ref[1]))}
+            "identical_to_first_mode": bool(torch.equal(idx, ref[0])
+                                            and torch.equal(dist, ref[1]))}
+        print(json.dumps({name: out["modes"][name]}), flush=True)
+    base = out["modes"].get("resident")
+    if base:
+        for v in out["modes"].values():
+            v["q_per_s_ratio_to_resident"] = (v["queries_per_s"]
+                                              / base["queries_per_s"])
     print(json.dumps(out), flush=True)
 
 

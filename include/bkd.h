@@ -94,7 +94,18 @@ enum bkd_option {
    * a candidate list, the rest are scored in float32 -- results identical to
    * 0.  1 at build also prepares the screen data (resident trees only;
    * chunked: BKD_EUNSUPPORTED); afterwards 0 / 1 may be switched any time. */
-  BKD_OPT_PRECISION = 6
+  BKD_OPT_PRECISION = 6,
+  /* Chunk bounds in chunked mode: 0 (default) = whole leaves (chunk c holds
+   * leaves [ceil(c L / N), ceil((c+1) L / N)), L = 2^h), scheduled so that
+   * the two chunks resident on the device keep running while they hold
+   * buffered queries; 1 = the point chunks of Sec. 3.2, positions
+   * [ceil(j n / N), ceil((j+1) n / N)) of the leaf structure (a bound inside
+   * a leaf moved down to a multiple of 4 points from the leaf's start), so
+   * a leaf may straddle two chunks and its queries are scanned in both;
+   * every chunk holding buffered queries is streamed every round.  Results
+   * do not depend on it.  Build only (with BKD_OPT_CHUNKS >= 1 or the
+   * memory cap). */
+  BKD_OPT_POINT_CHUNKS = 7
 };
 
 /* ------------------------------------------------------------------- stats

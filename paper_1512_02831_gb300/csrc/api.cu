@@ -135,7 +135,12 @@ struct bkd_tree {
   int n_chunks = 0;
   float* h_pts = nullptr;        // pinned, mapped
   int64_t* h_orig = nullptr;     // pinned, mapped
-  std::vector<int32_t> chunk_leaf;
+  std::vector<int32_t> chunk_leaf;   // leaf-aligned chunks: leaf bounds
+  bool point_chunks = false;         // chunks split at point positions
+  std::vector<int64_t> chunk_pos;    // point chunks: position bounds
+  std::vector<int32_t> chunk_la, chunk_lb;  // point chunks: first / last leaf
+  int chunk_idx = 0;                 // entries of d_chunk_leaf
+  int64_t* d_leaf_lo = nullptr;      // point chunks: leaf bounds (device)
   int32_t* d_chunk_leaf = nullptr;
   float* d_chunk_buf[2] = {nullptr, nullptr};
   int buf_chunk[2] = {-1, -1};
@@ -146,7 +151,10 @@ struct bkd_tree {
   DevBuf<uint64_t> state;  // per query: TravState
   DevBuf<int2> placed;  // per active position: (next leaf, rank in its buffer)
   DevBuf<int32_t> cnt, off, cursor, toff, chunk_item, nact;
-  DevBuf<Item> items;
+  DevBuf<Item> items, scr_ovf;
+  DevBuf<uint8_t> scr_bop;  // screened rounds: per item query operand tile
+  DevBuf<uint32_t> scr_seg; // per item survivor segment
+  DevBuf<int32_t> scr_cnt;  // per item survivor count
   DevBuf<int64_t> out_idx, inv;
   DevBuf<float> out_dist, score;
   Counters* d_ctr = nullptr;
@@ -198,6 +206,7 @@ void release(bkd_tree* t) {
   cudaFree(t->d_scr_bmax);
   cudaFree(t->d_scr_pnmax);
   cudaFree(t->d_chunk_leaf);
+  cudaFree(t->d_leaf_lo);
   cudaFree(t->d_chunk_buf[0]);
   cudaFree(t->d_chunk_buf[1]);
   if (t->h_pts) cudaFreeHost(t->h_pts);
@@ -218,6 +227,10 @@ void release(bkd_tree* t) {
   t->chunk_item.release();
   t->nact.release();
   t->items.release();
+  t->scr_ovf.release();
+  t->scr_bop.release();
+  t->scr_seg.release();
+  t->scr_cnt.release();
   t->out_idx.release();
   t->out_dist.release();
   t->inv.release();
@@ -277,7 +290,7 @@ int build_impl(const float* P, int64_t n, int d, int height,
                 (long long)((int64_t)1 << height), (long long)n);
   if (n_options < 0 || (n_options > 0 && !options))
     return fail(BKD_EINVAL, "bad options array");
-  int64_t cap = -1, chunks = 0, precision = 0;
+  int64_t cap = -1, chunks = 0, precision = 0, point_chunks = 0;
   for (int i = 0; i < n_options; ++i) {
     const int64_t key = options[2 * i], val = options[2 * i + 1];
     if (key == BKD_OPT_DEVICE_MEM_CAP) {
@@ -291,6 +304,10 @@ int build_impl(const float* P, int64_t n, int d, int height,
       if (val != 0 && val != 1)
         return fail(BKD_EINVAL, "precision must be 0 or 1");
       precision = val;
+    } else if (key == BKD_OPT_POINT_CHUNKS) {
+      if (val != 0 && val != 1)
+        return fail(BKD_EINVAL, "point chunks must be 0 or 1");
+      point_chunks = val;
     } else if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE ||
                key == BKD_OPT_TAIL_QUERIES) {
       // applied after construction below
@@ -426,22 +443,67 @@ int build_impl(const float* P, int64_t n, int d, int height,
                        pts_bytes + orig_bytes));
     }
     fill_quads(Ph, H, 0, L, t->h_pts, t->h_orig);
-    t->chunk_leaf.resize(t->n_chunks + 1);
-    for (int c = 0; c <= t->n_chunks; ++c)  // C_c = ceil(c L / N), leaves
-      t->chunk_leaf[c] = (int32_t)((c * L + t->n_chunks - 1) / t->n_chunks);
+    const int N = t->n_chunks;
     int64_t max_leaves = 0;
-    for (int c = 0; c < t->n_chunks; ++c)
-      max_leaves = std::max<int64_t>(max_leaves,
-                                     t->chunk_leaf[c + 1] - t->chunk_leaf[c]);
+    std::vector<int32_t> idx;  // leaves whose first item / query bound a
+                               // chunk's items and queries
+    if (!point_chunks) {
+      t->chunk_leaf.resize(N + 1);
+      for (int c = 0; c <= N; ++c)  // C_c = ceil(c L / N), leaves
+        t->chunk_leaf[c] = (int32_t)((c * L + N - 1) / N);
+      for (int c = 0; c < N; ++c)
+        max_leaves = std::max<int64_t>(max_leaves,
+                                       t->chunk_leaf[c + 1] - t->chunk_leaf[c]);
+      idx = t->chunk_leaf;
+    } else {
+      // Sec. 3.2: C_j holds the leaf-structure positions [ceil(j n / N),
+      // ceil((j + 1) n / N)); a bound inside a leaf moves down to the start
+      // of its group of four points (the quads the leaf kernel reads), so
+      // every chunk takes whole quads and every point lies in one chunk
+      auto leaf_of = [&](int64_t p) {
+        return (int32_t)(std::upper_bound(H.leaf_lo, H.leaf_lo + L + 1, p) -
+                         H.leaf_lo - 1);
+      };
+      t->chunk_pos.resize(N + 1);
+      for (int j = 0; j <= N; ++j) {
+        const int64_t p = (j * n + N - 1) / N;
+        if (j == 0 || j == N) {
+          t->chunk_pos[j] = p;
+          continue;
+        }
+        const int64_t b = H.leaf_lo[leaf_of(p)];
+        t->chunk_pos[j] = b + ((p - b) & ~(int64_t)3);
+      }
+      for (int j = 0; j < N; ++j)
+        if (t->chunk_pos[j + 1] <= t->chunk_pos[j])
+          return bail(fail(BKD_EINVAL, "%d point chunks are too many for n = "
+                                       "%lld points", N, (long long)n));
+      t->chunk_la.resize(N);
+      t->chunk_lb.resize(N);
+      for (int j = 0; j < N; ++j) {
+        t->chunk_la[j] = leaf_of(t->chunk_pos[j]);
+        t->chunk_lb[j] = leaf_of(t->chunk_pos[j + 1] - 1);
+        max_leaves = std::max<int64_t>(max_leaves,
+                                       t->chunk_lb[j] - t->chunk_la[j] + 1);
+        idx.push_back(t->chunk_la[j]);
+        idx.push_back(t->chunk_lb[j] + 1);
+      }
+      if (dev_malloc(&t->d_leaf_lo, (L + 1) * sizeof(int64_t)) != cudaSuccess)
+        return bail(fail(BKD_ENOMEM, "device leaf bounds"));
+      if (cudaMemcpy(t->d_leaf_lo, H.leaf_lo, (L + 1) * sizeof(int64_t),
+                     cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(BKD_ECUDA, "upload of leaf bounds failed"));
+    }
+    t->point_chunks = point_chunks != 0;
+    t->chunk_idx = (int)idx.size();
     const size_t buf_bytes = (size_t)max_leaves * H.lcap * H.Dp * sizeof(float);
     if (dev_malloc(&t->d_chunk_buf[0], buf_bytes) != cudaSuccess ||
         dev_malloc(&t->d_chunk_buf[1], buf_bytes) != cudaSuccess ||
-        dev_malloc(&t->d_chunk_leaf, (t->n_chunks + 1) * sizeof(int32_t)) !=
+        dev_malloc(&t->d_chunk_leaf, idx.size() * sizeof(int32_t)) !=
             cudaSuccess)
       return bail(fail(BKD_ENOMEM, "device chunk buffers (%zu bytes each)",
                        buf_bytes));
-    if (cudaMemcpy(t->d_chunk_leaf, t->chunk_leaf.data(),
-                   (t->n_chunks + 1) * sizeof(int32_t),
+    if (cudaMemcpy(t->d_chunk_leaf, idx.data(), idx.size() * sizeof(int32_t),
                    cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(fail(BKD_ECUDA, "upload of chunk bounds failed"));
     for (int b = 0; b < 2; ++b)
@@ -495,7 +557,8 @@ int build_impl(const float* P, int64_t n, int d, int height,
   if (dev_malloc(&t->d_ctr, sizeof(Counters)) != cudaSuccess ||
       host_alloc(&t->h_ctr, sizeof(Counters), cudaHostAllocDefault) !=
           cudaSuccess ||
-      host_alloc(&t->h_chunk_item, 2 * (t->n_chunks + 1) * sizeof(int32_t),
+      host_alloc(&t->h_chunk_item,
+                 2 * (size_t)std::max(t->chunk_idx, 1) * sizeof(int32_t),
                     cudaHostAllocDefault) != cudaSuccess ||
       (chunked &&
        (dev_malloc(&t->d_chunk_done, t->n_chunks) != cudaSuccess ||
@@ -515,7 +578,7 @@ int build_impl(const float* P, int64_t n, int d, int height,
   D.h = height;
   D.lcap = H.lcap;
   D.n_chunks = t->n_chunks;
-  D.chunk_done = chunked ? t->d_chunk_done : nullptr;
+  D.chunk_done = chunked && !t->point_chunks ? t->d_chunk_done : nullptr;
   for (int i = 0; i < n_options; ++i) {
     const int64_t key = options[2 * i], val = options[2 * i + 1];
     if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE ||
@@ -596,7 +659,7 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   CU(t->toff.ensure(L + 1));
   CU(t->items.ensure(max_items));
   CU(t->nact.ensure(2));
-  if (t->chunked) CU(t->chunk_item.ensure(2 * (t->n_chunks + 1)));
+  if (t->chunked) CU(t->chunk_item.ensure(2 * t->chunk_idx));
 
   CU(cudaMemsetAsync(t->d_ctr, 0, sizeof(Counters), s));
   CU(launch_init(t->qdev.p, m, D.d, Dp, t->qpad.p, t->lst_d.p, t->lst_i.p, K,
@@ -632,6 +695,18 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   // counts on the device, and a round whose queries have all finished does
   // nothing.  A chunked tree needs the host every round (the chunk
   // schedule).
+  ScreenWork sw;
+  if (screen_max > 0) {
+    const int64_t si = m / kScreenTile + L + 1;  // items of a screened round
+    CU(t->scr_bop.ensure(si * 4096 * t->screen.kh));
+    CU(t->scr_seg.ensure(si * screen_seg_cap()));
+    CU(t->scr_cnt.ensure(si));
+    CU(t->scr_ovf.ensure(2 * si));  // overflowed items, in halves
+    sw.bop = t->scr_bop.p;
+    sw.seg = t->scr_seg.p;
+    sw.seg_cnt = t->scr_cnt.p;
+    sw.ovf = t->scr_ovf.p;
+  }
   int round = 0;
   CU(launch_fill(t->nact.p, 1, (int32_t)m, s));
   t->st_launches += 1;
@@ -662,9 +737,9 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
     t->st_launches += 3;
     if (t->chunked) {
       CU(launch_chunk_items(t->toff.p, t->off.p, t->d_chunk_leaf,
-                            t->n_chunks, t->chunk_item.p, s));
+                            t->chunk_idx, t->chunk_item.p, s));
       CU(cudaMemcpyAsync(t->h_chunk_item, t->chunk_item.p,
-                         2 * (t->n_chunks + 1) * sizeof(int32_t),
+                         2 * t->chunk_idx * sizeof(int32_t),
                          cudaMemcpyDeviceToHost, s));
       t->st_launches += 1;
     }
@@ -679,8 +754,9 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
       // BF16 tensor-core screen + exact float32 rescoring
       cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
       if (e0) cudaEventRecord(e0, s);
-      CU(launch_screen(D, t->screen, t->items.p, 0, n_items, t->d_ctr, nxt,
-                       t->qpad.p, t->lst_d.p, t->lst_i.p, K, screen_max, s));
+      CU(launch_screen(D, t->screen, t->items.p, n_items, t->d_ctr, nxt,
+                       t->qpad.p, t->lst_d.p, t->lst_i.p, K, screen_max, sw,
+                       cap, grid_max, t->sm_count, s));
       if (e1) cudaEventRecord(e1, s);
       if (e0 && e1) t->screen_ev.push_back({e0, e1});
       t->st_launches += 1;
@@ -694,6 +770,60 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
       if (e0 && e1) t->leaf_ev.push_back({e0, e1});
       t->st_leaf_launches += 1;
       t->st_launches += 1;
+    } else if (t->point_chunks) {
+      // Brute / Copy / Wait (Sec. 3.2) with the paper's point chunks: every
+      // chunk whose leaves hold buffered queries, in order (alternating
+      // direction, so the chunk scanned last stays resident); a query whose
+      // leaf straddles two chunks is scanned in both, each time against the
+      // leaf's points inside the chunk.
+      const int N = t->n_chunks;
+      const int32_t* ci = t->h_chunk_item;  // [first item, end item) per chunk
+      const bool forward = (round % 2) == 0;
+      int prev_b = -1;
+      for (int i = 0; i < N; ++i) {
+        const int c = forward ? i : N - 1 - i;
+        const int ilo = ci[2 * c], ihi = ci[2 * c + 1];
+        if (ihi <= ilo) continue;
+        int b;
+        if (t->buf_chunk[0] == c)
+          b = 0;
+        else if (t->buf_chunk[1] == c)
+          b = 1;
+        else
+          b = prev_b < 0 ? (t->buf_chunk[0] == -1 ? 0 : 1) : 1 - prev_b;
+        const int64_t la = t->chunk_la[c], lb = t->chunk_lb[c] + 1;
+        if (t->buf_chunk[b] != c) {
+          const size_t bytes = (size_t)(lb - la) * D.lcap * Dp * sizeof(float);
+          CU(cudaStreamWaitEvent(t->copy_stream, t->ev_free[b], 0));
+          cudaEvent_t c0 = t->next_event(), c1 = t->next_event();
+          if (c0) cudaEventRecord(c0, t->copy_stream);
+          CU(cudaMemcpyAsync(t->d_chunk_buf[b],
+                             t->h_pts + (size_t)la * D.lcap * Dp, bytes,
+                             cudaMemcpyHostToDevice, t->copy_stream));
+          if (c1) cudaEventRecord(c1, t->copy_stream);
+          if (c0 && c1) t->copy_ev.push_back({c0, c1});
+          CU(cudaEventRecord(t->ev_copied[b], t->copy_stream));
+          t->buf_chunk[b] = c;
+          t->st_chunk_bytes += (double)bytes;
+        }
+        CU(cudaStreamWaitEvent(s, t->ev_copied[b], 0));
+        LeafPart part;
+        part.leaf_lo = t->d_leaf_lo;
+        part.pos_lo = t->chunk_pos[c];
+        part.pos_hi = t->chunk_pos[c + 1];
+        cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
+        if (e0) cudaEventRecord(e0, s);
+        CU(launch_leaf(D, cap, t->items.p, ilo, ihi, t->d_ctr,
+                       t->d_chunk_buf[b], la, nxt, t->qpad.p, t->lst_d.p,
+                       t->lst_i.p, K, std::min(grid_max, ihi - ilo), s,
+                       nullptr, part));
+        if (e1) cudaEventRecord(e1, s);
+        if (e0 && e1) t->leaf_ev.push_back({e0, e1});
+        CU(cudaEventRecord(t->ev_free[b], s));
+        t->st_leaf_launches += 1;
+        t->st_launches += 1;
+        prev_b = b;
+      }
     } else {
       // Brute / Copy / Wait (Sec. 3.2) on the chunks the schedule picks.
       // The paper streams every chunk in every ProcessAllBuffers call and
@@ -1076,6 +1206,7 @@ int bkd_set_option(bkd_tree* t, int key, int64_t value) {
       return BKD_OK;
     case BKD_OPT_DEVICE_MEM_CAP:
     case BKD_OPT_CHUNKS:
+    case BKD_OPT_POINT_CHUNKS:
       return fail(BKD_EINVAL, "option %d applies at build only", key);
     default:
       return fail(BKD_EINVAL, "unknown option %d", key);

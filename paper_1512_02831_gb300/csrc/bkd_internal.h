@@ -76,6 +76,7 @@ struct Counters {
   int32_t n_resorted;       // queries re-ordered by binary64 distances
   int32_t err;              // device-detected input errors (bit mask)
   int32_t screen_next;      // next work item of the running screen launch
+  int32_t screen_ovf_items; // screen items handed to the float32 kernel
   unsigned long long tail_pairs;   // (query, point) pairs of the tail kernel
   unsigned long long tail_visits;  // (query, leaf) visits of the tail kernel
   unsigned long long screen_kept;  // pairs the BF16 screen passed on
@@ -160,20 +161,31 @@ cudaError_t launch_bucket(const int2* placed, const uint32_t* act,
                           cudaStream_t s, const int32_t* n_act_dev = nullptr,
                           int32_t* n_next_dev = nullptr);
 
-// chunk_item[c] = first item of chunk c (leaves [chunk_leaf[c],
-// chunk_leaf[c+1])) and chunk_item[n_chunks + 1 + c] = its first buffered
-// query, for c = 0..n_chunks.
+// For the leaves leaf[0..count): chunk_item[i] = the first work item of
+// leaf[i] and chunk_item[count + i] = its first buffered query (leaf bounds
+// of the chunks -> their item and query ranges).
 cudaError_t launch_chunk_items(const int32_t* toff, const int32_t* off,
-                               const int32_t* chunk_leaf, int n_chunks,
+                               const int32_t* leaf, int count,
                                int32_t* chunk_item, cudaStream_t s);
 
+// The part of each leaf a leaf-kernel launch scans: every point (leaf_lo
+// nullptr), or the leaf-structure positions [pos_lo, pos_hi) of a
+// point-split chunk (leaf_lo: 2^h + 1 leaf bounds on the device).
+struct LeafPart {
+  const int64_t* leaf_lo = nullptr;
+  int64_t pos_lo = 0, pos_hi = 0;
+};
+
 // ProcessAllBuffers over items [item_lo, item_hi) (item_hi < 0: read the
-// count from ctr).  pts / leaf0: the quads of leaf `leaf0` start at pts.
+// count on the device, from count_dev if given, else ctr->n_items).  pts /
+// leaf0: the quads of leaf `leaf0` start at pts.
 cudaError_t launch_leaf(const DevTree& t, int cap, const Item* items,
                         int item_lo, int item_hi, Counters* ctr,
                         const float* pts, int64_t leaf0, const uint32_t* act,
                         const float* qpad, float* lst_d, uint32_t* lst_i,
-                        int K, int grid, cudaStream_t s);
+                        int K, int grid, cudaStream_t s,
+                        const int32_t* count_dev = nullptr,
+                        LeafPart part = LeafPart());
 
 int leaf_kernel_grid(int Dp, int cap, int sm_count);
 
@@ -203,17 +215,33 @@ __host__ __device__ inline uint32_t screen_row_offset(int r, int kg, int kh) {
   return (uint32_t)((r >> 3) * (256 * kh) + kg * 128 + (r & 7) * 16);
 }
 
+// Workspace of the screened rounds, sized for the most work items a round
+// can have: per item its query operand tile (128 x 32 kh bytes), a segment
+// of screen_seg_cap() survivor entries and their count, and room for the
+// items handed to the float32 kernel.
+struct ScreenWork {
+  uint8_t* bop = nullptr;
+  uint32_t* seg = nullptr;
+  int32_t* seg_cnt = nullptr;
+  Item* ovf = nullptr;
+};
+int64_t screen_seg_cap();
+
 // ProcessAllBuffers with the BF16 tensor-core screen and exact float32
 // rescoring (k_screen.cu); same candidate lists as launch_leaf on a
-// resident tree, over items of at most kScreenTile queries.  screen_grid:
-// resident CTAs (0 if the kernel does not fit: shared memory, tensor
-// memory, leaf capacity).
+// resident tree, over the round's items of at most kScreenTile queries
+// (n_items < 0: the count is read on the device).  Three kernels: the
+// items' query operands, the screen (survivors to per-item segments), the
+// exact rescoring; items whose segment overflowed go to the float32 leaf
+// kernel (capacity `cap`, grid leaf_grid).  screen_grid: resident CTAs (0
+// if the kernel does not fit: shared memory, tensor memory, leaf capacity).
 int screen_grid(int kh, int Dp, int64_t lcap, int K, int sm_count);
 cudaError_t launch_screen(const DevTree& t, const ScreenData& sd,
-                          const Item* items, int item_lo, int item_hi,
-                          Counters* ctr, const uint32_t* act,
-                          const float* qpad, float* lst_d, uint32_t* lst_i,
-                          int K, int grid, cudaStream_t s);
+                          const Item* items, int n_items, Counters* ctr,
+                          const uint32_t* act, const float* qpad,
+                          float* lst_d, uint32_t* lst_i, int K, int grid,
+                          const ScreenWork& w, int cap, int leaf_grid,
+                          int sm_count, cudaStream_t s);
 
 // Runs the traversal of each of the n_act queries in `act` to its end (one
 // warp per query); state[q] is the query's pending (not yet scanned) leaf.

@@ -37,11 +37,12 @@ cudaError_t launch_leaf(const DevTree& t, int cap, const Item* items,
                         int item_lo, int item_hi, Counters* ctr,
                         const float* pts, int64_t leaf0, const uint32_t* act,
                         const float* qpad, float* lst_d, uint32_t* lst_i,
-                        int K, int grid, cudaStream_t s) {
+                        int K, int grid, cudaStream_t s,
+                        const int32_t* count_dev, LeafPart part) {
   if (grid <= 0) return cudaSuccess;
 #define BKD_ARGS                                                          \
   t.Dp, items, item_lo, item_hi, ctr, pts, leaf0, t.leaf_cnt, t.lcap, act, \
-      qpad, lst_d, lst_i, K, grid, s
+      qpad, lst_d, lst_i, K, grid, s, count_dev, part
   switch (cap) {
     case 2: return leaf_launch_c2(BKD_ARGS);
     case 4: return leaf_launch_c4(BKD_ARGS);

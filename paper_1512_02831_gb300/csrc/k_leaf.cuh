@@ -147,11 +147,27 @@ struct SegCursor {
   int it, seg, nseg;
 };
 
+// The quads [x, y) of a leaf of `cnt` points that a launch scans: all of
+// them, or -- for the point-split chunks of Sec. 3.2 -- those holding the
+// leaf-structure positions [part.pos_lo, part.pos_hi) (a multiple of 4
+// points from the leaf's start, by construction of the chunk bounds).
+__device__ __forceinline__ int2 quad_range(const LeafPart& part, int leaf,
+                                           int cnt) {
+  int lo = 0, hi = cnt;
+  if (part.leaf_lo) {
+    const int64_t b = part.leaf_lo[leaf];
+    lo = (int)max((int64_t)0, part.pos_lo - b);
+    hi = (int)min((int64_t)cnt, part.pos_hi - b);
+  }
+  return make_int2(lo >> 2, (hi + 3) >> 2);
+}
+
 __device__ __forceinline__ int segments_of(const Item* __restrict__ items,
                                            const int32_t* __restrict__ cnt,
-                                           int it) {
-  const int nq = (cnt[items[it].leaf] + 3) >> 2;
-  return (nq + kPipeSegQuads - 1) / kPipeSegQuads;
+                                           int it, const LeafPart& part) {
+  const int leaf = items[it].leaf;
+  const int2 r = quad_range(part, leaf, cnt[leaf]);
+  return (r.y - r.x + kPipeSegQuads - 1) / kPipeSegQuads;
 }
 
 // Starts the copy of the segment under the cursor into `dst`, then advances.
@@ -159,18 +175,19 @@ template <int D>
 __device__ __forceinline__ void issue_segment(
     SegCursor& c, int hi, int stride, const Item* __restrict__ items,
     const int32_t* __restrict__ cnt, const float4* __restrict__ pts,
-    int64_t leaf0, int64_t qpl, float4* dst, uint32_t bar) {
+    int64_t leaf0, int64_t qpl, const LeafPart& part, float4* dst,
+    uint32_t bar) {
   if (c.it >= hi) return;
   const Item w = items[c.it];
-  const int nq = (cnt[w.leaf] + 3) >> 2;
-  const int q0 = c.seg * kPipeSegQuads;
-  const int sq = min(kPipeSegQuads, nq - q0);
+  const int2 r = quad_range(part, w.leaf, cnt[w.leaf]);
+  const int q0 = r.x + c.seg * kPipeSegQuads;
+  const int sq = min(kPipeSegQuads, r.y - q0);
   const float4* src = pts + ((int64_t)(w.leaf - leaf0) * qpl + q0) * D;
   bulk_load(smem_u32(dst), src, (uint32_t)(sq * D * 16), bar);
   if (++c.seg == c.nseg) {
     c.it += stride;
     c.seg = 0;
-    if (c.it < hi) c.nseg = segments_of(items, cnt, c.it);
+    if (c.it < hi) c.nseg = segments_of(items, cnt, c.it, part);
   }
 }
 
@@ -190,10 +207,12 @@ __global__ void __launch_bounds__(kPipeThreads)
                      const uint32_t* __restrict__ act,
                      const float* __restrict__ qpad,
                      float* __restrict__ lst_d, uint32_t* __restrict__ lst_i,
-                     int K) {
+                     int K, const int32_t* __restrict__ count_dev,
+                     LeafPart part) {
   __shared__ __align__(128) float4 buf[2][kPipeSegQuads * D];
   __shared__ __align__(8) uint64_t full[2];
-  const int hi = item_hi >= 0 ? item_hi : ctr->n_items;
+  const int hi = item_hi >= 0 ? item_hi
+                              : (count_dev ? *count_dev : ctr->n_items);
   const int tid = threadIdx.x;
   const int64_t qpl = lcap >> 2;
   const int sent = KT - K;
@@ -203,24 +222,27 @@ __global__ void __launch_bounds__(kPipeThreads)
     mbar_init(bar0, 1);
     mbar_init(bar1, 1);
     mbar_init_fence();
-    if (cur.it < hi) cur.nseg = segments_of(items, leaf_cnt, cur.it);
+    if (cur.it < hi) cur.nseg = segments_of(items, leaf_cnt, cur.it, part);
   }
   __syncthreads();
   if (tid == 0) {
     issue_segment<D>(cur, hi, gridDim.x, items, leaf_cnt, pts, leaf0, qpl,
-                     buf[0], bar0);
+                     part, buf[0], bar0);
     issue_segment<D>(cur, hi, gridDim.x, items, leaf_cnt, pts, leaf0, qpl,
-                     buf[1], bar1);
+                     part, buf[1], bar1);
   }
   uint32_t par0 = 0u, par1 = 0u;  // phase parity of each buffer's barrier
   int slot = 0;
   for (int it = item_lo + blockIdx.x; it < hi; it += gridDim.x) {
     const Item w = items[it];
-    const int nq = (leaf_cnt[w.leaf] + 3) >> 2;
-    const int nseg = (nq + kPipeSegQuads - 1) / kPipeSegQuads;
+    const int2 qr = quad_range(part, w.leaf, leaf_cnt[w.leaf]);
+    const int nq = qr.y;
+    const int nseg = (qr.y - qr.x + kPipeSegQuads - 1) / kPipeSegQuads;
     if (tid == 0)
       atomicAdd(&ctr->leaf_pairs,
-                (unsigned long long)w.count * (unsigned long long)leaf_cnt[w.leaf]);
+                (unsigned long long)w.count *
+                    (unsigned long long)min(leaf_cnt[w.leaf] - 4 * qr.x,
+                                            4 * (qr.y - qr.x)));
     const bool on = tid < w.count;
     uint32_t q = 0;
     uint64_t qq[D];
@@ -264,7 +286,7 @@ __global__ void __launch_bounds__(kPipeThreads)
         par0 ^= 1u;
       if (on) {
         const float4* b = buf[slot];
-        const int q0 = sg * kPipeSegQuads;
+        const int q0 = qr.x + sg * kPipeSegQuads;
         const int sq = min(kPipeSegQuads, nq - q0);
         float bound = Ld[KT - 1];
 #pragma unroll 2
@@ -296,7 +318,7 @@ __global__ void __launch_bounds__(kPipeThreads)
       if (tid == 0) {
         async_proxy_fence();
         issue_segment<D>(cur, hi, gridDim.x, items, leaf_cnt, pts, leaf0, qpl,
-                         buf[slot], slot ? bar1 : bar0);
+                         part, buf[slot], slot ? bar1 : bar0);
       }
       slot ^= 1;
     }
@@ -317,7 +339,8 @@ __global__ void __launch_bounds__(kPipeThreads)
   int Dp, const Item *items, int item_lo, int item_hi, Counters *ctr,       \
       const float *pts, int64_t leaf0, const int32_t *leaf_cnt,             \
       int64_t lcap, const uint32_t *act, const float *qpad, float *lst_d,   \
-      uint32_t *lst_i, int K, int grid, cudaStream_t s
+      uint32_t *lst_i, int K, int grid, cudaStream_t s,                     \
+      const int32_t *count_dev, LeafPart part
 
 #define BKD_LEAF_DECLARE(CAP)                    \
   cudaError_t leaf_launch_c##CAP(BKD_LEAF_ARGS); \
@@ -337,7 +360,7 @@ BKD_LEAF_DECLARE(64)
   case DIM:                                                                   \
     leaf_pipe_kernel<DIM, KT><<<grid, kPipeThreads, 0, s>>>(                  \
         items, item_lo, item_hi, ctr, reinterpret_cast<const float4*>(pts),    \
-        leaf0, leaf_cnt, lcap, act, qpad, lst_d, lst_i, K);                   \
+        leaf0, leaf_cnt, lcap, act, qpad, lst_d, lst_i, K, count_dev, part);  \
     return cudaGetLastError();
 
 #define BKD_LEAF_CASE_PTR(DIM) \

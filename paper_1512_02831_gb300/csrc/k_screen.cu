@@ -86,25 +86,25 @@ namespace bkd {
 namespace {
 
 constexpr int kEpiThreads = 128;              // 4 epilogue warps
-constexpr int kGrpThreads = 128;              // 4 warps per column group
-constexpr int kThreads = 64 + kEpiThreads + 2 * kGrpThreads;
-constexpr int kItemRing = 4;                  // published items in flight
-constexpr int kQcap = 1024;                   // rescoring queue per group
+constexpr int kThreads = 64 + kEpiThreads;    // + producer warp + MMA warp
+constexpr int kItemRing = 8;                  // published items in flight
+constexpr int kBops = 4;                      // query-operand buffers
+constexpr int kClaim = 4;                     // items claimed at a time
 constexpr uint32_t kAccCols = 128;            // tensor-memory columns per acc
 constexpr uint32_t kTmemCols = 2 * kAccCols;  // two accumulators
 
+// Point tiles in flight per CTA: about three leaves of 1,024 points, so
+// that the copies of the next items hide the HBM latency.
 __host__ __device__ constexpr int ring_stages(int kh) {
-  return kh == 1 ? 8 : 4;
+  return kh == 1 ? 20 : (kh == 2 ? 8 : 6);
 }
 __host__ __device__ constexpr uint32_t tile_bytes(int kh) {
   return 4096u * (uint32_t)kh;
 }
 
-// Shared-memory layout (byte offsets into the dynamic shared memory); the
-// per-group pieces exist twice (group g at offset + g * stride).
+// Shared-memory layout (byte offsets into the dynamic shared memory).
 struct Layout {
-  uint32_t ring, bop, grp, grp_stride, qc, colq, colb, colx, queue, qd,
-      items, bars, misc, total;
+  uint32_t ring, bop, items, bars, misc, total;
 };
 
 __host__ __device__ inline uint32_t take(uint32_t& o, uint32_t bytes,
@@ -115,22 +115,14 @@ __host__ __device__ inline uint32_t take(uint32_t& o, uint32_t bytes,
   return r;
 }
 
-__host__ __device__ inline Layout layout_of(int kh, int Dp) {
+__host__ __device__ inline Layout layout_of(int kh) {
   Layout L;
   uint32_t o = 0;
   L.ring = take(o, ring_stages(kh) * tile_bytes(kh), 1024);
-  L.bop = take(o, 2 * tile_bytes(kh), 1024);  // one B operand per group
-  uint32_t g = 0;  // offsets inside one group's block
-  L.qc = take(g, 128u * Dp * 4, 16);
-  L.colq = take(g, 128 * 4, 16);
-  L.colb = take(g, 128 * 4, 16);
-  L.colx = take(g, 128 * 4, 16);
-  L.queue = take(g, kQcap * 4, 16);
-  L.qd = take(g, kQcap * 4, 16);
-  L.grp_stride = (g + 15) / 16 * 16;
-  L.grp = take(o, 2 * L.grp_stride, 16);
+  L.bop = take(o, kBops * tile_bytes(kh), 1024);  // query operands
   L.items = take(o, kItemRing * 16, 16);
-  L.bars = take(o, (2 * ring_stages(kh) + 4 + 6 + 2 * kItemRing) * 8, 8);
+  L.bars = take(o, (2 * ring_stages(kh) + 4 + 2 * kBops + 2 * kItemRing) * 8,
+                8);
   L.misc = take(o, 32, 16);
   L.total = o;
   return L;
@@ -306,6 +298,99 @@ __device__ __forceinline__ float exact_dist(const float* qp,
   return e;
 }
 
+// ------------------------------------------------------------ prep kernel
+// The query operand of every work item of the round, written to HBM in the
+// layout of an operand tile (screen_row_offset, 128 rows): row e is query
+// column e of the item (v^, -1/2, -1/2, the threshold split into three
+// bf16 parts), rows e >= count padding columns (threshold -2^126: never
+// kept).  A column whose list is not full yet (bound +inf: every point may
+// enter) gets threshold +2^126.  One CTA of 128 threads per item, items
+// read from the device's count of the round.
+template <int KH>
+__global__ void __launch_bounds__(128)
+    prep_kernel(DevTree t, ScreenData sc, const Item* __restrict__ items,
+                const Counters* __restrict__ ctr,
+                const uint32_t* __restrict__ act,
+                const float* __restrict__ qpad,
+                const float* __restrict__ lst_d, int K,
+                uint8_t* __restrict__ bop) {
+  const int n_items = ctr->n_items;
+  const int e = threadIdx.x;
+  const int d = t.d;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const Item w = items[it];
+    uint16_t th = 0xfe80, tm = 0, tl = 0;  // -2^126: never kept
+    float vq[16 * KH];
+#pragma unroll
+    for (int i = 0; i < 16 * KH; ++i) vq[i] = 0.f;
+    if (e < w.count) {
+      const uint32_t q = act[w.start + e];
+      const float bound = lst_d[(size_t)q * K + K - 1];
+      const float* qp = qpad + (size_t)q * t.Dp;
+      const float* c = sc.center + (size_t)w.leaf * d;
+      float qn = 0.f, ss = 0.f;  // |v^|^2 rounded to nearest / upward
+#pragma unroll
+      for (int i = 0; i < 16 * KH; ++i)
+        if (i < d) {
+          const float v = bf16_value(bf16_bits(__fsub_rn(qp[i], c[i])));
+          vq[i] = v;
+          qn = __fmaf_rn(v, v, qn);
+          ss = __fmaf_ru(v, v, ss);
+        }
+      if (isinf(bound)) {
+        th = 0x7e80;  // +2^126: the list is not full, every point may enter
+      } else {
+        // thr of the header comment, every step rounded upward (divisors
+        // downward) so that the float result is never too small
+        const float rho = 0x1p-8f * 1.0001f;  // bf16: 8 significant bits
+        const float rr = __fdiv_ru(rho, __fsub_rd(1.f, rho));
+        const float one_m_g = __fsub_rd(1.f, (float)(d + 3) * 0x1p-24f);
+        const float aq = __fadd_ru(__fmul_ru(rr, __fsqrt_ru(ss)), 0x1p-123f);
+        const float R =
+            __fsqrt_ru(__fdiv_ru(__fadd_ru(bound, 0x1p-120f), one_m_g));
+        const float Rb = __fadd_ru(__fadd_ru(R, aq), sc.bmax[w.leaf]);
+        const float Rb2 = __fmul_ru(Rb, Rb);
+        const float E = __fadd_ru(
+            __fmul_ru(0x1p-13f, __fadd_ru(ss, Rb2)),
+            __fadd_ru(__fmul_ru(0x1p-14f, sc.pnmax[w.leaf]), 0x1p-120f));
+        const float thr = __fsub_ru(__fadd_ru(Rb2, E), qn);
+        // t = thr / 2 split into three bf16 parts; each remainder is exact
+        // in float32 (it keeps at most 16, then 8 significant bits)
+        const float tt = 0.5f * thr;
+        th = bf16_bits(tt);
+        const float r1 = __fsub_rn(tt, bf16_value(th));
+        tm = bf16_bits(r1);
+        const float r2 = __fsub_rn(r1, bf16_value(tm));
+        tl = bf16_bits(r2);
+      }
+    }
+    // slots: v^ (0..d-1), -1/2, -1/2 against the norm split, the threshold
+    uint8_t* tile = bop + (size_t)it * tile_bytes(KH);
+#pragma unroll
+    for (int kg = 0; kg < 2 * KH; ++kg) {
+      uint32_t wv[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        uint16_t h2[2];
+#pragma unroll
+        for (int x = 0; x < 2; ++x) {
+          const int slot = 8 * kg + 2 * j + x;
+          h2[x] = slot < d        ? bf16_bits(vq[slot < 16 * KH ? slot : 0])
+                  : slot < d + 2  ? (uint16_t)0xbf00
+                  : slot == d + 2 ? th
+                  : slot == d + 3 ? tm
+                  : slot == d + 4 ? tl
+                                  : (uint16_t)0;
+        }
+        wv[j] = (uint32_t)h2[0] | ((uint32_t)h2[1] << 16);
+      }
+      *reinterpret_cast<uint4*>(tile + screen_row_offset(e, kg, KH)) =
+          make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    }
+  }
+}
+
+// ---------------------------------------------------------- screen kernel
 // The screen's view of its dynamic shared memory.
 struct Smem {
   uint8_t* base;
@@ -318,211 +403,48 @@ struct Smem {
   __device__ uint32_t bop_u32(int g, int kh) const {
     return base_u32 + L.bop + (uint32_t)g * tile_bytes(kh);
   }
-  __device__ uint8_t* grp(int g) const {
-    return base + L.grp + (uint32_t)g * L.grp_stride;
-  }
   __device__ uint32_t bar(int i) const { return base_u32 + L.bars + 8u * i; }
   __device__ uint32_t afull(int s) const { return bar(s); }
   __device__ uint32_t aempty(int s) const { return bar(S + s); }
   __device__ uint32_t accfull(int b) const { return bar(2 * S + b); }
   __device__ uint32_t accempty(int b) const { return bar(2 * S + 2 + b); }
-  __device__ uint32_t bready(int g) const { return bar(2 * S + 4 + g); }
-  __device__ uint32_t epidone(int g) const { return bar(2 * S + 6 + g); }
-  __device__ uint32_t qfree(int g) const { return bar(2 * S + 8 + g); }
-  __device__ uint32_t itemfull(int i) const { return bar(2 * S + 10 + i); }
+  __device__ uint32_t bfull(int g) const { return bar(2 * S + 4 + g); }
+  __device__ uint32_t bempty(int g) const {
+    return bar(2 * S + 4 + kBops + g);
+  }
+  __device__ uint32_t itemfull(int i) const {
+    return bar(2 * S + 4 + 2 * kBops + i);
+  }
   __device__ uint32_t itemempty(int i) const {
-    return bar(2 * S + 10 + kItemRing + i);
+    return bar(2 * S + 4 + 2 * kBops + kItemRing + i);
   }
   __device__ int4* items() const {
     return reinterpret_cast<int4*>(base + L.items);
   }
-  // misc words: [0] tensor-memory base, [1] abort, [2 + g] queue count of
-  // group g, [4 + g] queue overflow of group g
+  // misc words: [0] tensor-memory base, [1] abort, [2 + g] survivors queued
+  // for the item of parity g
   __device__ uint32_t* misc() const {
     return reinterpret_cast<uint32_t*>(base + L.misc);
   }
 };
 
-// Column e of item (leaf, start, count), prepared by its column group g:
-// the query operand row of B (group g's buffer), the query's padded
-// coordinates, id and list bound.  A column whose list is not full yet
-// (bound +inf: every point may enter) is marked for an exact scan of the
-// whole leaf and screened out (threshold -2^126); rows e >= count are
-// padding columns (never kept).
-template <int KH>
-__device__ __forceinline__ void setup_column(
-    const DevTree& t, const ScreenData& sc, int leaf, int start, int count,
-    int e, int g, const uint32_t* __restrict__ act,
-    const float* __restrict__ qpad, const float* __restrict__ lst_d, int K,
-    const Smem& sm) {
-  uint8_t* gp = sm.grp(g);
-  float* qc = reinterpret_cast<float*>(gp + sm.L.qc) + e * t.Dp;
-  uint32_t* colq = reinterpret_cast<uint32_t*>(gp + sm.L.colq);
-  float* colb = reinterpret_cast<float*>(gp + sm.L.colb);
-  uint32_t* colx = reinterpret_cast<uint32_t*>(gp + sm.L.colx);
-  const int d = t.d;
-  uint16_t th = 0xfe80, tm = 0, tl = 0;  // -2^126: never kept
-  float vq[16 * KH];
-#pragma unroll
-  for (int i = 0; i < 16 * KH; ++i) vq[i] = 0.f;
-  if (e < count) {
-    const uint32_t q = act[start + e];
-    const float bound = lst_d[(size_t)q * K + K - 1];
-    colq[e] = q;
-    colb[e] = bound;
-    colx[e] = isinf(bound) ? 1u : 0u;
-    const float* qp = qpad + (size_t)q * t.Dp;
-    const float* c = sc.center + (size_t)leaf * d;
-    for (int i = 0; i < t.Dp; ++i) qc[i] = qp[i];
-    float qn = 0.f, ss = 0.f;  // |v^|^2 rounded to nearest / upward
-    for (int i = 0; i < d; ++i) {
-      const float v = bf16_value(bf16_bits(__fsub_rn(qp[i], c[i])));
-      vq[i] = v;
-      qn = __fmaf_rn(v, v, qn);
-      ss = __fmaf_ru(v, v, ss);
-    }
-    if (!isinf(bound)) {
-      // thr of the header comment, every step rounded upward (divisors
-      // downward) so that the float result is never too small
-      const float rho = 0x1p-8f * 1.0001f;  // bf16: 8 significant bits
-      const float rr = __fdiv_ru(rho, __fsub_rd(1.f, rho));
-      const float one_m_g = __fsub_rd(1.f, (float)(d + 3) * 0x1p-24f);
-      const float aq = __fadd_ru(__fmul_ru(rr, __fsqrt_ru(ss)), 0x1p-123f);
-      const float R =
-          __fsqrt_ru(__fdiv_ru(__fadd_ru(bound, 0x1p-120f), one_m_g));
-      const float Rb = __fadd_ru(__fadd_ru(R, aq), sc.bmax[leaf]);
-      const float Rb2 = __fmul_ru(Rb, Rb);
-      const float E = __fadd_ru(
-          __fmul_ru(0x1p-13f, __fadd_ru(ss, Rb2)),
-          __fadd_ru(__fmul_ru(0x1p-14f, sc.pnmax[leaf]), 0x1p-120f));
-      const float thr = __fsub_ru(__fadd_ru(Rb2, E), qn);
-      // t = thr / 2 split into three bf16 parts; each remainder is exact in
-      // float32 (it keeps at most 16, then 8 significant bits)
-      const float tt = 0.5f * thr;
-      th = bf16_bits(tt);
-      const float r1 = __fsub_rn(tt, bf16_value(th));
-      tm = bf16_bits(r1);
-      const float r2 = __fsub_rn(r1, bf16_value(tm));
-      tl = bf16_bits(r2);
-    }
-  }
-  // slots: v^ (0..d-1), -1/2, -1/2 against the norm split, the threshold
-  uint16_t hv[16 * KH];
-#pragma unroll
-  for (int i = 0; i < 16 * KH; ++i) hv[i] = bf16_bits(vq[i]);
-  hv[d] = 0xbf00;
-  hv[d + 1] = 0xbf00;
-  hv[d + 2] = th;
-  hv[d + 3] = tm;
-  hv[d + 4] = tl;
-  uint8_t* bop = sm.base + sm.L.bop + g * tile_bytes(KH);
-#pragma unroll
-  for (int kg = 0; kg < 2 * KH; ++kg) {
-    uint32_t w[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-      w[j] = (uint32_t)hv[8 * kg + 2 * j] |
-             ((uint32_t)hv[8 * kg + 2 * j + 1] << 16);
-    *reinterpret_cast<uint4*>(bop + screen_row_offset(e, kg, KH)) =
-        make_uint4(w[0], w[1], w[2], w[3]);
-  }
-}
-
-// Sorted insertion of (dv, id) into the list Ld/Li of K entries (dv below
-// the last entry); an equal entry already present stays in front.
-__device__ __forceinline__ void insert_entry(float* Ld, uint32_t* Li, int K,
-                                             float dv, uint32_t id) {
-  int pos = K - 1;
-  while (pos > 0 && Ld[pos - 1] > dv) {
-    Ld[pos] = Ld[pos - 1];
-    Li[pos] = Li[pos - 1];
-    --pos;
-  }
-  Ld[pos] = dv;
-  Li[pos] = id;
-}
-
-// Exact rescoring of item (leaf, count, np points) by its column group g
-// (thread e): the queued (point, column) pairs that passed the screen are
-// scored with the float32 chain, then thread e inserts its column's pairs
-// below the bound into the query's list, which it reads from HBM on the
-// first insertion and writes back once.  Columns marked for a full scan
-// (list not full at setup), and every column after a queue overflow, are
-// scored against every point of the leaf instead.
-__device__ void rescore_item(const DevTree& t, int leaf, int count, int np,
-                             int e, int g, int K, float* __restrict__ lst_d,
-                             uint32_t* __restrict__ lst_i, const Smem& sm,
-                             Counters* ctr) {
-  uint8_t* gp = sm.grp(g);
-  const float* qc = reinterpret_cast<const float*>(gp + sm.L.qc);
-  const uint32_t* colq = reinterpret_cast<const uint32_t*>(gp + sm.L.colq);
-  const float* colb = reinterpret_cast<const float*>(gp + sm.L.colb);
-  const uint32_t* colx = reinterpret_cast<const uint32_t*>(gp + sm.L.colx);
-  const uint32_t* queue = reinterpret_cast<const uint32_t*>(gp + sm.L.queue);
-  float* qd = reinterpret_cast<float*>(gp + sm.L.qd);
-  const int nq = min((int)sm.misc()[2 + g], kQcap);
-  const bool ovf = sm.misc()[4 + g] != 0;
-  if (e == 0) {
-    atomicAdd(&ctr->screen_queued, (unsigned long long)sm.misc()[2 + g]);
-    if (ovf) atomicAdd(&ctr->screen_overflow, 1ull);
-  }
-  const uint32_t slot0 = (uint32_t)((int64_t)leaf * t.lcap);
-  if (!ovf)
-    for (int i = e; i < nq; i += kGrpThreads) {
-      const uint32_t en = queue[i];
-      qd[i] = exact_dist(qc + (en & 127u) * t.Dp, t.pts, t.Dp,
-                         slot0 + (en >> 7));
-    }
-  group_sync(g);
-  if (e < count) {
-    float Ld[BKD_MAX_K + 1];
-    uint32_t Li[BKD_MAX_K + 1];
-    float bound = colb[e];
-    bool loaded = false;
-    const uint32_t q = colq[e];
-    auto take_pair = [&](float dv, uint32_t id) {
-      if (!(dv < bound)) return;
-      if (!loaded) {
-        for (int j = 0; j < K; ++j) {
-          Ld[j] = lst_d[(size_t)q * K + j];
-          Li[j] = lst_i[(size_t)q * K + j];
-        }
-        loaded = true;
-      }
-      insert_entry(Ld, Li, K, dv, id);
-      bound = Ld[K - 1];
-    };
-    if (ovf || colx[e]) {
-      for (int u = 0; u < np; ++u)
-        take_pair(exact_dist(qc + e * t.Dp, t.pts, t.Dp, slot0 + u),
-                  slot0 + u);
-    } else {
-      for (int i = 0; i < nq; ++i) {
-        const uint32_t en = queue[i];
-        if ((int)(en & 127u) == e) take_pair(qd[i], slot0 + (en >> 7));
-      }
-    }
-    if (loaded)
-      for (int j = 0; j < K; ++j) {
-        lst_d[(size_t)q * K + j] = Ld[j];
-        lst_i[(size_t)q * K + j] = Li[j];
-      }
-  }
-  group_sync(g);  // the group's queue and column data are free again
-}
+// Survivors of the screen: per work item a segment of kSegCap entries
+// (point index in the leaf << 7 | query column) and its count (a count above
+// kSegCap: the segment overflowed; the item is scored by the float32 leaf
+// kernel instead).
+constexpr int kSegCap = 512;
 
 template <int KH>
 __global__ void __launch_bounds__(kThreads, 2)
     screen_kernel(DevTree t, ScreenData sc, const Item* __restrict__ items,
                   int item_lo, int item_hi, Counters* ctr,
-                  const uint32_t* __restrict__ act,
-                  const float* __restrict__ qpad, float* __restrict__ lst_d,
-                  uint32_t* __restrict__ lst_i, int K) {
+                  const uint8_t* __restrict__ bop_g,
+                  uint32_t* __restrict__ seg, int32_t* __restrict__ seg_cnt) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   Smem sm;
   sm.base = smem_raw;
   sm.base_u32 = (uint32_t)__cvta_generic_to_shared(smem_raw);
-  sm.L = layout_of(KH, t.Dp);
+  sm.L = layout_of(KH);
   sm.S = ring_stages(KH);
   const int S = sm.S;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -535,13 +457,14 @@ __global__ void __launch_bounds__(kThreads, 2)
     for (int b = 0; b < 2; ++b) {
       mbar_init(sm.accfull(b), 1);
       mbar_init(sm.accempty(b), kEpiThreads);
-      mbar_init(sm.bready(b), kGrpThreads);
-      mbar_init(sm.epidone(b), kEpiThreads);
-      mbar_init(sm.qfree(b), kGrpThreads);
+    }
+    for (int g = 0; g < kBops; ++g) {
+      mbar_init(sm.bfull(g), 1);
+      mbar_init(sm.bempty(g), 1);
     }
     for (int i = 0; i < kItemRing; ++i) {
       mbar_init(sm.itemfull(i), 1);
-      mbar_init(sm.itemempty(i), 1 + kEpiThreads + kGrpThreads);
+      mbar_init(sm.itemempty(i), 1 + kEpiThreads);
     }
     for (int i = 1; i < 8; ++i) sm.misc()[i] = 0;
     mbar_init_fence();
@@ -567,31 +490,59 @@ __global__ void __launch_bounds__(kThreads, 2)
     // (item_hi < 0: this round's item count, read on the device)
     const int hi = item_hi >= 0 ? item_hi : ctr->n_items;
     if (lane == 0) {
-      uint32_t c = 0;  // tiles issued
-      uint32_t last[8];  // last tile issued into each ring slot + 1
+      uint32_t c = 0;  // point tiles issued
+      uint32_t last[20];  // last tile issued into each ring slot + 1
+      uint32_t lastb[kBops];  // last item (+1) whose operand went into each
+                              // query-operand buffer
       for (int s = 0; s < S; ++s) last[s] = 0;
-      for (int n = 0;; ++n) {
-        const int ir = n % kItemRing;
+      for (int g = 0; g < kBops; ++g) lastb[g] = 0;
+      // items are claimed kClaim at a time; their descriptors and leaf sizes
+      // are loaded together (one memory latency per claim)
+      Item wq[kClaim];
+      int nq[kClaim];
+      int have = 0, at = 0, first = 0;
+      int n = 0;
+      for (;; ++n) {
+        if (at == have) {
+          first = atomicAdd(&ctr->screen_next, kClaim) + item_lo;
+          have = max(0, min(kClaim, hi - first));
+          at = 0;
+#pragma unroll
+          for (int j = 0; j < kClaim; ++j)
+            if (j < have) wq[j] = items[first + j];
+#pragma unroll
+          for (int j = 0; j < kClaim; ++j)
+            if (j < have) nq[j] = t.leaf_cnt[wq[j].leaf];
+        }
+        const int ir = n % kItemRing, g = n % kBops;
         if (!bar_wait(sm.itemempty(ir), ((n / kItemRing) & 1) ^ 1, abort,
                       ctr))
           break;
-        const int it = atomicAdd(&ctr->screen_next, 1) + item_lo;
-        if (it >= hi) {
-          // two end marks: one for each column group
+        if (have == 0) {
           sm.items()[ir] = make_int4(-1, 0, 0, 0);
           bar_arrive(sm.itemfull(ir));
-          const int ir2 = (n + 1) % kItemRing;
-          if (bar_wait(sm.itemempty(ir2), (((n + 1) / kItemRing) & 1) ^ 1,
-                       abort, ctr)) {
-            sm.items()[ir2] = make_int4(-1, 0, 0, 0);
-            bar_arrive(sm.itemfull(ir2));
-          }
           break;
         }
-        const Item w = items[it];
-        const int nt = (t.leaf_cnt[w.leaf] + kScreenRows - 1) / kScreenRows;
-        sm.items()[ir] = make_int4(w.leaf, w.start, w.count, nt);
+        Item w = wq[0];
+        int np = nq[0];
+#pragma unroll
+        for (int j = 1; j < kClaim; ++j)
+          if (j == at) {
+            w = wq[j];
+            np = nq[j];
+          }
+        const int it = first + at;
+        ++at;
+        const int nt = (np + kScreenRows - 1) / kScreenRows;
+        sm.items()[ir] = make_int4(w.leaf, it, w.count, nt);
         bar_arrive(sm.itemfull(ir));
+        // the item's query operand, once the MMAs of the item kBops before
+        // are done with the buffer
+        if (!bar_wait(sm.bempty(g), ((n / kBops) & 1) ^ 1, abort, ctr))
+          break;
+        bulk_load(sm.bop_u32(g, KH), bop_g + (size_t)it * tile_bytes(KH),
+                  tile_bytes(KH), sm.bfull(g));
+        lastb[g] = (uint32_t)n + 1;
         const uint8_t* src = words + (size_t)w.leaf * tiles * tile_bytes(KH);
         bool ok = true;
         for (int ti = 0; ti < nt; ++ti, ++c) {
@@ -608,13 +559,21 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       if (c)
         atomicAdd(&ctr->screen_bytes,
-                  (unsigned long long)c * tile_bytes(KH));
+                  (unsigned long long)(c + n) * tile_bytes(KH));
       // copies still in flight land before the CTA leaves
       for (int s = 0; s < S; ++s)
         if (last[s]) {
           const uint32_t cl = last[s] - 1;
           const long long t0 = clock64();
           while (!bar_try(sm.afull(s), (cl / S) & 1) &&
+                 clock64() - t0 < (1ll << 31)) {
+          }
+        }
+      for (int g = 0; g < kBops; ++g)
+        if (lastb[g]) {
+          const uint32_t nl = lastb[g] - 1;
+          const long long t0 = clock64();
+          while (!bar_try(sm.bfull(g), (nl / kBops) & 1) &&
                  clock64() - t0 < (1ll << 31)) {
           }
         }
@@ -625,14 +584,13 @@ __global__ void __launch_bounds__(kThreads, 2)
       uint32_t c = 0;  // tiles consumed
       bool issued = false;
       for (int n = 0;; ++n) {
-        const int ir = n % kItemRing;
+        const int ir = n % kItemRing, g = n % kBops;
         if (!bar_wait(sm.itemfull(ir), (n / kItemRing) & 1, abort, ctr))
           break;
         const int4 dsc = sm.items()[ir];
         bar_arrive(sm.itemempty(ir));
         if (dsc.x < 0) break;
-        const int g = n & 1;
-        if (!bar_wait(sm.bready(g), (n >> 1) & 1, abort, ctr)) break;
+        if (!bar_wait(sm.bfull(g), (n / kBops) & 1, abort, ctr)) break;
         const uint32_t idesc = mma_idesc((dsc.z + 15) & ~15);
         const uint32_t bop = sm.bop_u32(g, KH);
         bool ok = true;
@@ -653,6 +611,7 @@ __global__ void __launch_bounds__(kThreads, 2)
           tc_commit(sm.accfull(b));
           issued = true;
         }
+        tc_commit(sm.bempty(g));  // the query operand buffer is free
         if (!ok) break;
       }
       if (issued) {
@@ -664,12 +623,11 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
       }
     }
-  } else if (warp < 6) {
+  } else {
     // ------------------------------------------------------- epilogue
-    // Every decision to leave is taken by all 128 epilogue threads together
-    // (an OR over the group at its named barrier); a failed wait inside an
-    // item only skips that tile's accumulator reads (warp-uniform, as
-    // tcgen05.ld requires).
+    // A decision to leave is taken by all 128 epilogue threads together (an
+    // OR at their named barrier); a failed wait inside an item only skips
+    // that tile's accumulator reads (warp-uniform, as tcgen05.ld requires).
     const int quarter = warp & 3;  // tensor-memory lanes 32 quarter ..
     const int row = 32 * quarter + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
@@ -677,23 +635,16 @@ __global__ void __launch_bounds__(kThreads, 2)
     unsigned long long kept = 0;
     for (int n = 0;; ++n) {
       const int ir = n % kItemRing, g = n & 1;
-      bool got = bar_wait(sm.itemfull(ir), (n / kItemRing) & 1, abort, ctr);
+      const bool got =
+          bar_wait(sm.itemfull(ir), (n / kItemRing) & 1, abort, ctr);
       int4 dsc = make_int4(-1, 0, 0, 0);
       if (got) {
         dsc = sm.items()[ir];
         bar_arrive(sm.itemempty(ir));
       }
-      // the group's queue is free once it rescored its previous item
-      if (got && dsc.x >= 0)
-        got = bar_wait(sm.qfree(g), ((n >> 1) & 1) ^ 1, abort, ctr);
-      if (threadIdx.x == 64 && got) {
-        sm.misc()[2 + g] = 0;
-        sm.misc()[4 + g] = 0;
-      }
       if (sync128_or<1>(!got) || dsc.x < 0) break;
-      const int nt = dsc.w, ncol = (dsc.z + 15) & ~15;
-      uint32_t* queue =
-          reinterpret_cast<uint32_t*>(sm.grp(g) + sm.L.queue);
+      const int it = dsc.y, nt = dsc.w, ncol = (dsc.z + 15) & ~15;
+      uint32_t* out = seg + (size_t)it * kSegCap;
       bool ok = true;
       for (int ti = 0; ti < nt; ++ti, ++c) {
         const int b = c & 1;
@@ -732,7 +683,7 @@ __global__ void __launch_bounds__(kThreads, 2)
           tc_fence_before();
           bar_arrive(sm.accempty(b));
         }
-        // rare: queue this row's passing columns for the column group
+        // rare: this row's passing columns go to the item's segment
         const int np = __popc(mask[0]) + __popc(mask[1]) + __popc(mask[2]) +
                        __popc(mask[3]);
         if (np) {
@@ -741,45 +692,20 @@ __global__ void __launch_bounds__(kThreads, 2)
           const uint32_t u = (uint32_t)(ti * kScreenRows + row);
           for (int w = 0; w < 4; ++w)
             for (uint32_t mw = mask[w]; mw; mw &= mw - 1u, ++at)
-              if (at < kQcap)
-                queue[at] = (u << 7) | (uint32_t)(32 * w + __ffs(mw) - 1);
-          if (at > kQcap) sm.misc()[4 + g] = 1;
+              if (at < kSegCap)
+                out[at] = (u << 7) | (uint32_t)(32 * w + __ffs(mw) - 1);
         }
       }
-      // queue complete: the column group may rescore
-      bar_arrive(sm.epidone(g));
-      if (sync128_or<1>(!ok)) break;
+      // every survivor of the item is queued: its count goes out and the
+      // counter is cleared for the item after next
+      const bool stop = sync128_or<1>(!ok);
+      if (threadIdx.x == 64) {
+        seg_cnt[it] = (int32_t)sm.misc()[2 + g];
+        sm.misc()[2 + g] = 0;
+      }
+      if (stop) break;
     }
     if (kept) atomicAdd(&ctr->screen_kept, kept);
-  } else {
-    // ------------------------------------------------- column groups
-    // Group g takes the items n = g, g + 2, ...: it prepares the query
-    // operand of item n, and once the epilogue has queued item n's
-    // survivors it rescores them; meanwhile the other group's item runs on
-    // the tensor cores.
-    const int g = (warp - 6) >> 2;
-    const int e = threadIdx.x - 64 - kEpiThreads - g * kGrpThreads;
-    for (int n = g;; n += 2) {
-      const int ir = n % kItemRing;
-      const bool got =
-          bar_wait(sm.itemfull(ir), (n / kItemRing) & 1, abort, ctr);
-      int4 dsc = make_int4(-1, 0, 0, 0);
-      if (got) {
-        dsc = sm.items()[ir];
-        bar_arrive(sm.itemempty(ir));
-      }
-      if (group_sync_or(g, !got) || dsc.x < 0) break;
-      setup_column<KH>(t, sc, dsc.x, dsc.y, dsc.z, e, g, act, qpad, lst_d, K,
-                       sm);
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      bar_arrive(sm.bready(g));
-      const bool done =
-          bar_wait(sm.epidone(g), (n >> 1) & 1, abort, ctr);
-      if (group_sync_or(g, !done)) break;
-      rescore_item(t, dsc.x, dsc.z, t.leaf_cnt[dsc.x], e, g, K, lst_d, lst_i,
-                   sm, ctr);
-      bar_arrive(sm.qfree(g));
-    }
   }
   tc_fence_before();
   __syncthreads();
@@ -789,6 +715,92 @@ __global__ void __launch_bounds__(kThreads, 2)
                      "r"(tmem),
                  "r"(kTmemCols)
                  : "memory");
+}
+
+// --------------------------------------------------------- rescore kernel
+// Exact rescoring of the survivors: one CTA of 128 threads per work item.
+// Thread e owns query column e: it scores the item's survivors in its
+// column with the float32 chain of the leaf kernel and inserts those below
+// the list's last entry (the list is read from HBM on the first insertion
+// and written back once).  An item whose segment overflowed is handed to
+// the float32 leaf kernel (appended to `ovf`) and not touched here.
+__global__ void __launch_bounds__(128)
+    rescore_kernel(DevTree t, const Item* __restrict__ items,
+                   Counters* ctr, const uint32_t* __restrict__ act,
+                   const float* __restrict__ qpad, float* __restrict__ lst_d,
+                   uint32_t* __restrict__ lst_i, int K,
+                   const uint32_t* __restrict__ seg,
+                   const int32_t* __restrict__ seg_cnt,
+                   Item* __restrict__ ovf) {
+  __shared__ uint32_t es[kSegCap];
+  const int n_items = ctr->n_items;
+  const int e = threadIdx.x;
+  unsigned long long queued = 0, overflow = 0;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int cnt = seg_cnt[it];
+    if (cnt == 0) continue;
+    const Item w = items[it];
+    if (cnt > kSegCap) {
+      // the float32 leaf kernel takes items of at most kPipeTile queries
+      if (e == 0) {
+        const int parts = (w.count + kPipeTile - 1) / kPipeTile;
+        const int at = atomicAdd(&ctr->screen_ovf_items, parts);
+        for (int j = 0; j < parts; ++j)
+          ovf[at + j] = Item{w.leaf, w.start + j * kPipeTile,
+                             min(kPipeTile, w.count - j * kPipeTile), 0};
+        ++overflow;
+      }
+      continue;
+    }
+    for (int i = e; i < cnt; i += 128) es[i] = seg[(size_t)it * kSegCap + i];
+    __syncthreads();
+    if (e < w.count) {
+      const uint32_t q = act[w.start + e];
+      const uint32_t slot0 = (uint32_t)((int64_t)w.leaf * t.lcap);
+      const float* qp = qpad + (size_t)q * t.Dp;
+      float Ld[BKD_MAX_K + 1];
+      uint32_t Li[BKD_MAX_K + 1];
+      float bound = 0.f;
+      bool loaded = false, changed = false;
+      for (int i = 0; i < cnt; ++i) {
+        const uint32_t en = es[i];
+        if ((int)(en & 127u) != e) continue;
+        if (!loaded) {
+          for (int j = 0; j < K; ++j) {
+            Ld[j] = lst_d[(size_t)q * K + j];
+            Li[j] = lst_i[(size_t)q * K + j];
+          }
+          bound = Ld[K - 1];
+          loaded = true;
+        }
+        const uint32_t slot = slot0 + (en >> 7);
+        const float dv = exact_dist(qp, t.pts, t.Dp, slot);
+        if (dv < bound) {
+          int pos = K - 1;
+          while (pos > 0 && Ld[pos - 1] > dv) {
+            Ld[pos] = Ld[pos - 1];
+            Li[pos] = Li[pos - 1];
+            --pos;
+          }
+          Ld[pos] = dv;
+          Li[pos] = slot;
+          bound = Ld[K - 1];
+          changed = true;
+        }
+      }
+      if (changed)
+        for (int j = 0; j < K; ++j) {
+          lst_d[(size_t)q * K + j] = Ld[j];
+          lst_i[(size_t)q * K + j] = Li[j];
+        }
+    }
+    if (e == 0) queued += (unsigned long long)cnt;
+    __syncthreads();
+  }
+  if (e == 0 && (queued || overflow)) {
+    atomicAdd(&ctr->screen_queued, queued);
+    atomicAdd(&ctr->screen_overflow, overflow);
+  }
 }
 
 const void* screen_kernel_for(int kh) {
@@ -803,8 +815,8 @@ const void* screen_kernel_for(int kh) {
 // Dynamic shared memory of a launch: the layout, raised if needed so that
 // at most two CTAs share an SM (two accumulator pairs fill its tensor
 // memory: an allocation never has to wait for another CTA).
-size_t screen_smem(int kh, int Dp) {
-  const size_t need = layout_of(kh, Dp).total;
+size_t screen_smem(int kh) {
+  const size_t need = layout_of(kh).total;
   return std::max<size_t>(need, 80 * 1024);
 }
 
@@ -891,14 +903,16 @@ __global__ void __launch_bounds__(128)
 }  // namespace
 
 int screen_grid(int kh, int Dp, int64_t lcap, int K, int sm_count) {
-  if (kh < 1 || kh > 3 || K < 1 || K > BKD_MAX_K + 1 ||
+  if (kh < 1 || kh > 3 || Dp < 1 || K < 1 || K > BKD_MAX_K + 1 ||
       lcap >= ((int64_t)1 << 24))
     return 0;
-  const size_t smem = screen_smem(kh, Dp);
+  const size_t smem = screen_smem(kh);
   const void* k = screen_kernel_for(kh);
   if (smem > 227 * 1024 ||
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem) != cudaSuccess)
+                           (int)smem) != cudaSuccess ||
+      cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           100) != cudaSuccess)
     return 0;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads,
@@ -906,41 +920,46 @@ int screen_grid(int kh, int Dp, int64_t lcap, int K, int sm_count) {
       per_sm < 1)
     return 0;
   // tensor memory: 512 columns per SM, kTmemCols per CTA
-  if (per_sm * kTmemCols > 512) return 0;
+  per_sm = std::min<int>(per_sm, 512 / kTmemCols);
   return per_sm * sm_count;
 }
 
+int64_t screen_seg_cap() { return kSegCap; }
+
 cudaError_t launch_screen(const DevTree& t, const ScreenData& sd,
-                          const Item* items, int item_lo, int item_hi,
-                          Counters* ctr, const uint32_t* act,
-                          const float* qpad, float* lst_d, uint32_t* lst_i,
-                          int K, int grid, cudaStream_t s) {
-  if (item_hi >= 0) {
-    const int n = item_hi - item_lo;
-    if (n <= 0) return cudaSuccess;
-    grid = std::min(grid, n);
-  }
-  if (grid <= 0) return cudaSuccess;
-  const size_t smem = screen_smem(sd.kh, t.Dp);
-  cudaError_t e = cudaMemsetAsync(&ctr->screen_next, 0, sizeof(int32_t), s);
+                          const Item* items, int n_items, Counters* ctr,
+                          const uint32_t* act, const float* qpad,
+                          float* lst_d, uint32_t* lst_i, int K, int grid,
+                          const ScreenWork& w, int cap, int leaf_grid,
+                          int sm_count, cudaStream_t s) {
+  if (n_items == 0 || grid <= 0) return cudaSuccess;
+  if (n_items > 0) grid = std::min(grid, n_items);
+  const int aux = n_items > 0 ? std::min(n_items, sm_count * 16)
+                              : sm_count * 16;
+  const size_t smem = screen_smem(sd.kh);
+  cudaError_t e = cudaMemsetAsync(&ctr->screen_next, 0,
+                                  2 * sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
+#define BKD_SCREEN_KH(KH)                                                    \
+  prep_kernel<KH><<<aux, 128, 0, s>>>(t, sd, items, ctr, act, qpad, lst_d,   \
+                                      K, w.bop);                             \
+  screen_kernel<KH><<<grid, kThreads, smem, s>>>(t, sd, items, 0, n_items,   \
+                                                 ctr, w.bop, w.seg,          \
+                                                 w.seg_cnt);
   switch (sd.kh) {
-    case 1:
-      screen_kernel<1><<<grid, kThreads, smem, s>>>(
-          t, sd, items, item_lo, item_hi, ctr, act, qpad, lst_d, lst_i, K);
-      break;
-    case 2:
-      screen_kernel<2><<<grid, kThreads, smem, s>>>(
-          t, sd, items, item_lo, item_hi, ctr, act, qpad, lst_d, lst_i, K);
-      break;
-    case 3:
-      screen_kernel<3><<<grid, kThreads, smem, s>>>(
-          t, sd, items, item_lo, item_hi, ctr, act, qpad, lst_d, lst_i, K);
-      break;
-    default:
-      return cudaErrorInvalidValue;
+    case 1: BKD_SCREEN_KH(1) break;
+    case 2: BKD_SCREEN_KH(2) break;
+    case 3: BKD_SCREEN_KH(3) break;
+    default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+#undef BKD_SCREEN_KH
+  rescore_kernel<<<aux, 128, 0, s>>>(t, items, ctr, act, qpad, lst_d, lst_i,
+                                     K, w.seg, w.seg_cnt, w.ovf);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // items whose survivors overflowed their segment: the float32 kernel
+  return launch_leaf(t, cap, w.ovf, 0, -1, ctr, t.pts, 0, act, qpad, lst_d,
+                     lst_i, K, leaf_grid, s, &ctr->screen_ovf_items);
 }
 
 }  // namespace bkd

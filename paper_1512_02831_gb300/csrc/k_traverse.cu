@@ -265,12 +265,12 @@ __global__ void scatter_kernel(const int2* __restrict__ placed,
 
 __global__ void chunk_items_kernel(const int32_t* __restrict__ toff,
                                    const int32_t* __restrict__ off,
-                                   const int32_t* __restrict__ chunk_leaf,
-                                   int n_chunks, int32_t* __restrict__ out) {
+                                   const int32_t* __restrict__ leaf,
+                                   int count, int32_t* __restrict__ out) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c <= n_chunks) {
-    out[c] = toff[chunk_leaf[c]];
-    out[n_chunks + 1 + c] = off[chunk_leaf[c]];
+  if (c < count) {
+    out[c] = toff[leaf[c]];
+    out[count + c] = off[leaf[c]];
   }
 }
 
@@ -359,10 +359,10 @@ cudaError_t launch_bucket(const int2* placed, const uint32_t* act,
 }
 
 cudaError_t launch_chunk_items(const int32_t* toff, const int32_t* off,
-                               const int32_t* chunk_leaf, int n_chunks,
+                               const int32_t* leaf, int count,
                                int32_t* chunk_item, cudaStream_t s) {
-  chunk_items_kernel<<<blocks(n_chunks + 1, 128), 128, 0, s>>>(
-      toff, off, chunk_leaf, n_chunks, chunk_item);
+  chunk_items_kernel<<<blocks(count, 128), 128, 0, s>>>(toff, off, leaf,
+                                                        count, chunk_item);
   return cudaGetLastError();
 }
 

@@ -114,6 +114,7 @@ struct bkd_server {
   // per leaf / per round
   int32_t *cnt = nullptr, *off = nullptr, *cursor = nullptr, *toff = nullptr;
   Item* items = nullptr;
+  ScreenWork sw;            // screened rounds' workspace (see ScreenWork)
   int32_t* batch_left = nullptr;  // device, kMaxBatches
   Counters *d_ctr = nullptr, *d_fin = nullptr;
   Counters *h_ctr = nullptr, *h_fin = nullptr;  // pinned
@@ -147,6 +148,10 @@ struct bkd_server {
     cudaFree(cursor);
     cudaFree(toff);
     cudaFree(items);
+    cudaFree(sw.bop);
+    cudaFree(sw.seg);
+    cudaFree(sw.seg_cnt);
+    cudaFree(sw.ovf);
     cudaFree(batch_left);
     cudaFree(d_ctr);
     cudaFree(d_fin);
@@ -245,8 +250,9 @@ int bkd_server::round() {
   const int n_next = h_ctr->n_next, n_items = h_ctr->n_items;
   if (n_next > 0) {
     if (screened)
-      SV_CU(launch_screen(D, v.screen, items, 0, n_items, d_ctr, nxt, qpad,
-                          lst_d, lst_i, K, screen_max, s));
+      SV_CU(launch_screen(D, v.screen, items, n_items, d_ctr, nxt, qpad,
+                          lst_d, lst_i, K, screen_max, sw, cap, grid_max,
+                          v.sm_count, s));
     else
       SV_CU(launch_leaf(D, cap, items, 0, n_items, d_ctr, v.d_pts, 0, nxt,
                         qpad, lst_d, lst_i, K, std::min(grid_max, n_items),
@@ -346,6 +352,13 @@ int bkd_serve_open(bkd_tree* t, int k_max, int64_t max_queries,
                         v.stream));
   SV_CU(cudaStreamSynchronize(v.stream));
   sv->grid_max = leaf_kernel_grid(D.Dp, sv->cap, v.sm_count);
+  if (v.screen.words) {
+    const int64_t si = Q / kScreenTile + L + 1;
+    SV_CU(dev_alloc(&sv->sw.bop, si * 4096 * v.screen.kh));
+    SV_CU(dev_alloc(&sv->sw.seg, si * screen_seg_cap()));
+    SV_CU(dev_alloc(&sv->sw.seg_cnt, si));
+    SV_CU(dev_alloc(&sv->sw.ovf, 2 * si));
+  }
   sv->screen_max = v.screen.words
                        ? screen_grid(v.screen.kh, D.Dp, D.lcap, sv->K,
                                      v.sm_count)

@@ -177,6 +177,42 @@ def test_chunked_mode_is_bit_identical(chunks):
           rows=np.arange(512))
 
 
+@pytest.mark.parametrize("chunks", [2, 3, 7])
+def test_point_split_chunks_are_bit_identical(chunks):
+    """The paper's point chunks (Sec. 3.2: positions ceil(j n / N) .. of the
+    leaf structure, so leaves straddle chunks and their queries are scanned
+    piecewise in consecutive chunks) give the same results as the resident
+    tree; n is not a multiple of the chunk count or of 4."""
+    w = workloads.scaled(workloads.MIXTURE_64M, (1 << 17) + 1237, 1 << 13, 9)
+    P, Q = w.points(), w.queries()
+    idx0, dist0, _ = run(P, Q, w.k, w.height)
+    idx1, dist1, st = run(P, Q, w.k, w.height, chunks=chunks, point_chunks=1)
+    assert np.array_equal(idx0, idx1) and np.array_equal(dist0, dist1)
+    assert st["chunk_bytes"] > 0
+    check(P, Q, w.k, idx1, dist1, oracle.brute_knn(P, Q[:512], w.k),
+          rows=np.arange(512))
+
+
+def test_chunk_schedule_streams_less_than_every_chunk_every_round():
+    """Leaf-aligned chunks keep the resident chunks running while they hold
+    buffered queries: far fewer bytes are copied than one pass over the
+    leaf structure per round, and the results stay those of the resident
+    tree."""
+    w = workloads.scaled(workloads.MIXTURE_64M, 1 << 18, 1 << 14, 10)
+    P, Q = w.points(), w.queries()
+    idx0, dist0, _ = run(P, Q, w.k, w.height)
+    tree = bkd.bkd_build(P, w.height, chunks=8, tail_queries=0)
+    try:
+        idx1, dist1 = bkd.bkd_query(tree, Q, w.k)
+        rounds = bkd.bkd_get_stat(tree, "rounds")
+        copied = bkd.bkd_get_stat(tree, "chunk_bytes")
+    finally:
+        bkd.bkd_free(tree)
+    assert np.array_equal(idx0, idx1) and np.array_equal(dist0, dist1)
+    structure = (1 << 18) * 10 * 4  # the leaf structure's float32 points
+    assert copied < 0.5 * rounds * structure, (copied, rounds)
+
+
 def test_chunked_by_memory_cap():
     P = workloads.uniform(50000, 10, 1)
     Q = workloads.uniform(3000, 10, 2)
