@@ -40,10 +40,15 @@ METRIC = ("kNN queries/s (k=10, d=10) FP32 vs BF16-screened; p50/p99 "
 LEAF_SRC = os.path.join(ROOT, "paper_1512_02831_gb300", "csrc", "k_leaf.cuh")
 TRAFFIC_NOTE = os.path.join(ROOT, "profiles",
                             "leaf_kernel_mixture64M_traffic.txt")
-SCREEN_SRC = os.path.join(ROOT, "paper_1512_02831_gb300", "csrc",
-                          "k_screen.cu")
-SCREEN_TRAFFIC_NOTE = os.path.join(ROOT, "profiles",
-                                   "screen_kernel_traffic.txt")
+# the two BF16 screen kernels: source file and committed ncu traffic note
+SCREEN_SRC = {0: os.path.join(ROOT, "paper_1512_02831_gb300", "csrc",
+                              "k_screen_warp.cu"),
+              1: os.path.join(ROOT, "paper_1512_02831_gb300", "csrc",
+                              "k_screen.cu")}
+SCREEN_TRAFFIC_NOTE = {0: os.path.join(ROOT, "profiles",
+                                       "screen_warp_kernel_traffic.txt"),
+                       1: os.path.join(ROOT, "profiles",
+                                       "screen_tcgen05_kernel_traffic.txt")}
 
 WORKLOADS = {"mixture64M": workloads.MIXTURE_64M,
              "uniform64K": workloads.UNIFORM_64K,
@@ -161,16 +166,16 @@ def leaf_traffic_per_launch():
     return float(m_b.group(1))
 
 
-def screen_traffic_per_launch(acc, launches):
+def screen_traffic_per_launch(acc, launches, kernel):
     """DRAM bytes (read + write) of an average screen launch, scaled from the
-    committed ncu capture of one launch if it was taken on the current screen
-    source: the capture's DRAM bytes per streamed operand byte times this
-    run's streamed bytes, over the run's screen launches."""
+    committed ncu capture of one launch if it was taken on the current source
+    of that screen kernel: the capture's DRAM bytes per streamed operand byte
+    times this run's streamed bytes, over the run's screen launches."""
     try:
-        text = open(SCREEN_TRAFFIC_NOTE).read()
+        text = open(SCREEN_TRAFFIC_NOTE[kernel]).read()
     except OSError:
         return None
-    sha = hashlib.sha256(open(SCREEN_SRC, "rb").read()).hexdigest()[:16]
+    sha = hashlib.sha256(open(SCREEN_SRC[kernel], "rb").read()).hexdigest()[:16]
     m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     m_r = re.search(r"dram_bytes_per_streamed_byte:\s*([0-9.e+-]+)", text)
     if not m_sha or not m_r or m_sha.group(1) != sha:
@@ -416,7 +421,9 @@ def run_ours(a, w, rank, world, local_rank):
     Q = rank_queries(w, rank)
     m, k, d = Q.shape[0], w.k, w.d
     t0 = time.perf_counter()
-    tree = bkd.bkd_build(P, w.height, precision=1)
+    # the point layouts of both BF16 screen kernels (warp / mma.sync and
+    # tcgen05): each is timed, the fastest configuration is the headline
+    tree = bkd.bkd_build(P, w.height, precision=1, screen_kernel=2)
     build_s = time.perf_counter() - t0
     Qd = torch.from_numpy(Q).to(dev)
     out_i = torch.empty((m, k), dtype=torch.int64, device=dev)
@@ -434,10 +441,12 @@ def run_ours(a, w, rank, world, local_rank):
     smi_index = (vis[local_rank] if local_rank < len(vis)
                  and vis[local_rank].strip().isdigit() else local_rank)
 
-    def timed(precision: int) -> dict:
+    def timed(precision: int, kernel: int = 0) -> dict:
         """W warm-up + K timed bkd_query steps with leaf scoring
-        `precision` (0 float32, 1 BF16 screen + float32 rescoring)."""
+        `precision` (0 float32, 1 BF16 screen + float32 rescoring) and, for
+        the screen, `kernel` (0 warp / mma.sync, 1 tcgen05)."""
         bkd.bkd_set_option(tree, "precision", precision)
+        bkd.bkd_set_option(tree, "screen_kernel", kernel)
         for _ in range(a.warmup):
             bkd.bkd_query(tree, Qd, k, out_i, out_d)
         barrier()
@@ -461,14 +470,17 @@ def run_ours(a, w, rank, world, local_rank):
                 "value": whole_job_rate(world, m, a.steps, ms_max),
                 "idx": out_i.clone(), "dist": out_d.clone()}
 
-    runs = {0: timed(0), 1: timed(1)}
-    identical = bool(torch.equal(runs[0]["idx"], runs[1]["idx"])
-                     and torch.equal(runs[0]["dist"], runs[1]["dist"]))
-    head = 1 if runs[1]["value"] > runs[0]["value"] else 0
+    # runs: 0 float32, 1 warp screen, 2 tcgen05 screen
+    runs = {0: timed(0), 1: timed(1, 0), 2: timed(1, 1)}
+    identical = all(bool(torch.equal(runs[0]["idx"], runs[r]["idx"])
+                         and torch.equal(runs[0]["dist"], runs[r]["dist"]))
+                    for r in (1, 2))
+    head = max(runs, key=lambda r: runs[r]["value"])
     acc, clk, ms, ms_max = (runs[head][x] for x in ("acc", "clk", "ms",
                                                      "ms_max"))
     value = runs[head]["value"]
-    bkd.bkd_set_option(tree, "precision", head)
+    bkd.bkd_set_option(tree, "precision", 0 if head == 0 else 1)
+    bkd.bkd_set_option(tree, "screen_kernel", 1 if head == 2 else 0)
     out_i.copy_(runs[head]["idx"])
 
     # end to end through the same call, host buffers (pinned), copies inside
@@ -519,54 +531,74 @@ def run_ours(a, w, rank, world, local_rank):
                       "achieved_tflops": 1.5 * achieved,
                       "peak_tflops_fma2": 2 * peak_ops},
     }
-    a1 = runs[1]["acc"]
-    kh = (d + 5 + 15) // 16  # k-halves: d offsets, 2 norm and 3 threshold slots
     dp = min(c for c in (2, 4, 6, 8, 10, 12, 16, 24, 32) if c >= d)
-    scr_s = a1["screen_ms"] / 1000.0
-    pairs_s = a1["screen_pairs"] / scr_s if scr_s else 0.0
     peak_bf16 = float(peaks.get("bf16_tflops") or 1900.0)
     peak_hbm = float(peaks.get("hbm_gbs") or 6800.0)
-    # algorithmic bytes of the screen: the bf16 operand tiles of every work
-    # item's leaf (counted by the kernel) plus, per (query, leaf) visit, the
-    # query's padded row and its list bound and id
-    scr_bytes = a1["screen_bytes"] + a1["screen_visits"] * (4 * dp + 8)
-    # one screen launch per LazySearch round after the first
-    scr_launches = max(a1["rounds"] - a.steps, 0)
-    scr_gbs = scr_bytes / scr_s / 1e9 if scr_s else 0.0
-    scr_tf = 2 * 16 * kh * pairs_s / 1e12
-    tensor_view = {"achieved": scr_tf, "peak": peak_bf16, "unit": "TFLOP/s",
-                   "frac": scr_tf / peak_bf16,
-                   "basis": (f"2 x {16 * kh} flops per screened pair; peak = "
-                             f"measured cuBLAS bf16 burst, 'of measured'")}
-    roof_bf16 = {
-        "bound": "hbm",
-        "kernel": "screen_kernel (BF16 tcgen05 screen, fp32 rescore)",
-        "achieved": scr_gbs, "peak": peak_hbm, "unit": "GB/s",
-        "frac": scr_gbs / peak_hbm,
-        "traffic": screen_traffic_per_launch(a1, scr_launches),
-        "algorithmic_bytes_per_launch": scr_bytes / max(scr_launches, 1),
-        "basis": ("algorithmic bytes = bf16 operand tiles streamed (128 "
-                  "points x 32 kh B, one pass per work item of <= 128 "
-                  f"queries of a leaf) + {4 * dp + 8} B per (query, leaf) "
-                  "visit; time = CUDA events around every screen launch on "
-                  "its stream; peak = measured HBM copy bandwidth, 'of "
-                  "measured'"),
-        "bytes_per_step": scr_bytes / a.steps,
-        "tensor_view": tensor_view,
-        "screen_share_of_step": scr_s / (runs[1]["ms"] / 1000.0),
-        "pairs_per_s": pairs_s,
-        "kept_fraction": (a1["screen_kept"] / a1["screen_pairs"]
-                          if a1["screen_pairs"] else None),
-    }
-    roofline = roof_bf16 if head == 1 else roof_fp32
-    names = {0: "fp32 exact path", 1: "bf16 tensor-core screen + fp32 rescore"}
+
+    def roof_screen(run: int) -> dict:
+        """Roofline of a BF16 screen kernel from its timed run (1 warp, 2
+        tcgen05): HBM-bound on the streamed bf16 point operands."""
+        kernel = run - 1
+        a1 = runs[run]["acc"]
+        # k-halves: d offsets + 2 norm slots (warp kernel; its threshold is
+        # compared in the epilogue), + 3 threshold slots (tcgen05)
+        kh = (d + 2 + 15) // 16 if kernel == 0 else (d + 5 + 15) // 16
+        scr_s = a1["screen_ms"] / 1000.0
+        pairs_s = a1["screen_pairs"] / scr_s if scr_s else 0.0
+        # algorithmic bytes of the screen: the bf16 operand tiles of every
+        # work item's leaf (counted by the kernel) plus, per (query, leaf)
+        # visit, the query's padded row and its list bound and id
+        scr_bytes = a1["screen_bytes"] + a1["screen_visits"] * (4 * dp + 8)
+        # one screen launch per LazySearch round after the first
+        scr_launches = max(a1["rounds"] - a.steps, 0)
+        scr_gbs = scr_bytes / scr_s / 1e9 if scr_s else 0.0
+        scr_tf = 2 * 16 * kh * pairs_s / 1e12
+        tensor_view = {"achieved": scr_tf, "peak": peak_bf16,
+                       "unit": "TFLOP/s", "frac": scr_tf / peak_bf16,
+                       "basis": (f"2 x {16 * kh} flops per screened pair; "
+                                 f"peak = measured cuBLAS bf16 burst, 'of "
+                                 f"measured'")}
+        unit = ("32-point super-tiles x 32 kh B per point, one pass per "
+                "work item of <= 32 queries of a leaf" if kernel == 0 else
+                "128-point tiles x 32 kh B per point, one pass per work "
+                "item of <= 128 queries of a leaf, + the items' query "
+                "operand rows")
+        return {
+            "bound": "hbm",
+            "kernel": ("screen_kernel (warp items, mma.sync, in-warp fp32 "
+                       "rescore)" if kernel == 0 else
+                       "prep + screen + rescore kernels (tcgen05.mma into "
+                       "tensor memory, bulk copies, fp32 rescore)"),
+            "achieved": scr_gbs, "peak": peak_hbm, "unit": "GB/s",
+            "frac": scr_gbs / peak_hbm,
+            "traffic": screen_traffic_per_launch(a1, scr_launches, kernel),
+            "algorithmic_bytes_per_launch": scr_bytes / max(scr_launches, 1),
+            "basis": (f"algorithmic bytes = bf16 operands streamed ({unit}) "
+                      f"+ {4 * dp + 8} B per (query, leaf) visit; time = "
+                      "CUDA events around every screened round's "
+                      "ProcessAllBuffers on its stream; peak = measured HBM "
+                      "copy bandwidth, 'of measured'"),
+            "bytes_per_step": scr_bytes / a.steps,
+            "tensor_view": tensor_view,
+            "screen_share_of_step": scr_s / (runs[run]["ms"] / 1000.0),
+            "pairs_per_s": pairs_s,
+            "kept_fraction": (a1["screen_kept"] / a1["screen_pairs"]
+                              if a1["screen_pairs"] else None),
+        }
+
+    roof_bf16 = roof_screen(1)
+    roof_tc = roof_screen(2)
+    roofline = {0: roof_fp32, 1: roof_bf16, 2: roof_tc}[head]
+    names = {0: "fp32 exact path",
+             1: "bf16 tensor-core screen (warp kernel) + fp32 rescore",
+             2: "bf16 tensor-core screen (tcgen05 kernel) + fp32 rescore"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s",
         "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms_max / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16+f32" if head == 1 else "f32",
+        "dtype": "bf16+f32" if head else "f32",
         "data": data_description(w),
         "config": dict(w.describe(), precision=names[head],
                        parallelism=f"replicas x{world}, queries sharded",
@@ -579,6 +611,7 @@ def run_ours(a, w, rank, world, local_rank):
         "roofline": roofline,
         "roofline_fp32_leaf": roof_fp32,
         "roofline_bf16_screen": roof_bf16,
+        "roofline_tcgen05_screen": roof_tc,
         "fp32_vs_bf16": {
             "fp32": {"value": runs[0]["value"],
                      "ms_per_step": runs[0]["ms_max"] / a.steps,
@@ -586,6 +619,11 @@ def run_ours(a, w, rank, world, local_rank):
             "bf16_screened": {"value": runs[1]["value"],
                               "ms_per_step": runs[1]["ms_max"] / a.steps,
                               "clocks": runs[1]["clk"]},
+            "bf16_screened_tcgen05": {
+                "value": runs[2]["value"],
+                "ms_per_step": runs[2]["ms_max"] / a.steps,
+                "screen_ms_per_step": runs[2]["acc"]["screen_ms"] / a.steps,
+                "clocks": runs[2]["clk"]},
             "identical_results": identical,
             "headline": names[head]},
         "clocks": clk,

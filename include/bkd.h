@@ -105,7 +105,30 @@ enum bkd_option {
    * every chunk holding buffered queries is streamed every round.  Results
    * do not depend on it.  Build only (with BKD_OPT_CHUNKS >= 1 or the
    * memory cap). */
-  BKD_OPT_POINT_CHUNKS = 7
+  BKD_OPT_POINT_CHUNKS = 7,
+  /* Launch shapes (results do not depend on them; any time):
+   * queries per work item of a screened round: the warp screen kernel
+   * 8..32 in steps of 8 (default 32), the tcgen05 screen kernel 16..128 in
+   * steps of 16 (default 128); reset to the default when the kernel is
+   * switched */
+  BKD_OPT_SCREEN_TILE = 8,
+  /* LazySearch rounds queued on a resident tree before the host looks at
+   * the counters again, 1..64; 0 (default) = automatic (16 far from the
+   * tail threshold, then 4, then 1) */
+  BKD_OPT_ROUND_BATCH = 9,
+  /* CTAs per SM of the screen kernel, 1..3; 0 (default) = as many as
+   * registers, shared and tensor memory allow */
+  BKD_OPT_SCREEN_CTAS = 10,
+  /* Which BF16 screen kernel runs the screened rounds (both keep the
+   * float32 result, Sec. 2.2 exactness; results do not depend on it):
+   * 0 (default) = one warp per work item of <= 32 queries, mma.sync
+   * m16n8k16 with the accumulators in registers; 1 = tcgen05.mma into
+   * tensor memory, 128-point tiles by bulk copy, work items of <= 128
+   * queries, survivors rescored by a separate kernel.  At build (with
+   * BKD_OPT_PRECISION=1) it picks the point layouts prepared: 0 or 1 that
+   * kernel's, 2 both (kernel 0 runs first); afterwards 0 / 1 may be
+   * switched any time among the layouts the tree holds (else BKD_EINVAL). */
+  BKD_OPT_SCREEN_KERNEL = 11
 };
 
 /* ------------------------------------------------------------------- stats
@@ -235,6 +258,18 @@ int bkd_outlier_scores(bkd_tree* t, int k, float* out_score);
  * returns BKD_ENOMEM and leaves its handle usable (bkd_build frees what it
  * had built).  Errors: BKD_EINVAL (nth < 0). */
 int bkd_test_fail_alloc(int64_t nth);
+
+/* bkd_probe_mma -- runs the warp screen kernel's tensor-core instruction
+ * (kind 0: mma.sync m16n8k16, bf16 inputs, fp32 accumulation) on `count`
+ * instances:
+ * D = C + A Bt^T, with A count x 16 x 16 and Bt count x 8 x 16 bf16 bit
+ * patterns (row-major; row c of Bt is column c of the B operand), C and D
+ * count x 16 x 8 float32, all HOST memory.  The screen's error bound
+ * (Sec. 2.2 exactness of the answer) assumes how far this accumulation may
+ * stray from the exact sum; tests compare D with exact sums.
+ * Errors: BKD_EINVAL, BKD_ENOMEM, BKD_ECUDA. */
+int bkd_probe_mma(int kind, int count, const uint16_t* A, const uint16_t* Bt,
+                  const float* C, float* D);
 
 /* bkd_probe_umma -- the BF16 screen's Blackwell tensor-core path (operands
  * staged in shared memory in the screen's layout, kh chained tcgen05.mma of

@@ -36,7 +36,9 @@ BKD_STATIC_MAX_HEIGHT = 16
 BKD_BATCH_QUEUED, BKD_BATCH_RUNNING, BKD_BATCH_DONE = 0, 1, 2
 
 OPTIONS = {"stream": 1, "device_mem_cap": 2, "chunks": 3, "max_active": 4,
-           "tail_queries": 5, "precision": 6, "point_chunks": 7}
+           "tail_queries": 5, "precision": 6, "point_chunks": 7,
+           "screen_tile": 8, "round_batch": 9, "screen_ctas": 10,
+           "screen_kernel": 11}
 STATS = {"rounds": 1, "leaf_visits": 2, "pairs": 3, "resorted": 4,
          "fallback": 5, "leaf_kernel_ms": 6, "chunk_bytes": 7, "copy_ms": 8,
          "leaf_launches": 9, "kernel_launches": 10, "tail_queries": 11,
@@ -88,6 +90,7 @@ def load():
         lib.bkd_serve_close.restype = None
         lib.bkd_outlier_scores.argtypes = [vp, i32, vp]
         lib.bkd_test_fail_alloc.argtypes = [i64]
+        lib.bkd_probe_mma.argtypes = [i32, i32, vp, vp, vp, vp]
         lib.bkd_probe_umma.argtypes = [i32, i32, i32, vp, vp, vp]
         lib.bkd_last_error.restype = ctypes.c_char_p
         for f in ("bkd_build", "bkd_build_with", "bkd_query",
@@ -96,7 +99,7 @@ def load():
                   "bkd_serve_open", "bkd_serve_submit", "bkd_serve_step",
                   "bkd_serve_status", "bkd_test_fail_alloc",
                   "bkd_outlier_scores",
-                  "bkd_probe_umma"):
+                  "bkd_probe_mma", "bkd_probe_umma"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -293,6 +296,23 @@ def bkd_free(tree: Tree):
 def bkd_test_fail_alloc(nth: int):
     """``bkd_test_fail_alloc``: the nth allocation from now fails (0: off)."""
     _check(load().bkd_test_fail_alloc(int(nth)))
+
+
+def bkd_probe_mma(A, Bt, C, kind: int = 0):
+    """``bkd_probe_mma``: D = C + A Bt^T per instance on the warp screen
+    kernel's tensor-core instruction (mma.sync m16n8k16).  A (count, 16, 16) and Bt (count, 8, 16) uint16 bf16
+    bit patterns, C (count, 16, 8) float32; returns D like C."""
+    A = np.ascontiguousarray(A, np.uint16)
+    Bt = np.ascontiguousarray(Bt, np.uint16)
+    C = np.ascontiguousarray(C, np.float32)
+    count = A.shape[0]
+    if A.shape != (count, 16, 16) or Bt.shape != (count, 8, 16) \
+            or C.shape != (count, 16, 8):
+        raise ValueError("shapes (count,16,16), (count,8,16), (count,16,8)")
+    D = np.empty_like(C)
+    _check(load().bkd_probe_mma(kind, count, A.ctypes.data, Bt.ctypes.data,
+                                C.ctypes.data, D.ctypes.data))
+    return D
 
 
 def bkd_probe_umma(A, Bt):

@@ -125,7 +125,8 @@ struct bkd_tree {
   int32_t* d_leaf_cnt = nullptr;
   float* d_box = nullptr;
   // BF16 screen data (built on request, resident trees only)
-  uint16_t* d_scr_words = nullptr;
+  uint16_t* d_scr_words = nullptr;   // tcgen05 screen layout
+  uint32_t* d_scr_wwords = nullptr;  // warp screen layout
   float *d_scr_center = nullptr, *d_scr_bmax = nullptr,
         *d_scr_pnmax = nullptr;
   ScreenData screen;
@@ -164,6 +165,9 @@ struct bkd_tree {
   uint8_t* h_chunk_done = nullptr;  // pinned staging of it
   int max_active = 0;
   int tail_queries = -1;
+  int screen_tile = kScreenTile;  // queries per screened work item
+  int round_batch = 0;            // rounds per host look (0: automatic)
+  int screen_ctas = 0;            // screen CTAs per SM (0: automatic)
   // timing
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
@@ -202,6 +206,7 @@ void release(bkd_tree* t) {
   cudaFree(t->d_leaf_cnt);
   cudaFree(t->d_box);
   cudaFree(t->d_scr_words);
+  cudaFree(t->d_scr_wwords);
   cudaFree(t->d_scr_center);
   cudaFree(t->d_scr_bmax);
   cudaFree(t->d_scr_pnmax);
@@ -290,7 +295,8 @@ int build_impl(const float* P, int64_t n, int d, int height,
                 (long long)((int64_t)1 << height), (long long)n);
   if (n_options < 0 || (n_options > 0 && !options))
     return fail(BKD_EINVAL, "bad options array");
-  int64_t cap = -1, chunks = 0, precision = 0, point_chunks = 0;
+  int64_t cap = -1, chunks = 0, precision = 0, point_chunks = 0,
+          screen_kernel = 0;
   for (int i = 0; i < n_options; ++i) {
     const int64_t key = options[2 * i], val = options[2 * i + 1];
     if (key == BKD_OPT_DEVICE_MEM_CAP) {
@@ -304,12 +310,17 @@ int build_impl(const float* P, int64_t n, int d, int height,
       if (val != 0 && val != 1)
         return fail(BKD_EINVAL, "precision must be 0 or 1");
       precision = val;
+    } else if (key == BKD_OPT_SCREEN_KERNEL) {
+      if (val < 0 || val > 2)
+        return fail(BKD_EINVAL, "screen kernel must be 0, 1 or 2");
+      screen_kernel = val;
     } else if (key == BKD_OPT_POINT_CHUNKS) {
       if (val != 0 && val != 1)
         return fail(BKD_EINVAL, "point chunks must be 0 or 1");
       point_chunks = val;
     } else if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE ||
-               key == BKD_OPT_TAIL_QUERIES) {
+               key == BKD_OPT_TAIL_QUERIES || key == BKD_OPT_SCREEN_TILE ||
+               key == BKD_OPT_ROUND_BATCH || key == BKD_OPT_SCREEN_CTAS) {
       // applied after construction below
     } else {
       return fail(BKD_EINVAL, "unknown build option %lld", (long long)key);
@@ -518,27 +529,45 @@ int build_impl(const float* P, int64_t n, int d, int height,
       return bail(fail(BKD_EUNSUPPORTED,
                        "the BF16 screen needs a tree resident in device "
                        "memory"));
-    const int kh = screen_halves(d);
+    // the layouts of the screen kernels asked for: 0 the warp kernel, 1
+    // the tcgen05 kernel, 2 both (the warp kernel runs; BKD_OPT_SCREEN_KERNEL
+    // switches)
+    const bool want_warp = screen_kernel != 1, want_tc = screen_kernel != 0;
+    const int kh = screen_halves(d), wkh = screen_halves_warp(d);
     const int64_t tiles = screen_tiles(H.lcap);
+    const int64_t stride = screen_stride(H.lcap);
     std::vector<uint16_t> words;
+    std::vector<uint32_t> wwords;
     std::vector<float> center, bmax, pnmax;
     try {
-      words.resize((size_t)L * tiles * kScreenRows * 16 * kh);
+      if (want_tc) words.resize((size_t)L * tiles * kScreenRows * 16 * kh);
+      if (want_warp) wwords.resize((size_t)L * wkh * stride * 8);
       center.resize((size_t)L * d);
       bmax.resize(L);
       pnmax.resize(L);
     } catch (...) {
       return bail(fail(BKD_ENOMEM, "host staging of the screen data"));
     }
-    fill_screen(Ph, H, tiles, words.data(), center.data(), bmax.data(),
-                pnmax.data());
-    if (dev_malloc(&t->d_scr_words, words.size() * 2) != cudaSuccess ||
+    if (want_tc)
+      fill_screen(Ph, H, tiles, words.data(), center.data(), bmax.data(),
+                  pnmax.data());
+    if (want_warp)
+      fill_screen_warp(Ph, H, stride, wwords.data(), center.data(),
+                       bmax.data(), pnmax.data());
+    if ((want_tc &&
+         dev_malloc(&t->d_scr_words, words.size() * 2) != cudaSuccess) ||
+        (want_warp &&
+         dev_malloc(&t->d_scr_wwords, wwords.size() * 4) != cudaSuccess) ||
         dev_malloc(&t->d_scr_center, center.size() * 4) != cudaSuccess ||
         dev_malloc(&t->d_scr_bmax, bmax.size() * 4) != cudaSuccess ||
         dev_malloc(&t->d_scr_pnmax, pnmax.size() * 4) != cudaSuccess)
       return bail(fail(BKD_ENOMEM, "device allocation failed (screen data)"));
-    if (cudaMemcpy(t->d_scr_words, words.data(), words.size() * 2,
-                   cudaMemcpyHostToDevice) != cudaSuccess ||
+    if ((want_tc &&
+         cudaMemcpy(t->d_scr_words, words.data(), words.size() * 2,
+                    cudaMemcpyHostToDevice) != cudaSuccess) ||
+        (want_warp &&
+         cudaMemcpy(t->d_scr_wwords, wwords.data(), wwords.size() * 4,
+                    cudaMemcpyHostToDevice) != cudaSuccess) ||
         cudaMemcpy(t->d_scr_center, center.data(), center.size() * 4,
                    cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(t->d_scr_bmax, bmax.data(), bmax.size() * 4,
@@ -547,11 +576,16 @@ int build_impl(const float* P, int64_t n, int d, int height,
                    cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(fail(BKD_ECUDA, "upload of the screen data failed"));
     t->screen.words = t->d_scr_words;
+    t->screen.wwords = t->d_scr_wwords;
     t->screen.tiles = tiles;
+    t->screen.stride = stride;
     t->screen.center = t->d_scr_center;
     t->screen.bmax = t->d_scr_bmax;
     t->screen.pnmax = t->d_scr_pnmax;
     t->screen.kh = kh;
+    t->screen.wkh = wkh;
+    t->screen.kind = want_warp ? 0 : 1;
+    t->screen_tile = screen_tile_of(t->screen.kind);
     t->precision = 1;
   }
   if (dev_malloc(&t->d_ctr, sizeof(Counters)) != cudaSuccess ||
@@ -582,7 +616,8 @@ int build_impl(const float* P, int64_t n, int d, int height,
   for (int i = 0; i < n_options; ++i) {
     const int64_t key = options[2 * i], val = options[2 * i + 1];
     if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE ||
-        key == BKD_OPT_TAIL_QUERIES) {
+        key == BKD_OPT_TAIL_QUERIES || key == BKD_OPT_SCREEN_TILE ||
+        key == BKD_OPT_ROUND_BATCH || key == BKD_OPT_SCREEN_CTAS) {
       int rc = bkd_set_option(t, (int)key, val);
       if (rc != BKD_OK) return bail(rc);
     }
@@ -644,7 +679,7 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   cudaStream_t s = t->stream;
   const int64_t L = t->n_leaves;
   const int64_t max_items =
-      m / std::min(kScreenTile, kPipeTile) + L + 1;  // items of any round
+      m / std::min(t->screen_tile, kPipeTile) + L + 1;  // items of any round
   CU(t->qpad.ensure(m * Dp));
   CU(t->lst_d.ensure(m * K));
   CU(t->lst_i.ensure(m * K));
@@ -676,10 +711,12 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   uint32_t* nxt = t->act_b.p;
   int n_act = (int)m;
   const int grid_max = leaf_kernel_grid(Dp, cap, t->sm_count);
-  const int screen_max =
+  int screen_max =
       t->precision == 1
-          ? screen_grid(t->screen.kh, Dp, D.lcap, K, t->sm_count)
+          ? screen_grid(t->screen, Dp, D.lcap, K, t->sm_count)
                         : 0;
+  if (t->screen_ctas > 0)
+    screen_max = std::min(screen_max, t->screen_ctas * t->sm_count);
   // the tail kernel spreads a list over the 32 lanes of a warp (two
   // entries per lane above 32); automatic threshold: 8,192 active queries, up to 32,768 for the largest query
   // sets (measured on 2^24 queries)
@@ -696,11 +733,11 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   // nothing.  A chunked tree needs the host every round (the chunk
   // schedule).
   ScreenWork sw;
-  if (screen_max > 0) {
-    const int64_t si = m / kScreenTile + L + 1;  // items of a screened round
+  if (screen_max > 0 && t->screen.kind == 1) {
+    const int64_t si = m / t->screen_tile + L + 1;  // items of a screened round
     CU(t->scr_bop.ensure(si * 4096 * t->screen.kh));
     CU(t->scr_seg.ensure(si * screen_seg_cap()));
-    CU(t->scr_cnt.ensure(si));
+    CU(t->scr_cnt.ensure(si * screen_cnt_per_item()));
     CU(t->scr_ovf.ensure(2 * si));  // overflowed items, in halves
     sw.bop = t->scr_bop.p;
     sw.seg = t->scr_seg.p;
@@ -729,7 +766,7 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
     cudaEvent_t b0 = t->next_event(), b1 = t->next_event();
     if (b0) cudaEventRecord(b0, s);
     CU(launch_bucket(t->placed.p, act, n_act, (int)L,
-                     screened ? kScreenTile : kPipeTile,
+                     screened ? t->screen_tile : kPipeTile,
                      t->d_leaf_cnt, t->cnt.p, t->off.p, t->cursor.p,
                      t->toff.p, t->items.p, nxt, t->d_ctr, s, nin, nout));
     if (b1) cudaEventRecord(b1, s);
@@ -944,7 +981,8 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
     n_act = n_next;  // an upper bound of every later round's active count
     // rounds queued before the host looks again: many while far from the
     // tail threshold, one when close to it (or chunked)
-    const int batch = t->chunked ? 1
+    const int batch = t->chunked            ? 1
+                      : t->round_batch > 0    ? t->round_batch
                       : n_next > 16 * std::max(tail, 1024) ? 16
                       : n_next > 4 * std::max(tail, 1024)  ? 4
                                                             : 1;
@@ -1048,6 +1086,7 @@ TreeView view_of(const bkd_tree* t) {
   v.h_ctr = t->h_ctr;
   v.screen = t->screen;
   v.precision = t->precision;
+  v.tail_queries = t->tail_queries;
   return v;
 }
 
@@ -1193,7 +1232,7 @@ int bkd_set_option(bkd_tree* t, int key, int64_t value) {
     case BKD_OPT_PRECISION:
       if (value != 0 && value != 1)
         return fail(BKD_EINVAL, "precision must be 0 or 1");
-      if (value == 1 && !t->screen.words)
+      if (value == 1 && !t->screen.on())
         return fail(BKD_EINVAL,
                     "the tree was built without BF16 screen data (pass "
                     "BKD_OPT_PRECISION=1 to bkd_build_with)");
@@ -1203,6 +1242,42 @@ int bkd_set_option(bkd_tree* t, int key, int64_t value) {
       if (value < -1 || value >= ((int64_t)1 << 31))
         return fail(BKD_EINVAL, "tail query count out of range");
       t->tail_queries = (int)value;
+      return BKD_OK;
+    case BKD_OPT_SCREEN_TILE: {
+      // the warp kernel: 8-query column blocks, one query per lane; the
+      // tcgen05 kernel: the MMA's N in steps of 16
+      const int step = t->screen.kind == 0 ? 8 : 16;
+      const int top = screen_tile_of(t->screen.kind);
+      if (value < step || value > top || value % step != 0)
+        return fail(BKD_EINVAL,
+                    "screen tile must be %d..%d, a multiple of %d", step, top,
+                    step);
+      t->screen_tile = (int)value;
+      return BKD_OK;
+    }
+    case BKD_OPT_SCREEN_KERNEL:
+      if (value != 0 && value != 1)
+        return fail(BKD_EINVAL, "screen kernel must be 0 or 1");
+      if (!t->screen.has((int)value))
+        return fail(BKD_EINVAL,
+                    "the tree holds no screen data for kernel %lld (build "
+                    "with BKD_OPT_PRECISION=1 and BKD_OPT_SCREEN_KERNEL=%lld "
+                    "or 2)",
+                    (long long)value, (long long)value);
+      if (t->screen.kind != (int)value) {
+        t->screen.kind = (int)value;
+        t->screen_tile = screen_tile_of(t->screen.kind);
+      }
+      return BKD_OK;
+    case BKD_OPT_ROUND_BATCH:
+      if (value < 0 || value > 64)
+        return fail(BKD_EINVAL, "round batch must be 0..64");
+      t->round_batch = (int)value;
+      return BKD_OK;
+    case BKD_OPT_SCREEN_CTAS:
+      if (value < 0 || value > 3)
+        return fail(BKD_EINVAL, "screen CTAs per SM must be 0..3");
+      t->screen_ctas = (int)value;
       return BKD_OK;
     case BKD_OPT_DEVICE_MEM_CAP:
     case BKD_OPT_CHUNKS:

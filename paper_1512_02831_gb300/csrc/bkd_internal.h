@@ -130,6 +130,10 @@ cudaError_t launch_fill(int32_t* v, int64_t n, int32_t value, cudaStream_t s);
 cudaError_t launch_retire(const int2* placed, const uint32_t* act, int n_act,
                           const int32_t* slot_batch, int32_t* batch_left,
                           cudaStream_t s);
+// ... and for every query of act[0..n) (all finished).
+cudaError_t launch_retire_list(const uint32_t* act, int n,
+                               const int32_t* slot_batch, int32_t* batch_left,
+                               cudaStream_t s);
 
 // FindLeafBatch from the traversal states in `state` (kStart for the first
 // round): per position of `act`, placed = (next leaf, rank among the
@@ -189,21 +193,38 @@ cudaError_t launch_leaf(const DevTree& t, int cap, const Item* items,
 
 int leaf_kernel_grid(int Dp, int cap, int sm_count);
 
-// BF16 screen data on the device (see fill_screen).
+// BF16 screen data on the device.  Two screen kernels, each with the point
+// operands in its own layout (either may be absent): the warp kernel
+// (mma.sync fragments, fill_screen_warp; kind 0) and the tcgen05 kernel
+// (128-row operand tiles, fill_screen; kind 1).  `kind` selects the kernel
+// that runs; the centre, bmax and pnmax arrays serve both.
 struct ScreenData {
-  const uint16_t* words = nullptr;  // operand tiles, `tiles` per leaf
+  const uint16_t* words = nullptr;  // tcgen05: operand tiles, `tiles` per leaf
+  const uint32_t* wwords = nullptr;  // warp kernel: fragments, `stride` slots
   const float* center = nullptr;
   const float* bmax = nullptr;
   const float* pnmax = nullptr;
-  int64_t tiles = 0;  // 128-point tiles per leaf
-  int kh = 0;
+  int64_t tiles = 0;   // tcgen05: 128-point tiles per leaf
+  int64_t stride = 0;  // warp kernel: slots per leaf
+  int kh = 0;          // tcgen05: k-halves (screen_halves)
+  int wkh = 0;         // warp kernel: k-halves (screen_halves_warp)
+  int kind = 0;
+  bool has(int k) const { return k == 0 ? wwords != nullptr : words != nullptr; }
+  bool on() const { return has(kind); }
 };
+// Queries per work item of a screened round, by kernel (the warp kernel:
+// one query column per lane; tcgen05: the MMA's N <= 128).
+constexpr int kWarpScreenTile = 32;
+inline int screen_tile_of(int kind) { return kind == 0 ? kWarpScreenTile : 128; }
+// Slots per leaf of the warp kernel's arrays: the leaf capacity rounded up
+// to its 32-point super-tile (two 16-point m-tiles).
+inline int64_t screen_stride(int64_t lcap) { return (lcap + 31) / 32 * 32; }
 
 // The screen's tensor-core shape: points are the MMA's M = 128 rows (one
 // operand tile of a leaf), the buffered queries of one leaf its N <= 128
 // columns (one work item), K = 16 slots per k-half.
 constexpr int kScreenRows = 128;
-constexpr int kScreenTile = 128;  // queries per work item of a screened round
+constexpr int kScreenTile = 128;  // tcgen05: queries per work item
 inline int64_t screen_tiles(int64_t lcap) {
   return (lcap + kScreenRows - 1) / kScreenRows;
 }
@@ -217,8 +238,9 @@ __host__ __device__ inline uint32_t screen_row_offset(int r, int kg, int kh) {
 
 // Workspace of the screened rounds, sized for the most work items a round
 // can have: per item its query operand tile (128 x 32 kh bytes), a segment
-// of screen_seg_cap() survivor entries and their count, and room for the
-// items handed to the float32 kernel.
+// of screen_seg_cap() survivor entries and screen_cnt_per_item() counts
+// (one per sub-segment), and room for the items handed to the float32
+// kernel.
 struct ScreenWork {
   uint8_t* bop = nullptr;
   uint32_t* seg = nullptr;
@@ -226,22 +248,37 @@ struct ScreenWork {
   Item* ovf = nullptr;
 };
 int64_t screen_seg_cap();
+int64_t screen_cnt_per_item();
 
 // ProcessAllBuffers with the BF16 tensor-core screen and exact float32
-// rescoring (k_screen.cu); same candidate lists as launch_leaf on a
-// resident tree, over the round's items of at most kScreenTile queries
-// (n_items < 0: the count is read on the device).  Three kernels: the
-// items' query operands, the screen (survivors to per-item segments), the
-// exact rescoring; items whose segment overflowed go to the float32 leaf
-// kernel (capacity `cap`, grid leaf_grid).  screen_grid: resident CTAs (0
-// if the kernel does not fit: shared memory, tensor memory, leaf capacity).
-int screen_grid(int kh, int Dp, int64_t lcap, int K, int sm_count);
+// rescoring; same candidate lists as launch_leaf on a resident tree, over
+// the round's items of at most screen_tile_of(sd.kind) queries (n_items <
+// 0: the count is read on the device), by the kernel sd.kind selects:
+//   kind 0 (k_screen_warp.cu): one warp per item, mma.sync, survivors
+//     rescored by the same warp (ScreenWork, cap and leaf_grid unused);
+//   kind 1 (k_screen.cu): three kernels: the items' query operands, the
+//     tcgen05 screen (survivors to per-item segments), the exact
+//     rescoring; items whose segment overflowed go to the float32 leaf
+//     kernel (capacity `cap`, grid leaf_grid).
+// screen_grid: resident CTAs of the selected kernel (0 if it does not fit:
+// shared memory, tensor memory, leaf capacity).
+int screen_grid(const ScreenData& sd, int Dp, int64_t lcap, int K,
+                int sm_count);
 cudaError_t launch_screen(const DevTree& t, const ScreenData& sd,
                           const Item* items, int n_items, Counters* ctr,
                           const uint32_t* act, const float* qpad,
                           float* lst_d, uint32_t* lst_i, int K, int grid,
                           const ScreenWork& w, int cap, int leaf_grid,
                           int sm_count, cudaStream_t s);
+// The warp kernel (k_screen_warp.cu), items [item_lo, item_hi) (item_hi <
+// 0: the device's count of the round).
+int screen_grid_warp(int kh, int64_t lcap, int K, int sm_count);
+cudaError_t launch_screen_warp(const DevTree& t, const ScreenData& sd,
+                               const Item* items, int item_lo, int item_hi,
+                               Counters* ctr, const uint32_t* act,
+                               const float* qpad, float* lst_d,
+                               uint32_t* lst_i, int K, int grid,
+                               cudaStream_t s);
 
 // Runs the traversal of each of the n_act queries in `act` to its end (one
 // warp per query); state[q] is the query's pending (not yet scanned) leaf.
@@ -285,6 +322,7 @@ struct TreeView {
   Counters* h_ctr;           // pinned host counter block of the handle
   ScreenData screen;         // BF16 screen data (words == nullptr: none)
   int precision;             // current leaf-scoring option (0 / 1)
+  int tail_queries;          // tail threshold option (-1: automatic)
 };
 TreeView view_of(const struct ::bkd_tree* t);
 
@@ -329,6 +367,10 @@ void fill_boxes(const float* P, const HostTree& t, float* box);
 // for the point's squared norm and three for the query's threshold (1 for
 // d <= 11, 2 for d <= 27, else 3).
 inline int screen_halves(int d) { return (d + 5 + 15) / 16; }
+// The warp kernel's k-halves: the d offsets and the norm split (its
+// threshold is compared in the epilogue): 1 for d <= 14, 2 for d <= 30,
+// else 3.
+inline int screen_halves_warp(int d) { return (d + 2 + 15) / 16; }
 
 // Data of the BF16 screen, per leaf: the centre c (midpoint of the leaf's
 // bounding box); per point (a row of the leaf's operand tiles, `tiles` of
@@ -340,6 +382,15 @@ inline int screen_halves(int d) { return (d + 5 + 15) / 16; }
 // bound on the offset rounding error norm) and pnmax (largest pn).
 void fill_screen(const float* P, const HostTree& t, int64_t tiles,
                  uint16_t* words, float* center, float* bmax, float* pnmax);
+// The warp kernel's layout of the same per-point slots (offsets, pn_hi,
+// pn_lo; no threshold slots): `stride` slots per leaf and k-half, 8 words
+// (bf16 pairs) per point in m16n8k16 A-fragment order, grouped in 32-point
+// super-tiles (lane (g, t) of a warp reads its two rows of both m-tiles of
+// a k-half with one 16-byte load); padding points pn_hi = +inf.  Fills
+// center, bmax and pnmax like fill_screen.
+void fill_screen_warp(const float* P, const HostTree& t, int64_t stride,
+                      uint32_t* words, float* center, float* bmax,
+                      float* pnmax);
 
 // Writes the quads and orig arrays for leaves [leaf_lo_id, leaf_hi_id)
 // into host buffers (`pts` and `orig` point at leaf leaf_lo_id's first slot).

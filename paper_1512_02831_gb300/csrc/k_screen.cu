@@ -52,25 +52,35 @@
 // float32 path, and the answers (re-check and fallback read nothing else)
 // are the same.
 //
-// Work layout (one CTA per work item at a time: one leaf, <= 128 of its
-// buffered queries, items taken from a launch-wide counter):
-//   warp 0 (one thread)  claims items, publishes them in a small ring, and
-//                        streams the leaf's 128-point operand tiles (bulk
-//                        copies, 4 KB per k-half) into a deep shared-memory
-//                        ring, across item boundaries;
-//   warp 1               allocates tensor memory; one thread issues, per
-//                        tile, KH tcgen05.mma (M = 128 points, N = the
-//                        item's queries rounded up to 16, K = 16) into one of
-//                        two fp32 accumulators in tensor memory, and commits
-//                        them to mbarriers (ring slot free, accumulator full);
-//   warps 2-5            the epilogue: prepare the item's query operand
-//                        (B) and thresholds; per tile read the accumulator
-//                        (tcgen05.ld, row = point, column = query), take the
-//                        largest value of each row with three-input max, and
-//                        hand the accumulator back; the rare rows with a
-//                        positive value are rescored exactly and inserted
-//                        into the queries' lists (shared memory, loaded from
-//                        HBM on first insertion, written back at item end).
+// A screened round runs three kernels:
+//   prep_kernel     one CTA per work item (one leaf, <= 128 of its buffered
+//                   queries): the item's query operand tile (v^, -1/2, -1/2,
+//                   threshold parts) written to HBM;
+//   screen_kernel   persistent CTAs (two per SM), items taken from a
+//                   launch-wide counter:
+//     warp 0 (one thread)  claims items, publishes them in a small ring, and
+//                          streams the query operand and the leaf's 128-point
+//                          operand tiles (bulk copies, 4 KB per k-half) into
+//                          a deep shared-memory ring, across item boundaries;
+//     warp 1               allocates tensor memory; one thread issues, per
+//                          tile, KH tcgen05.mma (M = 128 points, N = the
+//                          item's queries rounded up to 16, K = 16) into one
+//                          of two 128-column fp32 accumulator buffers in
+//                          tensor memory -- up to four tiles of a small item
+//                          side by side in one buffer -- and commits them to
+//                          mbarriers (ring slot free, buffer full);
+//     warps 2-9            the epilogue, two warpgroups (each half of a
+//                          buffer's column groups): per buffer read the
+//                          accumulator (tcgen05.ld, row = point, column =
+//                          query), take the largest value of each row over
+//                          each group of 16 columns with three-input max,
+//                          hand the buffer back, and append the rare (point,
+//                          group) pairs with a positive value to the item's
+//                          survivor segment in HBM;
+//   rescore_kernel  scores the survivors exactly (float32 chain of the leaf
+//                   kernel) against the 16 queries of their group and
+//                   inserts them into the lists; an item whose segment
+//                   overflowed goes to the float32 leaf kernel instead.
 // Every wait is bounded: a wait that runs out sets kErrTimeout, every role
 // then leaves, copies and MMAs in flight are waited for (bounded), and the
 // tensor memory is released.
@@ -85,7 +95,7 @@
 namespace bkd {
 namespace {
 
-constexpr int kEpiThreads = 128;              // 4 epilogue warps
+constexpr int kEpiThreads = 256;              // 2 x 4 epilogue warps
 constexpr int kThreads = 64 + kEpiThreads;    // + producer warp + MMA warp
 constexpr int kItemRing = 8;                  // published items in flight
 constexpr int kBops = 4;                      // query-operand buffers
@@ -100,6 +110,12 @@ __host__ __device__ constexpr int ring_stages(int kh) {
 }
 __host__ __device__ constexpr uint32_t tile_bytes(int kh) {
   return 4096u * (uint32_t)kh;
+}
+// Accumulator columns of one point tile of an item with G groups of 16
+// query columns: rounded up to 32, so that 128 / slot_cols tiles share an
+// accumulator buffer (4 for G <= 2, 2 for G <= 4, else 1).
+__host__ __device__ constexpr uint32_t slot_cols(int G) {
+  return G <= 2 ? 32u : (G <= 4 ? 64u : 128u);
 }
 
 // Shared-memory layout (byte offsets into the dynamic shared memory).
@@ -121,8 +137,8 @@ __host__ __device__ inline Layout layout_of(int kh) {
   L.ring = take(o, ring_stages(kh) * tile_bytes(kh), 1024);
   L.bop = take(o, kBops * tile_bytes(kh), 1024);  // query operands
   L.items = take(o, kItemRing * 16, 16);
-  L.bars = take(o, (2 * ring_stages(kh) + 4 + 2 * kBops + 2 * kItemRing) * 8,
-                8);
+  L.bars = take(o,
+                (2 * ring_stages(kh) + 5 + 2 * kBops + 2 * kItemRing) * 8, 8);
   L.misc = take(o, 32, 16);
   L.total = o;
   return L;
@@ -141,13 +157,31 @@ __device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
+// The same test, but a thread whose phase is not complete yet is suspended
+// by the hardware until it completes (or about a millisecond passes)
+// instead of returning at once: waiting threads take no issue slots from
+// the working ones.
+__device__ __forceinline__ bool bar_try_suspend(uint32_t bar,
+                                                uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(1000000u)
+      : "memory");
+  return ok != 0;
+}
+
 // Waits for phase `parity` of `bar`; false once the CTA aborted or the wait
 // ran out (~2^31 cycles: then it aborts the CTA and reports the timeout).
-__device__ __noinline__ bool bar_wait(uint32_t bar, uint32_t parity,
-                                      volatile int* abort, Counters* ctr) {
+__device__ __noinline__ bool bar_wait_slow(uint32_t bar, uint32_t parity,
+                                           volatile int* abort,
+                                           Counters* ctr) {
   const long long t0 = clock64();
   for (;;) {
-    if (bar_try(bar, parity)) return true;
+    if (bar_try_suspend(bar, parity)) return true;
     if (*abort) return false;
     if (clock64() - t0 > (1ll << 31)) {
       *abort = 1;
@@ -155,6 +189,10 @@ __device__ __noinline__ bool bar_wait(uint32_t bar, uint32_t parity,
       return false;
     }
   }
+}
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity,
+                                         volatile int* abort, Counters* ctr) {
+  return bar_try(bar, parity) || bar_wait_slow(bar, parity, abort, ctr);
 }
 
 __device__ __forceinline__ void bar_arrive(uint32_t bar) {
@@ -220,7 +258,9 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v) {
+// Two groups of 16 columns at arbitrary column addresses, one wait.
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t taddr2,
+                                        float* v) {
   uint32_t r[32];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, "
@@ -235,7 +275,7 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v) {
         "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
         "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
         "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr), "r"(taddr + 16u)
+      : "r"(taddr), "r"(taddr2)
       : "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
@@ -248,54 +288,12 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
   return r;
 }
 
-// Named barriers of 128 threads (id 1: the epilogue warps, id 2 + g:
-// column group g), with an OR over a predicate.
-template <int ID>
-__device__ __forceinline__ bool sync128_or(bool v) {
-  uint32_t r;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
-      " bar.red.or.pred q, %2, 128, p;\n selp.u32 %0, 1, 0, q;\n}"
-      : "=r"(r)
-      : "r"((uint32_t)v), "n"(ID)
-      : "memory");
-  return r != 0;
-}
-template <int ID>
-__device__ __forceinline__ void sync128() {
-  asm volatile("bar.sync %0, 128;" ::"n"(ID) : "memory");
-}
-__device__ __forceinline__ bool group_sync_or(int g, bool v) {
-  return g ? sync128_or<3>(v) : sync128_or<2>(v);
-}
-__device__ __forceinline__ void group_sync(int g) {
-  if (g)
-    sync128<3>();
-  else
-    sync128<2>();
-}
-
 __device__ __forceinline__ float bf16_value(uint16_t h) {
   return __uint_as_float((uint32_t)h << 16);
 }
 __device__ __forceinline__ uint16_t bf16_bits(float f) {
   const __nv_bfloat16 b = __float2bfloat16_rn(f);
   return *reinterpret_cast<const uint16_t*>(&b);
-}
-
-// Exact float32 distance of query coordinates qp (Dp, zero-padded) to the
-// point in `slot`: the leaf kernel's chain, one dimension at a time.
-__device__ __forceinline__ float exact_dist(const float* qp,
-                                            const float* __restrict__ pts,
-                                            int Dp, uint32_t slot) {
-  const float* quad = pts + (size_t)(slot >> 2) * 4 * Dp + (slot & 3);
-  float t = __fsub_rn(qp[0], quad[0]);
-  float e = __fmul_rn(t, t);
-  for (int i = 1; i < Dp; ++i) {
-    t = __fsub_rn(qp[i], quad[4 * i]);
-    e = __fmaf_rn(t, t, e);
-  }
-  return e;
 }
 
 // ------------------------------------------------------------ prep kernel
@@ -364,7 +362,10 @@ __global__ void __launch_bounds__(128)
         tl = bf16_bits(r2);
       }
     }
-    // slots: v^ (0..d-1), -1/2, -1/2 against the norm split, the threshold
+    // slots: v^ (0..d-1), -1/2, -1/2 against the norm split, the threshold;
+    // only the item's columns rounded up to 16 (the MMA's N) are written:
+    // the screen reads no other row of the tile
+    if (e >= ((w.count + 15) & ~15)) continue;
     uint8_t* tile = bop + (size_t)it * tile_bytes(KH);
 #pragma unroll
     for (int kg = 0; kg < 2 * KH; ++kg) {
@@ -418,21 +419,26 @@ struct Smem {
   __device__ uint32_t itemempty(int i) const {
     return bar(2 * S + 4 + 2 * kBops + kItemRing + i);
   }
+  __device__ uint32_t drain() const {
+    return bar(2 * S + 4 + 2 * kBops + 2 * kItemRing);
+  }
   __device__ int4* items() const {
     return reinterpret_cast<int4*>(base + L.items);
   }
-  // misc words: [0] tensor-memory base, [1] abort, [2 + g] survivors queued
-  // for the item of parity g
+  // misc words: [0] tensor-memory base, [1] abort
   __device__ uint32_t* misc() const {
     return reinterpret_cast<uint32_t*>(base + L.misc);
   }
 };
 
-// Survivors of the screen: per work item a segment of kSegCap entries
-// (point index in the leaf << 7 | query column) and its count (a count above
-// kSegCap: the segment overflowed; the item is scored by the float32 leaf
-// kernel instead).
-constexpr int kSegCap = 512;
+// Survivors of the screen: per work item and epilogue warp a sub-segment
+// of kWarpCap entries (point index in the leaf << 3 | group of 16 query
+// columns: the point passed the screen for at least one query of the
+// group) and its count (a count above kWarpCap: the sub-segment
+// overflowed; the item is scored by the float32 leaf kernel instead).
+constexpr int kEpiWarps = kEpiThreads / 32;
+constexpr int kWarpCap = 128;
+constexpr int kSegCap = kEpiWarps * kWarpCap;  // entries per item
 
 template <int KH>
 __global__ void __launch_bounds__(kThreads, 2)
@@ -466,6 +472,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       mbar_init(sm.itemfull(i), 1);
       mbar_init(sm.itemempty(i), 1 + kEpiThreads);
     }
+    mbar_init(sm.drain(), 1);
     for (int i = 1; i < 8; ++i) sm.misc()[i] = 0;
     mbar_init_fence();
   }
@@ -491,6 +498,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int hi = item_hi >= 0 ? item_hi : ctr->n_items;
     if (lane == 0) {
       uint32_t c = 0;  // point tiles issued
+      unsigned long long bop_bytes = 0;  // query operand bytes loaded
       uint32_t last[20];  // last tile issued into each ring slot + 1
       uint32_t lastb[kBops];  // last item (+1) whose operand went into each
                               // query-operand buffer
@@ -540,8 +548,12 @@ __global__ void __launch_bounds__(kThreads, 2)
         // are done with the buffer
         if (!bar_wait(sm.bempty(g), ((n / kBops) & 1) ^ 1, abort, ctr))
           break;
+        // (its first 16 G rows: the MMA's N columns, contiguous in the
+        // operand layout)
+        const uint32_t bbytes = 512u * KH * (uint32_t)((w.count + 15) >> 4);
         bulk_load(sm.bop_u32(g, KH), bop_g + (size_t)it * tile_bytes(KH),
-                  tile_bytes(KH), sm.bfull(g));
+                  bbytes, sm.bfull(g));
+        bop_bytes += bbytes;
         lastb[g] = (uint32_t)n + 1;
         const uint8_t* src = words + (size_t)w.leaf * tiles * tile_bytes(KH);
         bool ok = true;
@@ -559,7 +571,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       if (c)
         atomicAdd(&ctr->screen_bytes,
-                  (unsigned long long)(c + n) * tile_bytes(KH));
+                  (unsigned long long)c * tile_bytes(KH) + bop_bytes);
       // copies still in flight land before the CTA leaves
       for (int s = 0; s < S; ++s)
         if (last[s]) {
@@ -581,7 +593,8 @@ __global__ void __launch_bounds__(kThreads, 2)
   } else if (warp == 1) {
     // ------------------------------------------------------- MMA issuer
     if (lane == 0) {
-      uint32_t c = 0;  // tiles consumed
+      uint32_t c = 0;   // tiles consumed
+      uint32_t cb = 0;  // accumulator buffers filled
       bool issued = false;
       for (int n = 0;; ++n) {
         const int ir = n % kItemRing, g = n % kBops;
@@ -591,119 +604,160 @@ __global__ void __launch_bounds__(kThreads, 2)
         bar_arrive(sm.itemempty(ir));
         if (dsc.x < 0) break;
         if (!bar_wait(sm.bfull(g), (n / kBops) & 1, abort, ctr)) break;
-        const uint32_t idesc = mma_idesc((dsc.z + 15) & ~15);
+        const int G = (dsc.z + 15) >> 4;
+        const uint32_t sw = slot_cols(G);
+        const int T = (int)(kAccCols / sw);
+        const uint32_t idesc = mma_idesc(16 * G);
         const uint32_t bop = sm.bop_u32(g, KH);
         bool ok = true;
-        for (int ti = 0; ti < dsc.w; ++ti, ++c) {
-          const int s = c % S, b = c & 1;
-          if (!bar_wait(sm.afull(s), (c / S) & 1, abort, ctr) ||
-              !bar_wait(sm.accempty(b), ((c >> 1) & 1) ^ 1, abort, ctr)) {
+        for (int t0 = 0; ok && t0 < dsc.w; t0 += T, ++cb) {
+          const int b = cb & 1;
+          if (!bar_wait(sm.accempty(b), ((cb >> 1) & 1) ^ 1, abort, ctr)) {
             ok = false;
             break;
           }
-          tc_fence_after();
-          const uint32_t a0 = sm.ring_u32(s, KH);
+          const int nk = min(T, dsc.w - t0);
+          for (int k = 0; k < nk; ++k, ++c) {
+            const int s = c % S;
+            if (!bar_wait(sm.afull(s), (c / S) & 1, abort, ctr)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = sm.ring_u32(s, KH);
+            const uint32_t d = tmem + (uint32_t)b * kAccCols + (uint32_t)k * sw;
 #pragma unroll
-          for (int h = 0; h < KH; ++h)
-            tc_mma(tmem + (uint32_t)b * kAccCols, op_desc(a0 + 256u * h, KH),
-                   op_desc(bop + 256u * h, KH), idesc, h > 0 ? 1u : 0u);
-          tc_commit(sm.aempty(s));
-          tc_commit(sm.accfull(b));
-          issued = true;
+            for (int h = 0; h < KH; ++h)
+              tc_mma(d, op_desc(a0 + 256u * h, KH), op_desc(bop + 256u * h, KH),
+                     idesc, h > 0 ? 1u : 0u);
+            tc_commit(sm.aempty(s));
+            issued = true;
+          }
+          if (ok) tc_commit(sm.accfull(b));
         }
         tc_commit(sm.bempty(g));  // the query operand buffer is free
         if (!ok) break;
       }
       if (issued) {
-        // the last MMA (and with it every earlier one) has completed
-        const uint32_t cl = c - 1;
+        // every MMA issued has completed before the CTA leaves
+        tc_commit(sm.drain());
         const long long t0 = clock64();
-        while (!bar_try(sm.accfull(cl & 1), (cl >> 1) & 1) &&
-               clock64() - t0 < (1ll << 31)) {
+        while (!bar_try(sm.drain(), 0) && clock64() - t0 < (1ll << 31)) {
         }
       }
     }
   } else {
     // ------------------------------------------------------- epilogue
-    // A decision to leave is taken by all 128 epilogue threads together (an
-    // OR at their named barrier); a failed wait inside an item only skips
-    // that tile's accumulator reads (warp-uniform, as tcgen05.ld requires).
+    // Two warpgroups: warp w reads tensor-memory lanes 32 (w % 4) .. (its
+    // accumulator rows = points).  An accumulator buffer holds the tiles of
+    // T = 128 / slot_cols(G) consecutive point tiles of the item side by
+    // side (G groups of 16 query columns each): of its groups warpgroup 0
+    // takes the first half (rounded up), warpgroup 1 the rest.  Per buffer a
+    // thread takes the largest value of its row over each of its groups; a
+    // (point, group) pair with a positive value goes to the warp's
+    // sub-segment of the item (a warp-uniform count in registers: no
+    // atomics).  The rescoring kernel then scores that point exactly
+    // against every query of the group.  The warps run independently; a
+    // failed wait (abort or timeout) makes the warp leave.
     const int quarter = warp & 3;  // tensor-memory lanes 32 quarter ..
+    const int half = (warp - 2) >> 2;
+    const int ew = warp - 2;       // epilogue warp 0 .. kEpiWarps - 1
     const int row = 32 * quarter + lane;
+    const unsigned below = (1u << lane) - 1u;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * quarter) << 16);
-    uint32_t c = 0;
+    uint32_t cb = 0;
     unsigned long long kept = 0;
     for (int n = 0;; ++n) {
-      const int ir = n % kItemRing, g = n & 1;
-      const bool got =
-          bar_wait(sm.itemfull(ir), (n / kItemRing) & 1, abort, ctr);
-      int4 dsc = make_int4(-1, 0, 0, 0);
-      if (got) {
-        dsc = sm.items()[ir];
-        bar_arrive(sm.itemempty(ir));
-      }
-      if (sync128_or<1>(!got) || dsc.x < 0) break;
-      const int it = dsc.y, nt = dsc.w, ncol = (dsc.z + 15) & ~15;
-      uint32_t* out = seg + (size_t)it * kSegCap;
+      const int ir = n % kItemRing;
+      if (!__all_sync(0xffffffffu, bar_wait(sm.itemfull(ir),
+                                             (n / kItemRing) & 1, abort, ctr)))
+        break;
+      const int4 dsc = sm.items()[ir];
+      bar_arrive(sm.itemempty(ir));
+      if (dsc.x < 0) break;
+      const int it = dsc.y, nt = dsc.w;
+      const int G = (dsc.z + 15) >> 4;  // column groups of the item
+      const uint32_t sw = slot_cols(G);
+      const int T = (int)(kAccCols / sw);
+      uint32_t* out = seg + ((size_t)it * kEpiWarps + ew) * kWarpCap;
+      uint32_t cnt = 0;  // entries of this warp for the item
       bool ok = true;
-      for (int ti = 0; ti < nt; ++ti, ++c) {
-        const int b = c & 1;
-        const bool gt = __all_sync(
-            0xffffffffu, bar_wait(sm.accfull(b), (c >> 1) & 1, abort, ctr));
-        ok = ok && gt;
+      for (int t0 = 0; t0 < nt; t0 += T, ++cb) {
+        const int b = cb & 1;
+        if (!__all_sync(0xffffffffu,
+                        bar_wait(sm.accfull(b), (cb >> 1) & 1, abort, ctr))) {
+          ok = false;
+          break;
+        }
+        // this warp's groups [j0, j1) of the buffer's nk G groups (group
+        // j: tile j / G of the buffer, column group j % G; both walked
+        // incrementally from (k0, g0), no division in the loop)
+        const int GT = min(T, nt - t0) * G, gh = (GT + 1) >> 1;
+        const int j0 = half ? gh : 0, j1 = half ? GT : gh;
+        const int k0 = half ? gh / G : 0, g0 = half ? gh - k0 * G : 0;
         const uint32_t ta = lane_base + (uint32_t)b * kAccCols;
-        uint32_t mask[4] = {0u, 0u, 0u, 0u};
-        if (gt) tc_fence_after();
+        uint32_t grp = 0u;  // bit j - j0: group j passes for this row
+        tc_fence_after();
+        int kk = k0, gg = g0;  // (tile, group) of group j
 #pragma unroll 1
-        for (int c0 = 0; gt && c0 < ncol; c0 += 32) {
+        for (int j = j0; j < j1; j += 2) {
           float v[32];
-          if (c0 + 32 <= ncol) {
-            tc_ld32(ta + (uint32_t)c0, v);
+          const uint32_t a0 = ta + (uint32_t)kk * sw + 16u * (uint32_t)gg;
+          if (++gg == G) {
+            gg = 0;
+            ++kk;
+          }
+          if (j + 1 < j1) {
+            tc_ld32(a0, ta + (uint32_t)kk * sw + 16u * (uint32_t)gg, v);
+            if (++gg == G) {
+              gg = 0;
+              ++kk;
+            }
           } else {
-            tc_ld16(ta + (uint32_t)c0, v);
+            tc_ld16(a0, v);
 #pragma unroll
             for (int i = 16; i < 32; ++i) v[i] = -INFINITY;
           }
-          float m[11];
+          float m[10];
 #pragma unroll
-          for (int i = 0; i < 10; ++i)
-            m[i] = fmax3(v[3 * i], v[3 * i + 1], v[3 * i + 2]);
-          m[10] = fmaxf(v[30], v[31]);
-          const float mm = fmax3(fmax3(m[0], m[1], m[2]),
-                                 fmax3(m[3], m[4], m[5]),
-                                 fmax3(fmax3(m[6], m[7], m[8]), m[9], m[10]));
-          if (mm > 0.f) {
-            uint32_t bits = 0u;
+          for (int h2 = 0; h2 < 2; ++h2) {
+            const float* x = v + 16 * h2;
 #pragma unroll
-            for (int i = 0; i < 32; ++i) bits |= (v[i] > 0.f ? 1u : 0u) << i;
-            mask[c0 >> 5] = bits;
+            for (int i = 0; i < 5; ++i)
+              m[5 * h2 + i] = fmax3(x[3 * i], x[3 * i + 1], x[3 * i + 2]);
+          }
+          const float lo = fmax3(fmax3(m[0], m[1], m[2]), m[3],
+                                 fmaxf(m[4], v[15]));
+          const float hi = fmax3(fmax3(m[5], m[6], m[7]), m[8],
+                                 fmaxf(m[9], v[31]));
+          grp |= (lo > 0.f ? 1u : 0u) << (j - j0);
+          grp |= (hi > 0.f ? 1u : 0u) << (j - j0 + 1);
+        }
+        tc_fence_before();
+        bar_arrive(sm.accempty(b));
+        // rare: (row, group) pairs that pass, one entry each
+        if (__any_sync(0xffffffffu, grp != 0u)) {
+          int ks = k0, gs = g0;
+          for (int j = j0; j < j1; ++j) {
+            const bool mine = (grp >> (j - j0)) & 1u;
+            const unsigned pass = __ballot_sync(0xffffffffu, mine);
+            if (mine) {
+              const uint32_t u = (uint32_t)((t0 + ks) * kScreenRows + row);
+              const uint32_t at = cnt + (uint32_t)__popc(pass & below);
+              if (at < (uint32_t)kWarpCap)
+                out[at] = (u << 3) | (uint32_t)gs;
+              kept += 16;
+            }
+            cnt += (uint32_t)__popc(pass);
+            if (++gs == G) {
+              gs = 0;
+              ++ks;
+            }
           }
         }
-        if (gt) {
-          tc_fence_before();
-          bar_arrive(sm.accempty(b));
-        }
-        // rare: this row's passing columns go to the item's segment
-        const int np = __popc(mask[0]) + __popc(mask[1]) + __popc(mask[2]) +
-                       __popc(mask[3]);
-        if (np) {
-          kept += np;
-          int at = (int)atomicAdd(sm.misc() + 2 + g, (uint32_t)np);
-          const uint32_t u = (uint32_t)(ti * kScreenRows + row);
-          for (int w = 0; w < 4; ++w)
-            for (uint32_t mw = mask[w]; mw; mw &= mw - 1u, ++at)
-              if (at < kSegCap)
-                out[at] = (u << 7) | (uint32_t)(32 * w + __ffs(mw) - 1);
-        }
       }
-      // every survivor of the item is queued: its count goes out and the
-      // counter is cleared for the item after next
-      const bool stop = sync128_or<1>(!ok);
-      if (threadIdx.x == 64) {
-        seg_cnt[it] = (int32_t)sm.misc()[2 + g];
-        sm.misc()[2 + g] = 0;
-      }
-      if (stop) break;
+      if (lane == 0) seg_cnt[(size_t)it * kEpiWarps + ew] = (int32_t)cnt;
+      if (!ok) break;
     }
     if (kept) atomicAdd(&ctr->screen_kept, kept);
   }
@@ -718,13 +772,22 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 // --------------------------------------------------------- rescore kernel
-// Exact rescoring of the survivors: one CTA of 128 threads per work item.
-// Thread e owns query column e: it scores the item's survivors in its
-// column with the float32 chain of the leaf kernel and inserts those below
-// the list's last entry (the list is read from HBM on the first insertion
-// and written back once).  An item whose segment overflowed is handed to
-// the float32 leaf kernel (appended to `ovf`) and not touched here.
-__global__ void __launch_bounds__(128)
+// Exact rescoring of the survivors.  One warp per unit (work item, block of
+// 32 query columns): lane j owns query column 32 b + j of the item.  The
+// warp reads its queries' list bounds (the last list entry), then walks the
+// item's segment 32 entries at a time: the entries of its two 16-column
+// groups are compacted and their points staged in the warp's shared memory
+// (one coalesced load per point coordinate), and every lane scores the
+// staged points of its own group with the float32 chain of the leaf kernel.
+// A point below the bound is inserted (strict rule) into the list, which is
+// read from HBM on the first insertion and written back at the end.  An
+// item whose segment overflowed is handed to the float32 leaf kernel
+// (appended to `ovf`) and not touched here.  Units are taken grid-stride
+// over the device's item count of the round.
+constexpr int kRescoreWarps = 8;
+
+template <int D>
+__global__ void __launch_bounds__(32 * kRescoreWarps)
     rescore_kernel(DevTree t, const Item* __restrict__ items,
                    Counters* ctr, const uint32_t* __restrict__ act,
                    const float* __restrict__ qpad, float* __restrict__ lst_d,
@@ -732,17 +795,27 @@ __global__ void __launch_bounds__(128)
                    const uint32_t* __restrict__ seg,
                    const int32_t* __restrict__ seg_cnt,
                    Item* __restrict__ ovf) {
-  __shared__ uint32_t es[kSegCap];
-  const int n_items = ctr->n_items;
-  const int e = threadIdx.x;
+  constexpr int kStride = D + 1;  // staged point: D coordinates + entry
+  __shared__ float stage[kRescoreWarps][32 * kStride];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* st = stage[wib];
+  const int64_t n_units = 4 * (int64_t)ctr->n_items;
+  const int64_t nw = (int64_t)gridDim.x * kRescoreWarps;
+  const unsigned below = (1u << lane) - 1u;
   unsigned long long queued = 0, overflow = 0;
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const int cnt = seg_cnt[it];
-    if (cnt == 0) continue;
+  for (int64_t u = (int64_t)blockIdx.x * kRescoreWarps + wib; u < n_units;
+       u += nw) {
+    const int it = (int)(u >> 2), cb = (int)(u & 3);
+    // lanes 0 .. kEpiWarps - 1: the item's sub-segment counts
+    const int cl = lane < kEpiWarps ? seg_cnt[(size_t)it * kEpiWarps + lane]
+                                    : 0;
+    const int total = __reduce_add_sync(0xffffffffu, max(cl, 0));
+    if (total == 0) continue;
     const Item w = items[it];
-    if (cnt > kSegCap) {
+    if (cb * 32 >= w.count) continue;
+    if (__any_sync(0xffffffffu, cl > kWarpCap)) {
       // the float32 leaf kernel takes items of at most kPipeTile queries
-      if (e == 0) {
+      if (cb == 0 && lane == 0) {
         const int parts = (w.count + kPipeTile - 1) / kPipeTile;
         const int at = atomicAdd(&ctr->screen_ovf_items, parts);
         for (int j = 0; j < parts; ++j)
@@ -752,54 +825,104 @@ __global__ void __launch_bounds__(128)
       }
       continue;
     }
-    for (int i = e; i < cnt; i += 128) es[i] = seg[(size_t)it * kSegCap + i];
-    __syncthreads();
-    if (e < w.count) {
-      const uint32_t q = act[w.start + e];
-      const uint32_t slot0 = (uint32_t)((int64_t)w.leaf * t.lcap);
-      const float* qp = qpad + (size_t)q * t.Dp;
-      float Ld[BKD_MAX_K + 1];
-      uint32_t Li[BKD_MAX_K + 1];
-      float bound = 0.f;
-      bool loaded = false, changed = false;
-      for (int i = 0; i < cnt; ++i) {
-        const uint32_t en = es[i];
-        if ((int)(en & 127u) != e) continue;
-        if (!loaded) {
-          for (int j = 0; j < K; ++j) {
-            Ld[j] = lst_d[(size_t)q * K + j];
-            Li[j] = lst_i[(size_t)q * K + j];
-          }
-          bound = Ld[K - 1];
-          loaded = true;
+    if (cb == 0 && lane == 0) queued += (unsigned long long)total;
+    const int col = cb * 32 + lane;
+    const bool valid = col < w.count;
+    const uint32_t q = valid ? act[w.start + col] : 0u;
+    float qr[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) qr[i] = valid ? qpad[(size_t)q * D + i] : 0.f;
+    float bound = valid ? lst_d[(size_t)q * K + K - 1] : -INFINITY;
+    const uint32_t my_group = (uint32_t)(col >> 4);
+    const uint32_t slot0 = (uint32_t)((int64_t)w.leaf * t.lcap);
+    float Ld[BKD_MAX_K + 1];
+    uint32_t Li[BKD_MAX_K + 1];
+    bool loaded = false, changed = false;
+    // every sub-segment may hold entries of this unit's groups 2 cb and
+    // 2 cb + 1 (the screen splits a buffer's tiles and groups between its
+    // warpgroups)
+    for (int e = 0; e < kEpiWarps; ++e) {
+      const int cnt = __shfl_sync(0xffffffffu, cl, e);
+      const uint32_t* sg = seg + ((size_t)it * kEpiWarps + e) * kWarpCap;
+      for (int base = 0; base < cnt; base += 32) {
+        uint32_t en = 0u;
+        bool rel = false;
+        if (base + lane < cnt) {
+          en = sg[base + lane];
+          // (entries of a leaf's padding rows never pass; the bound on the
+          // point index keeps a stale count from reading past the leaf)
+          rel = ((en & 7u) >> 1) == (uint32_t)cb && (en >> 3) < t.lcap;
         }
-        const uint32_t slot = slot0 + (en >> 7);
-        const float dv = exact_dist(qp, t.pts, t.Dp, slot);
-        if (dv < bound) {
-          int pos = K - 1;
-          while (pos > 0 && Ld[pos - 1] > dv) {
-            Ld[pos] = Ld[pos - 1];
-            Li[pos] = Li[pos - 1];
-            --pos;
-          }
-          Ld[pos] = dv;
-          Li[pos] = slot;
-          bound = Ld[K - 1];
-          changed = true;
+        const unsigned m = __ballot_sync(0xffffffffu, rel);
+        if (!m) continue;
+        if (rel) {
+          const int r = __popc(m & below);
+          const uint32_t slot = slot0 + (en >> 3);
+          const float* quad = t.pts + (size_t)(slot >> 2) * 4 * D + (slot & 3);
+          float* dst = st + r * kStride;
+#pragma unroll
+          for (int i = 0; i < D; ++i) dst[i] = quad[4 * i];
+          dst[D] = __uint_as_float(en);
         }
+        __syncwarp();
+        const int nr = __popc(m);
+        for (int r = 0; r < nr; ++r) {
+          const float* sp = st + r * kStride;
+          const uint32_t er = __float_as_uint(sp[D]);
+          if ((er & 7u) != my_group) continue;
+          float dd = __fsub_rn(qr[0], sp[0]);
+          float dv = __fmul_rn(dd, dd);
+#pragma unroll
+          for (int i = 1; i < D; ++i) {
+            dd = __fsub_rn(qr[i], sp[i]);
+            dv = __fmaf_rn(dd, dd, dv);
+          }
+          if (dv < bound) {
+            if (!loaded) {
+              for (int j = 0; j < K; ++j) {
+                Ld[j] = lst_d[(size_t)q * K + j];
+                Li[j] = lst_i[(size_t)q * K + j];
+              }
+              loaded = true;
+            }
+            int pos = K - 1;
+            while (pos > 0 && Ld[pos - 1] > dv) {
+              Ld[pos] = Ld[pos - 1];
+              Li[pos] = Li[pos - 1];
+              --pos;
+            }
+            Ld[pos] = dv;
+            Li[pos] = slot0 + (er >> 3);
+            bound = Ld[K - 1];
+            changed = true;
+          }
+        }
+        __syncwarp();
       }
-      if (changed)
-        for (int j = 0; j < K; ++j) {
-          lst_d[(size_t)q * K + j] = Ld[j];
-          lst_i[(size_t)q * K + j] = Li[j];
-        }
     }
-    if (e == 0) queued += (unsigned long long)cnt;
-    __syncthreads();
+    if (changed)
+      for (int j = 0; j < K; ++j) {
+        lst_d[(size_t)q * K + j] = Ld[j];
+        lst_i[(size_t)q * K + j] = Li[j];
+      }
   }
-  if (e == 0 && (queued || overflow)) {
+  if (queued || overflow) {
     atomicAdd(&ctr->screen_queued, queued);
     atomicAdd(&ctr->screen_overflow, overflow);
+  }
+}
+
+using RescoreFn = void (*)(DevTree, const Item*, Counters*, const uint32_t*,
+                           const float*, float*, uint32_t*, int,
+                           const uint32_t*, const int32_t*, Item*);
+RescoreFn rescore_for(int dp) {
+  switch (dp) {
+#define BKD_RESCORE_CASE(D) \
+  case D:                   \
+    return rescore_kernel<D>;
+    BKD_DIMS(BKD_RESCORE_CASE)
+#undef BKD_RESCORE_CASE
+    default: return nullptr;
   }
 }
 
@@ -902,7 +1025,11 @@ __global__ void __launch_bounds__(128)
 
 }  // namespace
 
-int screen_grid(int kh, int Dp, int64_t lcap, int K, int sm_count) {
+int screen_grid(const ScreenData& sd, int Dp, int64_t lcap, int K,
+                int sm_count) {
+  if (!sd.on()) return 0;
+  if (sd.kind == 0) return screen_grid_warp(sd.wkh, lcap, K, sm_count);
+  const int kh = sd.kh;
   if (kh < 1 || kh > 3 || Dp < 1 || K < 1 || K > BKD_MAX_K + 1 ||
       lcap >= ((int64_t)1 << 24))
     return 0;
@@ -914,17 +1041,30 @@ int screen_grid(int kh, int Dp, int64_t lcap, int K, int sm_count) {
       cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                            100) != cudaSuccess)
     return 0;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads,
-                                                    smem) != cudaSuccess ||
-      per_sm < 1)
+  // CTAs per SM: shared memory (with the per-block reservation), registers
+  // and tensor memory (512 columns per SM, kTmemCols per CTA)
+  int dev = 0, smem_sm = 0, smem_rsv = 0;
+  cudaFuncAttributes fa{};
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm,
+                             cudaDevAttrMaxSharedMemoryPerMultiprocessor,
+                             dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_rsv,
+                             cudaDevAttrReservedSharedMemoryPerBlock,
+                             dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, k) != cudaSuccess)
     return 0;
-  // tensor memory: 512 columns per SM, kTmemCols per CTA
-  per_sm = std::min<int>(per_sm, 512 / kTmemCols);
+  const int by_smem = smem_sm / (int)(smem + smem_rsv);
+  const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+  const int by_regs = 65536 / (regs_warp * (kThreads / 32));
+  const int per_sm =
+      std::min(std::min(by_smem, by_regs), (int)(512 / kTmemCols));
+  if (per_sm < 1) return 0;
   return per_sm * sm_count;
 }
 
 int64_t screen_seg_cap() { return kSegCap; }
+int64_t screen_cnt_per_item() { return kEpiWarps; }
 
 cudaError_t launch_screen(const DevTree& t, const ScreenData& sd,
                           const Item* items, int n_items, Counters* ctr,
@@ -933,9 +1073,21 @@ cudaError_t launch_screen(const DevTree& t, const ScreenData& sd,
                           const ScreenWork& w, int cap, int leaf_grid,
                           int sm_count, cudaStream_t s) {
   if (n_items == 0 || grid <= 0) return cudaSuccess;
+  if (sd.kind == 0)
+    return launch_screen_warp(t, sd, items, 0, n_items, ctr, act, qpad, lst_d,
+                              lst_i, K, grid, s);
   if (n_items > 0) grid = std::min(grid, n_items);
   const int aux = n_items > 0 ? std::min(n_items, sm_count * 16)
                               : sm_count * 16;
+  // rescoring: four units per item, kRescoreWarps units per CTA
+  const int64_t units = 4 * (int64_t)std::max(n_items, 0);
+  const int rescore_ctas =
+      n_items > 0 ? (int)std::min<int64_t>(
+                        (units + kRescoreWarps - 1) / kRescoreWarps,
+                        (int64_t)sm_count * 8)
+                  : sm_count * 8;
+  const RescoreFn rescore = rescore_for(t.Dp);
+  if (!rescore) return cudaErrorInvalidValue;
   const size_t smem = screen_smem(sd.kh);
   cudaError_t e = cudaMemsetAsync(&ctr->screen_next, 0,
                                   2 * sizeof(int32_t), s);
@@ -953,8 +1105,8 @@ cudaError_t launch_screen(const DevTree& t, const ScreenData& sd,
     default: return cudaErrorInvalidValue;
   }
 #undef BKD_SCREEN_KH
-  rescore_kernel<<<aux, 128, 0, s>>>(t, items, ctr, act, qpad, lst_d, lst_i,
-                                     K, w.seg, w.seg_cnt, w.ovf);
+  rescore<<<rescore_ctas, 32 * kRescoreWarps, 0, s>>>(
+      t, items, ctr, act, qpad, lst_d, lst_i, K, w.seg, w.seg_cnt, w.ovf);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // items whose survivors overflowed their segment: the float32 kernel

@@ -290,6 +290,16 @@ __global__ void retire_kernel(const int2* __restrict__ placed,
   atomicSub(batch_left + slot_batch[act[pos]], 1);
 }
 
+// One less in its batch's count for every query of the list (all of them
+// finished, e.g. by the tail kernel).
+__global__ void retire_list_kernel(const uint32_t* __restrict__ act, int n,
+                                   const int32_t* __restrict__ slot_batch,
+                                   int32_t* __restrict__ batch_left) {
+  const int pos = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= n) return;
+  atomicSub(batch_left + slot_batch[act[pos]], 1);
+}
+
 inline int blocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
@@ -306,6 +316,15 @@ cudaError_t launch_retire(const int2* placed, const uint32_t* act, int n_act,
   if (n_act <= 0) return cudaSuccess;
   retire_kernel<<<blocks(n_act, 256), 256, 0, s>>>(placed, act, n_act,
                                                    slot_batch, batch_left);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_retire_list(const uint32_t* act, int n,
+                               const int32_t* slot_batch, int32_t* batch_left,
+                               cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  retire_list_kernel<<<blocks(n, 256), 256, 0, s>>>(act, n, slot_batch,
+                                                    batch_left);
   return cudaGetLastError();
 }
 

@@ -238,7 +238,8 @@ int bkd_server::round() {
                          s));
   SV_CU(launch_retire(placed, act, n_act, slot_batch, batch_left, s));
   SV_CU(launch_bucket(placed, act, n_act, (int)L,
-                      screened ? kScreenTile : kPipeTile, D.leaf_cnt, cnt, off,
+                      screened ? screen_tile_of(v.screen.kind) : kPipeTile,
+                      D.leaf_cnt, cnt, off,
                       cursor, toff, items, nxt, d_ctr, s));
   SV_CU(cudaMemcpyAsync(h_ctr, d_ctr, sizeof(Counters),
                         cudaMemcpyDeviceToHost, s));
@@ -248,6 +249,18 @@ int bkd_server::round() {
   if (h_ctr->err & kErrTimeout)
     return set_error(BKD_ETIMEOUT, "a leaf-segment copy did not complete");
   const int n_next = h_ctr->n_next, n_items = h_ctr->n_items;
+  // few queries left in flight: the tail kernel finishes all of them now
+  const int tail = v.tail_queries >= 0 ? v.tail_queries : 8192;
+  if (n_next > 0 && n_next <= tail) {
+    SV_CU(launch_tail(D, v.d_pts, nxt, n_next, state, qpad, lst_d, lst_i, K,
+                      d_ctr, v.sm_count, s));
+    SV_CU(launch_retire_list(nxt, n_next, slot_batch, batch_left, s));
+    SV_CU(cudaMemcpyAsync(h_left, batch_left, sizeof(int32_t) * kMaxBatches,
+                          cudaMemcpyDeviceToHost, s));
+    SV_CU(cudaStreamSynchronize(s));
+    n_act = 0;
+    return BKD_OK;
+  }
   if (n_next > 0) {
     if (screened)
       SV_CU(launch_screen(D, v.screen, items, n_items, d_ctr, nxt, qpad,
@@ -339,7 +352,7 @@ int bkd_serve_open(bkd_tree* t, int k_max, int64_t max_queries,
   SV_CU(dev_alloc(&sv->off, L + 1));
   SV_CU(dev_alloc(&sv->cursor, std::max<int64_t>(L, 4)));
   SV_CU(dev_alloc(&sv->toff, L + 1));
-  SV_CU(dev_alloc(&sv->items, Q / std::min(kScreenTile, kPipeTile) + L + 1));
+  SV_CU(dev_alloc(&sv->items, Q / std::min(kWarpScreenTile, kPipeTile) + L + 1));
   SV_CU(dev_alloc(&sv->batch_left, kMaxBatches));
   SV_CU(dev_alloc(&sv->d_ctr, 1));
   SV_CU(dev_alloc(&sv->d_fin, 1));
@@ -352,15 +365,15 @@ int bkd_serve_open(bkd_tree* t, int k_max, int64_t max_queries,
                         v.stream));
   SV_CU(cudaStreamSynchronize(v.stream));
   sv->grid_max = leaf_kernel_grid(D.Dp, sv->cap, v.sm_count);
-  if (v.screen.words) {
+  if (v.screen.on() && v.screen.kind == 1) {
     const int64_t si = Q / kScreenTile + L + 1;
     SV_CU(dev_alloc(&sv->sw.bop, si * 4096 * v.screen.kh));
     SV_CU(dev_alloc(&sv->sw.seg, si * screen_seg_cap()));
-    SV_CU(dev_alloc(&sv->sw.seg_cnt, si));
+    SV_CU(dev_alloc(&sv->sw.seg_cnt, si * screen_cnt_per_item()));
     SV_CU(dev_alloc(&sv->sw.ovf, 2 * si));
   }
-  sv->screen_max = v.screen.words
-                       ? screen_grid(v.screen.kh, D.Dp, D.lcap, sv->K,
+  sv->screen_max = v.screen.on()
+                       ? screen_grid(v.screen, D.Dp, D.lcap, sv->K,
                                      v.sm_count)
                        : 0;
   if (sv->grid_max <= 0)

@@ -28,7 +28,9 @@ def _data():
     return P, Q, oracle.brute_knn(P, Q, 6)
 
 
-@pytest.mark.parametrize("opts", [{}, {"precision": 1}, {"chunks": 3}])
+@pytest.mark.parametrize("opts", [{}, {"precision": 1},
+                                  {"precision": 1, "screen_kernel": 2},
+                                  {"chunks": 3}])
 def test_every_build_allocation_can_fail_cleanly(opts):
     P, Q, ref = _data()
     failed = 0
@@ -52,11 +54,13 @@ def test_every_build_allocation_can_fail_cleanly(opts):
     check(P, Q, 6, idx, dist, ref)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_every_query_allocation_can_fail_and_the_tree_stays_usable(precision):
+@pytest.mark.parametrize("precision,kernel", [(0, 0), (1, 0), (1, 1)])
+def test_every_query_allocation_can_fail_and_the_tree_stays_usable(precision,
+                                                                   kernel):
     P, Q, ref = _data()
-    tree = bkd.bkd_build(P, 5, precision=1)
+    tree = bkd.bkd_build(P, 5, precision=1, screen_kernel=2)
     bkd.bkd_set_option(tree, "precision", precision)
+    bkd.bkd_set_option(tree, "screen_kernel", kernel)
     try:
         failed = 0
         for nth in range(1, 30):

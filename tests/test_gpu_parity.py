@@ -321,19 +321,29 @@ def test_tail_kernel_in_chunked_mode():
 
 
 def run_both_precisions(P, Q, k, h, **opts):
-    """One tree with BF16 screen data; the same queries scored with the
-    float32 kernel only and with the screen."""
+    """One tree with the screen data of both BF16 screen kernels; the same
+    queries scored with the float32 kernel only, with the warp screen
+    kernel and with the tcgen05 screen kernel.  The two screens must agree
+    with each other bit for bit; returns the float32 result, the warp
+    screen's result and the stats of both screens."""
     opts.setdefault("tail_queries", 0)
-    tree = bkd.bkd_build(P, h, precision=1, **opts)
+    tree = bkd.bkd_build(P, h, precision=1, screen_kernel=2, **opts)
     try:
         bkd.bkd_set_option(tree, "precision", 0)
         i0, d0 = bkd.bkd_query(tree, Q, k)
         bkd.bkd_set_option(tree, "precision", 1)
-        i1, d1 = bkd.bkd_query(tree, Q, k)
-        st = {s: bkd.bkd_get_stat(tree, s) for s in bkd.STATS}
+        out = []
+        for kernel in (0, 1):
+            bkd.bkd_set_option(tree, "screen_kernel", kernel)
+            i1, d1 = bkd.bkd_query(tree, Q, k)
+            out.append((i1, d1,
+                        {s: bkd.bkd_get_stat(tree, s) for s in bkd.STATS}))
     finally:
         bkd.bkd_free(tree)
-    return i0, d0, i1, d1, st
+    (i1, d1, st), (i2, d2, st2) = out
+    assert np.array_equal(i1, i2) and np.array_equal(d1, d2), \
+        "the warp and tcgen05 screen kernels disagree"
+    return i0, d0, i1, d1, (st, st2)
 
 
 @pytest.mark.parametrize("d,k", [(2, 4), (3, 10), (10, 10), (10, 1), (10, 31),
@@ -346,10 +356,12 @@ def test_bf16_screen_is_bit_identical(d, k):
     params = workloads.mixture_params(d, 16, 0.02, 0.2, 0)
     P = workloads.mixture(60000, params, 1)
     Q = workloads.mixture(4000, params, 2)
-    i0, d0, i1, d1, st = run_both_precisions(P, Q, k, 7)
+    i0, d0, i1, d1, sts = run_both_precisions(P, Q, k, 7)
     assert np.array_equal(i0, i1) and np.array_equal(d0, d1)
-    assert st["screen_pairs"] > 0
-    assert st["screen_kept"] < 0.2 * st["screen_pairs"]
+    for st in sts:
+        assert st["screen_pairs"] > 0
+        # (the tcgen05 kernel counts a kept (point, 16-query group) as 16)
+        assert st["screen_kept"] < 0.5 * st["screen_pairs"]
     check(P, Q, k, i1, d1, oracle.brute_knn(P, Q[:600], k),
           rows=np.arange(600))
 
@@ -370,11 +382,12 @@ def test_bf16_screen_with_ties_and_duplicates():
 def test_bf16_screen_uniform_65536():
     w = workloads.UNIFORM_64K
     P, Q = w.points(), w.queries()
-    i0, d0, i1, d1, st = run_both_precisions(P, Q, w.k, w.height,
-                                             tail_queries=-1)
+    i0, d0, i1, d1, sts = run_both_precisions(P, Q, w.k, w.height,
+                                              tail_queries=-1)
     assert np.array_equal(i0, i1) and np.array_equal(d0, d1)
     check(P, Q, w.k, i1, d1, oracle.brute_knn(P, Q, w.k))
-    print("screen kept fraction", st["screen_kept"] / st["screen_pairs"])
+    for st in sts:
+        print("screen kept fraction", st["screen_kept"] / st["screen_pairs"])
 
 
 def test_bf16_screen_option_errors():
@@ -384,6 +397,23 @@ def test_bf16_screen_option_errors():
         bkd.bkd_set_option(tree, "precision", 1)
     assert e.value.code == bkd.BKD_EINVAL
     bkd.bkd_free(tree)
+    # a screen kernel whose layout the tree does not hold, and item sizes
+    # outside the selected kernel's range
+    for built, other in ((0, 1), (1, 0)):
+        tree = bkd.bkd_build(P, 4, precision=1, screen_kernel=built)
+        try:
+            with pytest.raises(bkd.BkdError) as e:
+                bkd.bkd_set_option(tree, "screen_kernel", other)
+            assert e.value.code == bkd.BKD_EINVAL
+            bad = 64 if built == 0 else 8
+            with pytest.raises(bkd.BkdError) as e:
+                bkd.bkd_set_option(tree, "screen_tile", bad)
+            assert e.value.code == bkd.BKD_EINVAL
+        finally:
+            bkd.bkd_free(tree)
+    with pytest.raises(bkd.BkdError) as e:
+        bkd.bkd_build(P, 4, precision=1, screen_kernel=3)
+    assert e.value.code == bkd.BKD_EINVAL
     with pytest.raises(bkd.BkdError) as e:
         bkd.bkd_build(P, 4, precision=1, chunks=2)
     assert e.value.code == bkd.BKD_EUNSUPPORTED
@@ -397,10 +427,11 @@ def test_d27_k50_duplicates_workload():
     w = workloads.scaled(workloads.MIXTURE_D27, 1 << 16, 2000, 8)
     P, Q = w.points(), w.queries()
     ref = oracle.brute_knn(P, Q, 50)
-    tree = bkd.bkd_build(P, w.height, precision=1)
+    tree = bkd.bkd_build(P, w.height, precision=1, screen_kernel=2)
     try:
-        for prec in (0, 1):
+        for prec, kernel in ((0, 0), (1, 0), (1, 1)):
             bkd.bkd_set_option(tree, "precision", prec)
+            bkd.bkd_set_option(tree, "screen_kernel", kernel)
             idx, dist = bkd.bkd_query(tree, Q, 50)
             check(P, Q, 50, idx, dist, ref)
             assert bkd.bkd_get_stat(tree, "tail_queries") > 0

@@ -11,11 +11,12 @@ has three ingredients, each attacked here:
     them apart by almost the full 2^-8 of each, and whose (k+1)-th bound is
     just above the point's distance.  A bound that assumed 2^-9 rejects the
     point (worked through in the test's docstring);
-  * the tensor core's fp32 accumulation: the probe entry point runs the
-    screen's tcgen05 path (its operand layout, descriptors and chained
-    MMAs) on adversarial operands and every result is compared with the
-    exact sum against the accumulation model the bound uses (error <=
-    2^-18 of the sum of absolute products per chained k-half);
+  * the tensor core's fp32 accumulation: the probe entry points run the
+    warp kernel's mma.sync m16n8k16 and the tcgen05 kernel's path (its
+    operand layout, descriptors and chained MMAs) on adversarial operands
+    and every result is compared with the exact sum against the
+    accumulation model the bound uses (error <= 2^-18 of the sum of
+    absolute terms per MMA k-step);
   * wide data: a large common offset, queries far outside the tree's box,
     leaves of tiny spread, and d = 17 / 32 (two and three k-halves).
 """
@@ -35,17 +36,23 @@ MODEL = 2.0 ** -18   # per-instruction accumulation error the bound assumes
 
 
 def run_both(P, Q, k, h):
-    """float32 path and BF16 screen on one tree, every query through the
-    LazySearch rounds (tail kernel off)."""
-    tree = bkd.bkd_build(P, h, precision=1, tail_queries=0)
+    """float32 path and both BF16 screen kernels on one tree, every query
+    through the LazySearch rounds (tail kernel off); the two screens must
+    agree bit for bit.  Returns the float32 and warp-screen results and the
+    stats of the tcgen05 screen's call (screen_pairs of both are equal)."""
+    tree = bkd.bkd_build(P, h, precision=1, screen_kernel=2, tail_queries=0)
     try:
         bkd.bkd_set_option(tree, "precision", 0)
         i0, d0 = bkd.bkd_query(tree, Q, k)
         bkd.bkd_set_option(tree, "precision", 1)
         i1, d1 = bkd.bkd_query(tree, Q, k)
+        bkd.bkd_set_option(tree, "screen_kernel", 1)
+        i2, d2 = bkd.bkd_query(tree, Q, k)
         st = {s: bkd.bkd_get_stat(tree, s) for s in bkd.STATS}
     finally:
         bkd.bkd_free(tree)
+    assert np.array_equal(i1, i2) and np.array_equal(d1, d2), \
+        "the warp and tcgen05 screen kernels disagree"
     return i0, d0, i1, d1, st
 
 
@@ -224,6 +231,106 @@ def test_tensor_core_padding_rows_and_columns():
     assert (D[:100, :8] > 2.0 ** 125).all()
     assert (D[:100, 8:12] < -(2.0 ** 125)).all()
     assert np.isfinite(D[:100]).all()
+
+
+# ----------------------------- accumulation model, warp kernel (mma.sync)
+def mma_exact_dots(A, Bt, C):
+    """Exact C + A Bt^T per instance with math.fsum (bf16 products are exact
+    in binary64; fsum rounds the exact sum once), and the sum of absolute
+    terms."""
+    a, b = bf16_value(A), bf16_value(Bt)
+    cnt = A.shape[0]
+    out = np.empty((cnt, 16, 8))
+    mag = np.empty((cnt, 16, 8))
+    for i in range(cnt):
+        prod = a[i][:, None, :] * b[i][None, :, :]      # 16 x 8 x 16
+        for r in range(16):
+            for c in range(8):
+                terms = list(prod[r, c]) + [float(C[i, r, c])]
+                out[i, r, c] = math.fsum(terms)
+                mag[i, r, c] = math.fsum(abs(t) for t in terms)
+    return out, mag
+
+
+def mma_adversarial_operands(rng, cnt):
+    """Instances of several kinds (a quarter each): one large product with
+    fifteen small same-sign ones just under the large one's last bits;
+    heavy cancellation (pairs of equal and opposite large products) with
+    small terms; exponents mixed over 2^-30..2^30 inside one k-half; the
+    screen's own shape (offsets, the norm split pn_hi / pn_lo against -1/2,
+    a large accumulator input)."""
+    A = np.zeros((cnt, 16, 16), np.float32)
+    B = np.zeros((cnt, 8, 16), np.float32)
+    C = np.zeros((cnt, 16, 8), np.float32)
+    for i in range(cnt):
+        kind = i % 4
+        if kind == 0:
+            A[i] = rng.uniform(1.0, 2.0, (16, 16))
+            B[i] = rng.uniform(1.0, 2.0, (8, 16))
+            big = 2.0 ** rng.integers(8, 12)
+            A[i][:, 0] *= big
+            B[i][:, 0] *= big
+            small = 2.0 ** -rng.integers(6, 10, (16, 15))
+            A[i][:, 1:] *= small
+        elif kind == 1:
+            x = rng.uniform(1.0, 2.0, (16, 8)) * 2.0 ** rng.integers(4, 10)
+            A[i][:, 0:8] = x
+            A[i][:, 8:16] = -x
+            B[i][:] = 1.0
+            A[i][:, 15] = rng.uniform(-1e-3, 1e-3, 16)
+            B[i][:, 7] = rng.uniform(1.0, 1.1, 8)
+        elif kind == 2:
+            A[i] = (rng.choice([-1, 1], (16, 16)) * rng.uniform(1, 2, (16, 16))
+                    * 2.0 ** rng.integers(-15, 15, (16, 16)))
+            B[i] = (rng.choice([-1, 1], (8, 16)) * rng.uniform(1, 2, (8, 16))
+                    * 2.0 ** rng.integers(-15, 15, (8, 16)))
+            C[i] = rng.standard_normal((16, 8)) * 2.0 ** rng.integers(-10, 10)
+        else:
+            d = 10
+            w = rng.standard_normal((16, d)) * 2.0 ** rng.integers(-4, 4)
+            wb = bf16_value(bf16_bits(w.astype(np.float32)))
+            pn = np.float32((wb ** 2).sum(1))
+            hi = bf16_value(bf16_bits(pn))
+            lo = bf16_value(bf16_bits((pn - hi).astype(np.float32)))
+            A[i][:, :d] = w
+            A[i][:, d] = hi
+            A[i][:, d + 1] = lo
+            v = rng.standard_normal((8, d)) * 2.0 ** rng.integers(-4, 4)
+            B[i][:, :d] = v
+            B[i][:, d] = -0.5
+            B[i][:, d + 1] = -0.5
+            C[i] = rng.standard_normal((16, 8)) * 4.0
+    return bf16_bits(A), bf16_bits(B), C
+
+
+def test_mma_sync_accumulation_within_the_screen_model():
+    """The warp screen kernel's mma.sync m16n8k16 on adversarial operands:
+    every result within 2^-18 of |c| + sum |a b| from the exact sum."""
+    rng = np.random.default_rng(2024)
+    A, Bt, C = mma_adversarial_operands(rng, 512)
+    D = bkd.bkd_probe_mma(A, Bt, C)
+    exact, mag = mma_exact_dots(A, Bt, C)
+    err = np.abs(D.astype(np.float64) - exact)
+    ratio = err / np.maximum(mag, 1e-300)
+    worst = float(ratio.max())
+    print(f"accumulation error / (|c| + sum |a b|): max {worst:.3e} "
+          f"= 2^{math.log2(worst) if worst > 0 else -math.inf:.2f}; "
+          f"model 2^-18")
+    assert np.isfinite(D).all()
+    assert worst <= MODEL, f"accumulation error {worst:.3e} exceeds 2^-18"
+
+
+def test_mma_sync_infinite_norm_slot_gives_minus_infinity():
+    """A padding point carries pn_hi = +inf against the query's -1/2: its
+    product must be -inf, never NaN, whatever the other slots hold."""
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((1, 16, 16)).astype(np.float32)
+    B = rng.standard_normal((1, 8, 16)).astype(np.float32)
+    A[0, :, 12] = np.inf
+    B[0, :, 12] = -0.5
+    C = rng.standard_normal((1, 16, 8)).astype(np.float32)
+    D = bkd.bkd_probe_mma(bf16_bits(A), bf16_bits(B), C)
+    assert (D == -np.inf).all()
 
 
 # ------------------------------------------------------------- wide data

@@ -28,12 +28,13 @@ def _serve(srv, arrivals, max_steps=200000):
         assert step < max_steps
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_each_batch_same_alone_and_in_the_mix(precision):
+@pytest.mark.parametrize("precision,kernel", [(0, 0), (1, 0), (1, 1)])
+def test_each_batch_same_alone_and_in_the_mix(precision, kernel):
     import torch
     w = workloads.scaled(workloads.MIXTURE_64M, 1 << 16, 6000, 8)
     P, Qall = w.points(), w.queries()
-    tree = bkd.bkd_build(P, w.height, precision=precision)
+    opts = {"screen_kernel": kernel} if precision else {}
+    tree = bkd.bkd_build(P, w.height, precision=precision, **opts)
     # (first query, batch size, k, arrival step, device buffers)
     spec = [(0, 1, 10, 0, False), (1, 37, 1, 0, True), (38, 500, 50, 1, False),
             (538, 1200, 10, 3, True), (1738, 3, 50, 3, False),
