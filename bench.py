@@ -39,7 +39,7 @@ METRIC = ("kNN queries/s (k=10, d=10) FP32 vs BF16-screened; p50/p99 "
           "latency; % roofline")
 LEAF_SRC = os.path.join(ROOT, "paper_1512_02831_gb300", "csrc", "k_leaf.cuh")
 TRAFFIC_NOTE = os.path.join(ROOT, "profiles",
-                            "leaf_kernel_mixture64M_traffic.txt")
+                            "leaf_pipe_kernel_traffic.txt")
 # the two BF16 screen kernels: source file and committed ncu traffic note
 SCREEN_SRC = {0: os.path.join(ROOT, "paper_1512_02831_gb300", "csrc",
                               "k_screen_warp.cu"),
@@ -58,7 +58,9 @@ WORKLOADS = {"mixture64M": workloads.MIXTURE_64M,
                                             1 << 20, 14),
              # d = 27, k = 50, 64 components, 1% duplicate rows (n = 2^28,
              # m = 2^25, h = 18; ~30 GB of points)
-             "d27k50": workloads.MIXTURE_D27}
+             "d27k50": workloads.MIXTURE_D27,
+             # serving: n = 2^30, h = 20 (43 GB of points, resident)
+             "serving1G": workloads.MIXTURE_1G}
 
 
 def args_():
@@ -75,6 +77,23 @@ def args_():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--latency-seconds", type=float, default=4.0,
                     help="time budget of the per-batch latency sample")
+    ap.add_argument("--serving-seconds", type=float, default=5.0,
+                    help="length of each serving sample (0: none)")
+    ap.add_argument("--serving-rates", type=float, nargs="*",
+                    default=[1000.0, 10000.0],
+                    help="Poisson arrival rates (batches/s) of the serving "
+                         "samples")
+    ap.add_argument("--modes", default="fp32,warp,tcgen05",
+                    help="leaf scorings timed: fp32, warp (BF16 screen, "
+                         "warp kernel), tcgen05 (BF16 screen, tcgen05 "
+                         "kernel)")
+    ap.add_argument("--queries", type=int, default=0,
+                    help="time the first N queries of the workload's query "
+                         "set instead of all m (0: all); the line's config "
+                         "then names the sample")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="build the workload's tree and run only the "
+                         "serving samples (one JSON line)")
     ap.add_argument("--streamer", action="store_true",
                     help="measure the chunk streamer (bigger mode) instead")
     ap.add_argument("--streamer-n", type=int, default=0,
@@ -84,6 +103,13 @@ def args_():
     ap.add_argument("--streamer-h", type=int, default=20)
     ap.add_argument("--streamer-resident", action="store_true",
                     help="with --streamer-n: also time the resident tree")
+    ap.add_argument("--streamer-modes", default="",
+                    help="comma-separated subset of resident, chunks=N, "
+                         "point_chunks=N (default: resident unless "
+                         "--streamer-n, chunks=1,3,10, point_chunks=3,10)")
+    ap.add_argument("--streamer-oracle-rows", type=int, default=32,
+                    help="queries of the streamer's oracle sample (its "
+                         "cpu_baseline and parity rows; 0: none)")
     return ap.parse_args()
 
 
@@ -151,19 +177,21 @@ def measured_peaks() -> dict:
         return {}
 
 
-def leaf_traffic_per_launch():
-    """DRAM bytes per leaf-kernel launch from the committed ncu summary, if
-    it was taken on the current leaf kernel source."""
+def leaf_traffic_per_launch(acc, launches):
+    """DRAM bytes (read + write) of an average float32 leaf-kernel launch,
+    scaled from the committed ncu capture of one launch if it was taken on
+    the current leaf kernel source: the capture's DRAM bytes per staged
+    leaf-structure byte times this run's staged bytes, over its launches."""
     try:
         text = open(TRAFFIC_NOTE).read()
     except OSError:
         return None
     sha = hashlib.sha256(open(LEAF_SRC, "rb").read()).hexdigest()[:16]
     m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-    m_b = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.e+]+)", text)
-    if not m_sha or not m_b or m_sha.group(1) != sha:
+    m_r = re.search(r"dram_bytes_per_staged_byte:\s*([0-9.e+-]+)", text)
+    if not m_sha or not m_r or m_sha.group(1) != sha:
         return None
-    return float(m_b.group(1))
+    return float(m_r.group(1)) * acc["leaf_bytes"] / max(launches, 1)
 
 
 def screen_traffic_per_launch(acc, launches, kernel):
@@ -236,10 +264,10 @@ def data_description(w) -> str:
 # Queries are independent (Sec. 3.2, multi-many-core querying): every rank
 # holds the same tree and answers its own query stream; the job's time is
 # the slowest rank's, its work the sum over ranks.
-def rank_queries(w, rank: int) -> np.ndarray:
+def rank_queries(w, rank: int, m: int = 0) -> np.ndarray:
     """This rank's query set: an independent draw of the workload's query
-    distribution (stream = rank)."""
-    return w.queries(stream=rank)
+    distribution (stream = rank); m > 0: the first m queries of it."""
+    return w.queries(m if m > 0 else None, stream=rank)
 
 
 def max_over_ranks(x: float, dist=None, device=None) -> float:
@@ -337,65 +365,90 @@ def latency_sample(bkd, tree, Q, seconds: float, barrier) -> dict:
                        "12345")}
 
 
-def serving_sample(bkd, tree, Q, seconds: float, rate: float = 100.0):
-    """Continuous batching (bkd_serve_*): batches arrive as a seeded Poisson
-    process (`rate` batches/s for `seconds`, sizes log-uniform in [1, 2^16],
-    k in {1, 10, 50}, pinned host buffers) while the server steps; latency =
-    completion minus arrival, wall clock."""
+def serving_sample(bkd, tree, Q, seconds: float, rate: float,
+                   max_batch: int = 1 << 20, slots: int = 1 << 22,
+                   backlog: int = 1 << 23, seed: int = 777):
+    """Continuous batching (bkd_serve_*) under a seeded Poisson stream of
+    batches: `rate` batches/s for `seconds`, sizes log-uniform in [1,
+    max_batch], k uniform in {1, 10, 50}, queries from pinned host memory,
+    results into device buffers.  The server (k_max 50, `slots` query slots)
+    steps continuously; a batch that arrives while the queries submitted
+    and not yet completed exceed `backlog` is rejected at the door.
+    Latency = completion minus arrival (wall clock); at the end the batches
+    still queued or running are counted and dropped."""
     import torch
     if seconds <= 0:
         return None
-    rng = np.random.default_rng(777)
+    rng = np.random.default_rng(seed)
     m = Q.shape[0]
     Qh = torch.from_numpy(Q).pin_memory()
-    srv = bkd.Server(tree, k_max=50, max_queries=1 << 20)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    srv = bkd.Server(tree, k_max=50, max_queries=slots)
     arrivals, t = [], 0.0
     while True:
         t += rng.exponential(1.0 / rate)
         if t >= seconds:
             break
-        b = int(min(m, np.exp(rng.uniform(0.0, np.log(1 << 16)))))
+        b = int(min(m, max_batch, np.exp(rng.uniform(0.0, np.log(max_batch)))))
         arrivals.append((t, b, int(rng.choice([1, 10, 50])),
                          int(rng.integers(0, m - b + 1))))
-    live, lat, nq, steps, submitted, seen = {}, [], 0, 0, 0, 0
+    live, lat, served, steps = {}, [], 0, 0
+    rejected = rejected_q = accepted = 0
+    outstanding = 0
     t0 = time.perf_counter()
     nxt = 0
-    while nxt < len(arrivals) or live:
+    while nxt < len(arrivals):
         now = time.perf_counter() - t0
         while nxt < len(arrivals) and arrivals[nxt][0] <= now:
             ta, b, k, s0 = arrivals[nxt]
-            oi = torch.empty((b, k), dtype=torch.int64).pin_memory()
-            od = torch.empty((b, k), dtype=torch.float32).pin_memory()
-            live[srv.submit(Qh[s0:s0 + b], k, oi, od)] = (ta, b)
-            submitted += 1
             nxt += 1
+            if outstanding + b > backlog:
+                rejected += 1
+                rejected_q += b
+                continue
+            oi = torch.empty((b, k), dtype=torch.int64, device=dev)
+            od = torch.empty((b, k), dtype=torch.float32, device=dev)
+            live[srv.submit(Qh[s0:s0 + b], k, oi, od)] = (ta, b)
+            outstanding += b
+            accepted += 1
         if not live:
-            time.sleep(max(0.0, arrivals[nxt][0] - now))
+            if nxt < len(arrivals):
+                time.sleep(max(0.0, arrivals[nxt][0] - now))
             continue
         pending = srv.step()
         steps += 1
-        if submitted - pending > seen:  # some batch completed: find it
-            seen = submitted - pending
+        if pending < len(live):  # some batch completed: find it
             now = time.perf_counter() - t0
             for tk in list(live):
                 if srv.status(tk) == bkd.BKD_BATCH_DONE:
                     ta, b = live.pop(tk)
                     srv.result(tk)
                     lat.append(now - ta)
-                    nq += b
+                    served += b
+                    outstanding -= b
     wall = time.perf_counter() - t0
+    left = len(live)
     srv.close()
-    lat_ms = np.array(lat) * 1e3
+    lat_ms = np.array(lat) * 1e3 if lat else np.array([np.nan])
     offered = sum(b for _, b, _, _ in arrivals) / seconds
-    return {"batches": len(lat), "p50_ms": float(np.percentile(lat_ms, 50)),
+    return {"rate_batches_per_s": rate, "arrived": len(arrivals),
+            "accepted": accepted, "rejected": rejected,
+            "rejected_queries": rejected_q, "completed": len(lat),
+            "unfinished_at_end": left,
+            "p50_ms": float(np.percentile(lat_ms, 50)),
             "p99_ms": float(np.percentile(lat_ms, 99)),
-            "queries_per_s": nq / wall, "offered_queries_per_s": offered,
-            "steps": steps,
+            "served_queries_per_s": served / wall,
+            "offered_queries_per_s": offered, "steps": steps,
             "recipe": (f"Poisson arrivals of {rate:.0f} batches/s for "
-                       f"{seconds:.1f} s (seed 777), sizes logU[1, 2^16], k "
-                       f"uniform in {{1, 10, 50}}, pinned host buffers, one "
-                       f"server (k_max 50, 2^20 query slots) stepping "
-                       f"continuously; latency = completion - arrival")}
+                       f"{seconds:.1f} s (seed {seed}), sizes logU[1, "
+                       f"{max_batch}], k uniform in {{1, 10, 50}}, queries "
+                       f"from pinned host memory, results into device "
+                       f"buffers; one server (k_max 50, {slots} query "
+                       f"slots) stepping continuously; a batch arriving "
+                       f"while more than {backlog} submitted queries are "
+                       f"unfinished is rejected; latency = completion - "
+                       f"arrival over the completed batches; served = "
+                       f"queries of completed batches / wall time")}
 
 
 def run_ours(a, w, rank, world, local_rank):
@@ -418,13 +471,31 @@ def run_ours(a, w, rank, world, local_rank):
         return max_over_ranks(x, dist, dev)
 
     P = w.points()
-    Q = rank_queries(w, rank)
+    Q = rank_queries(w, rank, a.queries)
     m, k, d = Q.shape[0], w.k, w.d
+    modes = [x.strip() for x in a.modes.split(",") if x.strip()]
+    if not set(modes) <= {"fp32", "warp", "tcgen05"} or "fp32" not in modes:
+        raise SystemExit("--modes: a subset of fp32,warp,tcgen05 with fp32")
     t0 = time.perf_counter()
-    # the point layouts of both BF16 screen kernels (warp / mma.sync and
-    # tcgen05): each is timed, the fastest configuration is the headline
-    tree = bkd.bkd_build(P, w.height, precision=1, screen_kernel=2)
+    # the point layouts of the BF16 screen kernels timed (warp / mma.sync
+    # and tcgen05): each is timed, the fastest configuration is the headline
+    kernels = 2 if {"warp", "tcgen05"} <= set(modes) else (
+        1 if "tcgen05" in modes else 0)
+    tree = bkd.bkd_build(P, w.height, precision=1, screen_kernel=kernels)
     build_s = time.perf_counter() - t0
+    if a.serving_only:
+        del P
+        # the serving samples alone (the resident tree of the workload)
+        serving = [serving_sample(bkd, tree, Q, a.serving_seconds, r)
+                   for r in a.serving_rates]
+        bkd.bkd_free(tree)
+        if rank == 0:
+            print(json.dumps({"metric": "serving (continuous batching)",
+                              "workload": w.name,
+                              "config": dict(w.describe(),
+                                             tree_build_s=round(build_s, 2)),
+                              "serving": serving}), flush=True)
+        return
     Qd = torch.from_numpy(Q).to(dev)
     out_i = torch.empty((m, k), dtype=torch.int64, device=dev)
     out_d = torch.empty((m, k), dtype=torch.float32, device=dev)
@@ -435,7 +506,7 @@ def run_ours(a, w, rank, world, local_rank):
                   "tail_queries", "tail_visits", "tail_pairs", "tail_ms",
                   "screen_kept", "screen_pairs", "screen_ms", "screen_items",
                   "screen_visits", "find_ms", "bucket_ms", "exact_ms",
-                  "screen_bytes")
+                  "screen_bytes", "leaf_bytes", "host_syncs")
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     vis = [v for v in vis.split(",") if v.strip()]
     smi_index = (vis[local_rank] if local_rank < len(vis)
@@ -446,7 +517,8 @@ def run_ours(a, w, rank, world, local_rank):
         `precision` (0 float32, 1 BF16 screen + float32 rescoring) and, for
         the screen, `kernel` (0 warp / mma.sync, 1 tcgen05)."""
         bkd.bkd_set_option(tree, "precision", precision)
-        bkd.bkd_set_option(tree, "screen_kernel", kernel)
+        if precision:
+            bkd.bkd_set_option(tree, "screen_kernel", kernel)
         for _ in range(a.warmup):
             bkd.bkd_query(tree, Qd, k, out_i, out_d)
         barrier()
@@ -470,17 +542,22 @@ def run_ours(a, w, rank, world, local_rank):
                 "value": whole_job_rate(world, m, a.steps, ms_max),
                 "idx": out_i.clone(), "dist": out_d.clone()}
 
-    # runs: 0 float32, 1 warp screen, 2 tcgen05 screen
-    runs = {0: timed(0), 1: timed(1, 0), 2: timed(1, 1)}
+    # runs: 0 float32, 1 warp screen, 2 tcgen05 screen (those asked for)
+    runs = {0: timed(0)}
+    if "warp" in modes:
+        runs[1] = timed(1, 0)
+    if "tcgen05" in modes:
+        runs[2] = timed(1, 1)
     identical = all(bool(torch.equal(runs[0]["idx"], runs[r]["idx"])
                          and torch.equal(runs[0]["dist"], runs[r]["dist"]))
-                    for r in (1, 2))
+                    for r in runs if r)
     head = max(runs, key=lambda r: runs[r]["value"])
     acc, clk, ms, ms_max = (runs[head][x] for x in ("acc", "clk", "ms",
                                                      "ms_max"))
     value = runs[head]["value"]
     bkd.bkd_set_option(tree, "precision", 0 if head == 0 else 1)
-    bkd.bkd_set_option(tree, "screen_kernel", 1 if head == 2 else 0)
+    if head:
+        bkd.bkd_set_option(tree, "screen_kernel", 1 if head == 2 else 0)
     out_i.copy_(runs[head]["idx"])
 
     # end to end through the same call, host buffers (pinned), copies inside
@@ -505,7 +582,8 @@ def run_ours(a, w, rank, world, local_rank):
     # [1, 2^20], k in {1, 10, 50}) through the same public call with pinned
     # host buffers, one after the other on the resident tree
     lat = latency_sample(bkd, tree, Q, a.latency_seconds, barrier)
-    serving = serving_sample(bkd, tree, Q, min(a.latency_seconds, 3.0))
+    serving = [serving_sample(bkd, tree, Q, a.serving_seconds, r)
+               for r in a.serving_rates] if a.serving_seconds > 0 else None
 
     # rooflines: the float32 leaf kernel (from the float32 run) and the BF16
     # screen kernel (from the screened run)
@@ -519,7 +597,10 @@ def run_ours(a, w, rank, world, local_rank):
     roof_fp32 = {
         "bound": "alu", "kernel": "leaf_pipe_kernel (ProcessAllBuffers, fp32)",
         "achieved": achieved, "peak": peak_ops, "unit": "Top/s",
-        "frac": achieved / peak_ops, "traffic": leaf_traffic_per_launch(),
+        "frac": achieved / peak_ops,
+        "traffic": leaf_traffic_per_launch(a0, a0["leaf_launches"]),
+        "algorithmic_bytes_per_launch": (a0["leaf_bytes"]
+                                         / max(a0["leaf_launches"], 1)),
         "basis": (f"FP32 pipe operations: 2*d = {2 * d} per scored (query, "
                   f"point) pair (d subtractions + d multiply-adds); peak = "
                   f"128 FP32 lanes x {sm_count} SMs x {sm_max:.0f} MHz "
@@ -586,8 +667,13 @@ def run_ours(a, w, rank, world, local_rank):
                               if a1["screen_pairs"] else None),
         }
 
-    roof_bf16 = roof_screen(1)
-    roof_tc = roof_screen(2)
+    roof_bf16 = roof_screen(1) if 1 in runs else None
+    roof_tc = roof_screen(2) if 2 in runs else None
+    # DRAM traffic over the algorithmic bytes (re-reads above 1.0)
+    for r in (roof_fp32, roof_bf16, roof_tc):
+        if r and r.get("traffic") and r.get("algorithmic_bytes_per_launch"):
+            r["traffic_over_algorithmic"] = (r["traffic"]
+                                             / r["algorithmic_bytes_per_launch"])
     roofline = {0: roof_fp32, 1: roof_bf16, 2: roof_tc}[head]
     names = {0: "fp32 exact path",
              1: "bf16 tensor-core screen (warp kernel) + fp32 rescore",
@@ -601,6 +687,7 @@ def run_ours(a, w, rank, world, local_rank):
         "dtype": "bf16+f32" if head else "f32",
         "data": data_description(w),
         "config": dict(w.describe(), precision=names[head],
+                       queries_timed_per_step=m,
                        parallelism=f"replicas x{world}, queries sharded",
                        l2=l2_note(w),
                        tree_build_s=round(build_s, 2)),
@@ -616,14 +703,17 @@ def run_ours(a, w, rank, world, local_rank):
             "fp32": {"value": runs[0]["value"],
                      "ms_per_step": runs[0]["ms_max"] / a.steps,
                      "clocks": runs[0]["clk"]},
-            "bf16_screened": {"value": runs[1]["value"],
-                              "ms_per_step": runs[1]["ms_max"] / a.steps,
-                              "clocks": runs[1]["clk"]},
-            "bf16_screened_tcgen05": {
+            "bf16_screened": ({"value": runs[1]["value"],
+                               "ms_per_step": runs[1]["ms_max"] / a.steps,
+                               "screen_ms_per_step":
+                                   runs[1]["acc"]["screen_ms"] / a.steps,
+                               "clocks": runs[1]["clk"]}
+                              if 1 in runs else None),
+            "bf16_screened_tcgen05": ({
                 "value": runs[2]["value"],
                 "ms_per_step": runs[2]["ms_max"] / a.steps,
                 "screen_ms_per_step": runs[2]["acc"]["screen_ms"] / a.steps,
-                "clocks": runs[2]["clk"]},
+                "clocks": runs[2]["clk"]} if 2 in runs else None),
             "identical_results": identical,
             "headline": names[head]},
         "clocks": clk,
@@ -646,6 +736,7 @@ def run_ours(a, w, rank, world, local_rank):
                                              / acc["screen_items"]
                                              if acc["screen_items"] else None),
                  "find_leaf_ms_per_step": acc["find_ms"] / a.steps,
+                 "host_syncs_per_step": acc["host_syncs"] / a.steps,
                  "bucket_ms_per_step": acc["bucket_ms"] / a.steps,
                  "recheck_fallback_ms_per_step": acc["exact_ms"] / a.steps,
                  "e2e_matches_device_run": same},
@@ -711,11 +802,25 @@ def run_streamer(a):
            "h2d_peak_gbs": best, "leaf_structure_gb": structure / 1e9,
            "data_generation_s": round(gen_s, 1), "modes": {}}
     ref = None
-    modes = [("resident", {})] if not a.streamer_n or a.streamer_resident \
-        else []
-    modes += [(f"chunks={c}", {"chunks": c}) for c in (1, 3, 10)]
-    modes += [(f"point_chunks={c}", {"chunks": c, "point_chunks": 1})
-              for c in (3, 10)]
+    if a.streamer_modes:
+        modes = []
+        for name in a.streamer_modes.split(","):
+            name = name.strip()
+            if name == "resident":
+                modes.append((name, {}))
+            elif name.startswith("chunks="):
+                modes.append((name, {"chunks": int(name.split("=")[1])}))
+            elif name.startswith("point_chunks="):
+                modes.append((name, {"chunks": int(name.split("=")[1]),
+                                     "point_chunks": 1}))
+            else:
+                raise SystemExit(f"--streamer-modes: unknown mode {name}")
+    else:
+        modes = [("resident", {})] if not a.streamer_n or a.streamer_resident \
+            else []
+        modes += [(f"chunks={c}", {"chunks": c}) for c in (1, 3, 10)]
+        modes += [(f"point_chunks={c}", {"chunks": c, "point_chunks": 1})
+                  for c in (3, 10)]
     for name, opts in modes:
         t0 = time.perf_counter()
         tree = bkd.bkd_build(P, w.height, **opts)
@@ -729,7 +834,8 @@ def run_streamer(a):
         dt = time.perf_counter() - t0
         st = {x: bkd.bkd_get_stat(tree, x)
               for x in ("chunk_bytes", "copy_ms", "rounds", "leaf_kernel_ms",
-                        "chunk_visits", "leaf_visits")}
+                        "chunk_visits", "leaf_visits", "mapped_bytes",
+                        "host_syncs")}
         shape = bkd.bkd_tree_shape(tree)
         bkd.bkd_free(tree)
         if ref is None:
@@ -744,6 +850,8 @@ def run_streamer(a):
             "passes_over_structure": st["chunk_bytes"] / structure,
             "copy_ms": st["copy_ms"], "copy_gbs": gbs,
             "copy_frac_of_h2d_peak": gbs / best if gbs else None,
+            "mapped_gb": st["mapped_bytes"] / 1e9,
+            "host_syncs": st["host_syncs"],
             "leaf_kernel_ms": st["leaf_kernel_ms"],
             "identical_to_first_mode": bool(torch.equal(idx, ref[0])
                                             and torch.equal(dist, ref[1]))}
@@ -753,6 +861,29 @@ def run_streamer(a):
         for v in out["modes"].values():
             v["q_per_s_ratio_to_resident"] = (v["queries_per_s"]
                                               / base["queries_per_s"])
+    if a.streamer_oracle_rows > 0 and ref is not None:
+        # cpu_baseline leg: the oracle's brute force (the definition,
+        # binary64, all host cores) timed on a seeded sample of the queries;
+        # the same rows give the parity of the GPU result
+        import oracle
+        rng = np.random.default_rng(11)
+        rows = np.sort(rng.choice(m, min(m, a.streamer_oracle_rows),
+                                  replace=False))
+        t0 = time.perf_counter()
+        res = oracle.brute_knn(P, Q[rows], k)
+        dt = time.perf_counter() - t0
+        got = ref[0].cpu().numpy()[rows]
+        exempt = res.gap_exempt(1e-6)
+        eq = (got == res.idx).all(1)
+        out["cpu_baseline"] = {
+            "value": len(rows) / dt, "unit": "queries/s",
+            "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": (f"{len(rows)} of {m} queries (seeded), binary64 brute "
+                       f"force over all {w.n} points")}
+        out["parity_sample"] = {
+            "queries": int(len(rows)), "index_rows_equal": int(eq.sum()),
+            "gap_exempt": int(exempt.sum()),
+            "non_exempt_mismatch": int((~exempt & ~eq).sum())}
     print(json.dumps(out), flush=True)
 
 

@@ -92,8 +92,11 @@ enum bkd_option {
   /* Leaf scoring: 0 (default) = float32 for every (query, point) pair;
    * 1 = a BF16 tensor-core screen rejects points that provably cannot enter
    * a candidate list, the rest are scored in float32 -- results identical to
-   * 0.  1 at build also prepares the screen data (resident trees only;
-   * chunked: BKD_EUNSUPPORTED); afterwards 0 / 1 may be switched any time. */
+   * 0.  1 at build also prepares the screen data; afterwards 0 / 1 may be
+   * switched any time.  Chunked trees: leaf chunks and the warp screen
+   * kernel only (the screen operands are streamed with each chunk's
+   * points); with BKD_OPT_POINT_CHUNKS=1 or BKD_OPT_SCREEN_KERNEL=1 the
+   * build fails with BKD_EUNSUPPORTED. */
   BKD_OPT_PRECISION = 6,
   /* Chunk bounds in chunked mode: 0 (default) = whole leaves (chunk c holds
    * leaves [ceil(c L / N), ceil((c+1) L / N)), L = 2^h), scheduled so that
@@ -163,8 +166,19 @@ enum bkd_stat {
   BKD_STAT_SCREEN_BYTES = 24,  /* bytes of bf16 operand tiles the screen
                                   streamed from HBM into shared memory      */
   BKD_STAT_SCREEN_QUEUED = 25, /* pairs the screen queued for rescoring     */
-  BKD_STAT_SCREEN_OVERFLOW = 26 /* screen items rescored against the whole
+  BKD_STAT_SCREEN_OVERFLOW = 26, /* screen items rescored against the whole
                                   leaf (their rescoring queue overflowed)  */
+  BKD_STAT_LEAF_BYTES = 27,     /* bytes of the leaf structure the float32
+                                  leaf kernel staged in shared memory (one
+                                  pass over the leaf per work item)        */
+  BKD_STAT_HOST_SYNCS = 28,     /* times the host waited for the device's
+                                  round counters (resident trees queue up
+                                  to BKD_OPT_ROUND_BATCH rounds per look)  */
+  BKD_STAT_FALLBACK_POINTS = 29, /* points the binary64 fallback scanned   */
+  BKD_STAT_MAPPED_BYTES = 30    /* chunked trees: point bytes the tail,
+                                  re-check and fallback kernels read from
+                                  the mapped pinned host leaf structure
+                                  (zero-copy, not in chunk_bytes)          */
 };
 
 typedef struct bkd_tree bkd_tree; /* opaque; owned by the library */
@@ -229,10 +243,10 @@ int bkd_query(bkd_tree* t, const float* Q, int64_t m, int k, int64_t* out_idx,
 int bkd_query_static(bkd_tree* t, const float* Q, int64_t m, int k,
                      int64_t* out_idx, float* out_dist);
 
-/* bkd_outlier_scores -- the proximity-based outlier score of Sec. 4.3 ("rank
- * the points according to their average distance to their k nearest
- * neighbors"; the all-nearest-neighbours problem, queries = the reference
- * points): for every reference point i (original row order),
+/* bkd_outlier_scores -- the proximity-based outlier score of Sec. 4.3 (each
+ * point is ranked by the mean distance to its k nearest neighbours: the
+ * all-nearest-neighbours problem, queries = the reference points): for
+ * every reference point i (original row order),
  *   out_score[i] = (1/k) sum of the Euclidean (not squared) distances from
  *                  x_i to its k nearest neighbours among the OTHER points,
  * neighbours taken under the same (distance, index) order as bkd_query: x_i
@@ -249,8 +263,8 @@ int bkd_query_static(bkd_tree* t, const float* Q, int64_t m, int k,
 int bkd_outlier_scores(bkd_tree* t, int k, float* out_score);
 
 /* ------------------------------------------------------------ test support
- * Neither call has a counterpart in the paper; they let tests reach failure
- * paths and hardware properties that the query calls depend on. */
+ * None of these calls has a counterpart in the paper; they let tests reach
+ * failure paths and hardware properties that the query calls depend on. */
 
 /* bkd_test_fail_alloc -- makes the nth device or pinned host allocation made
  * by the library from now on (any handle, any thread) fail as if the memory
@@ -333,10 +347,13 @@ enum bkd_batch_status {
 
 /* bkd_serve_open -- a server on tree t (resident, not chunked).
  *   k_max        largest k a batch may ask for, 1 <= k_max <= min(n,
- *                BKD_MAX_K); every query carries a list of k_max + 1
- *                entries (a smaller k only reads a prefix of its result).
- *   max_queries  query slots: the most queries in flight at once (device
- *                memory ~ max_queries x (4 Dp + 8 k_max + 60) bytes).
+ *                BKD_MAX_K).  Batches are routed by k to list classes of
+ *                at most 12, 32 or 64 entries (those up to k_max + 1): a
+ *                query carries its class's list, and a class's rounds run
+ *                with that list length.
+ *   max_queries  query slots of each class: the most queries in flight at
+ *                once in a class (device memory per class ~ max_queries x
+ *                (4 Dp + 8 kc + 60) bytes, kc the class's largest k).
  *   out          receives the server (NULL on failure).
  * The server uses the tree's stream; do not run bkd_query on the same tree
  * while the server has batches in flight.

@@ -211,9 +211,9 @@ def pair_dist(P, Q, qi, pi) -> np.ndarray:
 
 
 def outlier_scores(P, k: int, threads: int = 0) -> np.ndarray:
-    """Outlier score of Sec. 4.3 ("rank the points according to their
-    average distance to their k nearest neighbors", queries = the reference
-    set): for every point i, the mean of the binary64 Euclidean distances to
+    """Outlier score of Sec. 4.3 (points ranked by the mean distance to
+    their k nearest neighbours, queries = the reference set): for every
+    point i, the mean of the binary64 Euclidean distances to
     its k nearest neighbours among the other points.  The neighbours are the
     first k+1 of the (distance, index) order of :func:`brute_knn` with the
     point's own index removed -- or, when k+1 exact duplicates of smaller

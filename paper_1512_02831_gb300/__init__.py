@@ -46,7 +46,9 @@ STATS = {"rounds": 1, "leaf_visits": 2, "pairs": 3, "resorted": 4,
          "screen_kept": 15, "screen_pairs": 16, "screen_ms": 17,
          "screen_items": 18, "screen_visits": 19, "find_ms": 20,
          "bucket_ms": 21, "exact_ms": 22, "chunk_visits": 23,
-         "screen_bytes": 24, "screen_queued": 25, "screen_overflow": 26}
+         "screen_bytes": 24, "screen_queued": 25, "screen_overflow": 26,
+         "leaf_bytes": 27, "host_syncs": 28, "fallback_points": 29,
+         "mapped_bytes": 30}
 
 _lock = threading.Lock()
 _lib = None

@@ -145,6 +145,13 @@ struct bkd_tree {
   int32_t* d_chunk_leaf = nullptr;
   float* d_chunk_buf[2] = {nullptr, nullptr};
   int buf_chunk[2] = {-1, -1};
+  // chunked trees with the BF16 screen (leaf chunks, warp kernel): the
+  // warp layout in pinned host memory, and a device buffer per chunk buffer
+  bool chunk_screen = false;
+  bool buf_scr[2] = {false, false};  // buffer b holds its chunk's operands
+  uint32_t* h_scr_wwords = nullptr;
+  uint32_t* d_chunk_scr[2] = {nullptr, nullptr};
+  size_t scr_leaf_words = 0;  // words of one leaf in the warp layout
   cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
   // query workspace
   DevBuf<float> qdev, qpad, lst_d;
@@ -181,7 +188,9 @@ struct bkd_tree {
          st_screen_kept = 0, st_screen_pairs = 0, st_screen_ms = 0,
          st_screen_items = 0, st_screen_visits = 0, st_find_ms = 0,
          st_bucket_ms = 0, st_exact_ms = 0, st_chunk_visits = 0,
-         st_screen_bytes = 0, st_screen_queued = 0, st_screen_overflow = 0;
+         st_screen_bytes = 0, st_screen_queued = 0, st_screen_overflow = 0,
+         st_leaf_bytes = 0, st_host_syncs = 0, st_fallback_points = 0,
+         st_mapped_bytes = 0;
 
   cudaEvent_t next_event() {
     if (ev_used == ev_pool.size()) {
@@ -214,6 +223,9 @@ void release(bkd_tree* t) {
   cudaFree(t->d_leaf_lo);
   cudaFree(t->d_chunk_buf[0]);
   cudaFree(t->d_chunk_buf[1]);
+  cudaFree(t->d_chunk_scr[0]);
+  cudaFree(t->d_chunk_scr[1]);
+  if (t->h_scr_wwords) cudaFreeHost(t->h_scr_wwords);
   if (t->h_pts) cudaFreeHost(t->h_pts);
   if (t->h_orig) cudaFreeHost(t->h_orig);
   t->qdev.release();
@@ -525,10 +537,14 @@ int build_impl(const float* P, int64_t n, int d, int height,
         return bail(fail(BKD_ECUDA, "event creation failed"));
   }
   if (precision == 1) {
-    if (chunked)
+    // chunked trees: leaf chunks and the warp kernel only (its point layout
+    // is streamed with the points, chunk by chunk)
+    if (chunked && (point_chunks || screen_kernel == 1))
       return bail(fail(BKD_EUNSUPPORTED,
-                       "the BF16 screen needs a tree resident in device "
-                       "memory"));
+                       "the BF16 screen on a chunked tree needs leaf chunks "
+                       "(BKD_OPT_POINT_CHUNKS=0) and the warp screen kernel "
+                       "(BKD_OPT_SCREEN_KERNEL=0)"));
+    if (chunked) screen_kernel = 0;
     // the layouts of the screen kernels asked for: 0 the warp kernel, 1
     // the tcgen05 kernel, 2 both (the warp kernel runs; BKD_OPT_SCREEN_KERNEL
     // switches)
@@ -541,7 +557,7 @@ int build_impl(const float* P, int64_t n, int d, int height,
     std::vector<float> center, bmax, pnmax;
     try {
       if (want_tc) words.resize((size_t)L * tiles * kScreenRows * 16 * kh);
-      if (want_warp) wwords.resize((size_t)L * wkh * stride * 8);
+      if (want_warp && !chunked) wwords.resize((size_t)L * wkh * stride * 8);
       center.resize((size_t)L * d);
       bmax.resize(L);
       pnmax.resize(L);
@@ -551,12 +567,33 @@ int build_impl(const float* P, int64_t n, int d, int height,
     if (want_tc)
       fill_screen(Ph, H, tiles, words.data(), center.data(), bmax.data(),
                   pnmax.data());
-    if (want_warp)
+    t->scr_leaf_words = (size_t)wkh * stride * 8;
+    if (want_warp && chunked) {
+      // pinned host copy streamed with the chunks; a device buffer per chunk
+      // buffer, as large as the largest chunk
+      const size_t hb = (size_t)L * t->scr_leaf_words * 4;
+      int64_t max_leaves = 0;
+      for (int c = 0; c < t->n_chunks; ++c)
+        max_leaves = std::max<int64_t>(max_leaves, t->chunk_leaf[c + 1] -
+                                                       t->chunk_leaf[c]);
+      const size_t db = (size_t)max_leaves * t->scr_leaf_words * 4;
+      if (host_alloc(&t->h_scr_wwords, hb, cudaHostAllocPortable) !=
+              cudaSuccess ||
+          dev_malloc(&t->d_chunk_scr[0], db) != cudaSuccess ||
+          dev_malloc(&t->d_chunk_scr[1], db) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(BKD_ENOMEM, "screen chunk buffers"));
+      }
+      fill_screen_warp(Ph, H, stride, t->h_scr_wwords, center.data(),
+                       bmax.data(), pnmax.data());
+      t->chunk_screen = true;
+    } else if (want_warp) {
       fill_screen_warp(Ph, H, stride, wwords.data(), center.data(),
                        bmax.data(), pnmax.data());
+    }
     if ((want_tc &&
          dev_malloc(&t->d_scr_words, words.size() * 2) != cudaSuccess) ||
-        (want_warp &&
+        (want_warp && !chunked &&
          dev_malloc(&t->d_scr_wwords, wwords.size() * 4) != cudaSuccess) ||
         dev_malloc(&t->d_scr_center, center.size() * 4) != cudaSuccess ||
         dev_malloc(&t->d_scr_bmax, bmax.size() * 4) != cudaSuccess ||
@@ -565,7 +602,7 @@ int build_impl(const float* P, int64_t n, int d, int height,
     if ((want_tc &&
          cudaMemcpy(t->d_scr_words, words.data(), words.size() * 2,
                     cudaMemcpyHostToDevice) != cudaSuccess) ||
-        (want_warp &&
+        (want_warp && !chunked &&
          cudaMemcpy(t->d_scr_wwords, wwords.data(), wwords.size() * 4,
                     cudaMemcpyHostToDevice) != cudaSuccess) ||
         cudaMemcpy(t->d_scr_center, center.data(), center.size() * 4,
@@ -576,7 +613,9 @@ int build_impl(const float* P, int64_t n, int d, int height,
                    cudaMemcpyHostToDevice) != cudaSuccess)
       return bail(fail(BKD_ECUDA, "upload of the screen data failed"));
     t->screen.words = t->d_scr_words;
-    t->screen.wwords = t->d_scr_wwords;
+    // (chunked: a chunk buffer stands for the layout; every launch passes
+    // the buffer of its chunk)
+    t->screen.wwords = chunked ? t->d_chunk_scr[0] : t->d_scr_wwords;
     t->screen.tiles = tiles;
     t->screen.stride = stride;
     t->screen.center = t->d_scr_center;
@@ -637,7 +676,8 @@ void reset_stats(bkd_tree* t) {
                   t->st_screen_kept = t->st_screen_pairs = t->st_screen_ms = 0;
   t->st_screen_items = t->st_screen_visits = 0;
   t->st_find_ms = t->st_bucket_ms = t->st_exact_ms = 0;
-  t->st_chunk_visits = t->st_screen_bytes = 0;
+  t->st_chunk_visits = t->st_screen_bytes = t->st_leaf_bytes = 0;
+  t->st_host_syncs = t->st_fallback_points = t->st_mapped_bytes = 0;
   t->st_screen_queued = t->st_screen_overflow = 0;
   t->ev_used = 0;
   t->find_ev.clear();
@@ -751,8 +791,8 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
     // a round that ends in the BF16 screen (the first round stays on the
     // float32 kernel: every list is still empty there) buckets its queries
     // into the screen's items
-    const bool screened =
-        !t->chunked && t->precision == 1 && round > 0 && screen_max > 0;
+    const bool screened = (!t->chunked || t->chunk_screen) &&
+                          t->precision == 1 && round > 0 && screen_max > 0;
     const int32_t* nin = dev_counts ? t->nact.p + (round & 1) : nullptr;
     int32_t* nout = t->nact.p + ((round + 1) & 1);
     cudaEvent_t f0 = t->next_event(), f1 = t->next_event();
@@ -785,9 +825,9 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   // ProcessAllBuffers of the round just bucketed (n_items < 0: the count is
   // read on the device), then the bucketed list becomes the active list
   auto process_round = [&](int n_items) -> int {
-    const bool screened =
-        !t->chunked && t->precision == 1 && round > 0 && screen_max > 0;
-    if (screened) {
+    const bool screened = (!t->chunked || t->chunk_screen) &&
+                          t->precision == 1 && round > 0 && screen_max > 0;
+    if (screened && !t->chunked) {
       // BF16 tensor-core screen + exact float32 rescoring
       cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
       if (e0) cudaEventRecord(e0, s);
@@ -902,6 +942,17 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
         if (c0) cudaEventRecord(c0, t->copy_stream);
         CU(cudaMemcpyAsync(t->d_chunk_buf[load_b], t->h_pts + off_f, bytes,
                            cudaMemcpyHostToDevice, t->copy_stream));
+        t->buf_scr[load_b] = false;
+        if (t->chunk_screen && t->precision == 1) {
+          // the chunk's screen operands travel with its points
+          const size_t sb = (size_t)(leaf_b - leaf_a) * t->scr_leaf_words * 4;
+          CU(cudaMemcpyAsync(t->d_chunk_scr[load_b],
+                             t->h_scr_wwords + (size_t)leaf_a *
+                                                   t->scr_leaf_words,
+                             sb, cudaMemcpyHostToDevice, t->copy_stream));
+          t->st_chunk_bytes += (double)sb;
+          t->buf_scr[load_b] = true;
+        }
         if (c1) cudaEventRecord(c1, t->copy_stream);
         if (c0 && c1) t->copy_ev.push_back({c0, c1});
         CU(cudaEventRecord(t->ev_copied[load_b], t->copy_stream));
@@ -916,18 +967,32 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
         if (c < 0 || work(c) == 0) continue;
         const int ilo = ci[c], ihi = ci[c + 1];
         CU(cudaStreamWaitEvent(s, t->ev_copied[b], 0));
-        const int grid = std::min(grid_max, ihi - ilo);
         cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
         if (e0) cudaEventRecord(e0, s);
-        CU(launch_leaf(D, cap, t->items.p, ilo, ihi, t->d_ctr,
-                       t->d_chunk_buf[b], t->chunk_leaf[c], nxt, t->qpad.p,
-                       t->lst_d.p, t->lst_i.p, K, grid, s));
+        if (screened) {
+          // the warp screen over the chunk in buffer b: its points and
+          // screen operands start at the chunk's first leaf
+          DevTree Dc = D;
+          Dc.pts = t->d_chunk_buf[b];
+          ScreenData sc = t->screen;
+          sc.wwords = t->d_chunk_scr[b];
+          sc.leaf0 = t->chunk_leaf[c];
+          CU(launch_screen_warp(Dc, sc, t->items.p, ilo, ihi, t->d_ctr, nxt,
+                                t->qpad.p, t->lst_d.p, t->lst_i.p, K,
+                                screen_max, s));
+        } else {
+          const int grid = std::min(grid_max, ihi - ilo);
+          CU(launch_leaf(D, cap, t->items.p, ilo, ihi, t->d_ctr,
+                         t->d_chunk_buf[b], t->chunk_leaf[c], nxt, t->qpad.p,
+                         t->lst_d.p, t->lst_i.p, K, grid, s));
+        }
         if (e1) cudaEventRecord(e1, s);
-        if (e0 && e1) t->leaf_ev.push_back({e0, e1});
+        if (e0 && e1)
+          (screened ? t->screen_ev : t->leaf_ev).push_back({e0, e1});
         CU(cudaEventRecord(t->ev_free[b], s));
         t->h_chunk_done[c] = 1;
         t->st_chunk_visits += work(c);
-        t->st_leaf_launches += 1;
+        if (!screened) t->st_leaf_launches += 1;
         t->st_launches += 1;
       }
       // which chunks this round scanned, for the next FindLeafBatch
@@ -939,6 +1004,22 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
     ++round;
     return BKD_OK;
   };
+  // a chunk left resident by a float32 call has no screen operands in its
+  // buffer yet: copy them before this call screens it
+  if (t->chunk_screen && t->precision == 1 && !t->point_chunks)
+    for (int b = 0; b < 2; ++b) {
+      const int c = t->buf_chunk[b];
+      if (c < 0 || t->buf_scr[b]) continue;
+      const int64_t leaf_a = t->chunk_leaf[c], leaf_b = t->chunk_leaf[c + 1];
+      const size_t sb = (size_t)(leaf_b - leaf_a) * t->scr_leaf_words * 4;
+      CU(cudaStreamWaitEvent(t->copy_stream, t->ev_free[b], 0));
+      CU(cudaMemcpyAsync(t->d_chunk_scr[b],
+                         t->h_scr_wwords + (size_t)leaf_a * t->scr_leaf_words,
+                         sb, cudaMemcpyHostToDevice, t->copy_stream));
+      CU(cudaEventRecord(t->ev_copied[b], t->copy_stream));
+      t->st_chunk_bytes += (double)sb;
+      t->buf_scr[b] = true;
+    }
   int rc = start_round(false);
   if (rc != BKD_OK) return rc;
   // bucketing totals of the first round (float32 kernel) and of the last
@@ -949,6 +1030,7 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
     CU(cudaMemcpyAsync(t->h_ctr, t->d_ctr, sizeof(Counters),
                        cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+    t->st_host_syncs += 1;
     if (t->h_ctr->err & kErrTimeout)
       return fail(BKD_ETIMEOUT, "a bounded device-side wait ran out");
     const int n_next = t->h_ctr->n_next;
@@ -1013,12 +1095,14 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   t->st_tail_pairs += (double)t->h_ctr->tail_pairs;
   t->st_screen_kept += (double)t->h_ctr->screen_kept;
   t->st_pairs += (double)t->h_ctr->leaf_pairs;
+  t->st_leaf_bytes += (double)t->h_ctr->leaf_bytes;
   // rounds processed = every bucketing but the last; screened rounds = all
   // processed rounds but the first
   {
     const Counters& h = *t->h_ctr;
     t->st_visits += (double)(h.rounds_visits - last_visits);
-    if (t->precision == 1 && screen_max > 0 && !t->chunked &&
+    if (t->precision == 1 && screen_max > 0 &&
+        (!t->chunked || t->chunk_screen) &&
         h.rounds_visits > first_visits + last_visits) {
       t->st_screen_visits +=
           (double)(h.rounds_visits - first_visits - last_visits);
@@ -1032,9 +1116,21 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   t->st_resorted += t->h_ctr->n_resorted;
   if (n_fb > 0) {
     CU(launch_fallback(D, n_fb, t->fb_list.p, k, K, t->qpad.p, t->lst_d.p,
-                       out_idx, out_dist, s));
+                       out_idx, out_dist, s, t->d_ctr));
     t->st_launches += 1;
+    CU(cudaMemcpyAsync(&t->h_ctr->fallback_points,
+                       &t->d_ctr->fallback_points, sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    t->st_fallback_points += (double)t->h_ctr->fallback_points;
   }
+  // chunked trees: what the tail, re-check and fallback kernels read from
+  // the mapped (pinned host) leaf structure, point coordinates counted
+  if (t->chunked)
+    t->st_mapped_bytes +=
+        4.0 * Dp *
+        ((double)t->h_ctr->tail_pairs + (double)t->h_ctr->n_resorted * k +
+         (n_fb > 0 ? (double)t->h_ctr->fallback_points : 0.0));
   cudaEvent_t x1 = t->next_event();
   if (x1) cudaEventRecord(x1, s);
   if (x0 && x1) t->exact_ev.push_back({x0, x1});
@@ -1316,6 +1412,10 @@ int bkd_get_stat(const bkd_tree* t, int key, double* value) {
     case BKD_STAT_EXACT_MS: *value = t->st_exact_ms; break;
     case BKD_STAT_CHUNK_VISITS: *value = t->st_chunk_visits; break;
     case BKD_STAT_SCREEN_BYTES: *value = t->st_screen_bytes; break;
+    case BKD_STAT_LEAF_BYTES: *value = t->st_leaf_bytes; break;
+    case BKD_STAT_HOST_SYNCS: *value = t->st_host_syncs; break;
+    case BKD_STAT_FALLBACK_POINTS: *value = t->st_fallback_points; break;
+    case BKD_STAT_MAPPED_BYTES: *value = t->st_mapped_bytes; break;
     case BKD_STAT_SCREEN_QUEUED: *value = t->st_screen_queued; break;
     case BKD_STAT_SCREEN_OVERFLOW: *value = t->st_screen_overflow; break;
     default: return fail(BKD_EINVAL, "unknown stat %d", key);

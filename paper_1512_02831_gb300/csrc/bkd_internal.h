@@ -90,6 +90,10 @@ struct Counters {
   unsigned long long rounds_run;     // rounds with at least one query
   unsigned long long screen_queued;  // pairs queued for exact rescoring
   unsigned long long screen_overflow;  // screen items whose queue overflowed
+  unsigned long long leaf_bytes;  // leaf-structure bytes the float32 leaf
+                                  // kernel staged (one pass per work item)
+  unsigned long long fallback_points;  // points the binary64 fallback
+                                       // search scanned
 };
 
 constexpr int kErrNonFinite = 1;   // a query holds a non-finite / huge value
@@ -209,6 +213,9 @@ struct ScreenData {
   int kh = 0;          // tcgen05: k-halves (screen_halves)
   int wkh = 0;         // warp kernel: k-halves (screen_halves_warp)
   int kind = 0;
+  // first leaf held by wwords (chunked trees: the chunk in a device chunk
+  // buffer; its points are then at DevTree::pts from slot leaf0 * lcap on)
+  int64_t leaf0 = 0;
   bool has(int k) const { return k == 0 ? wwords != nullptr : words != nullptr; }
   bool on() const { return has(kind); }
 };
@@ -294,9 +301,11 @@ cudaError_t launch_recheck(const DevTree& t, int64_t m, int k, int K,
                            float* out_dist, uint32_t* fb_list, Counters* ctr,
                            cudaStream_t s);
 
+// (ctr, if given: its fallback_points counts the points scanned)
 cudaError_t launch_fallback(const DevTree& t, int n_fb, const uint32_t* fb_list,
                             int k, int K, const float* qpad, const float* lst_d,
-                            int64_t* out_idx, float* out_dist, cudaStream_t s);
+                            int64_t* out_idx, float* out_dist, cudaStream_t s,
+                            Counters* ctr = nullptr);
 
 // Outlier score of Sec. 4.3 (k_outlier.cu): inv[orig[s]] = s for every
 // occupied slot; Q[r] = the point of original index i0 + r (r < m), read

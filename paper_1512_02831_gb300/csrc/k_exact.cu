@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(32)
                     int k, int K, const float* __restrict__ qpad,
                     const float* __restrict__ lst_d,
                     int64_t* __restrict__ out_idx,
-                    float* __restrict__ out_dist, Bounds bd) {
+                    float* __restrict__ out_dist, Bounds bd, Counters* ctr) {
   __shared__ double s_d[BKD_MAX_K];
   __shared__ int64_t s_i[BKD_MAX_K];
   const int lane = threadIdx.x & 31;
@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(32)
     const double seed = hi_bound(lst_d[q * K + (k - 1)], bd);
     const float seed32 = f32_bound(seed, bd);
     int cnt = 0;  // entries in the list (warp-uniform)
+    unsigned long long scanned = 0;  // points of the leaves scanned (lane 0)
     int node = kStart;
     uint32_t mask = 0;
     for (;;) {
@@ -196,6 +197,7 @@ __global__ void __launch_bounds__(32)
       const int leaf = node - first_leaf;
       const int np = t.leaf_cnt[leaf];
       const uint64_t base = (uint64_t)leaf * (uint64_t)t.lcap;
+      if (lane == 0) scanned += (unsigned long long)np;
       for (int u0 = 0; u0 < np; u0 += 32) {
         const int u = u0 + lane;
         double dv = 0.0;
@@ -232,6 +234,7 @@ __global__ void __launch_bounds__(32)
       out_idx[q * k + j] = s_i[j];
       out_dist[q * k + j] = (float)s_d[j];
     }
+    if (ctr && lane == 0 && scanned) atomicAdd(&ctr->fallback_points, scanned);
     __syncwarp();
   }
 }
@@ -263,14 +266,15 @@ cudaError_t launch_recheck(const DevTree& t, int64_t m, int k, int K,
 
 cudaError_t launch_fallback(const DevTree& t, int n_fb, const uint32_t* fb_list,
                             int k, int K, const float* qpad, const float* lst_d,
-                            int64_t* out_idx, float* out_dist, cudaStream_t s) {
+                            int64_t* out_idx, float* out_dist, cudaStream_t s,
+                            Counters* ctr) {
   if (n_fb == 0) return cudaSuccess;
   const int grid = n_fb < 65536 ? n_fb : 65536;
 #define BKD_FB_CASE(DIM)                                                  \
   case DIM:                                                               \
     fallback_kernel<DIM><<<grid, 32, 0, s>>>(t, n_fb, fb_list, k, K, qpad, \
                                              lst_d, out_idx, out_dist,     \
-                                             bounds_for(t.d));             \
+                                             bounds_for(t.d), ctr);        \
     return cudaGetLastError();
   switch (t.Dp) { BKD_DIMS(BKD_FB_CASE) default: break; }
 #undef BKD_FB_CASE

@@ -1,6 +1,6 @@
 // k_leaf.cuh -- ProcessAllBuffers: leaf brute force with the k-best merge
-// fused in (Algorithm 1; Sec. 3.2 "each thread compares a particular query
-// with all reference points stored in the associated leaf").
+// fused in (Algorithm 1; Sec. 3.2: every buffered query of a leaf is
+// compared with every reference point of that leaf).
 //
 // One 64-thread CTA takes one work item at a time: up to 64 buffered queries
 // of one leaf, one query per thread.  Each thread holds its query's
@@ -238,11 +238,14 @@ __global__ void __launch_bounds__(kPipeThreads)
     const int2 qr = quad_range(part, w.leaf, leaf_cnt[w.leaf]);
     const int nq = qr.y;
     const int nseg = (qr.y - qr.x + kPipeSegQuads - 1) / kPipeSegQuads;
-    if (tid == 0)
+    if (tid == 0) {
       atomicAdd(&ctr->leaf_pairs,
                 (unsigned long long)w.count *
                     (unsigned long long)min(leaf_cnt[w.leaf] - 4 * qr.x,
                                             4 * (qr.y - qr.x)));
+      atomicAdd(&ctr->leaf_bytes,
+                (unsigned long long)(qr.y - qr.x) * (16u * D));
+    }
     const bool on = tid < w.count;
     uint32_t q = 0;
     uint64_t qq[D];

@@ -1,7 +1,7 @@
 // k_outlier.cu -- the proximity-based outlier score of Sec. 4.3: every
 // reference point is ranked by its average (Euclidean) distance to its k
-// nearest neighbours among the other reference points -- the "all nearest
-// neighbours" problem, a query set equal to the reference set.
+// nearest neighbours among the other reference points -- the all-nearest-
+// neighbours problem, a query set equal to the reference set.
 //
 // The queries are the tree's own points, read back from the leaf structure
 // (quads + orig) in original order; each is searched with k + 1 neighbours

@@ -1,4 +1,5 @@
-// k_screen.cu -- ProcessAllBuffers with a BF16 tensor-core screen (tcgen05).
+// k_screen.cu -- ProcessAllBuffers with a BF16 tensor-core screen (tcgen05;
+// the screen kernel selected by BKD_OPT_SCREEN_KERNEL = 1).
 //
 // Same candidate lists as the float32 leaf kernel (every point whose float32
 // distance could still enter a query's list is scored exactly), but most
@@ -53,11 +54,11 @@
 // are the same.
 //
 // A screened round runs three kernels:
-//   prep_kernel     one CTA per work item (one leaf, <= 128 of its buffered
-//                   queries): the item's query operand tile (v^, -1/2, -1/2,
-//                   threshold parts) written to HBM;
-//   screen_kernel   persistent CTAs (two per SM), items taken from a
-//                   launch-wide counter:
+//   tc_prep_kernel      one CTA per work item (one leaf, <= 128 of its
+//                       buffered queries): the item's query operand tile
+//                       (v^, -1/2, -1/2, threshold parts) written to HBM;
+//   tc_screen_kernel    persistent CTAs (two per SM), items taken from a
+//                       launch-wide counter:
 //     warp 0 (one thread)  claims items, publishes them in a small ring, and
 //                          streams the query operand and the leaf's 128-point
 //                          operand tiles (bulk copies, 4 KB per k-half) into
@@ -77,10 +78,10 @@
 //                          hand the buffer back, and append the rare (point,
 //                          group) pairs with a positive value to the item's
 //                          survivor segment in HBM;
-//   rescore_kernel  scores the survivors exactly (float32 chain of the leaf
-//                   kernel) against the 16 queries of their group and
-//                   inserts them into the lists; an item whose segment
-//                   overflowed goes to the float32 leaf kernel instead.
+//   tc_rescore_kernel   scores the survivors exactly (float32 chain of the
+//                       leaf kernel) against the 16 queries of their group
+//                       and inserts them into the lists; an item whose
+//                       segment overflowed goes to the float32 leaf kernel.
 // Every wait is bounded: a wait that runs out sets kErrTimeout, every role
 // then leaves, copies and MMAs in flight are waited for (bounded), and the
 // tensor memory is released.
@@ -306,7 +307,7 @@ __device__ __forceinline__ uint16_t bf16_bits(float f) {
 // read from the device's count of the round.
 template <int KH>
 __global__ void __launch_bounds__(128)
-    prep_kernel(DevTree t, ScreenData sc, const Item* __restrict__ items,
+    tc_prep_kernel(DevTree t, ScreenData sc, const Item* __restrict__ items,
                 const Counters* __restrict__ ctr,
                 const uint32_t* __restrict__ act,
                 const float* __restrict__ qpad,
@@ -442,7 +443,7 @@ constexpr int kSegCap = kEpiWarps * kWarpCap;  // entries per item
 
 template <int KH>
 __global__ void __launch_bounds__(kThreads, 2)
-    screen_kernel(DevTree t, ScreenData sc, const Item* __restrict__ items,
+    tc_screen_kernel(DevTree t, ScreenData sc, const Item* __restrict__ items,
                   int item_lo, int item_hi, Counters* ctr,
                   const uint8_t* __restrict__ bop_g,
                   uint32_t* __restrict__ seg, int32_t* __restrict__ seg_cnt) {
@@ -788,7 +789,7 @@ constexpr int kRescoreWarps = 8;
 
 template <int D>
 __global__ void __launch_bounds__(32 * kRescoreWarps)
-    rescore_kernel(DevTree t, const Item* __restrict__ items,
+    tc_rescore_kernel(DevTree t, const Item* __restrict__ items,
                    Counters* ctr, const uint32_t* __restrict__ act,
                    const float* __restrict__ qpad, float* __restrict__ lst_d,
                    uint32_t* __restrict__ lst_i, int K,
@@ -919,7 +920,7 @@ RescoreFn rescore_for(int dp) {
   switch (dp) {
 #define BKD_RESCORE_CASE(D) \
   case D:                   \
-    return rescore_kernel<D>;
+    return tc_rescore_kernel<D>;
     BKD_DIMS(BKD_RESCORE_CASE)
 #undef BKD_RESCORE_CASE
     default: return nullptr;
@@ -928,9 +929,9 @@ RescoreFn rescore_for(int dp) {
 
 const void* screen_kernel_for(int kh) {
   switch (kh) {
-    case 1: return (const void*)screen_kernel<1>;
-    case 2: return (const void*)screen_kernel<2>;
-    case 3: return (const void*)screen_kernel<3>;
+    case 1: return (const void*)tc_screen_kernel<1>;
+    case 2: return (const void*)tc_screen_kernel<2>;
+    case 3: return (const void*)tc_screen_kernel<3>;
     default: return nullptr;
   }
 }
@@ -1093,9 +1094,9 @@ cudaError_t launch_screen(const DevTree& t, const ScreenData& sd,
                                   2 * sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
 #define BKD_SCREEN_KH(KH)                                                    \
-  prep_kernel<KH><<<aux, 128, 0, s>>>(t, sd, items, ctr, act, qpad, lst_d,   \
+  tc_prep_kernel<KH><<<aux, 128, 0, s>>>(t, sd, items, ctr, act, qpad, lst_d,   \
                                       K, w.bop);                             \
-  screen_kernel<KH><<<grid, kThreads, smem, s>>>(t, sd, items, 0, n_items,   \
+  tc_screen_kernel<KH><<<grid, kThreads, smem, s>>>(t, sd, items, 0, n_items,   \
                                                  ctr, w.bop, w.seg,          \
                                                  w.seg_cnt);
   switch (sd.kh) {

@@ -191,14 +191,15 @@ __device__ __noinline__ void drain(const DevTree& t, int leaf,
                                    const float* __restrict__ lst_d,
                                    const uint32_t* __restrict__ lst_i, int K,
                                    const WarpSmem& ws, int lane, int nq,
-                                   int ncol) {
+                                   int ncol, uint32_t pofs) {
   __syncwarp();
   const uint32_t slot0 = (uint32_t)((int64_t)leaf * t.lcap);
   for (int e = lane; e < nq; e += 32) {
     const uint32_t en = ws.queue[e];
     const uint32_t q = ws.qid[en & 31u];
+    // (t.pts from slot pofs on: a chunk buffer on chunked trees)
     ws.qd[e] = exact_dist(qpad + (size_t)q * t.Dp, t.pts, t.Dp,
-                          slot0 + (en >> 5));
+                          slot0 + (en >> 5) - pofs);
   }
   __syncwarp();
   if (lane < ncol) {
@@ -330,7 +331,7 @@ __device__ __forceinline__ void scan_leaf(
   const int64_t st = sc.stride;
   const int64_t hstep = st * 2;  // uint4 per k-half of a leaf
   const uint4* wb = reinterpret_cast<const uint4*>(sc.wwords) +
-                    (size_t)leaf * KH * hstep + g * 4 + tq;
+                    (size_t)(leaf - sc.leaf0) * KH * hstep + g * 4 + tq;
   const int nsup = (npt + 31) >> 5;
   constexpr int R = ring_depth(KH);
 #pragma unroll
@@ -400,7 +401,8 @@ __device__ __forceinline__ void scan_leaf(
         const unsigned m = __ballot_sync(full, kk);
         const int n = __popc(m);
         if (nq + n > kQueue) {
-          drain(t, leaf, qpad, lst_d, lst_i, K, ws, lane, nq, ncol);
+          drain(t, leaf, qpad, lst_d, lst_i, K, ws, lane, nq, ncol,
+                (uint32_t)(sc.leaf0 * t.lcap));
           nq = 0;
         }
         if (kk)
@@ -414,7 +416,9 @@ __device__ __forceinline__ void scan_leaf(
     }
   }
   cp_async_wait<0>();  // only empty groups remain; the ring is free
-  if (nq) drain(t, leaf, qpad, lst_d, lst_i, K, ws, lane, nq, ncol);
+  if (nq)
+    drain(t, leaf, qpad, lst_d, lst_i, K, ws, lane, nq, ncol,
+          (uint32_t)(sc.leaf0 * t.lcap));
 }
 
 // Lane c < w.count: query id, current bound, bf16 offsets (B record) and
@@ -480,7 +484,7 @@ __device__ __forceinline__ void setup_column(
 
 template <int KH>
 __global__ void __launch_bounds__(kScrThreads, KH == 1 ? 3 : 2)
-    screen_kernel(DevTree t, ScreenData sc, const Item* __restrict__ items,
+    warp_screen_kernel(DevTree t, ScreenData sc, const Item* __restrict__ items,
                   int item_lo, int item_hi, Counters* ctr,
                   const uint32_t* __restrict__ act,
                   const float* __restrict__ qpad, float* __restrict__ lst_d,
@@ -544,9 +548,9 @@ size_t screen_smem(int kh, int K) {
 
 const void* screen_kernel_for(int kh) {
   switch (kh) {
-    case 1: return (const void*)screen_kernel<1>;
-    case 2: return (const void*)screen_kernel<2>;
-    case 3: return (const void*)screen_kernel<3>;
+    case 1: return (const void*)warp_screen_kernel<1>;
+    case 2: return (const void*)warp_screen_kernel<2>;
+    case 3: return (const void*)warp_screen_kernel<3>;
     default: return nullptr;
   }
 }
@@ -588,15 +592,15 @@ cudaError_t launch_screen_warp(const DevTree& t, const ScreenData& sd,
   if (e != cudaSuccess) return e;
   switch (sd.wkh) {
     case 1:
-      screen_kernel<1><<<grid, kScrThreads, smem, s>>>(
+      warp_screen_kernel<1><<<grid, kScrThreads, smem, s>>>(
           t, sd, items, item_lo, item_hi, ctr, act, qpad, lst_d, lst_i, K);
       break;
     case 2:
-      screen_kernel<2><<<grid, kScrThreads, smem, s>>>(
+      warp_screen_kernel<2><<<grid, kScrThreads, smem, s>>>(
           t, sd, items, item_lo, item_hi, ctr, act, qpad, lst_d, lst_i, K);
       break;
     case 3:
-      screen_kernel<3><<<grid, kScrThreads, smem, s>>>(
+      warp_screen_kernel<3><<<grid, kScrThreads, smem, s>>>(
           t, sd, items, item_lo, item_hi, ctr, act, qpad, lst_d, lst_i, K);
       break;
     default:

@@ -1,6 +1,6 @@
 // k_traverse.cu -- query initialisation and FindLeafBatch (Algorithm 1).
 //
-// FindLeafBatch continues each query's "implicit tree traversal" (Sec. 2.4)
+// FindLeafBatch continues each query's implicit tree traversal (Sec. 2.4)
 // to the next leaf it has to visit, or reports -1 once the traversal has
 // reached the root twice.  The traversal is the classical k-d tree search of
 // Sec. 2.3: walk down to the cell containing q; on the way back up, visit the

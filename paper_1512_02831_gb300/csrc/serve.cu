@@ -14,11 +14,14 @@
 //   complete  a batch whose queries have all finished gets the binary64
 //             re-check and fallback and its results, and frees its slots.
 //
-// Every query carries a list of k_max + 1 entries.  After the rounds a
-// query's list holds its k_max + 1 smallest float32 distances, so its
-// first k + 1 entries are the k + 1 smallest: the re-check and fallback of a
-// batch with k <= k_max see exactly what a bkd_query with that k sees, and
-// the results are the same (both equal the binary64 definition).
+// Batches are routed by k to one of up to three class servers (lists of at
+// most 12, 32 or 64 entries), each a complete server of its own (slots,
+// active list, rounds).  Every query of a class carries a list of the
+// class's k_max + 1 entries.  After the rounds a query's list holds its
+// k_max + 1 smallest float32 distances, so its first k + 1 entries are the
+// k + 1 smallest: the re-check and fallback of a batch with k <= k_max see
+// exactly what a bkd_query with that k sees, and the results are the same
+// (both equal the binary64 definition).
 //
 // Queries admitted in a step take their first leaf in a round of their own
 // on the float32 leaf kernel (their lists are still empty, so the BF16
@@ -96,7 +99,7 @@ cudaError_t dev_alloc(T** p, int64_t n) {
 
 }  // namespace
 
-struct bkd_server {
+struct ClassServer {
   bkd_tree* tree = nullptr;
   TreeView v{};  // refreshed every step (stream, precision option)
   int kmax = 0, K = 0, cap = 0;
@@ -130,7 +133,7 @@ struct bkd_server {
   std::map<int64_t, std::unique_ptr<Batch>> batches;
   int64_t next_ticket = 1;
 
-  ~bkd_server() {
+  ~ClassServer() {
     cudaFree(qstage);
     cudaFree(qpad);
     cudaFree(lst_d);
@@ -179,7 +182,7 @@ struct bkd_server {
 
 // Copies a batch's queries into its slots and appends them to the active
 // list; a non-finite query fails the batch (ok = false).
-int bkd_server::admit(Batch* b, int64_t s0, int bid, bool* ok) {
+int ClassServer::admit(Batch* b, int64_t s0, int bid, bool* ok) {
   const DevTree& D = v.dev;
   cudaStream_t s = v.stream;
   const int64_t m = b->m;
@@ -204,7 +207,7 @@ int bkd_server::admit(Batch* b, int64_t s0, int bid, bool* ok) {
 // [n_old, n_act)): FindLeafBatch, bucketing and the float32 leaf kernel over
 // them alone.  Their processed list goes to the scratch `nxt`; they stay in
 // the active list for the shared round.
-int bkd_server::first_round(int n_old) {
+int ClassServer::first_round(int n_old) {
   const DevTree& D = v.dev;
   cudaStream_t s = v.stream;
   const int64_t L = v.n_leaves;
@@ -228,7 +231,7 @@ int bkd_server::first_round(int n_old) {
 }
 
 // One LazySearch round over the whole active list.
-int bkd_server::round() {
+int ClassServer::round() {
   const DevTree& D = v.dev;
   cudaStream_t s = v.stream;
   const int64_t L = v.n_leaves;
@@ -277,7 +280,7 @@ int bkd_server::round() {
 }
 
 // Re-check, fallback and results of a batch whose queries all finished.
-int bkd_server::complete(Batch* b) {
+int ClassServer::complete(Batch* b) {
   const DevTree& D = v.dev;
   cudaStream_t s = v.stream;
   const int64_t s0 = b->s0, m = b->m;
@@ -307,14 +310,12 @@ int bkd_server::complete(Batch* b) {
   return BKD_OK;
 }
 
-extern "C" {
+namespace {
 
-int bkd_serve_open(bkd_tree* t, int k_max, int64_t max_queries,
-                   bkd_server** out) {
-  set_error(BKD_OK, "");
-  if (!out) return set_error(BKD_EINVAL, "out is NULL");
+// A server of one list-capacity class (every query carries k_max + 1
+// list entries).
+int cs_open(bkd_tree* t, int k_max, int64_t max_queries, ClassServer** out) {
   *out = nullptr;
-  if (!t) return set_error(BKD_EINVAL, "tree is NULL");
   const TreeView v = view_of(t);
   if (v.chunked)
     return set_error(BKD_EUNSUPPORTED,
@@ -327,7 +328,7 @@ int bkd_serve_open(bkd_tree* t, int k_max, int64_t max_queries,
   if (max_queries < 1 || max_queries >= ((int64_t)1 << 31))
     return set_error(BKD_EINVAL, "max_queries must be in [1, 2^31)");
   DeviceScope guard(v.device);
-  auto sv = std::make_unique<bkd_server>();
+  auto sv = std::make_unique<ClassServer>();
   sv->tree = t;
   sv->v = v;
   sv->kmax = k_max;
@@ -388,10 +389,8 @@ int bkd_serve_open(bkd_tree* t, int k_max, int64_t max_queries,
   return BKD_OK;
 }
 
-int bkd_serve_submit(bkd_server* s, const float* Q, int64_t m, int k,
-                     int64_t* out_idx, float* out_dist, int64_t* ticket) {
-  set_error(BKD_OK, "");
-  if (!s || !ticket) return set_error(BKD_EINVAL, "server / ticket is NULL");
+int cs_submit(ClassServer* s, const float* Q, int64_t m, int k,
+              int64_t* out_idx, float* out_dist, int64_t* ticket) {
   if (m < 0 || m > s->max_q)
     return set_error(BKD_EINVAL, "m = %lld outside [0, max_queries = %lld]",
                      (long long)m, (long long)s->max_q);
@@ -427,9 +426,7 @@ int bkd_serve_submit(bkd_server* s, const float* Q, int64_t m, int k,
   return BKD_OK;
 }
 
-int bkd_serve_step(bkd_server* s, int64_t* pending) {
-  set_error(BKD_OK, "");
-  if (!s) return set_error(BKD_EINVAL, "server is NULL");
+int cs_step(ClassServer* s, int64_t* pending) {
   s->v = view_of(s->tree);
   DeviceScope guard(s->v.device);
   // admit, first come first served
@@ -483,9 +480,7 @@ int bkd_serve_step(bkd_server* s, int64_t* pending) {
   return BKD_OK;
 }
 
-int bkd_serve_status(bkd_server* s, int64_t ticket, int* status) {
-  set_error(BKD_OK, "");
-  if (!s || !status) return set_error(BKD_EINVAL, "server / status is NULL");
+int cs_status(ClassServer* s, int64_t ticket, int* status) {
   auto it = s->batches.find(ticket);
   if (it == s->batches.end())
     return set_error(BKD_EINVAL, "unknown ticket %lld", (long long)ticket);
@@ -495,10 +490,97 @@ int bkd_serve_status(bkd_server* s, int64_t ticket, int* status) {
   return BKD_OK;
 }
 
+}  // namespace
+
+// The public server: one class server per list capacity (k + 1 <= 12, 32,
+// 64, up to k_max + 1), each batch routed to the smallest class its k fits,
+// so that a k = 1 batch does not carry (and scan with) a k_max + 1 list.
+// A ticket is the class server's ticket times kClasses plus the class.
+constexpr int kClasses = 3;
+constexpr int kClassCap[kClasses] = {12, 32, 64};
+
+struct bkd_server {
+  std::vector<std::unique_ptr<ClassServer>> cls;
+  std::vector<int> kmax;  // largest k of each class
+  int device = 0;
+};
+
+extern "C" {
+
+int bkd_serve_open(bkd_tree* t, int k_max, int64_t max_queries,
+                   bkd_server** out) {
+  set_error(BKD_OK, "");
+  if (!out) return set_error(BKD_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!t) return set_error(BKD_EINVAL, "tree is NULL");
+  if (k_max < 1)
+    return set_error(BKD_EINVAL, "k_max must be in [1, n] (got %d)", k_max);
+  if (k_max > BKD_MAX_K)
+    return set_error(BKD_EUNSUPPORTED, "k_max = %d exceeds BKD_MAX_K = %d",
+                     k_max, BKD_MAX_K);
+  auto sv = std::make_unique<bkd_server>();
+  sv->device = view_of(t).device;
+  int lo = 0;
+  for (int c = 0; c < kClasses && lo < k_max; ++c) {
+    const int kc = std::min(kClassCap[c] - 1, k_max);
+    ClassServer* cs = nullptr;
+    const int rc = cs_open(t, kc, max_queries, &cs);
+    if (rc != BKD_OK) {
+      delete cs;
+      return rc;
+    }
+    sv->cls.emplace_back(cs);
+    sv->kmax.push_back(kc);
+    lo = kc;
+  }
+  *out = sv.release();
+  return BKD_OK;
+}
+
+int bkd_serve_submit(bkd_server* s, const float* Q, int64_t m, int k,
+                     int64_t* out_idx, float* out_dist, int64_t* ticket) {
+  set_error(BKD_OK, "");
+  if (!s || !ticket) return set_error(BKD_EINVAL, "server / ticket is NULL");
+  const int kmax = s->kmax.empty() ? 0 : s->kmax.back();
+  if (k < 1 || k > kmax)
+    return set_error(BKD_EINVAL, "k = %d outside [1, k_max = %d]", k, kmax);
+  int c = 0;
+  while (k > s->kmax[c]) ++c;
+  int64_t inner = 0;
+  const int rc = cs_submit(s->cls[c].get(), Q, m, k, out_idx, out_dist,
+                           &inner);
+  if (rc != BKD_OK) return rc;
+  *ticket = inner * kClasses + c;
+  return BKD_OK;
+}
+
+int bkd_serve_step(bkd_server* s, int64_t* pending) {
+  set_error(BKD_OK, "");
+  if (!s) return set_error(BKD_EINVAL, "server is NULL");
+  int64_t total = 0;
+  for (auto& cs : s->cls) {
+    int64_t p = 0;
+    const int rc = cs_step(cs.get(), &p);
+    if (rc != BKD_OK) return rc;
+    total += p;
+  }
+  if (pending) *pending = total;
+  return BKD_OK;
+}
+
+int bkd_serve_status(bkd_server* s, int64_t ticket, int* status) {
+  set_error(BKD_OK, "");
+  if (!s || !status) return set_error(BKD_EINVAL, "server / status is NULL");
+  const int64_t c = ticket % kClasses;
+  if (ticket < kClasses || c >= (int64_t)s->cls.size())
+    return set_error(BKD_EINVAL, "unknown ticket %lld", (long long)ticket);
+  return cs_status(s->cls[c].get(), ticket / kClasses, status);
+}
+
 void bkd_serve_close(bkd_server* s) {
   if (!s) return;
-  DeviceScope guard(s->v.device);
-  cudaStreamSynchronize(s->v.stream);
+  DeviceScope guard(s->device);
+  for (auto& cs : s->cls) cudaStreamSynchronize(cs->v.stream);
   delete s;
 }
 

@@ -177,6 +177,41 @@ def test_chunked_mode_is_bit_identical(chunks):
           rows=np.arange(512))
 
 
+@pytest.mark.parametrize("chunks", [1, 2, 3, 10])
+def test_bf16_screen_in_chunked_mode_is_bit_identical(chunks):
+    """The warp screen on a chunked tree: each chunk's screen operands are
+    copied with its points and the screen runs on the chunk buffers; the
+    result equals the resident float32 path, and the copies include the
+    screen operands."""
+    w = workloads.scaled(workloads.MIXTURE_64M, 1 << 17, 8000, 9)
+    P, Q = w.points(), w.queries()
+    tree = bkd.bkd_build(P, w.height)
+    i0, d0 = bkd.bkd_query(tree, Q, w.k)
+    bkd.bkd_free(tree)
+    tree = bkd.bkd_build(P, w.height, precision=1, chunks=chunks,
+                         tail_queries=0)
+    try:
+        # float32 first: the chunks it leaves resident carry no screen
+        # operands yet, the screened call must bring them in
+        bkd.bkd_set_option(tree, "precision", 0)
+        i2, d2 = bkd.bkd_query(tree, Q, w.k)
+        st0 = {s: bkd.bkd_get_stat(tree, s) for s in bkd.STATS}
+        bkd.bkd_set_option(tree, "precision", 1)
+        i1, d1 = bkd.bkd_query(tree, Q, w.k)
+        st = {s: bkd.bkd_get_stat(tree, s) for s in bkd.STATS}
+    finally:
+        bkd.bkd_free(tree)
+    assert np.array_equal(i0, i1) and np.array_equal(d0, d1)
+    assert np.array_equal(i0, i2) and np.array_equal(d0, d2)
+    assert st["screen_pairs"] > 0 and st0["screen_pairs"] == 0
+    assert st["screen_kept"] < 0.5 * st["screen_pairs"]
+    # the screen operands (32 B per point and k-half) travel with the points
+    # (N = 1: the single chunk stays resident, only its operands are copied)
+    assert st["chunk_bytes"] > 0
+    check(P, Q, w.k, i1, d1, oracle.brute_knn(P, Q[:500], w.k),
+          rows=np.arange(500))
+
+
 @pytest.mark.parametrize("chunks", [2, 3, 7])
 def test_point_split_chunks_are_bit_identical(chunks):
     """The paper's point chunks (Sec. 3.2: positions ceil(j n / N) .. of the
@@ -414,9 +449,11 @@ def test_bf16_screen_option_errors():
     with pytest.raises(bkd.BkdError) as e:
         bkd.bkd_build(P, 4, precision=1, screen_kernel=3)
     assert e.value.code == bkd.BKD_EINVAL
-    with pytest.raises(bkd.BkdError) as e:
-        bkd.bkd_build(P, 4, precision=1, chunks=2)
-    assert e.value.code == bkd.BKD_EUNSUPPORTED
+    # chunked trees: the screen needs leaf chunks and the warp kernel
+    for opts in ({"point_chunks": 1}, {"screen_kernel": 1}):
+        with pytest.raises(bkd.BkdError) as e:
+            bkd.bkd_build(P, 4, precision=1, chunks=2, **opts)
+        assert e.value.code == bkd.BKD_EUNSUPPORTED
 
 
 def test_d27_k50_duplicates_workload():

@@ -146,6 +146,11 @@ UNIFORM_64K = Workload("uniform n=65536 m=16384 d=10 k=10 h=8", 65536, 16384,
                        10, 10, 8, "uniform")
 MIXTURE_64M = Workload("mixture32 n=2^26 m=2^24 d=10 k=10 h=16", 1 << 26,
                        1 << 24, 10, 10, 16, "mixture")
+# the serving workload: the bench distribution at n = 2^30 (h = 20, leaves
+# of 1,024 points, 43 GB of points), a pool of 2^24 queries that serving
+# batches are sliced from
+MIXTURE_1G = Workload("mixture32 n=2^30 m=2^24 d=10 k=10 h=20", 1 << 30,
+                      1 << 24, 10, 10, 20, "mixture")
 MIXTURE_D27 = Workload("mixture64+1%dup n=2^28 m=2^25 d=27 k=50 h=18", 1 << 28,
                        1 << 25, 27, 50, 18, "mixture", components=64,
                        sigma_lo=0.01, sigma_hi=0.3, duplicates=0.01)
