@@ -77,12 +77,17 @@ def args_():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--latency-seconds", type=float, default=4.0,
                     help="time budget of the per-batch latency sample")
-    ap.add_argument("--serving-seconds", type=float, default=5.0,
+    ap.add_argument("--serving-seconds", type=float, default=10.0,
                     help="length of each serving sample (0: none)")
     ap.add_argument("--serving-rates", type=float, nargs="*",
                     default=[1000.0, 10000.0],
                     help="Poisson arrival rates (batches/s) of the serving "
                          "samples")
+    ap.add_argument("--serving-slots", type=int, default=1 << 22,
+                    help="query slots per list class of the server")
+    ap.add_argument("--serving-backlog", type=int, default=1 << 23,
+                    help="unfinished submitted queries above which an "
+                         "arriving batch is rejected")
     ap.add_argument("--modes", default="fp32,warp,tcgen05",
                     help="leaf scorings timed: fp32, warp (BF16 screen, "
                          "warp kernel), tcgen05 (BF16 screen, tcgen05 "
@@ -94,6 +99,11 @@ def args_():
     ap.add_argument("--serving-only", action="store_true",
                     help="build the workload's tree and run only the "
                          "serving samples (one JSON line)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="run the autotuner (paper_1512_02831_gb300.tune) on "
+                         "the workload's tree and print its report")
+    ap.add_argument("--autotune-queries", type=int, default=1 << 20,
+                    help="query sample the autotuner times")
     ap.add_argument("--streamer", action="store_true",
                     help="measure the chunk streamer (bigger mode) instead")
     ap.add_argument("--streamer-n", type=int, default=0,
@@ -107,6 +117,11 @@ def args_():
                     help="comma-separated subset of resident, chunks=N, "
                          "point_chunks=N (default: resident unless "
                          "--streamer-n, chunks=1,3,10, point_chunks=3,10)")
+    ap.add_argument("--streamer-precision", type=int, default=1,
+                    choices=[0, 1],
+                    help="leaf scoring of the streamer modes: 1 (default) "
+                         "the BF16 warp screen (point-chunk modes, which "
+                         "cannot screen, run float32), 0 float32")
     ap.add_argument("--streamer-oracle-rows", type=int, default=32,
                     help="queries of the streamer's oracle sample (its "
                          "cpu_baseline and parity rows; 0: none)")
@@ -486,7 +501,9 @@ def run_ours(a, w, rank, world, local_rank):
     if a.serving_only:
         del P
         # the serving samples alone (the resident tree of the workload)
-        serving = [serving_sample(bkd, tree, Q, a.serving_seconds, r)
+        serving = [serving_sample(bkd, tree, Q, a.serving_seconds, r,
+                                  slots=a.serving_slots,
+                                  backlog=a.serving_backlog)
                    for r in a.serving_rates]
         bkd.bkd_free(tree)
         if rank == 0:
@@ -582,7 +599,9 @@ def run_ours(a, w, rank, world, local_rank):
     # [1, 2^20], k in {1, 10, 50}) through the same public call with pinned
     # host buffers, one after the other on the resident tree
     lat = latency_sample(bkd, tree, Q, a.latency_seconds, barrier)
-    serving = [serving_sample(bkd, tree, Q, a.serving_seconds, r)
+    serving = [serving_sample(bkd, tree, Q, a.serving_seconds, r,
+                              slots=a.serving_slots,
+                              backlog=a.serving_backlog)
                for r in a.serving_rates] if a.serving_seconds > 0 else None
 
     # rooflines: the float32 leaf kernel (from the float32 run) and the BF16
@@ -601,6 +620,7 @@ def run_ours(a, w, rank, world, local_rank):
         "traffic": leaf_traffic_per_launch(a0, a0["leaf_launches"]),
         "algorithmic_bytes_per_launch": (a0["leaf_bytes"]
                                          / max(a0["leaf_launches"], 1)),
+        "staged_bytes_per_step": a0["leaf_bytes"] / a.steps,
         "basis": (f"FP32 pipe operations: 2*d = {2 * d} per scored (query, "
                   f"point) pair (d subtractions + d multiply-adds); peak = "
                   f"128 FP32 lanes x {sm_count} SMs x {sm_max:.0f} MHz "
@@ -660,6 +680,7 @@ def run_ours(a, w, rank, world, local_rank):
                       "ProcessAllBuffers on its stream; peak = measured HBM "
                       "copy bandwidth, 'of measured'"),
             "bytes_per_step": scr_bytes / a.steps,
+            "streamed_operand_bytes_per_step": a1["screen_bytes"] / a.steps,
             "tensor_view": tensor_view,
             "screen_share_of_step": scr_s / (runs[run]["ms"] / 1000.0),
             "pairs_per_s": pairs_s,
@@ -822,11 +843,13 @@ def run_streamer(a):
         modes += [(f"point_chunks={c}", {"chunks": c, "point_chunks": 1})
                   for c in (3, 10)]
     for name, opts in modes:
+        if a.streamer_precision and not opts.get("point_chunks"):
+            opts = dict(opts, precision=1)
         t0 = time.perf_counter()
         tree = bkd.bkd_build(P, w.height, **opts)
         build_s = time.perf_counter() - t0
-        if not a.streamer_n:
-            bkd.bkd_query(tree, Qd, k)  # warm-up
+        if w.n <= (1 << 27):
+            bkd.bkd_query(tree, Qd, k)  # warm-up (skipped for huge trees)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         idx, dist = bkd.bkd_query(tree, Qd, k)
@@ -844,6 +867,7 @@ def run_streamer(a):
                if st["copy_ms"] > 0 else None)
         out["modes"][name] = {
             "chunked": shape["chunked"], "chunks": shape["chunks"],
+            "precision": opts.get("precision", 0),
             "queries_per_s": m / dt, "ms": dt * 1e3, "build_s": build_s,
             "rounds": st["rounds"],
             "copied_gb": st["chunk_bytes"] / 1e9,
@@ -887,6 +911,39 @@ def run_streamer(a):
     print(json.dumps(out), flush=True)
 
 
+def run_autotune(a, w):
+    """The autotuner's search on the workload's tree (both screen layouts):
+    every candidate's timing (best of 2 after a warm-up, CUDA-synchronous
+    wall time of bkd_query on a device-resident query sample), the setting
+    it keeps, and that setting's result checked against the default's."""
+    import torch
+    import paper_1512_02831_gb300 as bkd
+    from paper_1512_02831_gb300 import tune
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    P = w.points()
+    Q = w.queries(min(w.m, a.autotune_queries))
+    tree = bkd.bkd_build(P, w.height, precision=1, screen_kernel=2)
+    Qd = torch.from_numpy(Q).to(dev)
+    base = bkd.bkd_query(tree, Qd, w.k)
+    rep = tune.autotune(tree, Qd, w.k)
+    got = bkd.bkd_query(tree, Qd, w.k)
+    same = bool(torch.equal(base[0], got[0]) and torch.equal(base[1], got[1]))
+    default = {"precision": 1, "screen_kernel": 0, "tail_queries": -1,
+               "screen_tile": 32, "round_batch": 0, "screen_ctas": 0}
+    dsec = next((t for o, t in rep["timings"] if o == default), None)
+    bkd.bkd_free(tree)
+    print(json.dumps({"metric": "autotune", "workload": w.describe(),
+                      "queries": int(Q.shape[0]), "best": rep["best"],
+                      "best_seconds": rep["best_seconds"],
+                      "default_seconds": dsec,
+                      "best_queries_per_s": Q.shape[0] / rep["best_seconds"],
+                      "calls": rep["calls"],
+                      "identical_to_default_options": same,
+                      "timings": [[o, t] for o, t in rep["timings"]]}),
+          flush=True)
+
+
 def main():
     a = args_()
     w = WORKLOADS[a.workload]
@@ -900,6 +957,10 @@ def main():
     if a.streamer:
         if rank == 0:
             run_streamer(a)
+        return
+    if a.autotune:
+        if rank == 0:
+            run_autotune(a, w)
         return
     run_ours(a, w, rank, world, local_rank)
 

@@ -116,8 +116,8 @@ enum bkd_option {
    * switched */
   BKD_OPT_SCREEN_TILE = 8,
   /* LazySearch rounds queued on a resident tree before the host looks at
-   * the counters again, 1..64; 0 (default) = automatic (16 far from the
-   * tail threshold, then 4, then 1) */
+   * the counters again, 1..64; 0 (default) = automatic (64 far from the
+   * tail threshold, then 16, then 4) */
   BKD_OPT_ROUND_BATCH = 9,
   /* CTAs per SM of the screen kernel, 1..3; 0 (default) = as many as
    * registers, shared and tensor memory allow */
@@ -131,7 +131,12 @@ enum bkd_option {
    * BKD_OPT_PRECISION=1) it picks the point layouts prepared: 0 or 1 that
    * kernel's, 2 both (kernel 0 runs first); afterwards 0 / 1 may be
    * switched any time among the layouts the tree holds (else BKD_EINVAL). */
-  BKD_OPT_SCREEN_KERNEL = 11
+  BKD_OPT_SCREEN_KERNEL = 11,
+  /* Servers on this tree: a batch still running this many LazySearch rounds
+   * after its admission has its remaining queries finished by the tail
+   * kernel (bounds a batch's latency; results do not depend on it); 0 =
+   * never; default 384.  Any time. */
+  BKD_OPT_RESCUE_ROUNDS = 12
 };
 
 /* ------------------------------------------------------------------- stats

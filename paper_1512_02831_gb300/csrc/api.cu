@@ -175,6 +175,7 @@ struct bkd_tree {
   int screen_tile = kScreenTile;  // queries per screened work item
   int round_batch = 0;            // rounds per host look (0: automatic)
   int screen_ctas = 0;            // screen CTAs per SM (0: automatic)
+  int rescue_rounds = 384;        // server: rounds before the tail rescue
   // timing
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
@@ -332,7 +333,8 @@ int build_impl(const float* P, int64_t n, int d, int height,
       point_chunks = val;
     } else if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE ||
                key == BKD_OPT_TAIL_QUERIES || key == BKD_OPT_SCREEN_TILE ||
-               key == BKD_OPT_ROUND_BATCH || key == BKD_OPT_SCREEN_CTAS) {
+               key == BKD_OPT_ROUND_BATCH || key == BKD_OPT_SCREEN_CTAS ||
+               key == BKD_OPT_RESCUE_ROUNDS) {
       // applied after construction below
     } else {
       return fail(BKD_EINVAL, "unknown build option %lld", (long long)key);
@@ -418,7 +420,7 @@ int build_impl(const float* P, int64_t n, int d, int height,
     const int64_t nodes = 2 * L - 1;
     std::vector<float> box;
     try {
-      box.resize((size_t)nodes * 2 * H.Dp);
+      box.resize((size_t)nodes * box_stride(H.Dp));
     } catch (...) {
       return bail(fail(BKD_ENOMEM, "host allocation failed (boxes)"));
     }
@@ -656,7 +658,8 @@ int build_impl(const float* P, int64_t n, int d, int height,
     const int64_t key = options[2 * i], val = options[2 * i + 1];
     if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE ||
         key == BKD_OPT_TAIL_QUERIES || key == BKD_OPT_SCREEN_TILE ||
-        key == BKD_OPT_ROUND_BATCH || key == BKD_OPT_SCREEN_CTAS) {
+        key == BKD_OPT_ROUND_BATCH || key == BKD_OPT_SCREEN_CTAS ||
+        key == BKD_OPT_RESCUE_ROUNDS) {
       int rc = bkd_set_option(t, (int)key, val);
       if (rc != BKD_OK) return bail(rc);
     }
@@ -1049,9 +1052,20 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
       // starting from each one's pending leaf
       cudaEvent_t e0 = t->next_event(), e1 = t->next_event();
       if (e0) cudaEventRecord(e0, s);
+      // chunked: the leaves of the two resident chunk buffers are read
+      // there, the rest from the mapped host copy
+      ChunkBufs cb;
+      if (t->chunked && !t->point_chunks)
+        for (int b = 0; b < 2; ++b)
+          if (t->buf_chunk[b] >= 0) {
+            CU(cudaStreamWaitEvent(s, t->ev_copied[b], 0));
+            cb.buf[b] = t->d_chunk_buf[b];
+            cb.lo[b] = t->chunk_leaf[t->buf_chunk[b]];
+            cb.hi[b] = t->chunk_leaf[t->buf_chunk[b] + 1];
+          }
       CU(launch_tail(D, t->chunked ? t->h_pts : t->d_pts, nxt, n_next,
                      t->state.p, t->qpad.p, t->lst_d.p, t->lst_i.p, K,
-                     t->d_ctr, t->sm_count, s));
+                     t->d_ctr, t->sm_count, s, cb));
       if (e1) cudaEventRecord(e1, s);
       if (e0 && e1) t->tail_ev.push_back({e0, e1});
       t->st_tail_queries += n_next;
@@ -1062,12 +1076,14 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
     if (rc != BKD_OK) return rc;
     n_act = n_next;  // an upper bound of every later round's active count
     // rounds queued before the host looks again: many while far from the
-    // tail threshold, one when close to it (or chunked)
+    // tail threshold, a few when close to it (a round past the threshold
+    // only costs its few queries), one on chunked trees (the host picks
+    // the chunks of every round)
     const int batch = t->chunked            ? 1
                       : t->round_batch > 0    ? t->round_batch
-                      : n_next > 16 * std::max(tail, 1024) ? 16
-                      : n_next > 4 * std::max(tail, 1024)  ? 4
-                                                            : 1;
+                      : n_next > 16 * std::max(tail, 1024) ? 64
+                      : n_next > 4 * std::max(tail, 1024)  ? 16
+                                                            : 4;
     for (int j = 1; j < batch; ++j) {
       rc = start_round(true);
       if (rc == BKD_OK) rc = process_round(-1);
@@ -1129,7 +1145,8 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
   if (t->chunked)
     t->st_mapped_bytes +=
         4.0 * Dp *
-        ((double)t->h_ctr->tail_pairs + (double)t->h_ctr->n_resorted * k +
+        ((double)t->h_ctr->tail_mapped_pairs +
+         (double)t->h_ctr->n_resorted * k +
          (n_fb > 0 ? (double)t->h_ctr->fallback_points : 0.0));
   cudaEvent_t x1 = t->next_event();
   if (x1) cudaEventRecord(x1, s);
@@ -1183,6 +1200,7 @@ TreeView view_of(const bkd_tree* t) {
   v.screen = t->screen;
   v.precision = t->precision;
   v.tail_queries = t->tail_queries;
+  v.rescue_rounds = t->rescue_rounds;
   return v;
 }
 
@@ -1351,6 +1369,11 @@ int bkd_set_option(bkd_tree* t, int key, int64_t value) {
       t->screen_tile = (int)value;
       return BKD_OK;
     }
+    case BKD_OPT_RESCUE_ROUNDS:
+      if (value < 0 || value >= ((int64_t)1 << 31))
+        return fail(BKD_EINVAL, "rescue rounds out of range");
+      t->rescue_rounds = (int)value;
+      return BKD_OK;
     case BKD_OPT_SCREEN_KERNEL:
       if (value != 0 && value != 1)
         return fail(BKD_EINVAL, "screen kernel must be 0 or 1");

@@ -94,6 +94,8 @@ struct Counters {
                                   // kernel staged (one pass per work item)
   unsigned long long fallback_points;  // points the binary64 fallback
                                        // search scanned
+  unsigned long long tail_mapped_pairs;  // tail pairs read from mapped
+                                         // host memory (chunked trees)
 };
 
 constexpr int kErrNonFinite = 1;   // a query holds a non-finite / huge value
@@ -290,10 +292,21 @@ cudaError_t launch_screen_warp(const DevTree& t, const ScreenData& sd,
 // Runs the traversal of each of the n_act queries in `act` to its end (one
 // warp per query); state[q] is the query's pending (not yet scanned) leaf.
 // `pts` is the leaf structure (device or mapped host).
+// Leaves held in device chunk buffers (chunked trees): leaves [lo, hi) of
+// buffer b start at buf[b] (empty range: none); other leaves are read at
+// `pts` (mapped pinned host memory), counted in Counters::tail_mapped_pairs.
+struct ChunkBufs {
+  const float* buf[2] = {nullptr, nullptr};
+  int64_t lo[2] = {0, 0}, hi[2] = {0, 0};
+};
+// (after_scanned: state[q] holds the leaf the query scanned last, not one
+// still to scan: the walk starts at the leaf after it)
 cudaError_t launch_tail(const DevTree& t, const float* pts,
                         const uint32_t* act, int n_act, uint64_t* state,
                         const float* qpad, float* lst_d, uint32_t* lst_i,
-                        int K, Counters* ctr, int sm_count, cudaStream_t s);
+                        int K, Counters* ctr, int sm_count, cudaStream_t s,
+                        const ChunkBufs& cb = ChunkBufs(),
+                        bool after_scanned = false);
 
 cudaError_t launch_recheck(const DevTree& t, int64_t m, int k, int K,
                            const float* qpad, const float* lst_d,
@@ -332,6 +345,7 @@ struct TreeView {
   ScreenData screen;         // BF16 screen data (words == nullptr: none)
   int precision;             // current leaf-scoring option (0 / 1)
   int tail_queries;          // tail threshold option (-1: automatic)
+  int rescue_rounds;         // server straggler rescue (0: never)
 };
 TreeView view_of(const struct ::bkd_tree* t);
 
@@ -367,9 +381,14 @@ struct HostTree {
 const char* build_host_tree(const float* P, int64_t n, int d, int h,
                             HostTree* out);
 
-// Bounding box of the points under every heap node (2^(h+1) - 1 nodes):
-// box[v*2Dp .. v*2Dp+Dp) = per-dimension minimum, box[v*2Dp+Dp .. v*2Dp+2Dp)
-// = maximum; dimensions d..Dp-1 are [0, 0].
+// Floats per node record of the box array: minimum row, maximum row, the
+// node's split value, 3 floats of padding (a whole number of float4).
+inline int box_stride(int Dp) { return 2 * Dp + 4; }
+
+// Bounding box of the points under every heap node (2^(h+1) - 1 nodes),
+// record v at box + v * box_stride(Dp): [0, Dp) per-dimension minimum,
+// [Dp, 2Dp) maximum (dimensions d..Dp-1 are [0, 0]), [2Dp] the node's split
+// value (0 for leaves), so that a descent reads a node's split with its box.
 void fill_boxes(const float* P, const HostTree& t, float* box);
 
 // k-halves of 16 bf16 slots the BF16 screen uses: the d offsets, two slots

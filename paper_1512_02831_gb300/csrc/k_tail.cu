@@ -91,12 +91,12 @@ __global__ void __launch_bounds__(kTailWarps * 32)
                 const uint32_t* __restrict__ act, int n_act,
                 uint64_t* __restrict__ state, const float* __restrict__ qpad,
                 float* __restrict__ lst_d, uint32_t* __restrict__ lst_i, int K,
-                Counters* ctr) {
+                Counters* ctr, ChunkBufs cb, bool after_scanned) {
   const int lane = threadIdx.x & 31;
   const unsigned full = 0xffffffffu;
   const int first_leaf = (1 << t.h) - 1;
   const int64_t qpl = t.lcap >> 2;
-  unsigned long long pairs = 0, visits = 0;
+  unsigned long long pairs = 0, visits = 0, mapped = 0;
   for (int w = blockIdx.x * kTailWarps + (threadIdx.x >> 5); w < n_act;
        w += gridDim.x * kTailWarps) {
     const uint32_t q = act[w];
@@ -116,12 +116,24 @@ __global__ void __launch_bounds__(kTailWarps * 32)
     const uint64_t st = state[q];
     int node = state_node(st);
     uint32_t mask = state_mask(st);
-    if (node == kStart) node = next_leaf(t, bx, qp, node, mask, bound);
+    if (node == kStart || after_scanned)
+      node = next_leaf(t, bx, qp, node, mask, bound);
     for (; node != kDone; node = next_leaf(t, bx, qp, node, mask, bound)) {
       const int leaf = node - first_leaf;
       const int np = t.leaf_cnt[leaf];
       const int nq = (np + 3) >> 2;
-      const float4* lq = pts + (int64_t)leaf * qpl * D;
+      // the leaf in a device chunk buffer if one holds it, else at pts
+      const float4* lq;
+      if (leaf >= cb.lo[0] && leaf < cb.hi[0]) {
+        lq = reinterpret_cast<const float4*>(cb.buf[0]) +
+             (int64_t)(leaf - cb.lo[0]) * qpl * D;
+      } else if (leaf >= cb.lo[1] && leaf < cb.hi[1]) {
+        lq = reinterpret_cast<const float4*>(cb.buf[1]) +
+             (int64_t)(leaf - cb.lo[1]) * qpl * D;
+      } else {
+        lq = pts + (int64_t)leaf * qpl * D;
+        mapped += (unsigned long long)np;
+      }
       const uint32_t slot0 = (uint32_t)((int64_t)leaf * t.lcap);
       ++visits;
       pairs += (unsigned long long)np;
@@ -180,6 +192,7 @@ __global__ void __launch_bounds__(kTailWarps * 32)
   if (lane == 0 && visits) {
     atomicAdd(&ctr->tail_pairs, pairs);
     atomicAdd(&ctr->tail_visits, visits);
+    if (mapped) atomicAdd(&ctr->tail_mapped_pairs, mapped);
   }
 }
 
@@ -188,11 +201,11 @@ __global__ void __launch_bounds__(kTailWarps * 32)
     if (K <= 32)                                                             \
       tail_kernel<DIM, false><<<grid, kTailWarps * 32, 0, s>>>(              \
           t, reinterpret_cast<const float4*>(pts), act, n_act, state, qpad,  \
-          lst_d, lst_i, K, ctr);                                             \
+          lst_d, lst_i, K, ctr, cb, after_scanned);                          \
     else                                                                     \
       tail_kernel<DIM, true><<<grid, kTailWarps * 32, 0, s>>>(               \
           t, reinterpret_cast<const float4*>(pts), act, n_act, state, qpad,  \
-          lst_d, lst_i, K, ctr);                                             \
+          lst_d, lst_i, K, ctr, cb, after_scanned);                          \
     return cudaGetLastError();
 
 }  // namespace
@@ -200,7 +213,8 @@ __global__ void __launch_bounds__(kTailWarps * 32)
 cudaError_t launch_tail(const DevTree& t, const float* pts,
                         const uint32_t* act, int n_act, uint64_t* state,
                         const float* qpad, float* lst_d, uint32_t* lst_i,
-                        int K, Counters* ctr, int sm_count, cudaStream_t s) {
+                        int K, Counters* ctr, int sm_count, cudaStream_t s,
+                        const ChunkBufs& cb, bool after_scanned) {
   if (n_act <= 0) return cudaSuccess;
   if (K < 1 || K > 64) return cudaErrorInvalidValue;
   const int grid = std::min((n_act + kTailWarps - 1) / kTailWarps,

@@ -90,7 +90,32 @@ struct Batch {
   int64_t s0 = -1;  // first slot
   int bid = -1;     // index into batch_left
   int status = BKD_BATCH_QUEUED;
+  int64_t born = 0;  // the class server's round count at admission
 };
+
+// A batch still running BKD_OPT_RESCUE_ROUNDS rounds after its admission
+// has its remaining queries finished by the tail kernel (one warp per query,
+// to the end of its traversal): a batch completes only with its last query,
+// and the stragglers of a large batch would otherwise take hundreds of
+// rounds more.
+
+// Splits the active list by the rescue flag of each query's batch: young
+// queries to `young`, those of batches to rescue to `old` (counts in
+// cnt[0], cnt[1]; order within each list is free).
+__global__ void partition_kernel(const uint32_t* __restrict__ act, int n,
+                                 const int32_t* __restrict__ slot_batch,
+                                 const uint8_t* __restrict__ rescue,
+                                 uint32_t* __restrict__ young,
+                                 uint32_t* __restrict__ old,
+                                 int32_t* __restrict__ cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t q = act[i];
+  if (rescue[slot_batch[q]])
+    old[atomicAdd(cnt + 1, 1)] = q;
+  else
+    young[atomicAdd(cnt, 1)] = q;
+}
 
 template <class T>
 cudaError_t dev_alloc(T** p, int64_t n) {
@@ -122,6 +147,13 @@ struct ClassServer {
   Counters *d_ctr = nullptr, *d_fin = nullptr;
   Counters *h_ctr = nullptr, *h_fin = nullptr;  // pinned
   int32_t* h_left = nullptr;                    // pinned, kMaxBatches
+  // straggler rescue
+  int64_t rounds = 0;            // rounds run
+  uint8_t* d_rescue = nullptr;   // device, kMaxBatches flags
+  uint8_t* h_rescue = nullptr;   // pinned, kMaxBatches
+  uint32_t* resc = nullptr;      // device, queries to rescue
+  int32_t* d_part = nullptr;     // device, 2 counts
+  int32_t* h_part = nullptr;     // pinned, 2 counts
   // host state
   uint32_t* act = nullptr;
   uint32_t* nxt = nullptr;
@@ -161,6 +193,11 @@ struct ClassServer {
     cudaFreeHost(h_ctr);
     cudaFreeHost(h_fin);
     cudaFreeHost(h_left);
+    cudaFree(d_rescue);
+    cudaFree(resc);
+    cudaFree(d_part);
+    cudaFreeHost(h_rescue);
+    cudaFreeHost(h_part);
   }
 
   void finish(Batch* b, int status) {
@@ -177,6 +214,7 @@ struct ClassServer {
   int admit(Batch* b, int64_t s0, int bid, bool* ok);
   int complete(Batch* b);
   int first_round(int n_old);
+  int rescue();
   int round();
 };
 
@@ -230,6 +268,42 @@ int ClassServer::first_round(int n_old) {
   return BKD_OK;
 }
 
+// The queries of batches admitted BKD_OPT_RESCUE_ROUNDS rounds ago or
+// earlier leave the active list and are finished by the tail kernel (their
+// state holds the leaf they scanned last).
+int ClassServer::rescue() {
+  const int64_t after = v.rescue_rounds;
+  if (after <= 0) return BKD_OK;
+  bool any = false;
+  for (int bid = 0; bid < kMaxBatches; ++bid) {
+    const Batch* b = running[bid];
+    h_rescue[bid] = b && rounds - b->born >= after;
+    any = any || h_rescue[bid];
+  }
+  if (!any || n_act == 0) return BKD_OK;
+  const DevTree& D = v.dev;
+  cudaStream_t s = v.stream;
+  SV_CU(cudaMemcpyAsync(d_rescue, h_rescue, kMaxBatches,
+                        cudaMemcpyHostToDevice, s));
+  SV_CU(cudaMemsetAsync(d_part, 0, 2 * sizeof(int32_t), s));
+  partition_kernel<<<(n_act + 255) / 256, 256, 0, s>>>(act, n_act, slot_batch,
+                                                       d_rescue, nxt, resc,
+                                                       d_part);
+  SV_CU(cudaGetLastError());
+  SV_CU(cudaMemcpyAsync(h_part, d_part, 2 * sizeof(int32_t),
+                        cudaMemcpyDeviceToHost, s));
+  SV_CU(cudaStreamSynchronize(s));
+  const int n_young = h_part[0], n_old = h_part[1];
+  if (n_old > 0) {
+    SV_CU(launch_tail(D, v.d_pts, resc, n_old, state, qpad, lst_d, lst_i, K,
+                      d_ctr, v.sm_count, s, ChunkBufs(), true));
+    SV_CU(launch_retire_list(resc, n_old, slot_batch, batch_left, s));
+  }
+  std::swap(act, nxt);
+  n_act = n_young;
+  return BKD_OK;
+}
+
 // One LazySearch round over the whole active list.
 int ClassServer::round() {
   const DevTree& D = v.dev;
@@ -276,6 +350,7 @@ int ClassServer::round() {
   }
   std::swap(act, nxt);
   n_act = n_next;
+  ++rounds;
   return BKD_OK;
 }
 
@@ -361,6 +436,11 @@ int cs_open(bkd_tree* t, int k_max, int64_t max_queries, ClassServer** out) {
   SV_CU(host_alloc(&sv->h_fin, sizeof(Counters), cudaHostAllocDefault));
   SV_CU(host_alloc(&sv->h_left, sizeof(int32_t) * kMaxBatches,
                       cudaHostAllocDefault));
+  SV_CU(dev_alloc(&sv->d_rescue, kMaxBatches));
+  SV_CU(dev_alloc(&sv->resc, Q));
+  SV_CU(dev_alloc(&sv->d_part, 2));
+  SV_CU(host_alloc(&sv->h_rescue, kMaxBatches, cudaHostAllocDefault));
+  SV_CU(host_alloc(&sv->h_part, 2 * sizeof(int32_t), cudaHostAllocDefault));
   SV_CU(cudaMemsetAsync(sv->d_ctr, 0, sizeof(Counters), v.stream));
   SV_CU(cudaMemsetAsync(sv->batch_left, 0, sizeof(int32_t) * kMaxBatches,
                         v.stream));
@@ -451,6 +531,7 @@ int cs_step(ClassServer* s, int64_t* pending) {
       continue;
     }
     b->status = BKD_BATCH_RUNNING;
+    b->born = s->rounds;
     s->running[bid] = b;
     s->n_act += (int)b->m;
   }
@@ -459,7 +540,17 @@ int cs_step(ClassServer* s, int64_t* pending) {
     if (rc != BKD_OK) return rc;
   }
   if (s->n_act > 0) {
-    const int rc = s->round();
+    int rc = s->rescue();
+    if (rc != BKD_OK) return rc;
+    if (s->n_act > 0) {
+      rc = s->round();
+    } else {
+      // every active query was rescued: their batches' counts
+      SV_CU(cudaMemcpyAsync(s->h_left, s->batch_left,
+                            sizeof(int32_t) * kMaxBatches,
+                            cudaMemcpyDeviceToHost, s->v.stream));
+      SV_CU(cudaStreamSynchronize(s->v.stream));
+    }
     if (rc != BKD_OK) return rc;
     for (int bid = 0; bid < kMaxBatches; ++bid) {
       Batch* b = s->running[bid];

@@ -346,13 +346,21 @@ def test_tail_kernel_long_lists(k):
           rows=np.arange(300))
 
 
-def test_tail_kernel_in_chunked_mode():
+@pytest.mark.parametrize("chunks", [1, 2, 3, 10])
+def test_tail_kernel_in_chunked_mode(chunks):
+    """The tail kernel on a chunked tree reads the leaves of the two
+    resident chunk buffers there and the others from the mapped host copy
+    (N <= 2: nothing mapped)."""
     w = workloads.scaled(workloads.MIXTURE_64M, 1 << 16, 3000, 8)
     P, Q = w.points(), w.queries()
     i0, d0, _ = run(P, Q, 10, 8, tail_queries=0)
-    i1, d1, st = run(P, Q, 10, 8, chunks=3, tail_queries=1500)
+    i1, d1, st = run(P, Q, 10, 8, chunks=chunks, tail_queries=1500)
     assert st["tail_queries"] > 0
     assert np.array_equal(i0, i1) and np.array_equal(d0, d1)
+    if chunks <= 2:
+        # only the re-check's few binary64 rows (and the fallback) read
+        # mapped memory
+        assert st["mapped_bytes"] < 0.01 * st["tail_pairs"] * 4 * 10
 
 
 def run_both_precisions(P, Q, k, h, **opts):

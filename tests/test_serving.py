@@ -68,6 +68,37 @@ def test_each_batch_same_alone_and_in_the_mix(precision, kernel):
         bkd.bkd_free(tree)
 
 
+@pytest.mark.parametrize("rescue", [1, 3])
+def test_rescued_stragglers_give_the_same_results(rescue):
+    """Batches older than `rescue` rounds have their remaining queries
+    finished by the tail kernel; every batch's result still equals a
+    bkd_query of it alone (float32 and the warp screen)."""
+    w = workloads.scaled(workloads.MIXTURE_64M, 1 << 16, 4000, 8)
+    P, Qall = w.points(), w.queries()
+    tree = bkd.bkd_build(P, w.height, precision=1, rescue_rounds=rescue)
+    spec = [(0, 700, 10, 0), (700, 1300, 50, 1), (2000, 5, 1, 2),
+            (2005, 1995, 10, 4)]
+    try:
+        for prec in (0, 1):
+            bkd.bkd_set_option(tree, "precision", prec)
+            alone = [bkd.bkd_query(tree, np.ascontiguousarray(Qall[a:a + m]),
+                                   k) for a, m, k, _ in spec]
+            srv = bkd.Server(tree, k_max=50, max_queries=4000)
+
+            def submitter(a, m, k):
+                return lambda: srv.submit(np.ascontiguousarray(Qall[a:a + m]),
+                                          k)
+            tickets = _serve(srv, [(s[3], submitter(*s[:3])) for s in spec])
+            for j in range(len(spec)):
+                assert srv.status(tickets[j]) == bkd.BKD_BATCH_DONE
+                idx, dist = srv.result(tickets[j])
+                assert np.array_equal(idx, alone[j][0]), (prec, j)
+                assert np.array_equal(dist, alone[j][1]), (prec, j)
+            srv.close()
+    finally:
+        bkd.bkd_free(tree)
+
+
 def test_bad_batches_fail_alone():
     w = workloads.scaled(workloads.MIXTURE_64M, 1 << 14, 500, 6)
     P, Q = w.points(), w.queries()
