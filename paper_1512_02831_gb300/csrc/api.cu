@@ -420,7 +420,7 @@ int build_impl(const float* P, int64_t n, int d, int height,
     const int64_t nodes = 2 * L - 1;
     std::vector<float> box;
     try {
-      box.resize((size_t)nodes * box_stride(H.Dp));
+      box.resize((size_t)nodes * 2 * H.Dp);
     } catch (...) {
       return bail(fail(BKD_ENOMEM, "host allocation failed (boxes)"));
     }

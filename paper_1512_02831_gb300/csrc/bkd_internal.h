@@ -381,14 +381,9 @@ struct HostTree {
 const char* build_host_tree(const float* P, int64_t n, int d, int h,
                             HostTree* out);
 
-// Floats per node record of the box array: minimum row, maximum row, the
-// node's split value, 3 floats of padding (a whole number of float4).
-inline int box_stride(int Dp) { return 2 * Dp + 4; }
-
-// Bounding box of the points under every heap node (2^(h+1) - 1 nodes),
-// record v at box + v * box_stride(Dp): [0, Dp) per-dimension minimum,
-// [Dp, 2Dp) maximum (dimensions d..Dp-1 are [0, 0]), [2Dp] the node's split
-// value (0 for leaves), so that a descent reads a node's split with its box.
+// Bounding box of the points under every heap node (2^(h+1) - 1 nodes):
+// box[v*2Dp .. v*2Dp+Dp) = per-dimension minimum, box[v*2Dp+Dp .. v*2Dp+2Dp)
+// = maximum; dimensions d..Dp-1 are [0, 0].
 void fill_boxes(const float* P, const HostTree& t, float* box);
 
 // k-halves of 16 bf16 slots the BF16 screen uses: the d offsets, two slots

@@ -177,13 +177,11 @@ void fill_quads(const float* P, const HostTree& t, int64_t leaf_a,
 
 void fill_boxes(const float* P, const HostTree& t, float* box) {
   const int d = t.d, Dp = t.Dp;
-  const int64_t S = box_stride(Dp);
   const int64_t L = (int64_t)1 << t.h;
   const int64_t first_leaf = L - 1;
   parallel_items(L, [&](int64_t leaf) {
-    float* lo = box + (first_leaf + leaf) * S;
+    float* lo = box + (first_leaf + leaf) * 2 * Dp;
     float* hi = lo + Dp;
-    for (int i = 2 * Dp; i < S; ++i) lo[i] = 0.f;  // no split at a leaf
     for (int i = 0; i < Dp; ++i) {
       // padding dimensions: q_i = 0 lies in [0, 0] and adds nothing
       lo[i] = i < d ? INFINITY : 0.f;
@@ -198,15 +196,13 @@ void fill_boxes(const float* P, const HostTree& t, float* box) {
     }
   });
   for (int64_t v = first_leaf - 1; v >= 0; --v) {
-    float* b = box + v * S;
-    const float* l = box + (2 * v + 1) * S;
-    const float* r = box + (2 * v + 2) * S;
+    float* b = box + v * 2 * Dp;
+    const float* l = box + (2 * v + 1) * 2 * Dp;
+    const float* r = box + (2 * v + 2) * 2 * Dp;
     for (int i = 0; i < Dp; ++i) {
       b[i] = std::min(l[i], r[i]);
       b[Dp + i] = std::max(l[Dp + i], r[Dp + i]);
     }
-    b[2 * Dp] = t.split[v];
-    for (int i = 2 * Dp + 1; i < S; ++i) b[i] = 0.f;
   }
 }
 

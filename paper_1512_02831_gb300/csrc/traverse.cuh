@@ -45,9 +45,8 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
 }
 
 // float32 pruning bound of one query; D = Dp (compile time), the query in
-// registers and each node record (box + split value, box_stride floats)
-// read as D/2 + 1 16-byte loads.  Padding dimensions (q_i = 0, box [0, 0])
-// add fma(0, 0, B) = B.
+// registers and each box read as 2D/4 16-byte loads.  Padding dimensions
+// (q_i = 0, box [0, 0]) add fma(0, 0, B) = B.
 template <int D>
 struct F32Bound {
   using T = float;
@@ -57,11 +56,10 @@ struct F32Bound {
     for (int i = 0; i < D; ++i) x[i] = qp[i];
   }
   __device__ static bool keep(float b, float bound) { return b < bound; }
-  // the bound of `node`'s box; `split` receives the node's split value
-  __device__ float box(const DevTree& t, int node, float& split) const {
+  __device__ float box(const DevTree& t, int node) const {
     static_assert(D % 2 == 0, "a box row pair is a whole number of float4");
     const float4* p =
-        reinterpret_cast<const float4*>(t.box + (size_t)node * (2 * D + 4));
+        reinterpret_cast<const float4*>(t.box + (size_t)node * 2 * D);
     float f[2 * D];
 #pragma unroll
     for (int j = 0; j < D / 2; ++j) {
@@ -71,7 +69,6 @@ struct F32Bound {
       f[4 * j + 2] = v.z;
       f[4 * j + 3] = v.w;
     }
-    split = __ldg(p + D / 2).x;
     float b = 0.f;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
@@ -105,10 +102,9 @@ __device__ __forceinline__ int next_leaf(const DevTree& t, const B& bx,
   const int h = t.h;
   int u;      // descending: the node entered last; climbing: a finished node
   bool down;  // descending (near child next) or climbing (open far child)
-  float su = 0.f;  // descending: u's split value (read with u's box)
   if (node == kStart) {
     mask = 0u;
-    if (!B::keep(bx.box(t, 0, su), bound)) return kDone;
+    if (!B::keep(bx.box(t, 0), bound)) return kDone;
     u = 0;
     down = true;
   } else {
@@ -120,7 +116,7 @@ __device__ __forceinline__ int next_leaf(const DevTree& t, const B& bx,
     int c, l = 0;
     if (down) {
       if (lu == h) return u;  // a leaf: visit it
-      c = 2 * u + (qp[lu % t.d] < su ? 1 : 2);  // near
+      c = 2 * u + (qp[lu % t.d] < __ldg(t.split + u) ? 1 : 2);  // near
     } else {
       // the far child at the deepest level with a clear bit
       const uint32_t open = ~mask & ((1u << lu) - 1u);
@@ -131,15 +127,12 @@ __device__ __forceinline__ int next_leaf(const DevTree& t, const B& bx,
       mask |= 1u << l;  // finished from here on: pruned now, or entered now
                         // (then it is on the path)
     }
-    float sc;
-    const bool pass = B::keep(bx.box(t, c, sc), bound);
+    const bool pass = B::keep(bx.box(t, c), bound);
     if (down) {
       u = c;  // a pruned near child is finished without a visit; its far
-      su = sc;  // sibling (clear bit) is next in line
-      down = pass;
+      down = pass;  // sibling (clear bit) is next in line
     } else if (pass) {
       u = c;
-      su = sc;
       mask &= (2u << l) - 1u;  // levels below l: a new path
       down = true;
     }
