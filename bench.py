@@ -85,6 +85,10 @@ def args_():
                          "samples")
     ap.add_argument("--serving-slots", type=int, default=1 << 22,
                     help="query slots per list class of the server")
+    ap.add_argument("--serving-defer", type=int, default=0,
+                    help="the servers' buffer trigger (BKD_OPT_DEFER_QUERIES: "
+                         "a leaf's buffer is processed once it holds this "
+                         "many queries or waited 4 rounds; 0: off)")
     ap.add_argument("--serving-backlog", type=int, default=1 << 23,
                     help="unfinished submitted queries above which an "
                          "arriving batch is rejected")
@@ -498,6 +502,8 @@ def run_ours(a, w, rank, world, local_rank):
         1 if "tcgen05" in modes else 0)
     tree = bkd.bkd_build(P, w.height, precision=1, screen_kernel=kernels)
     build_s = time.perf_counter() - t0
+    if a.serving_defer:
+        bkd.bkd_set_option(tree, "defer_queries", a.serving_defer)
     if a.serving_only:
         del P
         # the serving samples alone (the resident tree of the workload)
@@ -510,7 +516,10 @@ def run_ours(a, w, rank, world, local_rank):
             print(json.dumps({"metric": "serving (continuous batching)",
                               "workload": w.name,
                               "config": dict(w.describe(),
-                                             tree_build_s=round(build_s, 2)),
+                                             tree_build_s=round(build_s, 2),
+                                             slots=a.serving_slots,
+                                             backlog=a.serving_backlog,
+                                             defer_queries=a.serving_defer),
                               "serving": serving}), flush=True)
         return
     Qd = torch.from_numpy(Q).to(dev)

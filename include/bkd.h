@@ -136,7 +136,14 @@ enum bkd_option {
    * after its admission has its remaining queries finished by the tail
    * kernel (bounds a batch's latency; results do not depend on it); 0 =
    * never; default 384.  Any time. */
-  BKD_OPT_RESCUE_ROUNDS = 12
+  BKD_OPT_RESCUE_ROUNDS = 12,
+  /* Servers on this tree: the buffer trigger of Algorithm 1 -- a round
+   * processes a leaf's buffer only when it holds at least this many queries
+   * or was deferred 4 rounds in a row; the other buffered queries wait at
+   * their leaf (fewer, fuller leaf scans on trees with many leaves; results
+   * do not depend on it); 0 (default) = every buffer every round, 0..4096.
+   * Any time. */
+  BKD_OPT_DEFER_QUERIES = 13
 };
 
 /* ------------------------------------------------------------------- stats

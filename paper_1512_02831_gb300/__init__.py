@@ -38,7 +38,7 @@ BKD_BATCH_QUEUED, BKD_BATCH_RUNNING, BKD_BATCH_DONE = 0, 1, 2
 OPTIONS = {"stream": 1, "device_mem_cap": 2, "chunks": 3, "max_active": 4,
            "tail_queries": 5, "precision": 6, "point_chunks": 7,
            "screen_tile": 8, "round_batch": 9, "screen_ctas": 10,
-           "screen_kernel": 11, "rescue_rounds": 12}
+           "screen_kernel": 11, "rescue_rounds": 12, "defer_queries": 13}
 STATS = {"rounds": 1, "leaf_visits": 2, "pairs": 3, "resorted": 4,
          "fallback": 5, "leaf_kernel_ms": 6, "chunk_bytes": 7, "copy_ms": 8,
          "leaf_launches": 9, "kernel_launches": 10, "tail_queries": 11,

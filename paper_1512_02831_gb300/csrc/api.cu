@@ -176,6 +176,7 @@ struct bkd_tree {
   int round_batch = 0;            // rounds per host look (0: automatic)
   int screen_ctas = 0;            // screen CTAs per SM (0: automatic)
   int rescue_rounds = 384;        // server: rounds before the tail rescue
+  int defer_queries = 0;          // server: buffer trigger (0: off)
   // timing
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
@@ -334,7 +335,7 @@ int build_impl(const float* P, int64_t n, int d, int height,
     } else if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE ||
                key == BKD_OPT_TAIL_QUERIES || key == BKD_OPT_SCREEN_TILE ||
                key == BKD_OPT_ROUND_BATCH || key == BKD_OPT_SCREEN_CTAS ||
-               key == BKD_OPT_RESCUE_ROUNDS) {
+               key == BKD_OPT_RESCUE_ROUNDS || key == BKD_OPT_DEFER_QUERIES) {
       // applied after construction below
     } else {
       return fail(BKD_EINVAL, "unknown build option %lld", (long long)key);
@@ -659,7 +660,7 @@ int build_impl(const float* P, int64_t n, int d, int height,
     if (key == BKD_OPT_STREAM || key == BKD_OPT_MAX_ACTIVE ||
         key == BKD_OPT_TAIL_QUERIES || key == BKD_OPT_SCREEN_TILE ||
         key == BKD_OPT_ROUND_BATCH || key == BKD_OPT_SCREEN_CTAS ||
-        key == BKD_OPT_RESCUE_ROUNDS) {
+        key == BKD_OPT_RESCUE_ROUNDS || key == BKD_OPT_DEFER_QUERIES) {
       int rc = bkd_set_option(t, (int)key, val);
       if (rc != BKD_OK) return bail(rc);
     }
@@ -1201,6 +1202,7 @@ TreeView view_of(const bkd_tree* t) {
   v.precision = t->precision;
   v.tail_queries = t->tail_queries;
   v.rescue_rounds = t->rescue_rounds;
+  v.defer_queries = t->defer_queries;
   return v;
 }
 
@@ -1373,6 +1375,11 @@ int bkd_set_option(bkd_tree* t, int key, int64_t value) {
       if (value < 0 || value >= ((int64_t)1 << 31))
         return fail(BKD_EINVAL, "rescue rounds out of range");
       t->rescue_rounds = (int)value;
+      return BKD_OK;
+    case BKD_OPT_DEFER_QUERIES:
+      if (value < 0 || value > 4096)
+        return fail(BKD_EINVAL, "deferral threshold must be 0..4096");
+      t->defer_queries = (int)value;
       return BKD_OK;
     case BKD_OPT_SCREEN_KERNEL:
       if (value != 0 && value != 1)

@@ -77,6 +77,7 @@ struct Counters {
   int32_t err;              // device-detected input errors (bit mask)
   int32_t screen_next;      // next work item of the running screen launch
   int32_t screen_ovf_items; // screen items handed to the float32 kernel
+  int32_t n_items_kept;     // servers with deferral: items processed
   unsigned long long tail_pairs;   // (query, point) pairs of the tail kernel
   unsigned long long tail_visits;  // (query, leaf) visits of the tail kernel
   unsigned long long screen_kept;  // pairs the BF16 screen passed on
@@ -118,6 +119,10 @@ struct DevTree {
   // in resident mode, where every round scans every buffer)
   int n_chunks;
   const uint8_t* chunk_done;
+  // servers with buffer deferral: per query slot, 1 while the query's
+  // pending leaf was left unscanned (its buffer deferred); FindLeafBatch then
+  // keeps it there (nullptr: every round scans every buffer)
+  const uint8_t* q_wait = nullptr;
 };
 
 // ------------------------------------------------------------- launchers
@@ -300,7 +305,8 @@ struct ChunkBufs {
   int64_t lo[2] = {0, 0}, hi[2] = {0, 0};
 };
 // (after_scanned: state[q] holds the leaf the query scanned last, not one
-// still to scan: the walk starts at the leaf after it)
+// still to scan: the walk starts at the leaf after it -- except for the
+// queries whose t.q_wait flag is set: their pending leaf is still to scan)
 cudaError_t launch_tail(const DevTree& t, const float* pts,
                         const uint32_t* act, int n_act, uint64_t* state,
                         const float* qpad, float* lst_d, uint32_t* lst_i,
@@ -346,6 +352,7 @@ struct TreeView {
   int precision;             // current leaf-scoring option (0 / 1)
   int tail_queries;          // tail threshold option (-1: automatic)
   int rescue_rounds;         // server straggler rescue (0: never)
+  int defer_queries;         // server buffer trigger (0: off)
 };
 TreeView view_of(const struct ::bkd_tree* t);
 

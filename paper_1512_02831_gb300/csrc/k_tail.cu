@@ -116,7 +116,8 @@ __global__ void __launch_bounds__(kTailWarps * 32)
     const uint64_t st = state[q];
     int node = state_node(st);
     uint32_t mask = state_mask(st);
-    if (node == kStart || after_scanned)
+    if (node == kStart ||
+        (after_scanned && !(t.q_wait && t.q_wait[q])))
       node = next_leaf(t, bx, qp, node, mask, bound);
     for (; node != kDone; node = next_leaf(t, bx, qp, node, mask, bound)) {
       const int leaf = node - first_leaf;

@@ -65,6 +65,12 @@ __global__ void __launch_bounds__(kFindThreads)
   const uint64_t st = state[q];
   const int node = state_node(st);
   uint32_t mask = state_mask(st);
+  if (t.q_wait && node >= 0 && t.q_wait[q]) {
+    // a deferred buffer: the pending leaf is still to scan
+    const int leaf = node - ((1 << t.h) - 1);
+    placed[pos] = make_int2(leaf, atomicAdd(cnt + leaf, 1));
+    return;
+  }
   if (t.chunk_done && node >= 0) {
     // chunked mode: was the pending leaf's chunk scanned last round?
     const int leaf = node - ((1 << t.h) - 1);

@@ -99,6 +99,51 @@ struct Batch {
 // and the stragglers of a large batch would otherwise take hundreds of
 // rounds more.
 
+// Buffer trigger (BKD_OPT_DEFER_QUERIES): a leaf's buffer is processed in
+// a round when it holds at least min_q queries or was deferred kDeferMax
+// rounds in a row; go[l] says which, leaf_wait[l] counts the deferrals.
+constexpr int kDeferMax = 4;
+
+__global__ void defer_leaves_kernel(const int32_t* __restrict__ cnt,
+                                    int64_t L, int min_q,
+                                    int32_t* __restrict__ leaf_wait,
+                                    uint8_t* __restrict__ go) {
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= L) return;
+  const int c = cnt[l];
+  if (c == 0) {
+    leaf_wait[l] = 0;
+    go[l] = 0;
+    return;
+  }
+  const bool g = c >= min_q || leaf_wait[l] >= kDeferMax;
+  go[l] = g ? 1 : 0;
+  leaf_wait[l] = g ? 0 : leaf_wait[l] + 1;
+}
+
+// The round's work items of the leaves that go, to `out` (count in
+// ctr->n_items_kept; order free); each item's queries get their wait flag:
+// 0 (scanned this round) or 1 (the pending leaf stays to scan).
+__global__ void filter_items_kernel(const Item* __restrict__ items,
+                                    Counters* ctr,
+                                    const uint8_t* __restrict__ go,
+                                    const uint32_t* __restrict__ act,
+                                    uint8_t* __restrict__ q_wait,
+                                    Item* __restrict__ out) {
+  const int n = ctr->n_items;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < n;
+       it += gridDim.x * blockDim.x) {
+    const Item w = items[it];
+    const bool g = go[w.leaf] != 0;
+    if (g) out[atomicAdd(&ctr->n_items_kept, 1)] = w;
+    for (int j = 0; j < w.count; ++j) q_wait[act[w.start + j]] = g ? 0 : 1;
+  }
+}
+
+__global__ void take_kept_items_kernel(Counters* ctr) {
+  ctr->n_items = ctr->n_items_kept;
+}
+
 // Splits the active list by the rescue flag of each query's batch: young
 // queries to `young`, those of batches to rescue to `old` (counts in
 // cnt[0], cnt[1]; order within each list is free).
@@ -154,6 +199,18 @@ struct ClassServer {
   uint32_t* resc = nullptr;      // device, queries to rescue
   int32_t* d_part = nullptr;     // device, 2 counts
   int32_t* h_part = nullptr;     // pinned, 2 counts
+  // buffer trigger
+  uint8_t* q_wait = nullptr;     // device, per slot
+  int32_t* leaf_wait = nullptr;  // device, per leaf
+  uint8_t* leaf_go = nullptr;    // device, per leaf
+  Item* items2 = nullptr;        // device, the items processed in a round
+  bool waiting = false;          // some q_wait flag may be set
+  // the tree with this server's wait flags (while any may be set)
+  DevTree dev() const {
+    DevTree D = v.dev;
+    if (waiting) D.q_wait = q_wait;
+    return D;
+  }
   // host state
   uint32_t* act = nullptr;
   uint32_t* nxt = nullptr;
@@ -198,6 +255,10 @@ struct ClassServer {
     cudaFree(d_part);
     cudaFreeHost(h_rescue);
     cudaFreeHost(h_part);
+    cudaFree(q_wait);
+    cudaFree(leaf_wait);
+    cudaFree(leaf_go);
+    cudaFree(items2);
   }
 
   void finish(Batch* b, int status) {
@@ -234,6 +295,7 @@ int ClassServer::admit(Batch* b, int64_t s0, int bid, bool* ok) {
                     act + n_act, (uint32_t)s0, d_fin, s));
   SV_CU(launch_fill(slot_batch + s0, m, bid, s));
   SV_CU(launch_fill(batch_left + bid, 1, (int32_t)m, s));
+  SV_CU(cudaMemsetAsync(q_wait + s0, 0, m, s));
   SV_CU(cudaMemcpyAsync(h_fin, d_fin, sizeof(Counters),
                         cudaMemcpyDeviceToHost, s));
   SV_CU(cudaStreamSynchronize(s));
@@ -274,6 +336,7 @@ int ClassServer::first_round(int n_old) {
 int ClassServer::rescue() {
   const int64_t after = v.rescue_rounds;
   if (after <= 0) return BKD_OK;
+  const DevTree D = dev();  // a deferred query's pending leaf is unscanned
   bool any = false;
   for (int bid = 0; bid < kMaxBatches; ++bid) {
     const Batch* b = running[bid];
@@ -281,7 +344,6 @@ int ClassServer::rescue() {
     any = any || h_rescue[bid];
   }
   if (!any || n_act == 0) return BKD_OK;
-  const DevTree& D = v.dev;
   cudaStream_t s = v.stream;
   SV_CU(cudaMemcpyAsync(d_rescue, h_rescue, kMaxBatches,
                         cudaMemcpyHostToDevice, s));
@@ -306,7 +368,7 @@ int ClassServer::rescue() {
 
 // One LazySearch round over the whole active list.
 int ClassServer::round() {
-  const DevTree& D = v.dev;
+  const DevTree D = dev();
   cudaStream_t s = v.stream;
   const int64_t L = v.n_leaves;
   const bool screened = v.precision == 1 && screen_max > 0;
@@ -339,14 +401,34 @@ int ClassServer::round() {
     return BKD_OK;
   }
   if (n_next > 0) {
+    // the buffer trigger: only the leaves that go are processed (the item
+    // count is then read on the device); with the trigger off, one pass with
+    // every leaf going clears flags a previous setting left
+    const Item* its = items;
+    int nit = n_items;
+    if (v.defer_queries > 0 || waiting) {
+      const int min_q = std::max(v.defer_queries, 1);
+      SV_CU(cudaMemsetAsync(&d_ctr->n_items_kept, 0, sizeof(int32_t), s));
+      defer_leaves_kernel<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(
+          cnt, L, min_q, leaf_wait, leaf_go);
+      filter_items_kernel<<<std::max(1, std::min((n_items + 255) / 256,
+                                                 v.sm_count * 8)),
+                            256, 0, s>>>(items, d_ctr, leaf_go, nxt, q_wait,
+                                         items2);
+      take_kept_items_kernel<<<1, 1, 0, s>>>(d_ctr);
+      SV_CU(cudaGetLastError());
+      its = items2;
+      nit = -1;
+      waiting = v.defer_queries > 0;
+    }
     if (screened)
-      SV_CU(launch_screen(D, v.screen, items, n_items, d_ctr, nxt, qpad,
-                          lst_d, lst_i, K, screen_max, sw, cap, grid_max,
+      SV_CU(launch_screen(D, v.screen, its, nit, d_ctr, nxt, qpad, lst_d,
+                          lst_i, K, screen_max, sw, cap, grid_max,
                           v.sm_count, s));
     else
-      SV_CU(launch_leaf(D, cap, items, 0, n_items, d_ctr, v.d_pts, 0, nxt,
-                        qpad, lst_d, lst_i, K, std::min(grid_max, n_items),
-                        s));
+      SV_CU(launch_leaf(D, cap, its, 0, nit, d_ctr, v.d_pts, 0, nxt, qpad,
+                        lst_d, lst_i, K,
+                        nit >= 0 ? std::min(grid_max, nit) : grid_max, s));
   }
   std::swap(act, nxt);
   n_act = n_next;
@@ -436,6 +518,13 @@ int cs_open(bkd_tree* t, int k_max, int64_t max_queries, ClassServer** out) {
   SV_CU(host_alloc(&sv->h_fin, sizeof(Counters), cudaHostAllocDefault));
   SV_CU(host_alloc(&sv->h_left, sizeof(int32_t) * kMaxBatches,
                       cudaHostAllocDefault));
+  SV_CU(dev_alloc(&sv->q_wait, Q));
+  SV_CU(dev_alloc(&sv->leaf_wait, L));
+  SV_CU(dev_alloc(&sv->leaf_go, L));
+  SV_CU(dev_alloc(&sv->items2, Q / std::min(kWarpScreenTile, kPipeTile) + L + 1));
+  SV_CU(cudaMemsetAsync(sv->q_wait, 0, std::max<int64_t>(Q, 1), v.stream));
+  SV_CU(cudaMemsetAsync(sv->leaf_wait, 0, sizeof(int32_t) * std::max<int64_t>(L, 1),
+                        v.stream));
   SV_CU(dev_alloc(&sv->d_rescue, kMaxBatches));
   SV_CU(dev_alloc(&sv->resc, Q));
   SV_CU(dev_alloc(&sv->d_part, 2));

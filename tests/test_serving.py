@@ -68,14 +68,17 @@ def test_each_batch_same_alone_and_in_the_mix(precision, kernel):
         bkd.bkd_free(tree)
 
 
-@pytest.mark.parametrize("rescue", [1, 3])
-def test_rescued_stragglers_give_the_same_results(rescue):
+@pytest.mark.parametrize("rescue,defer", [(1, 0), (3, 0), (384, 8),
+                                          (3, 64)])
+def test_rescued_and_deferred_queries_give_the_same_results(rescue, defer):
     """Batches older than `rescue` rounds have their remaining queries
-    finished by the tail kernel; every batch's result still equals a
-    bkd_query of it alone (float32 and the warp screen)."""
+    finished by the tail kernel, and with the buffer trigger (`defer`) a
+    leaf holding fewer queries waits up to 4 rounds; every batch's result
+    still equals a bkd_query of it alone (float32 and the warp screen)."""
     w = workloads.scaled(workloads.MIXTURE_64M, 1 << 16, 4000, 8)
     P, Qall = w.points(), w.queries()
-    tree = bkd.bkd_build(P, w.height, precision=1, rescue_rounds=rescue)
+    tree = bkd.bkd_build(P, w.height, precision=1, rescue_rounds=rescue,
+                         defer_queries=defer)
     spec = [(0, 700, 10, 0), (700, 1300, 50, 1), (2000, 5, 1, 2),
             (2005, 1995, 10, 4)]
     try:
@@ -94,6 +97,23 @@ def test_rescued_stragglers_give_the_same_results(rescue):
                 idx, dist = srv.result(tickets[j])
                 assert np.array_equal(idx, alone[j][0]), (prec, j)
                 assert np.array_equal(dist, alone[j][1]), (prec, j)
+            srv.close()
+        # switching the trigger off with flags still set: the next rounds
+        # clear them and every batch still completes
+        if defer:
+            srv = bkd.Server(tree, k_max=50, max_queries=4000)
+            a, m, k, _ = spec[3]
+            t1 = srv.submit(np.ascontiguousarray(Qall[a:a + m]), k)
+            for _ in range(3):
+                srv.step()
+            bkd.bkd_set_option(tree, "defer_queries", 0)
+            steps = 0
+            while srv.step():
+                steps += 1
+                assert steps < 100000
+            assert srv.status(t1) == bkd.BKD_BATCH_DONE
+            idx, dist = srv.result(t1)
+            assert np.array_equal(idx, alone[3][0])
             srv.close()
     finally:
         bkd.bkd_free(tree)
