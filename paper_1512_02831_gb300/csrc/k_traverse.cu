@@ -42,7 +42,11 @@ __global__ void init_kernel(const float* __restrict__ Q, int64_t m, int d,
   if (bad) atomicOr(&ctr->err, kErrNonFinite);
 }
 
-constexpr int kFindThreads = 128;
+// One warp per CTA: traversal lengths differ from warp to warp, and a warp
+// that finishes frees its slot at once instead of waiting for the other
+// warps of its CTA (measured on the 2^24-point mixture: 21.9 ms per call
+// against 25.3 ms with 128-thread and 64-thread CTAs).
+constexpr int kFindThreads = 32;
 
 // One thread per active query.  The active list is ordered by leaf (the
 // previous round's scatter), so the lanes of a warp start from the same
