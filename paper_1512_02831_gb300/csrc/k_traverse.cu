@@ -52,7 +52,10 @@ constexpr int kFindThreads = 32;
 // previous round's scatter), so the lanes of a warp start from the same
 // leaf and mostly test the same boxes at the same time.  (Persistent lanes
 // that take a new query as soon as theirs is done were measured slower:
-// they lose that locality.)
+// they lose that locality.)  For the same reason most lanes of a warp count
+// their query into the same few leaves: the count is warp-aggregated, one
+// atomic per distinct leaf, each lane's rank from its place among the
+// lanes of that leaf (the order inside a buffer is irrelevant).
 template <int D>
 __global__ void __launch_bounds__(kFindThreads)
     find_leaf_kernel(DevTree t, const float* __restrict__ qpad,
@@ -62,41 +65,52 @@ __global__ void __launch_bounds__(kFindThreads)
                      const float* __restrict__ lst_d, int K,
                      int2* __restrict__ placed,
                      int32_t* __restrict__ cnt) {
+  static_assert(kFindThreads == 32, "one warp per CTA: the count below");
   const int pos = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pos >= (n_act_dev ? *n_act_dev : n_act)) return;
-  const uint32_t q = act[pos];
-  const float* qp = qpad + (size_t)q * D;
-  const uint64_t st = state[q];
-  const int node = state_node(st);
-  uint32_t mask = state_mask(st);
-  if (t.q_wait && node >= 0 && t.q_wait[q]) {
-    // a deferred buffer: the pending leaf is still to scan
-    const int leaf = node - ((1 << t.h) - 1);
-    placed[pos] = make_int2(leaf, atomicAdd(cnt + leaf, 1));
-    return;
-  }
-  if (t.chunk_done && node >= 0) {
-    // chunked mode: was the pending leaf's chunk scanned last round?
-    const int leaf = node - ((1 << t.h) - 1);
-    const int c = (int)(((int64_t)leaf * t.n_chunks) >> t.h);
-    if (!t.chunk_done[c]) {
-      placed[pos] = make_int2(leaf, atomicAdd(cnt + leaf, 1));
-      return;  // still buffered there; the traversal waits
+  const int lane = threadIdx.x;
+  const int first_leaf = (1 << t.h) - 1;
+  int leaf_out = -1;  // the leaf this query is counted into (-1: none)
+  if (pos < (n_act_dev ? *n_act_dev : n_act)) {
+    const uint32_t q = act[pos];
+    const float* qp = qpad + (size_t)q * D;
+    const uint64_t st = state[q];
+    const int node = state_node(st);
+    uint32_t mask = state_mask(st);
+    bool waits = false;  // the pending leaf is still to scan: stay there
+    if (node >= 0) {
+      // a deferred buffer (servers), or a chunk not scanned last round
+      // (chunked mode)
+      if (t.q_wait && t.q_wait[q]) waits = true;
+      if (t.chunk_done &&
+          !t.chunk_done[(int)(((int64_t)(node - first_leaf) * t.n_chunks) >>
+                              t.h)])
+        waits = true;
+    }
+    if (waits) {
+      leaf_out = node - first_leaf;
+    } else {
+      const float bound = node == kStart ? __int_as_float(0x7f800000)
+                                         : lst_d[(size_t)q * K + (K - 1)];
+      F32Bound<D> bx;
+      bx.load(qp);
+      const int next = next_leaf(t, bx, qp, node, mask, bound);
+      state[q] = trav_state(next, mask);
+      if (next == kDone)
+        placed[pos] = make_int2(-1, 0);
+      else
+        leaf_out = next - first_leaf;
     }
   }
-  const float bound = node == kStart ? __int_as_float(0x7f800000)
-                                     : lst_d[(size_t)q * K + (K - 1)];
-  F32Bound<D> bx;
-  bx.load(qp);
-  const int next = next_leaf(t, bx, qp, node, mask, bound);
-  state[q] = trav_state(next, mask);
-  if (next == kDone) {
-    placed[pos] = make_int2(-1, 0);
-  } else {
-    // the count before this query is its rank in the leaf's buffer
-    const int leaf = next - ((1 << t.h) - 1);
-    placed[pos] = make_int2(leaf, atomicAdd(cnt + leaf, 1));
-  }
+  // every lane of the warp arrives here
+  const unsigned peers = __match_any_sync(0xffffffffu, leaf_out);
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (leaf_out >= 0 && lane == leader)
+    base = atomicAdd(cnt + leaf_out, __popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (leaf_out >= 0)
+    placed[pos] =
+        make_int2(leaf_out, base + __popc(peers & ((1u << lane) - 1u)));
 }
 
 // ------------------------------------------------------------- bucketing
