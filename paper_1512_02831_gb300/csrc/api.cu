@@ -33,6 +33,7 @@
 
 #include "bkd.h"
 #include "bkd_internal.h"
+#include "chunk_schedule.h"
 
 using namespace bkd;
 
@@ -859,19 +860,12 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
       // leaf's points inside the chunk.
       const int N = t->n_chunks;
       const int32_t* ci = t->h_chunk_item;  // [first item, end item) per chunk
-      const bool forward = (round % 2) == 0;
       int prev_b = -1;
       for (int i = 0; i < N; ++i) {
-        const int c = forward ? i : N - 1 - i;
+        const int c = point_chunk_at(round, i, N);
         const int ilo = ci[2 * c], ihi = ci[2 * c + 1];
         if (ihi <= ilo) continue;
-        int b;
-        if (t->buf_chunk[0] == c)
-          b = 0;
-        else if (t->buf_chunk[1] == c)
-          b = 1;
-        else
-          b = prev_b < 0 ? (t->buf_chunk[0] == -1 ? 0 : 1) : 1 - prev_b;
+        const int b = point_chunk_buffer(c, t->buf_chunk, prev_b);
         const int64_t la = t->chunk_la[c], lb = t->chunk_lb[c] + 1;
         if (t->buf_chunk[b] != c) {
           const size_t bytes = (size_t)(lb - la) * D.lcap * Dp * sizeof(float);
@@ -920,23 +914,10 @@ int search(bkd_tree* t, int64_t m, int k, int64_t* out_idx, float* out_dist) {
       const int32_t* ci = t->h_chunk_item;          // first item per chunk
       const int32_t* cq = t->h_chunk_item + N + 1;  // first query per chunk
       auto work = [&](int c) { return c < 0 ? 0 : cq[c + 1] - cq[c]; };
-      int best = -1;
-      for (int c = 0; c < N; ++c)
-        if (c != t->buf_chunk[0] && c != t->buf_chunk[1] && work(c) > 0 &&
-            (best < 0 || work(c) > work(best)))
-          best = c;
-      const int wres = work(t->buf_chunk[0]) + work(t->buf_chunk[1]);
-      int load_b = -1;
-      if (best >= 0) {
-        if (t->buf_chunk[0] < 0)
-          load_b = 0;
-        else if (t->buf_chunk[1] < 0)
-          load_b = 1;
-        else if (wres == 0 || work(best) > 2 * wres)
-          load_b = work(t->buf_chunk[0]) <= work(t->buf_chunk[1]) ? 0 : 1;
-      }
+      const ChunkLoad pick = pick_leaf_chunk_load(N, t->buf_chunk, work);
+      const int load_b = pick.buffer;
       if (load_b >= 0) {
-        const int c = best;
+        const int c = pick.chunk;
         const int64_t leaf_a = t->chunk_leaf[c], leaf_b = t->chunk_leaf[c + 1];
         const size_t off_f = (size_t)leaf_a * D.lcap * Dp;
         const size_t bytes =
