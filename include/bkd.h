@@ -68,7 +68,10 @@ extern "C" {
  * bkd_build_with (at build).  Unknown keys are rejected with BKD_EINVAL. */
 enum bkd_option {
   /* cudaStream_t (as an integer) on which all work of the handle runs;
-   * 0 selects the library's own stream.  Any time. */
+   * 0 selects the library's own stream, a non-blocking stream that is not
+   * ordered with the legacy default stream: inputs written there must be
+   * complete before the call (synchronise it first, or pass CUDA's handle of
+   * that stream, cudaStreamLegacy).  Any time. */
   BKD_OPT_STREAM = 1,
   /* Bytes of device memory the leaf structure may occupy.  If the leaf
    * structure is larger, the tree is built in chunked ("bigger") mode: it

@@ -116,6 +116,26 @@ def _is_torch(x) -> bool:
     return type(x).__module__.split(".")[0] == "torch"
 
 
+def _stream_for_call(stream) -> int:
+    """The BKD_OPT_STREAM value that orders a call after the work queued on
+    torch stream ``stream`` (which wrote its inputs).  A stream with a handle
+    of its own is passed on: the call runs on it.  The legacy default stream
+    has the handle 0, which the library reads as "its own stream" (not
+    ordered with the default stream), so for it the host first waits for the
+    stream.  Either way the call returns after its results are complete."""
+    handle = int(stream.cuda_stream)
+    if handle == 0:
+        stream.synchronize()
+    return handle
+
+
+def _run_on_current_stream(tree: "Tree", device):
+    import torch
+    _check(load().bkd_set_option(
+        tree.handle, OPTIONS["stream"],
+        _stream_for_call(torch.cuda.current_stream(device))))
+
+
 def _ptr(x, dtype: str, rows_cols=None):
     """(pointer, shape) of a contiguous numpy array / torch tensor."""
     if _is_torch(x):
@@ -204,10 +224,7 @@ def bkd_query(tree: Tree, Q, k: int, out_idx=None, out_dist=None):
     if tuple(si) != (m, k) or tuple(sd) != (m, k):
         raise ValueError("outputs must be (m, k)")
     if _is_torch(Q) and Q.is_cuda:
-        import torch
-        _check(lib.bkd_set_option(tree.handle, OPTIONS["stream"],
-                                  torch.cuda.current_stream(Q.device)
-                                  .cuda_stream))
+        _run_on_current_stream(tree, Q.device)
     _check(lib.bkd_query(tree.handle, q, m, k, oi, od))
     return out_idx, out_dist
 
@@ -224,13 +241,9 @@ def bkd_query_static(tree: Tree, Q, k: int, out_idx, out_dist):
     if tuple(si) != (m, k) or tuple(sd) != (m, k):
         raise ValueError("outputs must be (m, k)")
     if _is_torch(Q) and Q.is_cuda:
-        # the call runs on the tree's stream: make it torch's current one, so
-        # it is ordered after the work that wrote Q and before the reads of
-        # the outputs
-        import torch
-        _check(lib.bkd_set_option(tree.handle, OPTIONS["stream"],
-                                  torch.cuda.current_stream(Q.device)
-                                  .cuda_stream))
+        # the call runs on the tree's stream: order it after the work that
+        # wrote Q on torch's current stream
+        _run_on_current_stream(tree, Q.device)
     _check(lib.bkd_query_static(tree.handle, q, m, k, oi, od))
     return out_idx, out_dist
 
@@ -251,10 +264,7 @@ def bkd_outlier_scores(tree: Tree, k: int, out=None, device=None):
     if tuple(shape) != (n,):
         raise ValueError("out must be (n,)")
     if _is_torch(out) and out.is_cuda:
-        import torch
-        _check(lib.bkd_set_option(tree.handle, OPTIONS["stream"],
-                                  torch.cuda.current_stream(out.device)
-                                  .cuda_stream))
+        _run_on_current_stream(tree, out.device)
     _check(lib.bkd_outlier_scores(tree.handle, k, o))
     return out
 
@@ -372,6 +382,11 @@ class Server:
                 out_dist = np.empty((m, k), np.float32)
         oi, _ = _ptr(out_idx, "i64")
         od, _ = _ptr(out_dist, "f32")
+        if _is_torch(Q) and Q.is_cuda:
+            # the server copies Q in a later step, on the tree's stream: Q
+            # must be final now (it stays unchanged until the batch is done)
+            import torch
+            torch.cuda.current_stream(Q.device).synchronize()
         ticket = ctypes.c_int64()
         _check(lib.bkd_serve_submit(self.handle, q, m, k, oi, od,
                                     ctypes.byref(ticket)))

@@ -94,3 +94,22 @@ def test_serving_rejects_bad_arguments_before_any_device_work():
     st = ctypes.c_int()
     assert lib.bkd_serve_status(None, 1, ctypes.byref(st)) == bkd.BKD_EINVAL
     lib.bkd_serve_close(None)  # NULL is ignored
+
+
+def test_calls_are_ordered_after_the_callers_stream():
+    """The binding's stream choice for a call on CUDA tensors: a stream with
+    a handle of its own is passed on untouched; the legacy default stream
+    (handle 0, which the library reads as its own stream) is first waited
+    for on the host, so the call cannot read inputs still being written."""
+    class FakeStream:
+        def __init__(self, handle):
+            self.cuda_stream = handle
+            self.waits = 0
+
+        def synchronize(self):
+            self.waits += 1
+
+    side = FakeStream(0x7f00dead0000)
+    assert bkd._stream_for_call(side) == 0x7f00dead0000 and side.waits == 0
+    default = FakeStream(0)
+    assert bkd._stream_for_call(default) == 0 and default.waits == 1
