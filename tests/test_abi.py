@@ -113,3 +113,31 @@ def test_calls_are_ordered_after_the_callers_stream():
     assert bkd._stream_for_call(side) == 0x7f00dead0000 and side.waits == 0
     default = FakeStream(0)
     assert bkd._stream_for_call(default) == 0 and default.waits == 1
+
+
+def test_binding_constants_match_the_header():
+    """Option and statistic numbers, status codes and limits of the binding
+    are the values include/bkd.h defines (the binding passes them as plain
+    integers, so a mismatch would silently set the wrong option)."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    opts = {k.lower(): int(v)
+            for k, v in re.findall(r"\bBKD_OPT_([A-Z_]+)\s*=\s*(\d+)", text)}
+    stats = {k.lower(): int(v)
+             for k, v in re.findall(r"\bBKD_STAT_([A-Z_]+)\s*=\s*(\d+)", text)}
+    assert opts == bkd.OPTIONS
+    assert stats == bkd.STATS
+    defines = {k: int(v) for k, v in
+               re.findall(r"#define\s+(BKD_[A-Z_]+)\s+\(?(-?\d+)\)?", text)}
+    for name, value in defines.items():
+        if hasattr(bkd, name):
+            assert getattr(bkd, name) == value, name
+    for name in ("BKD_OK", "BKD_EINVAL", "BKD_ENOMEM", "BKD_ECUDA",
+                 "BKD_ETIMEOUT", "BKD_EUNSUPPORTED", "BKD_MAX_DIM",
+                 "BKD_MAX_K", "BKD_MAX_HEIGHT", "BKD_STATIC_MAX_QUERIES",
+                 "BKD_STATIC_MAX_HEIGHT"):
+        assert name in defines and hasattr(bkd, name), name
+    batch = dict(re.findall(r"\b(BKD_BATCH_[A-Z]+)\s*=\s*(\d+)", text))
+    assert {k: int(v) for k, v in batch.items()} == {
+        "BKD_BATCH_QUEUED": bkd.BKD_BATCH_QUEUED,
+        "BKD_BATCH_RUNNING": bkd.BKD_BATCH_RUNNING,
+        "BKD_BATCH_DONE": bkd.BKD_BATCH_DONE}
