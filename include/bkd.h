@@ -288,6 +288,39 @@ int bkd_outlier_scores(bkd_tree* t, int k, float* out_score);
  * had built).  Errors: BKD_EINVAL (nth < 0). */
 int bkd_test_fail_alloc(int64_t nth);
 
+/* bkd_test_host_screen -- the host half of bkd_build(P, n, d, height) with
+ * BKD_OPT_PRECISION=1, without a GPU: the median-split tree (Sec. 2.3), the
+ * bounding box of every heap node, and the BF16 warp screen's operands and
+ * per-leaf bounds, computed by the functions bkd_build uses and written to
+ * caller buffers (all host memory, caller-owned).
+ *   P, n, d, height  as bkd_build (P host memory).
+ *   shape    out: int64[5] = {lcap, stride, kh, words, Dp}: slots per leaf
+ *            (largest leaf rounded up to 4), screen rows per leaf (lcap
+ *            rounded up to 32), k-halves of 16 bf16 slots, uint32 words of
+ *            the operand array, padded dimension.
+ *   split    float[max(2^h - 1, 1)]: split values in heap order.
+ *   leaf_lo  int64[2^h + 1]: leaf l holds tree positions [leaf_lo[l],
+ *            leaf_lo[l+1]).
+ *   perm     int64[n]: the row of P at each tree position.
+ *   box      float[(2^(h+1) - 1) * 2 Dp]: per heap node its minimum row and
+ *            then its maximum row (dimensions d..Dp-1 are [0, 0]).
+ *   words    uint32[words]: per leaf and k-half, stride rows of 8 words in
+ *            the screen's fragment order; a word holds two bf16 slots (low
+ *            half first); slots 0..d-1 of a row are the point's offset from
+ *            the leaf centre, slots d and d+1 the split of its squared norm,
+ *            the rest 0; rows past the leaf's points have slot d = +inf.
+ *   center   float[2^h * d]: per leaf the midpoint of its bounding box.
+ *   bmax     float[2^h]: per leaf an upper bound of the Euclidean norm
+ *            ||w - w_hat|| over its points (w = x - centre, exact; w_hat
+ *            its bf16 operand).
+ *   pnmax    float[2^h]: per leaf an upper bound of ||w_hat||^2.
+ * Pass all of split ... pnmax to fill them, or none of them to learn
+ * shape only.  Errors: BKD_EINVAL, BKD_ENOMEM. */
+int bkd_test_host_screen(const float* P, int64_t n, int d, int height,
+                         int64_t* shape, float* split, int64_t* leaf_lo,
+                         int64_t* perm, float* box, uint32_t* words,
+                         float* center, float* bmax, float* pnmax);
+
 /* bkd_probe_mma -- runs the warp screen kernel's tensor-core instruction
  * (kind 0: mma.sync m16n8k16, bf16 inputs, fp32 accumulation) on `count`
  * instances:

@@ -92,6 +92,8 @@ def load():
         lib.bkd_serve_close.restype = None
         lib.bkd_outlier_scores.argtypes = [vp, i32, vp]
         lib.bkd_test_fail_alloc.argtypes = [i64]
+        lib.bkd_test_host_screen.argtypes = [vp, i64, i32, i32, vp, vp, vp,
+                                             vp, vp, vp, vp, vp, vp]
         lib.bkd_probe_mma.argtypes = [i32, i32, vp, vp, vp, vp]
         lib.bkd_probe_umma.argtypes = [i32, i32, i32, vp, vp, vp]
         lib.bkd_last_error.restype = ctypes.c_char_p
@@ -100,6 +102,7 @@ def load():
                   "bkd_get_stat", "bkd_tree_shape", "bkd_export_tree",
                   "bkd_serve_open", "bkd_serve_submit", "bkd_serve_step",
                   "bkd_serve_status", "bkd_test_fail_alloc",
+                  "bkd_test_host_screen",
                   "bkd_outlier_scores",
                   "bkd_probe_mma", "bkd_probe_umma"):
             getattr(lib, f).restype = ctypes.c_int
@@ -308,6 +311,41 @@ def bkd_free(tree: Tree):
 def bkd_test_fail_alloc(nth: int):
     """``bkd_test_fail_alloc``: the nth allocation from now fails (0: off)."""
     _check(load().bkd_test_fail_alloc(int(nth)))
+
+
+def bkd_test_host_screen(P, height: int) -> dict:
+    """``bkd_test_host_screen``: the host half of ``bkd_build`` (tree, node
+    boxes, BF16 warp-screen operands and bounds) for host float32 P (n, d),
+    without a GPU.  Returns numpy arrays keyed like the C arguments, plus
+    ``lcap``, ``stride``, ``kh`` and ``Dp``."""
+    lib = load()
+    P = np.ascontiguousarray(P, np.float32)
+    if P.ndim != 2:
+        raise ValueError("P must be (n, d)")
+    n, d = P.shape
+    shape = np.zeros(5, np.int64)
+    nul = ctypes.c_void_p(0)
+    _check(lib.bkd_test_host_screen(P.ctypes.data, n, d, height,
+                                    shape.ctypes.data, nul, nul, nul, nul,
+                                    nul, nul, nul, nul))
+    lcap, stride, kh, nwords, Dp = (int(x) for x in shape)
+    L = 1 << height
+    out = {"split": np.empty(max(L - 1, 1), np.float32),
+           "leaf_lo": np.empty(L + 1, np.int64),
+           "perm": np.empty(n, np.int64),
+           "box": np.empty((2 * L - 1, 2 * Dp), np.float32),
+           "words": np.empty(nwords, np.uint32),
+           "center": np.empty((L, d), np.float32),
+           "bmax": np.empty(L, np.float32),
+           "pnmax": np.empty(L, np.float32)}
+    _check(lib.bkd_test_host_screen(
+        P.ctypes.data, n, d, height, shape.ctypes.data,
+        *(out[key].ctypes.data for key in ("split", "leaf_lo", "perm", "box",
+                                           "words", "center", "bmax",
+                                           "pnmax"))))
+    out["split"] = out["split"][:L - 1]
+    out.update(lcap=lcap, stride=stride, kh=kh, Dp=Dp)
+    return out
 
 
 def bkd_probe_mma(A, Bt, C, kind: int = 0):

@@ -208,6 +208,13 @@ void fill_boxes(const float* P, const HostTree& t, float* box) {
 
 namespace {
 
+// Floor of a leaf's pn_max.  The screens' error term E holds 2^-14 pn_max,
+// so E >= 2^-100: the absolute errors that underflow adds (products or an
+// accumulator below 2^-126, the norm split of a subnormal pn, |v_hat|^2
+// below 2^-126) stay under 2^-118 and are covered; for any leaf whose
+// points are not all within ~2^-43 of its centre the floor changes nothing.
+constexpr float kPnMaxFloor = 0x1p-86f;
+
 // float -> bfloat16, round to nearest even (inputs are finite).
 inline uint16_t bf16_rn(float f) {
   uint32_t x;
@@ -285,7 +292,7 @@ void fill_screen(const float* P, const HostTree& t, int64_t tiles,
     }
     bmax[leaf] = std::nextafter((float)(rho / (1.0 - rho) * wmax + tiny),
                                 INFINITY);
-    pnmax[leaf] = std::nextafter(pmax, INFINITY);
+    pnmax[leaf] = std::nextafter(std::max(pmax, kPnMaxFloor), INFINITY);
   });
 }
 
@@ -354,7 +361,7 @@ void fill_screen_warp(const float* P, const HostTree& t, int64_t stride,
     }
     bmax[leaf] = std::nextafter((float)(rho / (1.0 - rho) * wmax + tiny),
                                 INFINITY);
-    pnmax[leaf] = std::nextafter(pmax, INFINITY);
+    pnmax[leaf] = std::nextafter(std::max(pmax, kPnMaxFloor), INFINITY);
   });
 }
 
