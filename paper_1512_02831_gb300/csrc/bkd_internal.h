@@ -409,7 +409,9 @@ inline int screen_halves_warp(int d) { return (d + 2 + 15) / 16; }
 // squared norm pn (binary64 sum rounded to float) split as pn_hi = bf16(pn),
 // pn_lo = bf16(pn - pn_hi) in slots d, d+1, and 1.0 in slots d+2..d+4
 // (padding rows: pn_hi = +inf, everything else 0); per leaf bmax (upper
-// bound on the offset rounding error norm) and pnmax (largest pn).
+// bound on the offset rounding error norm) and pnmax (largest pn, floored
+// at 2^-86, so that the screens' error term 2^-14 (|v^|^2 + pnmax) holds an
+// absolute 2^-100 that covers the errors of underflow).
 void fill_screen(const float* P, const HostTree& t, int64_t tiles,
                  uint16_t* words, float* center, float* bmax, float* pnmax);
 // The warp kernel's layout of the same per-point slots (offsets, pn_hi,
