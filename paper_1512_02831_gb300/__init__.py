@@ -190,6 +190,11 @@ def bkd_build(P, height: int, **options) -> Tree:
     if len(shape) != 2:
         raise ValueError("P must be (n, d)")
     n, d = shape
+    if _is_torch(P) and P.is_cuda:
+        # the build reads P with a synchronous copy that is not ordered with
+        # torch's other streams: P must be final now
+        import torch
+        torch.cuda.current_stream(P.device).synchronize()
     out = ctypes.c_void_p()
     if options:
         flat = []
