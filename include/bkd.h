@@ -294,10 +294,12 @@ int bkd_test_fail_alloc(int64_t nth);
  * per-leaf bounds, computed by the functions bkd_build uses and written to
  * caller buffers (all host memory, caller-owned).
  *   P, n, d, height  as bkd_build (P host memory).
- *   shape    out: int64[5] = {lcap, stride, kh, words, Dp}: slots per leaf
- *            (largest leaf rounded up to 4), screen rows per leaf (lcap
- *            rounded up to 32), k-halves of 16 bf16 slots, uint32 words of
- *            the operand array, padded dimension.
+ *   shape    out: int64[8] = {lcap, stride, kh, words, Dp, tiles, tc_kh,
+ *            tc_elems}: slots per leaf (largest leaf rounded up to 4),
+ *            screen rows per leaf (lcap rounded up to 32), k-halves of 16
+ *            bf16 slots, uint32 words of the operand array, padded
+ *            dimension; then for the tcgen05 kernel's operands: 128-row
+ *            tiles per leaf, k-halves, bf16 elements of tc_words.
  *   split    float[max(2^h - 1, 1)]: split values in heap order.
  *   leaf_lo  int64[2^h + 1]: leaf l holds tree positions [leaf_lo[l],
  *            leaf_lo[l+1]).
@@ -314,12 +316,20 @@ int bkd_test_fail_alloc(int64_t nth);
  *            ||w - w_hat|| over its points (w = x - centre, exact; w_hat
  *            its bf16 operand).
  *   pnmax    float[2^h]: per leaf an upper bound of ||w_hat||^2.
- * Pass all of split ... pnmax to fill them, or none of them to learn
+ *   tc_words uint16[tc_elems]: the tcgen05 kernel's operand tiles, per leaf
+ *            `tiles` tiles of 128 rows x 16 tc_kh bf16, row r's slots
+ *            8 g .. 8 g + 7 at byte (r / 8) 256 tc_kh + 128 g + 16 (r % 8)
+ *            of its tile; a row holds the same offsets and norm split as
+ *            above, then 1.0 in slots d+2 .. d+4; padding rows slot d =
+ *            +inf.  Its centre and bounds equal the ones above (checked:
+ *            BKD_EINVAL otherwise).
+ * Pass all of split ... tc_words to fill them, or none of them to learn
  * shape only.  Errors: BKD_EINVAL, BKD_ENOMEM. */
 int bkd_test_host_screen(const float* P, int64_t n, int d, int height,
                          int64_t* shape, float* split, int64_t* leaf_lo,
                          int64_t* perm, float* box, uint32_t* words,
-                         float* center, float* bmax, float* pnmax);
+                         float* center, float* bmax, float* pnmax,
+                         uint16_t* tc_words);
 
 /* bkd_probe_mma -- runs the warp screen kernel's tensor-core instruction
  * (kind 0: mma.sync m16n8k16, bf16 inputs, fp32 accumulation) on `count`

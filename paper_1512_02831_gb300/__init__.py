@@ -93,7 +93,7 @@ def load():
         lib.bkd_outlier_scores.argtypes = [vp, i32, vp]
         lib.bkd_test_fail_alloc.argtypes = [i64]
         lib.bkd_test_host_screen.argtypes = [vp, i64, i32, i32, vp, vp, vp,
-                                             vp, vp, vp, vp, vp, vp]
+                                             vp, vp, vp, vp, vp, vp, vp]
         lib.bkd_probe_mma.argtypes = [i32, i32, vp, vp, vp, vp]
         lib.bkd_probe_umma.argtypes = [i32, i32, i32, vp, vp, vp]
         lib.bkd_last_error.restype = ctypes.c_char_p
@@ -322,18 +322,19 @@ def bkd_test_host_screen(P, height: int) -> dict:
     """``bkd_test_host_screen``: the host half of ``bkd_build`` (tree, node
     boxes, BF16 warp-screen operands and bounds) for host float32 P (n, d),
     without a GPU.  Returns numpy arrays keyed like the C arguments, plus
-    ``lcap``, ``stride``, ``kh`` and ``Dp``."""
+    ``lcap``, ``stride``, ``kh``, ``Dp``, ``tiles`` and ``tc_kh``."""
     lib = load()
     P = np.ascontiguousarray(P, np.float32)
     if P.ndim != 2:
         raise ValueError("P must be (n, d)")
     n, d = P.shape
-    shape = np.zeros(5, np.int64)
+    shape = np.zeros(8, np.int64)
     nul = ctypes.c_void_p(0)
     _check(lib.bkd_test_host_screen(P.ctypes.data, n, d, height,
                                     shape.ctypes.data, nul, nul, nul, nul,
-                                    nul, nul, nul, nul))
-    lcap, stride, kh, nwords, Dp = (int(x) for x in shape)
+                                    nul, nul, nul, nul, nul))
+    lcap, stride, kh, nwords, Dp, tiles, tc_kh, tc_elems = (
+        int(x) for x in shape)
     L = 1 << height
     out = {"split": np.empty(max(L - 1, 1), np.float32),
            "leaf_lo": np.empty(L + 1, np.int64),
@@ -342,14 +343,16 @@ def bkd_test_host_screen(P, height: int) -> dict:
            "words": np.empty(nwords, np.uint32),
            "center": np.empty((L, d), np.float32),
            "bmax": np.empty(L, np.float32),
-           "pnmax": np.empty(L, np.float32)}
+           "pnmax": np.empty(L, np.float32),
+           "tc_words": np.empty(tc_elems, np.uint16)}
     _check(lib.bkd_test_host_screen(
         P.ctypes.data, n, d, height, shape.ctypes.data,
         *(out[key].ctypes.data for key in ("split", "leaf_lo", "perm", "box",
                                            "words", "center", "bmax",
-                                           "pnmax"))))
+                                           "pnmax", "tc_words"))))
     out["split"] = out["split"][:L - 1]
-    out.update(lcap=lcap, stride=stride, kh=kh, Dp=Dp)
+    out.update(lcap=lcap, stride=stride, kh=kh, Dp=Dp, tiles=tiles,
+               tc_kh=tc_kh)
     return out
 
 

@@ -1,7 +1,8 @@
 """The host half of bkd_build, checked without a GPU (bkd_test_host_screen):
 the median-split tree against the oracle's (Sec. 2.3), the node bounding
-boxes against their definition, and the BF16 warp screen's operands and
-per-leaf bounds against exact rational arithmetic.
+boxes against their definition, and the BF16 screens' operands (the warp
+kernel's fragments and the tcgen05 kernel's tiles) and per-leaf bounds
+against exact rational arithmetic.
 
 The screen drops a point only if a bound that uses these host values says it
 cannot enter the list, so the host half of that bound is pinned here on data
@@ -75,6 +76,31 @@ def decode_slots(r) -> np.ndarray:
     return slots
 
 
+def decode_tc_slots(r) -> np.ndarray:
+    """slots[leaf, row, 16 tc_kh] of the tcgen05 kernel's tiles, by the
+    layout the header states (the MMA's no-swizzle K-major form): row r's
+    slots 8 g .. 8 g + 7 at byte (r / 8) 256 kh + 128 g + 16 (r % 8) of its
+    128-row tile.  Every element is written exactly once."""
+    kh, tiles = r["tc_kh"], r["tiles"]
+    L = len(r["leaf_lo"]) - 1
+    words = r["tc_words"]
+    tile_elems = 128 * 16 * kh
+    rows = np.arange(128)
+    slots = np.zeros((L, tiles * 128, 16 * kh), np.uint16)
+    seen = np.zeros(words.size, np.int64)
+    for leaf in range(L):
+        for t in range(tiles):
+            base = (leaf * tiles + t) * tile_elems
+            for g in range(2 * kh):
+                off = ((rows >> 3) * (256 * kh) + 128 * g + 16 * (rows & 7)) // 2
+                for e in range(8):
+                    idx = base + off + e
+                    slots[leaf, t * 128 + rows, 8 * g + e] = words[idx]
+                    np.add.at(seen, idx, 1)
+    assert (seen == 1).all(), "tile elements overlap or are left out"
+    return slots
+
+
 def check_host_half(P: np.ndarray, h: int):
     """Every property of bkd_test_host_screen's output; returns the largest
     ||w - w_hat||^2 / max ||w_hat||^2 over the points of a leaf (exact): the
@@ -108,6 +134,16 @@ def check_host_half(P: np.ndarray, h: int):
         assert not box[v, d:Dp].any() and not box[v, Dp + d:].any()
 
     slots = decode_slots(r)
+    # the tcgen05 kernel's rows: the same offsets and norm split, then three
+    # 1.0 slots that meet the query's threshold parts; padding rows +inf
+    tc = decode_tc_slots(r)
+    for leaf in range(L):
+        cnt = leaf_lo[leaf + 1] - leaf_lo[leaf]
+        assert np.array_equal(tc[leaf, :cnt, :d + 2], slots[leaf, :cnt, :d + 2])
+        assert (tc[leaf, :cnt, d + 2:d + 5] == 0x3F80).all()
+        assert not tc[leaf, :cnt, d + 5:].any()
+        assert (tc[leaf, cnt:, d] == 0x7F80).all()
+        assert not np.delete(tc[leaf, cnt:], d, axis=1).any()
     half = np.float32(0.5)
     worst = Fraction(0)
     for leaf in range(L):
