@@ -232,67 +232,89 @@ inline float bf16_to_float(uint16_t h) {
 
 }  // namespace
 
+namespace {
+
+// One leaf of either screen layout: its centre c (midpoint of the leaf's
+// bounding box) into `c`, then `rows` rows of bf16 slots -- the point's
+// offsets bf16(fl(x - c)) in 0..d-1 and its squared norm pn (binary64 sum
+// rounded to float) split as pn_hi = bf16(pn), pn_lo = bf16(pn - pn_hi) in
+// d, d+1; rows past the leaf's points hold pn_hi = +inf and zeros -- each
+// handed to place(u, hv, real); finally the leaf's bmax and pnmax.
+template <class Place>
+void screen_leaf(const float* P, const HostTree& t, int64_t leaf,
+                 int64_t rows, float* c, float* bmax, float* pnmax,
+                 Place place) {
+  const int d = t.d;
+  // BF16 rounding error (relative, round to nearest: 8 significant bits, so
+  // 2^-8) with margin for the float32 subtraction before it, and its effect
+  // on a norm: |w_hat - w| <= rho |w|, |w| <= |w_hat| / (1 - rho).
+  const double rho = std::ldexp(1.0, -8) * (1.0 + 1e-4);
+  const double tiny = std::ldexp(1.0, -126) * std::sqrt((double)d);
+  const int64_t lo = t.leaf_lo[leaf], cnt = t.leaf_lo[leaf + 1] - lo;
+  for (int i = 0; i < d; ++i) {
+    float mn = INFINITY, mx = -INFINITY;
+    for (int64_t u = 0; u < cnt; ++u) {
+      const float x = P[t.perm[lo + u] * d + i];
+      mn = std::min(mn, x);
+      mx = std::max(mx, x);
+    }
+    c[i] = 0.5f * mn + 0.5f * mx;
+  }
+  double wmax = 0.0;
+  float pmax = 0.f;
+  for (int64_t u = 0; u < rows; ++u) {
+    uint16_t hv[48] = {0};
+    const bool real = u < cnt;
+    if (real) {
+      const float* x = P + t.perm[lo + u] * d;
+      double ss = 0.0;
+      for (int i = 0; i < d; ++i) {
+        hv[i] = bf16_rn(x[i] - c[i]);
+        const double w = bf16_to_float(hv[i]);
+        ss += w * w;
+      }
+      const float pv = (float)ss;
+      // pv - pn_hi is exact (at most 16 significant bits remain); its
+      // bf16 rounding leaves pn_hi + pn_lo within 2^-16 pv of pv
+      hv[d] = bf16_rn(pv);
+      hv[d + 1] = bf16_rn(pv - bf16_to_float(hv[d]));
+      wmax = std::max(wmax, std::sqrt(ss));
+      pmax = std::max(pmax, pv);
+    } else {
+      hv[d] = 0x7f80;  // +inf: the row's product is -inf, never kept
+    }
+    place(u, hv, real);
+  }
+  *bmax = std::nextafter((float)(rho / (1.0 - rho) * wmax + tiny), INFINITY);
+  *pnmax = std::nextafter(std::max(pmax, kPnMaxFloor), INFINITY);
+}
+
+}  // namespace
+
 void fill_screen(const float* P, const HostTree& t, int64_t tiles,
                  uint16_t* words, float* center, float* bmax, float* pnmax) {
   const int d = t.d;
   const int kh = screen_halves(d);
   const int64_t L = (int64_t)1 << t.h;
   const int64_t tile_elems = (int64_t)kScreenRows * 16 * kh;  // bf16 per tile
-  // BF16 rounding error (relative, round to nearest: 8 significant bits, so
-  // 2^-8) with margin for the float32 subtraction before it, and its effect
-  // on a norm: |w_hat - w| <= rho |w|, |w| <= |w_hat| / (1 - rho).
-  const double rho = std::ldexp(1.0, -8) * (1.0 + 1e-4);
-  const double tiny = std::ldexp(1.0, -126) * std::sqrt((double)d);
   const uint16_t one = 0x3f80;  // bf16 1.0
   parallel_items(L, [&](int64_t leaf) {
-    const int64_t lo = t.leaf_lo[leaf], cnt = t.leaf_lo[leaf + 1] - lo;
-    float* c = center + leaf * d;
-    for (int i = 0; i < d; ++i) {
-      float mn = INFINITY, mx = -INFINITY;
-      for (int64_t u = 0; u < cnt; ++u) {
-        const float x = P[t.perm[lo + u] * d + i];
-        mn = std::min(mn, x);
-        mx = std::max(mx, x);
-      }
-      c[i] = 0.5f * mn + 0.5f * mx;
-    }
-    double wmax = 0.0;
-    float pmax = 0.f;
     uint16_t* lw = words + leaf * tiles * tile_elems;
-    for (int64_t u = 0; u < tiles * kScreenRows; ++u) {
-      uint16_t hv[48] = {0};
-      if (u < cnt) {
-        const float* x = P + t.perm[lo + u] * d;
-        double ss = 0.0;
-        for (int i = 0; i < d; ++i) {
-          hv[i] = bf16_rn(x[i] - c[i]);
-          const double w = bf16_to_float(hv[i]);
-          ss += w * w;
-        }
-        const float pv = (float)ss;
-        // pv - pn_hi is exact (at most 16 significant bits remain); its
-        // bf16 rounding leaves pn_hi + pn_lo within 2^-16 pv of pv
-        hv[d] = bf16_rn(pv);
-        hv[d + 1] = bf16_rn(pv - bf16_to_float(hv[d]));
-        // the three threshold slots of the query column meet 1.0 here
-        hv[d + 2] = hv[d + 3] = hv[d + 4] = one;
-        wmax = std::max(wmax, std::sqrt(ss));
-        pmax = std::max(pmax, pv);
-      } else {
-        hv[d] = 0x7f80;  // +inf against -1/2: the row scores -inf
-      }
-      // tile T = u / 128, row r = u % 128; the row's 2 kh groups of eight
-      // slots go to the canonical no-swizzle K-major layout of the MMA
-      // operand (screen_row_offset)
-      uint16_t* tile = lw + (u / kScreenRows) * tile_elems;
-      const int r = (int)(u % kScreenRows);
-      for (int kg = 0; kg < 2 * kh; ++kg)
-        for (int e = 0; e < 8; ++e)
-          tile[screen_row_offset(r, kg, kh) / 2 + e] = hv[8 * kg + e];
-    }
-    bmax[leaf] = std::nextafter((float)(rho / (1.0 - rho) * wmax + tiny),
-                                INFINITY);
-    pnmax[leaf] = std::nextafter(std::max(pmax, kPnMaxFloor), INFINITY);
+    screen_leaf(P, t, leaf, tiles * kScreenRows, center + leaf * d,
+                bmax + leaf, pnmax + leaf,
+                [&](int64_t u, uint16_t* hv, bool real) {
+                  // the three threshold slots of the query column meet 1.0
+                  if (real) hv[d + 2] = hv[d + 3] = hv[d + 4] = one;
+                  // tile T = u / 128, row r = u % 128; the row's 2 kh groups
+                  // of eight slots go to the canonical no-swizzle K-major
+                  // layout of the MMA operand (screen_row_offset)
+                  uint16_t* tile = lw + (u / kScreenRows) * tile_elems;
+                  const int r = (int)(u % kScreenRows);
+                  for (int kg = 0; kg < 2 * kh; ++kg)
+                    for (int e = 0; e < 8; ++e)
+                      tile[screen_row_offset(r, kg, kh) / 2 + e] =
+                          hv[8 * kg + e];
+                });
   });
 }
 
@@ -302,66 +324,29 @@ void fill_screen_warp(const float* P, const HostTree& t, int64_t stride,
   const int d = t.d;
   const int kh = screen_halves_warp(d);
   const int64_t L = (int64_t)1 << t.h;
-  // BF16 rounding error (relative, round to nearest: 8 significant bits, so
-  // 2^-8) with margin for the float32 subtraction before it, and its effect
-  // on a norm: |w_hat - w| <= rho |w|, |w| <= |w_hat| / (1 - rho).
-  const double rho = std::ldexp(1.0, -8) * (1.0 + 1e-4);
-  const double tiny = std::ldexp(1.0, -126) * std::sqrt((double)d);
   parallel_items(L, [&](int64_t leaf) {
-    const int64_t lo = t.leaf_lo[leaf], cnt = t.leaf_lo[leaf + 1] - lo;
-    float* c = center + leaf * d;
-    for (int i = 0; i < d; ++i) {
-      float mn = INFINITY, mx = -INFINITY;
-      for (int64_t u = 0; u < cnt; ++u) {
-        const float x = P[t.perm[lo + u] * d + i];
-        mn = std::min(mn, x);
-        mx = std::max(mx, x);
-      }
-      c[i] = 0.5f * mn + 0.5f * mx;
-    }
-    double wmax = 0.0;
-    float pmax = 0.f;
-    for (int64_t u = 0; u < stride; ++u) {
-      uint16_t hv[48] = {0};
-      if (u < cnt) {
-        const float* x = P + t.perm[lo + u] * d;
-        double ss = 0.0;
-        for (int i = 0; i < d; ++i) {
-          hv[i] = bf16_rn(x[i] - c[i]);
-          const double w = bf16_to_float(hv[i]);
-          ss += w * w;
-        }
-        const float pv = (float)ss;
-        // pv - pn_hi is exact (at most 16 significant bits remain); its
-        // bf16 rounding leaves pn_hi + pn_lo within 2^-16 pv of pv
-        hv[d] = bf16_rn(pv);
-        hv[d + 1] = bf16_rn(pv - bf16_to_float(hv[d]));
-        wmax = std::max(wmax, std::sqrt(ss));
-        pmax = std::max(pmax, pv);
-      } else {
-        hv[d] = 0x7f80;  // +inf: the row's product is -inf, never kept
-      }
-      // 32-point super-tiles S = u / 32 of two 16-point m-tiles a; in tile
-      // a the point is row 8 r + g (r = 0, 1; g = 0..7).  Lane (g, t) of a
-      // warp loads, with one 16-byte load per row half r, words (t, t + 4)
-      // of row 8 r + g of both tiles: its m16n8k16 A fragments.
-      const int64_t S = u / 32, a = (u % 32) / 16, r = (u % 16) / 8,
-                    g = u % 8;
-      for (int h = 0; h < kh; ++h) {
-        // word j of a k-half = slots (2j, 2j+1) of the half
-        uint32_t* blk = words + (leaf * kh + h) * stride * 8 +
-                        ((S * 2 + r) * 8 + g) * 16 + 2 * a;
-        for (int tq = 0; tq < 4; ++tq)
-          for (int e = 0; e < 2; ++e) {
-            const int k0 = 16 * h + 2 * (tq + 4 * e);
-            blk[tq * 4 + e] =
-                (uint32_t)hv[k0] | ((uint32_t)hv[k0 + 1] << 16);
+    screen_leaf(
+        P, t, leaf, stride, center + leaf * d, bmax + leaf, pnmax + leaf,
+        [&](int64_t u, const uint16_t* hv, bool) {
+          // 32-point super-tiles S = u / 32 of two 16-point m-tiles a; in
+          // tile a the point is row 8 r + g (r = 0, 1; g = 0..7).  Lane
+          // (g, t) of a warp loads, with one 16-byte load per row half r,
+          // words (t, t + 4) of row 8 r + g of both tiles: its m16n8k16 A
+          // fragments.
+          const int64_t S = u / 32, a = (u % 32) / 16, r = (u % 16) / 8,
+                        g = u % 8;
+          for (int h = 0; h < kh; ++h) {
+            // word j of a k-half = slots (2j, 2j+1) of the half
+            uint32_t* blk = words + (leaf * kh + h) * stride * 8 +
+                            ((S * 2 + r) * 8 + g) * 16 + 2 * a;
+            for (int tq = 0; tq < 4; ++tq)
+              for (int e = 0; e < 2; ++e) {
+                const int k0 = 16 * h + 2 * (tq + 4 * e);
+                blk[tq * 4 + e] =
+                    (uint32_t)hv[k0] | ((uint32_t)hv[k0 + 1] << 16);
+              }
           }
-      }
-    }
-    bmax[leaf] = std::nextafter((float)(rho / (1.0 - rho) * wmax + tiny),
-                                INFINITY);
-    pnmax[leaf] = std::nextafter(std::max(pmax, kPnMaxFloor), INFINITY);
+        });
   });
 }
 
